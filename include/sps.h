@@ -1,0 +1,283 @@
+/*
+ * sps.h -- C ABI of the B300 (sm_103a) sequential posterior simulator for logit models.
+ *
+ * The method is the sequential posterior simulator (SPS) of Geweke, Durham & Xu (2013),
+ * "Bayesian Inference for Logistic Regression Models using Sequential Posterior Simulation":
+ * J groups of N particles are moved through the data in cycles, each a correction (C) phase
+ * that reweights particles by the likelihood of new observations, a selection (S) phase that
+ * resamples within each group, and a mutation (M) phase of Metropolis steps (Algorithms 1-2,
+ * Sec. 2.2-2.3). The model is the multinomial logit of Eq. (1) with base outcome 0 (theta_0 = 0).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns sps_status; none aborts, traps or prints. sps_last_error(ctx) keeps a
+ *   message for the last failure on that context.
+ * - The caller owns every buffer it passes. sps_init copies and encodes X and y to the device;
+ *   the context owns its device memory until sps_destroy.
+ * - Parameter vectors are FP64 and class-major: theta[p*D + (c-1)*k + i] is the coefficient of
+ *   covariate i for outcome c (c = 1..C-1) of particle p; D = k*(C-1).
+ * - Pointers marked "mem" are host pointers when mem == SPS_MEM_HOST (the call copies, runs and
+ *   synchronises before returning) or device pointers when mem == SPS_MEM_DEVICE (the call only
+ *   enqueues work on the context's stream and returns; results are ready when that stream is).
+ * - One context per stream; calls on one context must not run concurrently from several host
+ *   threads.
+ * - Library errors: SPS_ERR_INVALID_ARG for shapes, ranges or non-finite inputs;
+ *   SPS_ERR_CUDA for a failed CUDA runtime call or kernel launch (the CUDA error string is kept);
+ *   SPS_ERR_OOM when device memory cannot be allocated; SPS_ERR_DEGENERATE when the proposal
+ *   covariance h*V is not positive definite (the failure of Algorithm 2 step 2(c)i described in
+ *   Sec. 4.2) or all of a group's resampling weights vanish; SPS_ERR_NONFINITE when a
+ *   log-likelihood is not finite; SPS_ERR_TIMEOUT when a bounded device wait gave up;
+ *   SPS_ERR_STATE for a call out of order (e.g. an S phase before any C phase).
+ */
+#ifndef SPS_H_
+#define SPS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sps_status {
+  SPS_OK = 0,
+  SPS_ERR_INVALID_ARG = 1,
+  SPS_ERR_CUDA = 2,
+  SPS_ERR_OOM = 3,
+  SPS_ERR_DEGENERATE = 4,
+  SPS_ERR_NONFINITE = 5,
+  SPS_ERR_TIMEOUT = 6,
+  SPS_ERR_STATE = 7,
+  SPS_ERR_UNSUPPORTED = 8
+} sps_status;
+
+typedef enum sps_mem { SPS_MEM_HOST = 0, SPS_MEM_DEVICE = 1 } sps_mem;
+
+/* Arithmetic of the log-likelihood kernel.
+ * SPS_PREC_SPLIT: X and theta as BF16 hi+lo pairs (exact 0/1 and integer columns as one BF16),
+ *   tcgen05 tensor-core products with FP32 accumulation, FP32 log-sum-exp, FP64 sums across
+ *   observation tiles.
+ * SPS_PREC_FP32: plain FP32 SIMT dot products and log-sum-exp, FP64 sums across tiles. */
+typedef enum sps_precision { SPS_PREC_SPLIT = 0, SPS_PREC_FP32 = 1 } sps_precision;
+
+/* M-phase transition kernel. RW is the Gaussian random walk of Algorithm 2 step 2(c);
+ * MALA adds the drift (h/2) V grad log p(theta | y) and the matching proposal-density ratio. */
+typedef enum sps_mkernel { SPS_MKERNEL_RW = 0, SPS_MKERNEL_MALA = 1 } sps_mkernel;
+
+typedef enum sps_prior_kind {
+  SPS_PRIOR_ISO = 0,   /* cov = sd^2 I, cov_or_sd points to 1 value (sd) */
+  SPS_PRIOR_DIAG = 1,  /* cov = diag(sd^2), cov_or_sd points to D values (sd) */
+  SPS_PRIOR_FULL = 2   /* cov_or_sd points to a D x D row-major covariance */
+} sps_prior_kind;
+
+/* Gaussian prior on the normalised parameter vector (Eq. 16 with theta_0 = 0; Sec. 3.1).
+ * mean: D values, or NULL for the zero vector. Host pointers, copied by sps_init. */
+typedef struct sps_prior {
+  int32_t kind;
+  const double* mean;
+  const double* cov_or_sd;
+} sps_prior;
+
+/* The design constants of Algorithm 2 (Sec. 2.3 calls them hard-wired but user-changeable)
+ * and the library's own settings. sps_options_default fills the paper's values. */
+typedef struct sps_options {
+  double ess_fraction;     /* 0.5: the C phase ends when ESS/(J N) < ess_fraction (Eq. 14) */
+  double h_init;           /* 0.5: h_11 */
+  double h_step;           /* 0.01 */
+  double h_min;            /* 0.1 */
+  double h_max;            /* 1.0 */
+  double target_accept;    /* 0.25 (RW); the step-size rule compares alpha_lr > target */
+  double rne_cycle;        /* 0.35: K when s < T */
+  double rne_final;        /* 0.9: K when s = T */
+  int32_t r_max;           /* 200: cap on M steps per cycle (not in the paper) */
+  int32_t precision;       /* sps_precision, default SPS_PREC_SPLIT */
+  int32_t mkernel;         /* sps_mkernel, default SPS_MKERNEL_RW */
+  int32_t cphase_block;    /* observations per C-phase block launch, default 64 */
+  double mala_target_accept; /* 0.5: step-size target when mkernel == MALA (not in the paper) */
+  uint64_t seed;           /* Philox key for sps_run's random numbers */
+} sps_options;
+
+typedef struct sps_ctx sps_ctx;
+typedef struct sps_state sps_state;
+
+/* Recorded schedule of an adaptive run, the input of the second pass of the two-pass
+ * simulator (Algorithm 3, Sec. 2.4): t_l, R_l and Sigma_lr. Caller-allocated arrays with the
+ * stated capacities; sps_run writes n_cycles and the used entries, or returns
+ * SPS_ERR_INVALID_ARG when a capacity is too small. When passed as the schedule argument of
+ * sps_run, the run replays it (C phases end at t[l], M phases take R[l] steps with the recorded
+ * Sigma matrices). */
+typedef struct sps_schedule {
+  int32_t n_cycles;
+  int32_t cap_cycles;
+  int64_t* t;              /* [cap_cycles] t_l */
+  int32_t* R;              /* [cap_cycles] R_l */
+  int64_t cap_steps;       /* capacity of sigma/h/accept in steps (sum of R_l) */
+  double* sigma;           /* [cap_steps * D * D] Sigma_lr, row-major, steps in order; may be NULL
+                              when only recording t and R */
+  double* h;               /* [cap_steps] h_lr, may be NULL */
+  double* accept;          /* [cap_steps] alpha_lr, may be NULL */
+} sps_schedule;
+
+/* Output of sps_run. All arrays are caller-allocated host memory.
+ * Moments are for the D coordinates of theta followed by the C-1 log-odds theta_c' xbar
+ * (Eq. 15 at the covariate mean xbar over all T observations): m = D + C - 1 entries each. */
+typedef struct sps_result {
+  double* mean;            /* [m] grand mean, Eq. (5) */
+  double* sd;              /* [m] posterior SD from the pooled particles */
+  double* nse;             /* [m] numerical standard error, (v-hat / (J N))^(1/2), Eqs. (6)-(7) */
+  double* rne;             /* [m] relative numerical efficiency, Eq. (10) */
+  double* log_ml_group;    /* [J] per-group log marginal likelihood */
+  double log_ml;           /* mean over groups of log_ml_group */
+  double log_ml_nse;       /* sd over groups / sqrt(J) */
+  double log_ml_pooled;    /* log of the mean over groups of the group marginal likelihoods */
+  int32_t n_cycles;        /* L */
+  int64_t m_steps;         /* sum of R_l */
+  double seconds;          /* wall time of the run on the host clock */
+} sps_result;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Fill *opt with the paper's Algorithm 2 constants and the library defaults. */
+void sps_options_default(sps_options* opt);
+
+/* Create a context for the data (X, y) and prior (Sec. 2.1, Eq. 1; Sec. 3.1, Eq. 16).
+ *   X: host FP64 [n x k] row-major covariates; y: host int32 [n], values 0..n_outcomes-1.
+ *   n >= 1, 1 <= k <= 256, 2 <= n_outcomes <= 4 for the tensor-core path (the FP32 path
+ *   accepts up to 16 outcomes). prior: Gaussian on the D = k*(n_outcomes-1) free coefficients.
+ *   opt may be NULL (defaults). Copies and encodes X and y to the current CUDA device.
+ * Errors: SPS_ERR_INVALID_ARG for bad sizes, y out of range, non-finite X or a prior covariance
+ * that is not positive definite; SPS_ERR_OOM; SPS_ERR_CUDA. *out is NULL on failure. */
+sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const int32_t* y,
+                    int32_t n_outcomes, const sps_prior* prior, const sps_options* opt);
+
+/* Release every device and host resource of the context (NULL is a no-op). States created on
+ * it must be destroyed first. */
+void sps_destroy(sps_ctx* ctx);
+
+/* Run the context's work on `stream` (a cudaStream_t; NULL = the legacy default stream). */
+sps_status sps_set_stream(sps_ctx* ctx, void* stream);
+
+/* Message for a status code, and the last error message recorded on ctx (never NULL). */
+const char* sps_status_string(sps_status s);
+const char* sps_last_error(const sps_ctx* ctx);
+
+/* Sizes of the context: n, k, C, D. Any pointer may be NULL. */
+sps_status sps_get_dims(const sps_ctx* ctx, int64_t* n, int32_t* k, int32_t* C, int32_t* D);
+
+/* ------------------------------------------------------------------ the likelihood hot path */
+
+/* Log-likelihood of every particle over the first t observations (Eq. 1, product form of
+ * Sec. 2.1): ll[p] = sum_{s<=t} log P(Y_s = y_s | x_s, theta_p).
+ *   theta: [P x D] FP64 class-major (mem); ll: [P] FP64 output (mem); 1 <= P; 0 <= t <= n.
+ *   precision: sps_precision (the context's option is only the default of sps_run).
+ * Deterministic: the same theta always gives the same bits. */
+sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
+                      int32_t precision, int32_t mem);
+
+/* Log-likelihood and its gradient d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s
+ * (the derivative of Eq. 1; the paper prints no gradient).
+ *   grad: [P x D] FP64 output, class-major like theta (mem). Split precision only. */
+sps_status sps_loglik_grad(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
+                           double* grad, int32_t mem);
+
+/* ------------------------------------------------------------------ simulator state and phases */
+
+/* Create the particle state of J groups of N particles and draw them iid from the prior
+ * (Algorithm 1 step 1) with Philox key `seed`. 2 <= J, 2 <= N <= 4096. t = 0, h = h_init. */
+sps_status sps_state_create(sps_ctx* ctx, int32_t J, int32_t N, uint64_t seed, sps_state** out);
+void sps_state_destroy(sps_state* st);
+
+/* Copy the state's particles [J*N x D], cached log-likelihoods [J*N] and log weights [J*N]
+ * (host pointers, any may be NULL) and its scalars (t, h; any may be NULL). */
+sps_status sps_state_get(sps_ctx* ctx, const sps_state* st, double* theta, double* ll,
+                         double* logw, int64_t* t, double* h);
+/* Overwrite particles and cached log-likelihoods (host pointers, [J*N x D] and [J*N]; ll may be
+ * NULL to recompute it at the state's t) and set t (0 <= t <= n). */
+sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const double* ll,
+                         int64_t t);
+
+/* C phase (Algorithm 1 step 2(a), Eq. 11, ended by the ESS rule of Algorithm 2 step 1, Eq. 14):
+ * from the state's t, multiply the weights by p(y_s | theta) for s = t+1, ... until
+ * ESS(s)/(J N) < ess_fraction or s = n; with t_target > 0 stop at s = t_target instead
+ * (a recorded schedule). Adds log N^-1 sum_n w_jn to each group's log marginal likelihood,
+ * updates the cached log-likelihoods and sets t. Outputs (host, may be NULL): t_new, ess at
+ * t_new, logml_inc [J]. */
+sps_status sps_cphase(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new,
+                      double* ess, double* logml_inc);
+
+/* S phase (Algorithm 1 step 2(b)): multinomial resampling of each group from its C-phase
+ * weights, then the gather of particles and cached log-likelihoods.
+ *   uniforms: [J*N] FP64 on [0,1) (mem) to use instead of the state's Philox stream, or NULL.
+ *   idx_out: [J*N] int32 (mem) receives the selected index within the group, or NULL. */
+sps_status sps_sphase(sps_ctx* ctx, sps_state* st, const double* uniforms, int32_t* idx_out,
+                      int32_t mem);
+
+/* Diagnostics of one M step. */
+typedef struct sps_mstep_info {
+  double h;                /* step-size factor used by this step */
+  double accept_rate;      /* alpha_lr */
+  double rne_min;          /* smallest RNE of the monitoring set after the step */
+  double h_next;           /* h after the +-h_step rule */
+} sps_mstep_info;
+
+/* One M step (Algorithm 2 step 2(c)): V = pooled particle covariance (divisor J N - 1),
+ * Sigma = h V (or the given sigma [D x D] host, row-major, e.g. from a recorded schedule),
+ * theta' = theta + chol(Sigma) z, Metropolis accept with log u < log alpha; then the step-size
+ * rule and the RNE of the monitoring set {ll, theta_c' xbar}. kernel: sps_mkernel.
+ *   sigma_used: [D x D] host output of the Sigma used (may be NULL).
+ * The state's h is updated to info.h_next unless sigma was given. */
+sps_status sps_mstep(sps_ctx* ctx, sps_state* st, int32_t kernel, const double* sigma,
+                     double* sigma_used, sps_mstep_info* info);
+
+/* M phase (Algorithm 2 step 2): M steps until the smallest RNE of the monitoring set reaches
+ * K (rne_cycle if t < n, rne_final if t == n) or r_max steps; with fixed_steps > 0, exactly that
+ * many steps. Outputs (host, may be NULL): steps taken, last acceptance rate, last RNE min. */
+sps_status sps_mphase(sps_ctx* ctx, sps_state* st, int32_t kernel, int32_t fixed_steps,
+                      int32_t* steps, double* accept_rate, double* rne_min);
+
+/* The whole simulator: adaptive Algorithm 2 with J groups of N particles, or, when `schedule`
+ * is non-NULL with n_cycles > 0, the replay of that schedule (Algorithm 3 pass 2). When
+ * `record` is non-NULL the run's schedule is written into it. Results in *out (caller arrays). */
+sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
+                   const sps_schedule* schedule, sps_schedule* record, sps_result* out);
+
+/* ------------------------------------------------------------------ building blocks */
+
+/* Multinomial resampling by an integer CDF, each of J groups of N independently (the S phase
+ * of Algorithm 1): q_n = floor(w_n 2^40) with w the group's FP64 weights divided by their
+ * maximum (w is given already divided: max w_n = 1 in each group), cumulative sums in uint64,
+ * tau = min(floor(u_i * Q), Q - 1), idx_i = first n with cumulative q > tau.
+ *   w, u: [J*N] FP64 (mem); idx: [J*N] int32 within-group indices (mem). N <= 4096.
+ * SPS_ERR_DEGENERATE (host memory only) when a group's weights all quantise to zero. */
+sps_status sps_resample(sps_ctx* ctx, const double* w, const double* u, int32_t J, int32_t N,
+                        int32_t* idx, int32_t mem);
+
+/* Philox4x32-10 blocks (Salmon et al., SC'11) for counters (ctr0 + i, ctr1, ctr2, ctr3),
+ * i = 0..count-1, key (key0, key1): out [count x 4] uint32 (mem). */
+sps_status sps_philox(sps_ctx* ctx, uint32_t key0, uint32_t key1, uint32_t ctr0, uint32_t ctr1,
+                      uint32_t ctr2, uint32_t ctr3, int64_t count, uint32_t* out, int32_t mem);
+
+/* ESS (Eq. 14) of P log weights and log N^-1 sum exp(logw) of each of J groups of N = P/J
+ * (the per-cycle log marginal likelihood increment). logw: [P] (mem); ess: 1 value (mem);
+ * lme: [J] (mem). */
+sps_status sps_ess(sps_ctx* ctx, const double* logw, int64_t P, int32_t J, double* ess,
+                   double* lme, int32_t mem);
+
+/* Pooled sample covariance of P particles (divisor P - 1), V: [D x D] FP64 (mem). */
+sps_status sps_particle_cov(sps_ctx* ctx, const double* theta, int64_t P, double* V, int32_t mem);
+
+/* One random-walk Metropolis step with given randomness, for step-level parity:
+ * theta' = theta + L z with L the lower Cholesky factor of sigma (host [D x D]); log alpha =
+ * ll(theta'; y_1:t) - ll + log p(theta') - log p(theta); accept when log u < log alpha.
+ *   theta [P x D], ll [P] are updated in place (mem); z [P x D], u [P] (mem);
+ *   log_alpha [P], accepted [P] (int32) outputs (mem, may be NULL). */
+sps_status sps_rw_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P, int64_t t,
+                             const double* sigma, const double* z, const double* u,
+                             int32_t precision, double* log_alpha, int32_t* accepted,
+                             int32_t mem);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPS_H_ */

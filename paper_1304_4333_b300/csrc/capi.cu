@@ -1,0 +1,423 @@
+// C ABI of the SPS library: context lifecycle, data encoding and the likelihood entry points.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sps {
+
+DevBuf::~DevBuf() {
+  if (ptr) cudaFree(ptr);
+}
+
+cudaError_t DevBuf::reserve(size_t nbytes) {
+  if (nbytes <= bytes && ptr) return cudaSuccess;
+  if (ptr) {
+    cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  if (nbytes == 0) nbytes = 16;
+  cudaError_t e = cudaMalloc(&ptr, nbytes);
+  if (e == cudaSuccess) bytes = nbytes;
+  else ptr = nullptr;
+  return e;
+}
+
+sps_status fail(sps_ctx* ctx, sps_status s, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return s;
+}
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Columns with every value exactly representable in BF16 (0/1 dummies, the intercept, small
+// integers) need no low part.
+__global__ void nonexact_columns_kernel(const double* __restrict__ X, int64_t n, int k,
+                                        int* __restrict__ nonexact, int* __restrict__ nonfinite) {
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (idx >= n * k) return;
+  const double v = X[idx];
+  if (!isfinite(v)) {
+    atomicOr(nonfinite, 1);
+    return;
+  }
+  const int col = static_cast<int>(idx % k);
+  const double h = static_cast<double>(__bfloat162float(__double2bfloat16(v)));
+  if (h != v) atomicOr(&nonexact[col], 1);
+}
+
+__global__ void encode_x_kernel(const double* __restrict__ X, int64_t n, int k,
+                                const int* __restrict__ perm, int kpad, int kc, int kcpad,
+                                __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
+                                float* __restrict__ Xf) {
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (idx >= n * kpad) return;
+  const int64_t s = idx / kpad;
+  const int j = static_cast<int>(idx - s * kpad);
+  double v = 0.0;
+  if (j < k) v = X[s * k + perm[j]];
+  const __nv_bfloat16 h = __double2bfloat16(v);
+  Xh[idx] = h;
+  if (j < kcpad) {
+    const double rem = (j < kc) ? v - static_cast<double>(__bfloat162float(h)) : 0.0;
+    Xl[s * kcpad + j] = __double2bfloat16(rem);
+  }
+  if (j < k) Xf[s * k + j] = static_cast<float>(X[s * k + j]);
+}
+
+// lin[c*k + i] = prefix[tile] + sum over the remaining rows s in [128*tile, t) of w_c(y_s) x_{s,i}.
+__global__ void lin_tail_kernel(const double* __restrict__ prefix, const double* __restrict__ X,
+                                const int* __restrict__ y, int k, int NC, int64_t t,
+                                double* __restrict__ lin) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NC * k) return;
+  const int c = idx / k;
+  const int i = idx - c * k;
+  const int64_t tile = t / 128;
+  double a = prefix[tile * NC * k + idx];
+  for (int64_t s = tile * 128; s < t; ++s) {
+    const int ys = y[s];
+    const double w = (NC == 1) ? (ys == 1 ? 0.5 : -0.5) : (ys == c + 1 ? 1.0 : 0.0);
+    a = fma(w, X[s * k + i], a);
+  }
+  lin[idx] = a;
+}
+
+sps_status to_device(sps_ctx* ctx, DevBuf& buf, const void* host, size_t bytes) {
+  SPS_CUDA_TRY(buf.reserve(bytes));
+  SPS_CUDA_TRY(cudaMemcpy(buf.ptr, host, bytes, cudaMemcpyHostToDevice));
+  return SPS_OK;
+}
+
+// Lower Cholesky factor of a symmetric positive definite matrix (host FP64, row-major).
+bool cholesky_host(const std::vector<double>& A, int D, std::vector<double>& L) {
+  L.assign(static_cast<size_t>(D) * D, 0.0);
+  for (int j = 0; j < D; ++j) {
+    double s = A[j * D + j];
+    for (int m = 0; m < j; ++m) s -= L[j * D + m] * L[j * D + m];
+    if (!(s > 0.0) || !std::isfinite(s)) return false;
+    const double d = std::sqrt(s);
+    L[j * D + j] = d;
+    for (int i = j + 1; i < D; ++i) {
+      double r = A[i * D + j];
+      for (int m = 0; m < j; ++m) r -= L[i * D + m] * L[j * D + m];
+      L[i * D + j] = r / d;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+sps_status make_map_bf16(sps_ctx* ctx, CUtensorMap* map, const void* base, uint64_t rows,
+                         uint64_t cols, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(ctx, SPS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t gdim[2] = {cols, rows};
+  cuuint64_t gstride[1] = {cols * sizeof(__nv_bfloat16)};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box,
+                  estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char msg[96];
+    snprintf(msg, sizeof msg, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return fail(ctx, SPS_ERR_CUDA, msg);
+  }
+  return SPS_OK;
+}
+
+sps_status ensure_lin(sps_ctx* ctx, int64_t t) {
+  if (ctx->lin_t == t) return SPS_OK;
+  const int nk = ctx->NC * ctx->k;
+  lin_tail_kernel<<<(nk + 127) / 128, 128, 0, ctx->stream>>>(ctx->lin_prefix.as<double>(), ctx->Xd.as<double>(),
+                                                            ctx->y.as<int>(), ctx->k, ctx->NC, t,
+                                                            ctx->lin.as<double>());
+  SPS_CUDA_TRY(cudaGetLastError());
+  ctx->lin_t = t;
+  return SPS_OK;
+}
+
+sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
+                           int precision) {
+  if (precision == SPS_PREC_FP32) return loglik_fp32(ctx, d_theta, P, t, d_ll);
+  if (precision == SPS_PREC_SPLIT) return loglik_split(ctx, d_theta, P, t, d_ll);
+  return fail(ctx, SPS_ERR_INVALID_ARG, "unknown precision");
+}
+
+}  // namespace sps
+
+using namespace sps;
+
+extern "C" {
+
+void sps_options_default(sps_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->ess_fraction = 0.5;
+  o->h_init = 0.5;
+  o->h_step = 0.01;
+  o->h_min = 0.1;
+  o->h_max = 1.0;
+  o->target_accept = 0.25;
+  o->rne_cycle = 0.35;
+  o->rne_final = 0.9;
+  o->r_max = 200;
+  o->precision = SPS_PREC_SPLIT;
+  o->mkernel = SPS_MKERNEL_RW;
+  o->cphase_block = 64;
+  o->mala_target_accept = 0.5;
+  o->seed = 0;
+}
+
+const char* sps_status_string(sps_status s) {
+  switch (s) {
+    case SPS_OK: return "ok";
+    case SPS_ERR_INVALID_ARG: return "invalid argument";
+    case SPS_ERR_CUDA: return "CUDA error";
+    case SPS_ERR_OOM: return "out of device memory";
+    case SPS_ERR_DEGENERATE: return "degenerate particle set (proposal covariance not positive definite)";
+    case SPS_ERR_NONFINITE: return "non-finite log-likelihood";
+    case SPS_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SPS_ERR_STATE: return "call out of order";
+    case SPS_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* sps_last_error(const sps_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+sps_status sps_get_dims(const sps_ctx* ctx, int64_t* n, int32_t* k, int32_t* C, int32_t* D) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (n) *n = ctx->n;
+  if (k) *k = ctx->k;
+  if (C) *C = ctx->C;
+  if (D) *D = ctx->D;
+  return SPS_OK;
+}
+
+sps_status sps_set_stream(sps_ctx* ctx, void* stream) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return SPS_OK;
+}
+
+void sps_destroy(sps_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const int32_t* y,
+                    int32_t n_outcomes, const sps_prior* prior, const sps_options* opt) {
+  if (!out) return SPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!X || !y || !prior || n < 1 || k < 1 || k > 256 || n_outcomes < 2 || n_outcomes > 16 ||
+      n > (1LL << 31) - 256)
+    return SPS_ERR_INVALID_ARG;
+  for (int64_t s = 0; s < n; ++s)
+    if (y[s] < 0 || y[s] >= n_outcomes) return SPS_ERR_INVALID_ARG;
+  sps_ctx* ctx = new sps_ctx();
+  auto bail = [&](sps_status s) {
+    delete ctx;
+    return s;
+  };
+  if (opt) ctx->opt = *opt;
+  else sps_options_default(&ctx->opt);
+  ctx->n = n;
+  ctx->k = k;
+  ctx->C = n_outcomes;
+  ctx->NC = n_outcomes - 1;
+  ctx->D = k * ctx->NC;
+  const int D = ctx->D, NC = ctx->NC;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(SPS_ERR_CUDA);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) return bail(SPS_ERR_CUDA);
+  ctx->num_sms = prop.multiProcessorCount;
+
+  // ---- prior
+  ctx->prior_kind = prior->kind;
+  ctx->prior_mean.assign(D, 0.0);
+  if (prior->mean)
+    for (int i = 0; i < D; ++i) ctx->prior_mean[i] = prior->mean[i];
+  ctx->prior_cov.assign(static_cast<size_t>(D) * D, 0.0);
+  if (!prior->cov_or_sd) return bail(SPS_ERR_INVALID_ARG);
+  if (prior->kind == SPS_PRIOR_ISO) {
+    const double sd = prior->cov_or_sd[0];
+    if (!(sd > 0.0) || !std::isfinite(sd)) return bail(SPS_ERR_INVALID_ARG);
+    for (int i = 0; i < D; ++i) ctx->prior_cov[i * D + i] = sd * sd;
+  } else if (prior->kind == SPS_PRIOR_DIAG) {
+    for (int i = 0; i < D; ++i) {
+      const double sd = prior->cov_or_sd[i];
+      if (!(sd > 0.0) || !std::isfinite(sd)) return bail(SPS_ERR_INVALID_ARG);
+      ctx->prior_cov[i * D + i] = sd * sd;
+    }
+  } else if (prior->kind == SPS_PRIOR_FULL) {
+    for (int i = 0; i < D * D; ++i) ctx->prior_cov[i] = prior->cov_or_sd[i];
+  } else {
+    return bail(SPS_ERR_INVALID_ARG);
+  }
+  for (double v : ctx->prior_mean)
+    if (!std::isfinite(v)) return bail(SPS_ERR_INVALID_ARG);
+  if (!cholesky_host(ctx->prior_cov, D, ctx->prior_chol)) {
+    ctx->last_error = "prior covariance is not positive definite";
+    return bail(SPS_ERR_INVALID_ARG);
+  }
+  {
+    // precision: diagonal for ISO/DIAG, full inverse (via the Cholesky factor) for FULL
+    std::vector<double> prec;
+    if (prior->kind == SPS_PRIOR_FULL) {
+      std::vector<double> Linv(static_cast<size_t>(D) * D, 0.0);
+      const auto& L = ctx->prior_chol;
+      for (int j = 0; j < D; ++j) {
+        Linv[j * D + j] = 1.0 / L[j * D + j];
+        for (int i = j + 1; i < D; ++i) {
+          double s = 0.0;
+          for (int m = j; m < i; ++m) s += L[i * D + m] * Linv[m * D + j];
+          Linv[i * D + j] = -s / L[i * D + i];
+        }
+      }
+      prec.assign(static_cast<size_t>(D) * D, 0.0);
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+          for (int m = std::max(i, j); m < D; ++m) s += Linv[m * D + i] * Linv[m * D + j];
+          prec[i * D + j] = s;
+        }
+    } else {
+      prec.resize(D);
+      for (int i = 0; i < D; ++i) prec[i] = 1.0 / ctx->prior_cov[i * D + i];
+    }
+    if (to_device(ctx, ctx->d_prior_prec, prec.data(), prec.size() * sizeof(double)) != SPS_OK)
+      return bail(SPS_ERR_OOM);
+    if (to_device(ctx, ctx->d_prior_mean, ctx->prior_mean.data(), D * sizeof(double)) != SPS_OK ||
+        to_device(ctx, ctx->d_prior_chol, ctx->prior_chol.data(), ctx->prior_chol.size() * sizeof(double)) !=
+            SPS_OK)
+      return bail(SPS_ERR_OOM);
+  }
+
+  // ---- data
+  sps_status st;
+  if ((st = to_device(ctx, ctx->Xd, X, static_cast<size_t>(n) * k * sizeof(double))) != SPS_OK) return bail(st);
+  if ((st = to_device(ctx, ctx->y, y, static_cast<size_t>(n) * sizeof(int32_t))) != SPS_OK) return bail(st);
+  {
+    DevBuf flags;
+    if (flags.reserve((k + 1) * sizeof(int)) != cudaSuccess) return bail(SPS_ERR_OOM);
+    cudaMemset(flags.ptr, 0, (k + 1) * sizeof(int));
+    const int64_t tot = n * k;
+    nonexact_columns_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256>>>(
+        ctx->Xd.as<double>(), n, k, flags.as<int>(), flags.as<int>() + k);
+    std::vector<int> h(k + 1);
+    if (cudaMemcpy(h.data(), flags.ptr, (k + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail(SPS_ERR_CUDA);
+    if (h[k]) {
+      ctx->last_error = "X holds non-finite values";
+      return bail(SPS_ERR_INVALID_ARG);
+    }
+    XEncoding& enc = ctx->enc;
+    enc.k = k;
+    enc.perm.clear();
+    for (int j = 0; j < k; ++j)
+      if (h[j]) enc.perm.push_back(j);
+    enc.kc = static_cast<int>(enc.perm.size());
+    for (int j = 0; j < k; ++j)
+      if (!h[j]) enc.perm.push_back(j);
+    enc.kpad = (k + 63) / 64 * 64;
+    enc.kcpad = (enc.kc + 63) / 64 * 64;
+    enc.bn = (NC <= 2) ? 128 : 64;
+    if ((st = to_device(ctx, enc.perm_dev, enc.perm.data(), k * sizeof(int))) != SPS_OK) return bail(st);
+    if (enc.Xh.reserve(static_cast<size_t>(n) * enc.kpad * 2) != cudaSuccess ||
+        enc.Xl.reserve(static_cast<size_t>(n) * std::max(enc.kcpad, 64) * 2) != cudaSuccess ||
+        ctx->Xf.reserve(static_cast<size_t>(n) * k * 4) != cudaSuccess)
+      return bail(SPS_ERR_OOM);
+    const int64_t tot2 = n * enc.kpad;
+    encode_x_kernel<<<static_cast<unsigned>((tot2 + 255) / 256), 256>>>(
+        ctx->Xd.as<double>(), n, k, enc.perm_dev.as<int>(), enc.kpad, enc.kc, enc.kcpad,
+        enc.Xh.as<__nv_bfloat16>(), enc.Xl.as<__nv_bfloat16>(), ctx->Xf.as<float>());
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(SPS_ERR_CUDA);
+    if ((st = make_map_bf16(ctx, &enc.mapXh, enc.Xh.ptr, n, enc.kpad, enc.bn)) != SPS_OK) return bail(st);
+    if (enc.kcpad > 0 && (st = make_map_bf16(ctx, &enc.mapXl, enc.Xl.ptr, n, enc.kcpad, enc.bn)) != SPS_OK)
+      return bail(st);
+  }
+  // covariate means and prefix sums of the linear term, host FP64 in observation order
+  {
+    ctx->xbar_host.assign(k, 0.0);
+    const int64_t ntiles = n / 128 + 1;
+    std::vector<double> pre(static_cast<size_t>(ntiles) * NC * k, 0.0);
+    std::vector<double> run(static_cast<size_t>(NC) * k, 0.0);
+    for (int64_t s = 0; s < n; ++s) {
+      if (s % 128 == 0) std::copy(run.begin(), run.end(), pre.begin() + (s / 128) * NC * k);
+      const double* xs = X + s * k;
+      for (int i = 0; i < k; ++i) ctx->xbar_host[i] += xs[i];
+      for (int c = 0; c < NC; ++c) {
+        const double w = (NC == 1) ? (y[s] == 1 ? 0.5 : -0.5) : (y[s] == c + 1 ? 1.0 : 0.0);
+        if (w == 0.0) continue;
+        for (int i = 0; i < k; ++i) run[c * k + i] += w * xs[i];
+      }
+    }
+    if (n % 128 == 0) std::copy(run.begin(), run.end(), pre.begin() + (n / 128) * NC * k);
+    for (int i = 0; i < k; ++i) ctx->xbar_host[i] /= static_cast<double>(n);
+    if ((st = to_device(ctx, ctx->lin_prefix, pre.data(), pre.size() * sizeof(double))) != SPS_OK) return bail(st);
+    if ((st = to_device(ctx, ctx->xbar, ctx->xbar_host.data(), k * sizeof(double))) != SPS_OK) return bail(st);
+    if (ctx->lin.reserve(static_cast<size_t>(NC) * k * sizeof(double)) != cudaSuccess) return bail(SPS_ERR_OOM);
+  }
+  *out = ctx;
+  return SPS_OK;
+}
+
+static sps_status check_finite_ll(sps_ctx* ctx, const double* h_ll, int64_t P) {
+  for (int64_t p = 0; p < P; ++p)
+    if (!std::isfinite(h_ll[p])) return fail(ctx, SPS_ERR_NONFINITE, "non-finite log-likelihood");
+  return SPS_OK;
+}
+
+sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
+                      int32_t precision, int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!theta || !ll || P < 1 || t < 0 || t > ctx->n || P > (1LL << 28))
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik: bad arguments");
+  if (mem == SPS_MEM_DEVICE) return loglik_dispatch(ctx, theta, P, t, ll, precision);
+  if (mem != SPS_MEM_HOST) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik: bad mem kind");
+  LoglikScratch& S = ctx->ll;
+  const size_t tb = static_cast<size_t>(P) * ctx->D * sizeof(double);
+  SPS_CUDA_TRY(S.theta_in.reserve(tb));
+  SPS_CUDA_TRY(S.ll_out.reserve(P * sizeof(double)));
+  SPS_CUDA_TRY(cudaMemcpyAsync(S.theta_in.ptr, theta, tb, cudaMemcpyHostToDevice, ctx->stream));
+  SPS_TRY(loglik_dispatch(ctx, S.theta_in.as<double>(), P, t, S.ll_out.as<double>(), precision));
+  SPS_CUDA_TRY(cudaMemcpyAsync(ll, S.ll_out.ptr, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (precision == SPS_PREC_SPLIT) {
+    int flag = 0;
+    SPS_CUDA_TRY(cudaMemcpy(&flag, S.flag.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(ctx, SPS_ERR_TIMEOUT, "loglik kernel: bounded wait timed out");
+  }
+  return check_finite_ll(ctx, ll, P);
+}
+
+}  // extern "C"

@@ -1,0 +1,325 @@
+// Internal declarations of the SPS library: context and state structures, status handling,
+// and the inline-PTX wrappers (mbarrier, TMA, tcgen05) the sm_103a kernels use.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sps.h"
+
+namespace sps {
+
+// ------------------------------------------------------------------------------------------
+// Status plumbing
+
+#define SPS_CUDA_TRY(expr)                                                           \
+  do {                                                                               \
+    cudaError_t _e = (expr);                                                         \
+    if (_e != cudaSuccess) {                                                         \
+      return ::sps::fail(ctx, _e == cudaErrorMemoryAllocation ? SPS_ERR_OOM          \
+                                                              : SPS_ERR_CUDA,        \
+                         std::string(#expr) + ": " + cudaGetErrorString(_e));        \
+    }                                                                                \
+  } while (0)
+
+#define SPS_TRY(expr)                  \
+  do {                                 \
+    sps_status _s = (expr);            \
+    if (_s != SPS_OK) return _s;       \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// Device buffers owned by the context or a state. Growth only; freed in the destructor.
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  ~DevBuf();
+  cudaError_t reserve(size_t nbytes);
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Encoding of X for the tensor-core path: columns permuted so that the columns that are not
+// exact in BF16 ("continuous") come first. Xh = bf16(X), Xl = bf16(X - Xh) for the first kc
+// columns (zero for the exact ones). Row pitch kpad / kcpad elements (multiples of 64).
+struct XEncoding {
+  int k = 0, kc = 0;          // covariates, continuous covariates
+  int kpad = 0, kcpad = 0;    // padded widths of Xh and Xl (64-element K blocks)
+  int bn = 128;               // observation rows per TMA box of X
+  std::vector<int> perm;      // internal column j holds original column perm[j]
+  DevBuf perm_dev;            // int [k]
+  DevBuf Xh, Xl;              // bf16 [n x kpad], [n x kcpad]
+  CUtensorMap mapXh;
+  CUtensorMap mapXl;
+};
+
+// Per-call scratch of the likelihood kernels.
+struct LoglikScratch {
+  DevBuf thetaH, thetaL;      // bf16 [NC * Ppad x kpad] operand rows (class-major row blocks)
+  int64_t ppad_cap = 0;       // particle capacity of thetaH/thetaL
+  CUtensorMap mapTH;
+  CUtensorMap mapTL;
+  DevBuf partial;             // FP64 partial sums [slices x Ppad]
+  DevBuf flag;                // int error/timeout flag
+  DevBuf theta_in, ll_out, grad_out, aux;   // staging for host-memory calls
+};
+
+}  // namespace sps
+
+struct sps_ctx {
+  int device = 0;
+  int num_sms = 148;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0;
+  int k = 0, C = 2, NC = 1, D = 0;
+  sps_options opt;
+  std::string last_error;
+
+  // data
+  sps::XEncoding enc;
+  sps::DevBuf Xd;             // FP64 [n x k] original column order
+  sps::DevBuf Xf;             // FP32 [n x k] original column order (FP32 path, C phase)
+  sps::DevBuf y;              // int32 [n]
+  sps::DevBuf xbar;           // FP64 [k] covariate means over all n observations
+  std::vector<double> xbar_host;
+  // linear term of the split path: lin(t) [NC x k] FP64 (original order), cached by t.
+  // binary: sum_{s<t} (y_s - 1/2) x_s; C > 2: sum_{s<t, y_s = c} x_s for c = 1..C-1.
+  sps::DevBuf lin;
+  int64_t lin_t = -1;
+  sps::DevBuf lin_prefix;     // FP64 [(n/128 + 1) x NC x k] prefix sums at 128-row boundaries
+  // prior: N(mean, cov) on the D free coefficients
+  int prior_kind = SPS_PRIOR_ISO;
+  std::vector<double> prior_mean, prior_cov, prior_chol;
+  sps::DevBuf d_prior_mean;   // FP64 [D]
+  sps::DevBuf d_prior_prec;   // FP64 [D x D] (FULL) or [D] diagonal precision (ISO / DIAG)
+  sps::DevBuf d_prior_chol;   // FP64 [D x D] lower Cholesky factor of cov
+
+  sps::LoglikScratch ll;
+};
+
+struct sps_state {
+  sps_ctx* ctx = nullptr;
+  int32_t J = 0, N = 0;
+  int64_t P = 0;
+  uint64_t seed = 0;
+  int64_t t = 0;
+  double h = 0.5;
+  bool have_weights = false;      // a C phase has run since the last S phase
+  uint64_t step_counter = 0;      // Philox counter word for per-step streams
+  uint64_t cycle_counter = 0;
+  sps::DevBuf theta, theta_prop;  // FP64 [P x D]
+  sps::DevBuf ll, ll_prop;        // FP64 [P]
+  sps::DevBuf lp, lp_prop;        // FP64 [P] prior log kernel
+  sps::DevBuf logw;               // FP64 [P]
+  sps::DevBuf logml;              // FP64 [J]
+  sps::DevBuf lwbuf;              // FP64 [block x P] C-phase running log weights
+  sps::DevBuf ess_buf;            // FP64 [block] ESS per observation of a block
+  sps::DevBuf idx;                // int32 [P]
+  sps::DevBuf scratch;            // moments, covariance partials, counters
+  sps::DevBuf cov;                // FP64 [D x D]
+  sps::DevBuf chol;               // FP64 [D x D]
+  sps::DevBuf mean;               // FP64 [D]
+  sps::DevBuf counters;           // int/unsigned counters (accepts, error flags)
+  sps::DevBuf grad, grad_prop;    // FP64 [P x D] (MALA)
+  std::vector<double> host_tmp;
+};
+
+namespace sps {
+
+// Record an error on ctx and return its status.
+sps_status fail(sps_ctx* ctx, sps_status s, const std::string& msg);
+inline sps_status fail(const sps_ctx* ctx, sps_status s, const std::string& msg) {
+  return fail(const_cast<sps_ctx*>(ctx), s, msg);
+}
+
+// Build a 2D bf16 tensor map with 128-byte swizzle: rows x cols (cols contiguous, multiple of
+// 64), box {64, box_rows}.
+sps_status make_map_bf16(sps_ctx* ctx, CUtensorMap* map, const void* base, uint64_t rows,
+                         uint64_t cols, uint32_t box_rows);
+
+// Likelihood launchers (loglik_tc.cu, loglik_simt.cu). Device pointers, context stream.
+sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
+sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
+sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
+                           int precision);
+sps_status ensure_lin(sps_ctx* ctx, int64_t t);
+// C-phase running log weights for observations [s_lo, s_hi): d_lw[j*P + p] (FP64).
+sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
+                             int64_t s_hi, const double* d_logw_in, double* d_lw);
+
+}  // namespace sps
+
+// ------------------------------------------------------------------------------------------
+// Inline PTX wrappers (device). Written for sm_103a.
+
+namespace sps {
+namespace ptx {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase. Gives up when *abort becomes non-zero or after
+// `limit_ns` of wall time; returns false in both cases (and sets *abort on a timeout).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  volatile int* abort, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (globaltimer() - t0 > limit_ns) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int32_t x, int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---- tcgen05 ----
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, bf16 inputs, fp32 accumulate, one CTA.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive once on `bar` when all tcgen05.mma issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns: thread i of the warp gets lane (base + i).
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with 128-byte
+// swizzle: rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte offset),
+// descriptor version 1, swizzle mode 2 (128B). The leading byte offset is unused in this mode.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1u) << 16;
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(2u) << 61;
+  return d;
+}
+
+// Instruction descriptor for kind::f16 with bf16 A/B, fp32 D, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+}  // namespace ptx
+}  // namespace sps

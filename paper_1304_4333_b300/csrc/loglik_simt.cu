@@ -1,0 +1,150 @@
+// Plain FP32 SIMT log-likelihood (the baseline path) and the C-phase increment kernel.
+//
+// Both evaluate, per particle and observation, the log probability of the observed outcome of
+// the multinomial logit (Eq. 1, Sec. 2.1) in FP32: eta_c = theta_c' x_s (eta_0 = 0),
+// term = eta_{y_s} - (m + log(exp(-m) + sum_c exp(eta_c - m))), m = max(0, eta_1..eta_{C-1}),
+// one thread per particle, 128 particles per block, theta transposed in shared memory so that
+// each thread reads its own column without bank conflicts and X rows are broadcast.
+// Sums over observations are FP32 within a 32-observation tile and FP64 across tiles.
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace sps {
+namespace {
+
+constexpr int kP = 128;    // particles per block
+constexpr int kTS = 32;    // observations per shared-memory tile
+
+// Load theta [P x D] (FP64) of particles p0..p0+127 into sm[D][128] FP32.
+__device__ __forceinline__ void load_theta_t(float* sm, const double* __restrict__ theta, int64_t P,
+                                             int D, int64_t p0) {
+  for (int idx = threadIdx.x; idx < D * kP; idx += blockDim.x) {
+    const int pp = idx / D;
+    const int d = idx - pp * D;
+    const int64_t p = p0 + pp;
+    sm[d * kP + pp] = (p < P) ? static_cast<float>(theta[p * D + d]) : 0.f;
+  }
+}
+
+// Log probability of outcome yo for linear predictors eta[1..NC] (eta[0] = 0), FP32.
+__device__ __forceinline__ float logit_term(const float* eta, int NC, int yo) {
+  float m = 0.f;
+  for (int c = 0; c < NC; ++c) m = fmaxf(m, eta[c]);
+  float s = expf(-m);
+  for (int c = 0; c < NC; ++c) s += expf(eta[c] - m);
+  const float obs = (yo == 0) ? 0.f : eta[yo - 1];
+  return obs - (m + logf(s));
+}
+
+constexpr int kMaxNC = 15;
+
+// Each thread: particle p0 + threadIdx.x; observations [s_lo, s_hi).
+// mode 0: partial[blockIdx.y * P + p] = sum of terms (FP64 across tiles);
+// mode 1: C-phase increments: lw[j * P + p] = logw_in[p] + sum_{s_lo <= s' <= s_lo + j} term.
+__global__ void __launch_bounds__(kP)
+fp32_terms_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
+                  const float* __restrict__ X, const int* __restrict__ y, int64_t s_begin,
+                  int64_t s_end, int64_t chunk, int mode, double* __restrict__ out,
+                  const double* __restrict__ logw_in) {
+  extern __shared__ float smf[];
+  const int D = k * NC;
+  float* th = smf;                          // [D][128]
+  float* xs = th + D * kP;                  // [kTS][k]
+  int* ys = reinterpret_cast<int*>(xs + kTS * k);   // [kTS]
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kP;
+  const int64_t p = p0 + threadIdx.x;
+  const int64_t s_lo = s_begin + static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t s_hi = (s_lo + chunk < s_end) ? s_lo + chunk : s_end;
+  load_theta_t(th, theta, P, D, p0);
+  double acc = (mode == 1 && p < P) ? logw_in[p] : 0.0;
+  float eta[kMaxNC];
+  for (int64_t s0 = s_lo; s0 < s_hi; s0 += kTS) {
+    const int ns = static_cast<int>(s_hi - s0 < kTS ? s_hi - s0 : kTS);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ns * k; idx += blockDim.x) xs[idx] = X[s0 * k + idx];
+    for (int idx = threadIdx.x; idx < ns; idx += blockDim.x) ys[idx] = y[s0 + idx];
+    __syncthreads();
+    float tile = 0.f;
+    for (int j = 0; j < ns; ++j) {
+      const float* xr = xs + j * k;
+      for (int c = 0; c < NC; ++c) {
+        const float* tc = th + (c * k) * kP + threadIdx.x;
+        float e = 0.f;
+        for (int i = 0; i < k; ++i) e = fmaf(tc[i * kP], xr[i], e);
+        eta[c] = e;
+      }
+      const float term = logit_term(eta, NC, ys[j]);
+      if (mode == 1) {
+        acc += static_cast<double>(term);
+        if (p < P) out[(s0 - s_lo + j) * P + p] = acc;
+      } else {
+        tile += term;
+      }
+    }
+    if (mode == 0) acc += static_cast<double>(tile);
+  }
+  if (mode == 0 && p < P) out[static_cast<int64_t>(blockIdx.y) * P + p] = acc;
+}
+
+__global__ void sum_slices_kernel(const double* __restrict__ partial, int64_t P, int slices,
+                                  double* __restrict__ ll) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= P) return;
+  double s = 0.0;
+  for (int q = 0; q < slices; ++q) s += partial[static_cast<int64_t>(q) * P + p];
+  ll[p] = s;
+}
+
+size_t fp32_smem(int k, int NC) {
+  return sizeof(float) * (static_cast<size_t>(k) * NC * kP + static_cast<size_t>(kTS) * k) +
+         sizeof(int) * kTS;
+}
+
+}  // namespace
+
+sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll) {
+  if (ctx->NC > kMaxNC) return fail(ctx, SPS_ERR_UNSUPPORTED, "FP32 path supports at most 16 outcomes");
+  const size_t smem = fp32_smem(ctx->k, ctx->NC);
+  if (smem > 200 * 1024) return fail(ctx, SPS_ERR_UNSUPPORTED, "FP32 path: k*(C-1) too large");
+  const int64_t ptiles = (P + kP - 1) / kP;
+  int64_t chunks = 1;
+  if (t > 0) {
+    const int64_t want = 8LL * ctx->num_sms;
+    chunks = std::max<int64_t>(1, std::min<int64_t>((want + ptiles - 1) / ptiles, (t + kTS - 1) / kTS));
+  }
+  int64_t chunk = (t + chunks - 1) / chunks;
+  chunk = std::max<int64_t>(kTS, (chunk + kTS - 1) / kTS * kTS);
+  chunks = std::max<int64_t>(1, (t + chunk - 1) / chunk);
+  SPS_CUDA_TRY(ctx->ll.partial.reserve(static_cast<size_t>(chunks) * P * sizeof(double)));
+  double* partial = ctx->ll.partial.as<double>();
+  SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  dim3 grid(static_cast<unsigned>(ptiles), static_cast<unsigned>(chunks));
+  fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
+                                                     ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr);
+  SPS_CUDA_TRY(cudaGetLastError());
+  sum_slices_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+      partial, P, t > 0 ? static_cast<int>(chunks) : 0, d_ll);
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
+sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
+                             int64_t s_hi, const double* d_logw_in, double* d_lw) {
+  const size_t smem = fp32_smem(ctx->k, ctx->NC);
+  if (ctx->NC > kMaxNC || smem > 200 * 1024)
+    return fail(ctx, SPS_ERR_UNSUPPORTED, "C phase: k*(C-1) too large");
+  SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  const int64_t ptiles = (P + kP - 1) / kP;
+  dim3 grid(static_cast<unsigned>(ptiles), 1);
+  fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
+                                                     ctx->y.as<int>(), s_lo, s_hi, s_hi - s_lo, 1, d_lw,
+                                                     d_logw_in);
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
+}  // namespace sps

@@ -1,0 +1,139 @@
+"""GPU parity of the fused log-likelihood (sps_loglik) against the FP64 oracle.
+
+Tolerances (per particle):
+* split BF16 path: |ll - ll_oracle| <= 1e-5 |ll_oracle| + bound_split, FP32 path: 1e-6 |ll| + bound_fp32,
+  where bound_* is a bound on the linear-predictor rounding propagated into the sum: each eta_s is
+  off by at most u * sum_i |theta_i x_si| (u = 3 * 2^-16 for the split products, u = k * 2^-23 for
+  FP32 dot products) and |d term / d eta| <= 1, so the sum moves by at most u * B with
+  B = sum_s sum_i |theta_i x_si|. The bound only matters for short prefixes and diffuse
+  particles; on the benchmark workloads the 1e-5 / 1e-6 relative terms dominate.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle.logit import loglik as oracle_loglik
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _mk(n, k, C, seed, exact_cols=0):
+    g = np.random.Generator(np.random.PCG64(seed))
+    X = g.standard_normal((n, k))
+    X[:, 0] = 1.0
+    if exact_cols:
+        X[:, k - exact_cols:] = (g.random((n, exact_cols)) < 0.3).astype(float)
+    y = g.integers(0, C, n).astype(np.int32)
+    return X, y
+
+
+def _l1_mass(X, theta, C, t):
+    k = X.shape[1]
+    A = np.abs(X[:t])
+    out = np.zeros(theta.shape[0])
+    for c in range(C - 1):
+        out += (np.abs(theta[:, c * k:(c + 1) * k]) @ A.T).sum(axis=1)
+    return out
+
+
+def _tol(X, theta, C, t, ref, prec):
+    k = X.shape[1]
+    B = _l1_mass(X, theta, C, t)
+    if prec == "split":
+        return 1e-5 * np.abs(ref) + 3 * 2.0 ** -16 * B + 1e-9 * t
+    return 1e-6 * np.abs(ref) + k * 2.0 ** -23 * B + 1e-9 * t
+
+
+def _sps(X, y, C):
+    from paper_1304_4333_b300 import Sps
+    return Sps(X, y, C, prior_sd=5.0)
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+@pytest.mark.parametrize("C", [2, 3, 4])
+def test_theta_zero_closed_form(torch_cuda, C, prec):
+    X, y = _mk(700, 7, C, 1)
+    s = _sps(X, y, C)
+    th = np.zeros((200, 7 * (C - 1)))
+    for t in (0, 1, 128, 700):
+        ll = s.loglik(th, t, prec)
+        np.testing.assert_allclose(ll, -t * math.log(C), rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+@pytest.mark.parametrize("C,k,exact", [(2, 5, 0), (2, 30, 10), (2, 70, 20), (3, 12, 4), (4, 50, 10), (4, 9, 0)])
+def test_parity_ragged_sizes(torch_cuda, C, k, exact, prec):
+    n = 1000                       # 7 full tiles of 128 (or 15 of 64) and a ragged tail
+    X, y = _mk(n, k, C, 10 + k, exact)
+    g = np.random.Generator(np.random.PCG64(77))
+    center = g.normal(0, 0.3, size=k * (C - 1))
+    theta = center[None, :] + 0.1 * g.standard_normal((300, k * (C - 1)))   # 2 full particle tiles + tail
+    s = _sps(X, y, C)
+    for t in (1, 127, 128, 129, 777, n):
+        ref = oracle_loglik(X, y, theta, C, t)
+        got = s.loglik(theta, t, prec)
+        tol = _tol(X, theta, C, t, ref, prec)
+        assert np.all(np.abs(got - ref) <= tol), (t, np.max(np.abs(got - ref) - tol))
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+@pytest.mark.parametrize("C", [2, 4])
+def test_parity_diffuse_prior_draws(torch_cuda, C, prec):
+    # prior draws N(0, 25 I): |eta| in the tens, where a naive exp would overflow
+    n, k = 400, 10
+    X, y = _mk(n, k, C, 3)
+    theta = synthetic.prior_draws(k * (C - 1), 256, 5.0, seed=4)
+    s = _sps(X, y, C)
+    ref = oracle_loglik(X, y, theta, C, n)
+    got = s.loglik(theta, n, prec)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= _tol(X, theta, C, n, ref, prec))
+
+
+def test_deterministic_and_device_path_bitwise(torch_cuda):
+    torch = torch_cuda
+    X, y = _mk(900, 20, 2, 5, 5)
+    theta = 0.2 * np.random.Generator(np.random.PCG64(1)).standard_normal((500, 20))
+    s = _sps(X, y, 2)
+    a = s.loglik(theta, 900)
+    b = s.loglik(theta, 900)
+    np.testing.assert_array_equal(a, b)
+    d = s.loglik(torch.from_numpy(theta).cuda(), 900)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy(), a)
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+def test_c2_full_size_sampled(torch_cuda, prec):
+    # the benchmark workload: binary logit n = 20000, k = 30, P = 65536 particles near beta
+    w = synthetic.make_c2()
+    theta = synthetic.particles_around(w.theta_true, w.P, 0.1, seed=1)
+    s = _sps(w.X, w.y, w.C)
+    got = s.loglik(theta, w.n, prec)
+    idx = np.random.Generator(np.random.PCG64(9)).choice(w.P, 48, replace=False)
+    idx = np.concatenate([idx, [0, 127, 128, w.P - 1]])
+    ref = oracle_loglik(w.X, w.y, theta[idx], w.C, w.n)
+    rtol = 1e-5 if prec == "split" else 1e-6
+    np.testing.assert_allclose(got[idx], ref, rtol=rtol)
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+def test_c3_multinomial_sampled(torch_cuda, prec):
+    w = synthetic.make_c3(n=12_000)
+    theta = synthetic.particles_around(w.theta_true, 4096, 0.05, seed=2)
+    s = _sps(w.X, w.y, w.C)
+    got = s.loglik(theta, w.n, prec)
+    idx = np.arange(0, 4096, 97)
+    ref = oracle_loglik(w.X, w.y, theta[idx], w.C, w.n)
+    rtol = 1e-5 if prec == "split" else 1e-6
+    np.testing.assert_allclose(got[idx], ref, rtol=rtol)

@@ -1,0 +1,316 @@
+"""Benchmark of the SPS logit hot path on one B300 (or N independent replicas under torchrun).
+
+Metric: particle-observation log-likelihood evaluations per second on the binary-logit workload
+c2 (n = 20 000 observations, k = 30 covariates, 16 groups x 4096 particles; synthetic data,
+seed 0). A step is one cycle of the simulator over one batch of new observations: the C phase
+over the next 64 observations (reweighting, ESS, log-ML increment), the S phase (resampling
+within each group and the gather), and one M step at the new prefix length (refresh of the
+cached log-likelihood with the M-phase kernel, particle covariance, FP64 Cholesky, Philox
+proposal, fused log-likelihood of the proposals, Metropolis accept, RNE of the monitoring
+functions). Units counted per step: P x 64 (C phase) + 2 P t (the refresh and the proposals).
+
+Between timed steps the L2 cache is flushed by writing a 512 MB buffer (X of c2 fits in L2);
+each step is timed with CUDA events on the library's stream and the flush is outside the
+timed events. `e2e` is the same metric through sps_loglik with pinned host buffers (theta in,
+log-likelihoods out, copies inside the timed region). The oracle (plain FP64 numpy) is timed on
+a bounded sample as the CPU baseline, and is the `--impl reference` arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle·obs loglik evals/s; SPS wall-s to log-ML NSE≤0.05 vs plain FP32"
+UNIT = "particle-obs evals/s"
+C_BLOCK = 64
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_throughput(w, seconds: float = 12.0, particles: int = 256):
+    """The oracle's log-likelihood (plain FP64 numpy) on a bounded sample of the workload."""
+    import synthetic
+    from oracle.logit import loglik
+    th = synthetic.particles_around(w.theta_true, particles, 0.05, seed=3)
+    loglik(w.X, w.y, th[:8], w.C, w.n)   # warm-up
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        loglik(w.X, w.y, th, w.C, w.n)
+        calls += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    units = calls * particles * w.n
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": units / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{calls} calls of loglik on {particles} particles x all {w.n} observations "
+                      f"({el:.1f} s, numpy FP64; BLAS threads for X theta', one thread elsewhere)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import synthetic
+    w = synthetic.make_c2()
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_throughput(w, seconds=2.0, particles=128)
+        if i >= args.warmup:
+            per_step.append(r)
+    value = statistics.median(r["value"] for r in per_step)
+    ms = 1e3 * (128 * w.n) / value
+    cpu = dict(per_step[-1])
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c2 binary logit n=20000 k=30 P=65536 (oracle: 128-particle sample per step)",
+                       "global_batch": 65536, "seq_len": w.n, "parallelism": "cpu"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    import synthetic
+    from paper_1304_4333_b300 import Sps
+    from paper_1304_4333_b300 import _native as N
+    import ctypes as C
+
+    torch.cuda.set_device(local)
+    w = synthetic.make_c2()
+    P, n = w.P, w.n
+    steps, warm = args.steps, args.warmup
+    s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=1 + rank, precision=args.precision)
+    stream = torch.cuda.Stream()
+    lib = s.lib
+    lib.sps_set_stream(s.ctx, C.c_void_p(stream.cuda_stream))
+    st = s.state(w.J, w.N, seed=100 + rank)
+    t0 = n - C_BLOCK * (warm + steps)
+    theta0 = synthetic.particles_around(w.theta_true, P, 0.05, seed=2)
+    st.set(theta0, None, t0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def counters(reset=0):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_double()
+        lib.sps_counters(s.ctx, reset, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
+    # warm-up steps
+    for _ in range(warm):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        st.cphase(st.get_t() + C_BLOCK)
+        st.sphase()
+        st.mstep()
+    torch.cuda.synchronize()
+    counters(reset=1)
+    lib.sps_set_timing(s.ctx, 1)
+    units = 0
+    hot_units = 0
+    ev_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t_new, _, _ = st.cphase(st.get_t() + C_BLOCK)
+            st.sphase()
+            st.mstep()
+            b.record(stream)
+            b.synchronize()
+            ev_ms.append(a.elapsed_time(b))
+            units += P * C_BLOCK + 2 * P * t_new
+            hot_units += 2 * P * t_new
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    launches, hot_launches, hot_ms = counters(reset=1)
+    lib.sps_set_timing(s.ctx, 0)
+    dev_s = max_over_ranks(sum(ev_ms) / 1e3, world)
+    total_units = units * world
+    value = total_units / dev_s
+    t_end = st.get_t()
+
+    # e2e: sps_loglik through the C ABI with pinned host buffers, copies inside the timed region
+    th_host = torch.from_numpy(synthetic.particles_around(w.theta_true, P, 0.05, seed=4)).pin_memory()
+    ll_host = torch.empty(P, dtype=torch.float64).pin_memory()
+    for _ in range(warm):
+        s.loglik_host_ptr(th_host.data_ptr(), ll_host.data_ptr(), P, n, args.precision)
+    e2e_t = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t1 = time.perf_counter()
+        s.loglik_host_ptr(th_host.data_ptr(), ll_host.data_ptr(), P, n, args.precision)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_s = max_over_ranks(sum(e2e_t), world)
+    e2e_value = world * steps * P * n / e2e_s
+
+    if rank != 0:
+        return
+    pk = peaks()
+    clock = clk.summary()
+    # roofline of the fused log-likelihood kernel: SFU-bound (one ex2 per particle-observation
+    # term for C = 2); peak = 148 SMs x 32 ex2/clk x max SM clock
+    sm_max = pk.get("sm_max_mhz", 2032.0)
+    sfu_peak = 148 * 32 * sm_max * 1e6 / 1e9        # Gop/s
+    hot_avg_ms = hot_ms / max(hot_launches, 1)
+    # algorithmic SFU work of the timed launches: one ex2 per particle-observation term (C = 2)
+    achieved = hot_units * (w.C - 1) / (hot_ms * 1e-3) / 1e9 if hot_ms > 0 else 0.0
+    tensor_ms = P * n * 2 * (w.C - 1) * (3 * 19 + 2 * 11) / (pk.get("bf16_tflops", 1778.4) * 1e12) * 1e3
+    sfu_ms = P * n * (w.C - 1) / (sfu_peak * 1e9) * 1e3
+    hbm_ms = n * 128 / (pk.get("hbm_gbs", 6496.8) * 1e9) * 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm,
+        "ms_per_step": 1e3 * dev_s / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x2-split/f32/f64" if args.precision == "split" else "f32/f64", "data": "synthetic",
+        "config": {"workload": "c2 binary logit n=20000 k=30 (intercept, 19 AR(1) N(0,1), 10 Bernoulli(0.3)), "
+                               "16 groups x 4096 particles, one SPS cycle per step (C phase 64 obs, S phase, M step)",
+                   "global_batch": P * world, "seq_len": n, "parallelism": f"replicas{world}",
+                   "precision": args.precision, "l2": "flushed between steps (512 MB write)"},
+        "wall_s": wall,
+        "gpu_launches": launches,
+        "clocks": clock,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P * w.D * 8, "d2h_bytes_per_step": P * 8,
+                "call": "sps_loglik(mem=HOST) on pinned buffers, full t = n"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Gop/s (ex2)",
+                     "frac": achieved / sfu_peak, "traffic": args.traffic,
+                     "kernel": "loglik_tc_kernel<1,128>", "launches_timed": hot_launches,
+                     "avg_launch_ms": hot_avg_ms,
+                     "bounds_ms_full_t": {"sfu": sfu_ms, "tensor_split": tensor_ms, "hbm": hbm_ms},
+                     "peak_source": "148 SMs x 32 ex2/clk/SM x sm_max_mhz of MEASURED_PEAKS (ex2 rate from a probe)"},
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = oracle_throughput(w)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="split", choices=["split", "fp32"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the fused kernel from an ncu capture")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,15 @@ const char* sps_last_error(const sps_ctx* ctx);
 /* Sizes of the context: n, k, C, D. Any pointer may be NULL. */
 sps_status sps_get_dims(const sps_ctx* ctx, int64_t* n, int32_t* k, int32_t* C, int32_t* D);
 
+/* Instrumentation (the paper has no counterpart). sps_set_timing(ctx, 1) records CUDA events on
+ * the context's stream around every launch of the fused log-likelihood kernel from then on.
+ * sps_counters synchronises the stream and reports, since the last reset: the number of kernels
+ * the library launched on ctx, the number of timed fused-kernel launches and their total device
+ * time in milliseconds (any output may be NULL); reset != 0 then clears the counts. */
+sps_status sps_set_timing(sps_ctx* ctx, int32_t on);
+sps_status sps_counters(sps_ctx* ctx, int32_t reset, int64_t* launches, int64_t* hot_launches,
+                        double* hot_ms);
+
 /* ------------------------------------------------------------------ the likelihood hot path */
 
 /* Log-likelihood of every particle over the first t observations (Eq. 1, product form of
@@ -176,7 +185,8 @@ sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, d
 
 /* Log-likelihood and its gradient d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s
  * (the derivative of Eq. 1; the paper prints no gradient).
- *   grad: [P x D] FP64 output, class-major like theta (mem). Split precision only. */
+ *   grad: [P x D] FP64 output, class-major like theta (mem). FP32 products and residuals,
+ *   FP64 sums across 32-observation tiles. */
 sps_status sps_loglik_grad(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
                            double* grad, int32_t mem);
 

@@ -62,6 +62,8 @@ SIGNATURES = {
     "sps_last_error": (C.c_char_p, [_P]),
     "sps_get_dims": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32)]),
+    "sps_set_timing": (C.c_int, [_P, C.c_int32]),
+    "sps_counters": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "sps_loglik": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, C.c_int32, C.c_int32]),
     "sps_loglik_grad": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P, C.c_int32]),
     "sps_state_create": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P)]),

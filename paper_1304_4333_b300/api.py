@@ -181,6 +181,13 @@ class Sps:
         self._call("sps_loglik", _ptr(th), th.shape[0], t, _ptr(out), prec, N.MEM_HOST)
         return out
 
+    def loglik_host_ptr(self, theta_ptr: int, ll_ptr: int, P: int, t: Optional[int] = None,
+                        precision: str = "split"):
+        """sps_loglik on caller-owned host buffers given by address (e.g. pinned torch tensors)."""
+        t = self.n if t is None else int(t)
+        self._call("sps_loglik", C.c_void_p(theta_ptr), int(P), t, C.c_void_p(ll_ptr), PRECISIONS[precision],
+                   N.MEM_HOST)
+
     def loglik_grad(self, theta, t: Optional[int] = None):
         t = self.n if t is None else int(t)
         if _is_device(theta):
@@ -309,6 +316,11 @@ class State:
         t = C.c_int64(); h = C.c_double()
         self.sps._call("sps_state_get", self.st, _ptr(th), _ptr(ll), _ptr(lw), C.byref(t), C.byref(h))
         return {"theta": th, "ll": ll, "logw": lw, "t": t.value, "h": h.value}
+
+    def get_t(self) -> int:
+        t = C.c_int64()
+        self.sps._call("sps_state_get", self.st, None, None, None, C.byref(t), None)
+        return t.value
 
     def set(self, theta, ll=None, t: int = 0):
         th = _f64(theta)

@@ -28,6 +28,14 @@ cudaError_t DevBuf::reserve(size_t nbytes) {
   return e;
 }
 
+}  // namespace sps
+
+sps_ctx::~sps_ctx() {
+  for (cudaEvent_t e : hot_events) cudaEventDestroy(e);
+}
+
+namespace sps {
+
 sps_status fail(sps_ctx* ctx, sps_status s, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
   return s;
@@ -158,10 +166,28 @@ sps_status ensure_lin(sps_ctx* ctx, int64_t t) {
   const int nk = ctx->NC * ctx->k;
   lin_tail_kernel<<<(nk + 127) / 128, 128, 0, ctx->stream>>>(ctx->lin_prefix.as<double>(), ctx->Xd.as<double>(),
                                                             ctx->y.as<int>(), ctx->k, ctx->NC, t,
-                                                            ctx->lin.as<double>());
+                                                            ctx->lin.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   ctx->lin_t = t;
   return SPS_OK;
+}
+
+void hot_begin(sps_ctx* ctx) {
+  if (!ctx->timing) return;
+  if (ctx->hot_used + 2 > ctx->hot_events.size()) {
+    for (int q = 0; q < 2; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      ctx->hot_events.push_back(e);
+    }
+  }
+  cudaEventRecord(ctx->hot_events[ctx->hot_used], ctx->stream);
+}
+
+void hot_end(sps_ctx* ctx) {
+  if (!ctx->timing || ctx->hot_used + 2 > ctx->hot_events.size()) return;
+  cudaEventRecord(ctx->hot_events[ctx->hot_used + 1], ctx->stream);
+  ctx->hot_used += 2;
 }
 
 sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
@@ -232,6 +258,31 @@ void sps_destroy(sps_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   delete ctx;
+}
+
+sps_status sps_set_timing(sps_ctx* ctx, int32_t on) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  ctx->timing = (on != 0);
+  return SPS_OK;
+}
+
+sps_status sps_counters(sps_ctx* ctx, int32_t reset, int64_t* launches, int64_t* hot_launches, double* hot_ms) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  double ms = 0.0;
+  for (size_t q = 0; q + 1 < ctx->hot_used; q += 2) {
+    float e = 0.f;
+    SPS_CUDA_TRY(cudaEventElapsedTime(&e, ctx->hot_events[q], ctx->hot_events[q + 1]));
+    ms += e;
+  }
+  if (launches) *launches = ctx->launches;
+  if (hot_launches) *hot_launches = static_cast<int64_t>(ctx->hot_used / 2);
+  if (hot_ms) *hot_ms = ms;
+  if (reset) {
+    ctx->launches = 0;
+    ctx->hot_used = 0;
+  }
+  return SPS_OK;
 }
 
 sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const int32_t* y,
@@ -332,7 +383,7 @@ sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const 
     cudaMemset(flags.ptr, 0, (k + 1) * sizeof(int));
     const int64_t tot = n * k;
     nonexact_columns_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256>>>(
-        ctx->Xd.as<double>(), n, k, flags.as<int>(), flags.as<int>() + k);
+        ctx->Xd.as<double>(), n, k, flags.as<int>(), flags.as<int>() + k); ++ctx->launches;
     std::vector<int> h(k + 1);
     if (cudaMemcpy(h.data(), flags.ptr, (k + 1) * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
       return bail(SPS_ERR_CUDA);
@@ -359,7 +410,7 @@ sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const 
     const int64_t tot2 = n * enc.kpad;
     encode_x_kernel<<<static_cast<unsigned>((tot2 + 255) / 256), 256>>>(
         ctx->Xd.as<double>(), n, k, enc.perm_dev.as<int>(), enc.kpad, enc.kc, enc.kcpad,
-        enc.Xh.as<__nv_bfloat16>(), enc.Xl.as<__nv_bfloat16>(), ctx->Xf.as<float>());
+        enc.Xh.as<__nv_bfloat16>(), enc.Xl.as<__nv_bfloat16>(), ctx->Xf.as<float>()); ++ctx->launches;
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(SPS_ERR_CUDA);
     if ((st = make_map_bf16(ctx, &enc.mapXh, enc.Xh.ptr, n, enc.kpad, enc.bn)) != SPS_OK) return bail(st);
     if (enc.kcpad > 0 && (st = make_map_bf16(ctx, &enc.mapXl, enc.Xl.ptr, n, enc.kcpad, enc.bn)) != SPS_OK)
@@ -421,3 +472,22 @@ sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, d
 }
 
 }  // extern "C"
+
+extern "C" sps_status sps_loglik_grad(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
+                                      double* grad, int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!theta || !ll || !grad || P < 1 || t < 0 || t > ctx->n || P > (1LL << 28))
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik_grad: bad arguments");
+  if (mem == SPS_MEM_DEVICE) return loglik_grad_fp32(ctx, theta, P, t, ll, grad);
+  LoglikScratch& S = ctx->ll;
+  const size_t tb = static_cast<size_t>(P) * ctx->D * sizeof(double);
+  SPS_CUDA_TRY(S.theta_in.reserve(tb));
+  SPS_CUDA_TRY(S.ll_out.reserve(P * sizeof(double)));
+  SPS_CUDA_TRY(S.grad_out.reserve(tb));
+  SPS_CUDA_TRY(cudaMemcpyAsync(S.theta_in.ptr, theta, tb, cudaMemcpyHostToDevice, ctx->stream));
+  SPS_TRY(loglik_grad_fp32(ctx, S.theta_in.as<double>(), P, t, S.ll_out.as<double>(), S.grad_out.as<double>()));
+  SPS_CUDA_TRY(cudaMemcpyAsync(ll, S.ll_out.ptr, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(grad, S.grad_out.ptr, tb, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return check_finite_ll(ctx, ll, P);
+}

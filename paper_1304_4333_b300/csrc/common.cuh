@@ -100,6 +100,14 @@ struct sps_ctx {
   sps::DevBuf d_prior_chol;   // FP64 [D x D] lower Cholesky factor of cov
 
   sps::LoglikScratch ll;
+
+  // instrumentation: kernels launched on this context; CUDA events around each launch of the
+  // fused log-likelihood kernel when timing is on
+  int64_t launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> hot_events;   // pairs (start, stop)
+  size_t hot_used = 0;                   // events in use (2 per recorded launch)
+  ~sps_ctx();
 };
 
 struct sps_state {
@@ -110,6 +118,7 @@ struct sps_state {
   int64_t t = 0;
   double h = 0.5;
   bool have_weights = false;      // a C phase has run since the last S phase
+  bool ll_stale = false;          // ll holds C-phase sums: recompute with the M-phase kernel
   uint64_t step_counter = 0;      // Philox counter word for per-step streams
   uint64_t cycle_counter = 0;
   sps::DevBuf theta, theta_prop;  // FP64 [P x D]
@@ -148,9 +157,15 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
 sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                            int precision);
 sps_status ensure_lin(sps_ctx* ctx, int64_t t);
+// Start/stop event of one timed launch of the fused kernel (no-ops when timing is off).
+void hot_begin(sps_ctx* ctx);
+void hot_end(sps_ctx* ctx);
 // C-phase running log weights for observations [s_lo, s_hi): d_lw[j*P + p] (FP64).
 sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
                              int64_t s_hi, const double* d_logw_in, double* d_lw);
+// Log-likelihood and gradient (FP32 products, FP64 sums across 32-observation tiles).
+sps_status loglik_grad_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
+                            double* d_grad);
 
 }  // namespace sps
 

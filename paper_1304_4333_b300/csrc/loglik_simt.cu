@@ -123,10 +123,10 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
                                     static_cast<int>(smem)));
   dim3 grid(static_cast<unsigned>(ptiles), static_cast<unsigned>(chunks));
   fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
-                                                     ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr);
+                                                     ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   sum_slices_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
-      partial, P, t > 0 ? static_cast<int>(chunks) : 0, d_ll);
+      partial, P, t > 0 ? static_cast<int>(chunks) : 0, d_ll); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
 }
@@ -142,7 +142,138 @@ sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int
   dim3 grid(static_cast<unsigned>(ptiles), 1);
   fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
                                                      ctx->y.as<int>(), s_lo, s_hi, s_hi - s_lo, 1, d_lw,
-                                                     d_logw_in);
+                                                     d_logw_in); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
+}  // namespace sps
+
+// ------------------------------------------------------------------------------------------
+// Gradient of the log-likelihood, d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s (the
+// derivative of Eq. 1 summed over observations). One thread per particle, 64 particles per
+// block; residual-times-covariate products accumulate in FP32 over a 32-observation tile (in
+// shared memory, [D][64]) and are added to FP64 accumulators once per tile.
+
+namespace sps {
+namespace {
+
+constexpr int kGP = 64;
+
+__global__ void __launch_bounds__(kGP)
+grad_fp32_kernel(const double* __restrict__ theta, int64_t P, int k, int NC, const float* __restrict__ X,
+                 const int* __restrict__ y, int64_t t, int64_t chunk, double* __restrict__ llp,
+                 double* __restrict__ gp) {
+  extern __shared__ double smd[];
+  const int D = k * NC;
+  double* g64 = smd;                                   // [D][64]
+  float* th = reinterpret_cast<float*>(g64 + D * kGP); // [D][64]
+  float* g32 = th + D * kGP;                           // [D][64]
+  float* xs = g32 + D * kGP;                           // [kTS][k]
+  int* ys = reinterpret_cast<int*>(xs + kTS * k);      // [kTS]
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kGP;
+  const int64_t p = p0 + threadIdx.x;
+  const int64_t s_lo = static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t s_hi = (s_lo + chunk < t) ? s_lo + chunk : t;
+  for (int idx = threadIdx.x; idx < D * kGP; idx += blockDim.x) {
+    const int pp = idx / D, d = idx - pp * D;
+    th[d * kGP + pp] = (p0 + pp < P) ? static_cast<float>(theta[(p0 + pp) * D + d]) : 0.f;
+  }
+  for (int d = 0; d < D; ++d) {
+    g64[d * kGP + threadIdx.x] = 0.0;
+    g32[d * kGP + threadIdx.x] = 0.f;
+  }
+  double acc = 0.0;
+  float eta[kMaxNC], pr[kMaxNC];
+  for (int64_t s0 = s_lo; s0 < s_hi; s0 += kTS) {
+    const int ns = static_cast<int>(s_hi - s0 < kTS ? s_hi - s0 : kTS);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ns * k; idx += blockDim.x) xs[idx] = X[s0 * k + idx];
+    for (int idx = threadIdx.x; idx < ns; idx += blockDim.x) ys[idx] = y[s0 + idx];
+    __syncthreads();
+    float tile = 0.f;
+    for (int j = 0; j < ns; ++j) {
+      const float* xr = xs + j * k;
+      float m = 0.f;
+      for (int c = 0; c < NC; ++c) {
+        const float* tc = th + (c * k) * kGP + threadIdx.x;
+        float e = 0.f;
+        for (int i = 0; i < k; ++i) e = fmaf(tc[i * kGP], xr[i], e);
+        eta[c] = e;
+        m = fmaxf(m, e);
+      }
+      float z = expf(-m);
+      for (int c = 0; c < NC; ++c) {
+        pr[c] = expf(eta[c] - m);
+        z += pr[c];
+      }
+      const float inv = 1.f / z;
+      const int yo = ys[j];
+      tile += ((yo == 0) ? 0.f : eta[yo - 1]) - (m + logf(z));
+      for (int c = 0; c < NC; ++c) {
+        const float r = ((yo == c + 1) ? 1.f : 0.f) - pr[c] * inv;
+        float* gc = g32 + (c * k) * kGP + threadIdx.x;
+        for (int i = 0; i < k; ++i) gc[i * kGP] = fmaf(r, xr[i], gc[i * kGP]);
+      }
+    }
+    acc += static_cast<double>(tile);
+    for (int d = 0; d < D; ++d) {
+      g64[d * kGP + threadIdx.x] += static_cast<double>(g32[d * kGP + threadIdx.x]);
+      g32[d * kGP + threadIdx.x] = 0.f;
+    }
+  }
+  if (p < P) {
+    llp[static_cast<int64_t>(blockIdx.y) * P + p] = acc;
+    double* go = gp + (static_cast<int64_t>(blockIdx.y) * P + p) * D;
+    for (int d = 0; d < D; ++d) go[d] = g64[d * kGP + threadIdx.x];
+  }
+}
+
+__global__ void grad_sum_kernel(const double* __restrict__ llp, const double* __restrict__ gp, int64_t P, int D,
+                                int slices, double* __restrict__ ll, double* __restrict__ grad) {
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (idx >= P * (D + 1)) return;
+  if (idx < P) {
+    double s = 0.0;
+    for (int q = 0; q < slices; ++q) s += llp[q * P + idx];
+    ll[idx] = s;
+  } else {
+    const int64_t e = idx - P;   // p * D + d
+    double s = 0.0;
+    for (int q = 0; q < slices; ++q) s += gp[q * P * D + e];
+    grad[e] = s;
+  }
+}
+
+}  // namespace
+
+sps_status loglik_grad_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
+                            double* d_grad) {
+  const int D = ctx->D, k = ctx->k;
+  if (ctx->NC > kMaxNC) return fail(ctx, SPS_ERR_UNSUPPORTED, "gradient: at most 16 outcomes");
+  const size_t smem = sizeof(double) * D * kGP + sizeof(float) * (2 * static_cast<size_t>(D) * kGP + kTS * k) +
+                      sizeof(int) * kTS;
+  if (smem > 220 * 1024) return fail(ctx, SPS_ERR_UNSUPPORTED, "gradient: k*(C-1) too large");
+  const int64_t ptiles = (P + kGP - 1) / kGP;
+  int64_t chunks = 1;
+  if (t > 0) {
+    const int64_t want = 4LL * ctx->num_sms;
+    const int64_t cap = std::max<int64_t>(1, (int64_t{1} << 26) / (P * (D + 1)));
+    chunks = std::max<int64_t>(1, std::min<int64_t>({(want + ptiles - 1) / ptiles, (t + kTS - 1) / kTS, cap}));
+  }
+  int64_t chunk = std::max<int64_t>(kTS, ((t + chunks - 1) / chunks + kTS - 1) / kTS * kTS);
+  chunks = std::max<int64_t>(1, (t + chunk - 1) / chunk);
+  SPS_CUDA_TRY(ctx->ll.partial.reserve(sizeof(double) * chunks * P));
+  SPS_CUDA_TRY(ctx->ll.aux.reserve(sizeof(double) * chunks * P * D));
+  SPS_CUDA_TRY(cudaFuncSetAttribute(grad_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  dim3 grid(static_cast<unsigned>(ptiles), static_cast<unsigned>(chunks));
+  grad_fp32_kernel<<<grid, kGP, smem, ctx->stream>>>(d_theta, P, k, ctx->NC, ctx->Xf.as<float>(), ctx->y.as<int>(),
+                                                     t, chunk, ctx->ll.partial.as<double>(), ctx->ll.aux.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  const int64_t tot = P * (D + 1);
+  grad_sum_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, ctx->stream>>>(
+      ctx->ll.partial.as<double>(), ctx->ll.aux.as<double>(), P, D, t > 0 ? static_cast<int>(chunks) : 0, d_ll, d_grad); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
 }

@@ -408,7 +408,9 @@ sps_status launch_tc(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
   const XEncoding& enc = ctx->enc;
   const CUtensorMap& mxl = enc.kcpad > 0 ? enc.mapXl : enc.mapXh;
-  kern<<<grid, kThreads, smem_bytes, ctx->stream>>>(enc.mapXh, mxl, ctx->ll.mapTH, ctx->ll.mapTL, prm);
+  hot_begin(ctx);
+  kern<<<grid, kThreads, smem_bytes, ctx->stream>>>(enc.mapXh, mxl, ctx->ll.mapTH, ctx->ll.mapTL, prm); ++ctx->launches;
+  hot_end(ctx);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("loglik_tc launch: ") + cudaGetErrorString(e));
   return SPS_OK;
@@ -438,7 +440,7 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
     const int threads = 256;
     encode_theta_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, ctx->stream>>>(
         d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.kpad, ppad, S.thetaH.as<__nv_bfloat16>(),
-        S.thetaL.as<__nv_bfloat16>());
+        S.thetaL.as<__nv_bfloat16>()); ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
   }
   SPS_TRY(ensure_lin(ctx, t));
@@ -499,7 +501,7 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
     const int threads = 256;
     loglik_finalize_kernel<<<static_cast<unsigned>((P + threads - 1) / threads), threads, 0, ctx->stream>>>(
         d_theta, P, ctx->D, ctx->lin.as<double>(), prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0,
-        ppad, d_ll);
+        ppad, d_ll); ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
   }
   return SPS_OK;

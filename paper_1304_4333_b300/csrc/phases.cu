@@ -1,20 +1,1271 @@
-// Simulator phases (temporary: entry points not yet implemented return SPS_ERR_UNSUPPORTED).
+// Simulator phases of the SPS library (Algorithms 1-3 of Sec. 2): particle state, the C phase
+// with the ESS rule (Eq. 14), the S phase (multinomial resampling within groups), the M phase
+// (random-walk Metropolis with Sigma = h V, Algorithm 2 step 2), group moments, NSE and RNE
+// (Eqs. 3-10), and the sps_run driver.
+//
+// Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by the state's seed, with
+// counter (index, stream, step_lo, step_hi): every draw is a pure function of its position, so
+// runs are reproducible and independent of launch configuration.
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "common.cuh"
 
-extern "C" {
-sps_status sps_loglik_grad(sps_ctx*, const double*, int64_t, int64_t, double*, double*, int32_t) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_state_create(sps_ctx*, int32_t, int32_t, uint64_t, sps_state** out) { if (out) *out = nullptr; return SPS_ERR_UNSUPPORTED; }
-void sps_state_destroy(sps_state* st) { delete st; }
-sps_status sps_state_get(sps_ctx*, const sps_state*, double*, double*, double*, int64_t*, double*) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_state_set(sps_ctx*, sps_state*, const double*, const double*, int64_t) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_cphase(sps_ctx*, sps_state*, int64_t, int64_t*, double*, double*) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_sphase(sps_ctx*, sps_state*, const double*, int32_t*, int32_t) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_mstep(sps_ctx*, sps_state*, int32_t, const double*, double*, sps_mstep_info*) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_mphase(sps_ctx*, sps_state*, int32_t, int32_t, int32_t*, double*, double*) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_run(sps_ctx*, int32_t, int32_t, const sps_schedule*, sps_schedule*, sps_result*) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_resample(sps_ctx*, const double*, const double*, int32_t, int32_t, int32_t*, int32_t) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_philox(sps_ctx*, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, int64_t, uint32_t*, int32_t) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_ess(sps_ctx*, const double*, int64_t, int32_t, double*, double*, int32_t) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_particle_cov(sps_ctx*, const double*, int64_t, double*, int32_t) { return SPS_ERR_UNSUPPORTED; }
-sps_status sps_rw_step_given(sps_ctx*, double*, double*, int64_t, int64_t, const double*, const double*, const double*, int32_t, double*, int32_t*, int32_t) { return SPS_ERR_UNSUPPORTED; }
+namespace sps {
+namespace {
+
+// ------------------------------------------------------------------------------ Philox
+
+constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+
+enum Stream : uint32_t { kStreamInit = 1, kStreamPropose = 2, kStreamAccept = 3, kStreamResample = 4 };
+
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kWeyl0;
+      k1 += kWeyl1;
+    }
+    const uint32_t hi0 = __umulhi(kMul0, c.x), lo0 = kMul0 * c.x;
+    const uint32_t hi1 = __umulhi(kMul1, c.z), lo1 = kMul1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
 }
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t idx, uint32_t stream, uint64_t step) {
+  return philox(make_uint4(idx, stream, static_cast<uint32_t>(step), static_cast<uint32_t>(step >> 32)),
+                static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+}
+
+// FP64 uniform on [0, 1): the top 53 bits of (hi:lo) times 2^-53.
+__device__ __forceinline__ double uniform53(uint32_t lo, uint32_t hi) {
+  const uint64_t b = ((static_cast<uint64_t>(hi) << 32) | lo) >> 11;
+  return static_cast<double>(b) * 0x1.0p-53;
+}
+
+// Two FP32 standard normals by the Box-Muller transform of two 24-bit uniforms.
+__device__ __forceinline__ float2 normals2(uint32_t a, uint32_t b) {
+  const float u1 = (static_cast<float>(a >> 8) + 1.0f) * 0x1.0p-24f;   // (0, 1]
+  const float u2 = static_cast<float>(b >> 8) * 0x1.0p-24f;            // [0, 1)
+  const float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+__global__ void philox_kernel(uint32_t k0, uint32_t k1, uint4 ctr, int64_t count, uint4* out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= count) return;
+  uint4 c = ctr;
+  c.x += static_cast<uint32_t>(i);
+  out[i] = philox(c, k0, k1);
+}
+
+// ------------------------------------------------------------------------------ reductions
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum / max (blockDim a multiple of 32, <= 1024); result valid in every thread.
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) {
+    t = warp_sum(t);
+    if (l == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+__device__ double block_max(double v, double* sh) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? sh[threadIdx.x] : -INFINITY;
+  if (w == 0) {
+    t = warp_max(t);
+    if (l == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// ------------------------------------------------------------------------------ prior
+
+// Prior log kernel -(1/2) (theta - mu)' Prec (theta - mu); prec is diagonal [D] unless full.
+__device__ double prior_log_kernel(const double* th, const double* mu, const double* prec, int D, bool full) {
+  double a = 0.0;
+  if (!full) {
+    for (int i = 0; i < D; ++i) {
+      const double d = th[i] - mu[i];
+      a = fma(d * d, prec[i], a);
+    }
+  } else {
+    for (int i = 0; i < D; ++i) {
+      const double di = th[i] - mu[i];
+      double r = 0.0;
+      for (int j = 0; j < D; ++j) r = fma(prec[i * D + j], th[j] - mu[j], r);
+      a = fma(di, r, a);
+    }
+  }
+  return -0.5 * a;
+}
+
+// Algorithm 1 step 1: theta_p = mu + L0 z, z iid N(0, 1) (FP64 Box-Muller from Philox).
+__global__ void prior_init_kernel(uint64_t seed, int64_t P, int D, const double* __restrict__ mu,
+                                  const double* __restrict__ L0, const double* __restrict__ prec, bool full,
+                                  double* __restrict__ theta, double* __restrict__ lp, double* __restrict__ zbuf) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= P) return;
+  double* z = zbuf + p * D;
+  for (int d = 0; d < D; d += 2) {
+    const uint4 r = draw(seed, static_cast<uint32_t>(p * ((D + 1) / 2) + d / 2), kStreamInit, 0);
+    const double u1 = 1.0 - uniform53(r.x, r.y);   // (0, 1]
+    const double u2 = uniform53(r.z, r.w);
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z[d] = rad * c;
+    if (d + 1 < D) z[d + 1] = rad * s;
+  }
+  double* th = theta + p * D;
+  for (int i = 0; i < D; ++i) {
+    double a = mu[i];
+    if (full) {
+      for (int j = 0; j <= i; ++j) a = fma(L0[i * D + j], z[j], a);
+    } else {
+      a = fma(L0[i * D + i], z[i], a);
+    }
+    th[i] = a;
+  }
+  lp[p] = prior_log_kernel(th, mu, prec, D, full);
+}
+
+__global__ void prior_lp_kernel(const double* __restrict__ theta, int64_t P, int D, const double* __restrict__ mu,
+                                const double* __restrict__ prec, bool full, double* __restrict__ lp) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= P) return;
+  lp[p] = prior_log_kernel(theta + p * D, mu, prec, D, full);
+}
+
+// ------------------------------------------------------------------------------ C phase
+
+// ESS(s) of one row of running log weights per block (Eq. 14), with exp of the FP64 difference
+// to the row maximum in FP32 and FP64 sums.
+__global__ void ess_rows_kernel(const double* __restrict__ lw, int64_t P, double* __restrict__ ess) {
+  __shared__ double sh[33];
+  const double* row = lw + static_cast<int64_t>(blockIdx.x) * P;
+  double m = -INFINITY;
+  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) m = fmax(m, row[p]);
+  m = block_max(m, sh);
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) {
+    const double w = static_cast<double>(expf(static_cast<float>(row[p] - m)));
+    s1 += w;
+    s2 += w * w;
+  }
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) ess[blockIdx.x] = (s2 > 0.0) ? s1 * s1 / s2 : 0.0;
+}
+
+// Per-group log N^-1 sum_n exp(logw_jn) in FP64 (one block per group).
+__global__ void group_lme_kernel(const double* __restrict__ logw, int N, double* __restrict__ lme,
+                                 double* __restrict__ logml) {
+  __shared__ double sh[33];
+  const double* row = logw + static_cast<int64_t>(blockIdx.x) * N;
+  double m = -INFINITY;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) m = fmax(m, row[n]);
+  m = block_max(m, sh);
+  double s = 0.0;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) s += exp(row[n] - m);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    const double v = m + log(s / static_cast<double>(N));
+    lme[blockIdx.x] = v;
+    if (logml) logml[blockIdx.x] += v;
+  }
+}
+
+__global__ void add_kernel(double* __restrict__ a, const double* __restrict__ b, int64_t n) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) a[i] += b[i];
+}
+
+// ------------------------------------------------------------------------------ S phase
+
+constexpr int kMaxN = 4096;
+constexpr int kResThreads = 1024;
+
+// Multinomial resampling of one group per block by an integer CDF (S phase, Algorithm 1):
+// q_n = floor(w_n 2^40) with w_n = exp(logw_n - max) (mode 0) or the given w_n (mode 1),
+// c = inclusive uint64 prefix sums, tau_i = min(floor(u_i Q), Q - 1), idx_i = first n with c_n > tau.
+__global__ void __launch_bounds__(kResThreads)
+resample_kernel(const double* __restrict__ src, int mode, int N, const double* __restrict__ u_given,
+                uint64_t seed, uint64_t step, int* __restrict__ idx, int* __restrict__ flag) {
+  __shared__ unsigned long long c[kMaxN];
+  __shared__ unsigned long long part[kResThreads];
+  __shared__ double sh[33];
+  const int j = blockIdx.x;
+  const double* row = src + static_cast<int64_t>(j) * N;
+  double m = 0.0;
+  if (mode == 0) {
+    m = -INFINITY;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) m = fmax(m, row[n]);
+    m = block_max(m, sh);
+  }
+  // each thread owns a contiguous run of ceil(N / threads) elements
+  const int per = (N + blockDim.x - 1) / blockDim.x;
+  const int n0 = threadIdx.x * per;
+  unsigned long long run = 0;
+  for (int q = 0; q < per; ++q) {
+    const int n = n0 + q;
+    if (n < N) {
+      const double w = (mode == 0) ? exp(row[n] - m) : row[n];
+      const unsigned long long qn = static_cast<unsigned long long>(floor(ldexp(w, 40)));
+      run += qn;
+      c[n] = run;
+    }
+  }
+  part[threadIdx.x] = run;
+  __syncthreads();
+  // inclusive scan of the per-thread totals (Hillis-Steele over <= 1024 values)
+  for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {
+    const unsigned long long v = (threadIdx.x >= static_cast<unsigned>(o)) ? part[threadIdx.x - o] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const unsigned long long off = (threadIdx.x > 0) ? part[threadIdx.x - 1] : 0ull;
+  for (int q = 0; q < per; ++q) {
+    const int n = n0 + q;
+    if (n < N) c[n] += off;
+  }
+  __syncthreads();
+  const unsigned long long Q = c[N - 1];
+  if (Q == 0ull) {
+    if (threadIdx.x == 0) atomicOr(flag, 1);
+    return;
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double u;
+    if (u_given) {
+      u = u_given[static_cast<int64_t>(j) * N + i];
+    } else {
+      const uint4 r = draw(seed, static_cast<uint32_t>(j * N + i), kStreamResample, step);
+      u = uniform53(r.x, r.y);
+    }
+    unsigned long long tau = static_cast<unsigned long long>(floor(__dmul_rn(u, static_cast<double>(Q))));
+    if (tau > Q - 1) tau = Q - 1;
+    int lo = 0, hi = N - 1;   // first n with c[n] > tau; c[N-1] = Q > tau
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (c[mid] > tau) hi = mid;
+      else lo = mid + 1;
+    }
+    idx[static_cast<int64_t>(j) * N + i] = lo;
+  }
+}
+
+// dst[p] = src[group(p) * N + idx[p]] for theta rows and the per-particle scalars.
+__global__ void gather_kernel(const double* __restrict__ th, const double* __restrict__ ll,
+                              const double* __restrict__ lp, const int* __restrict__ idx, int64_t P, int N, int D,
+                              double* __restrict__ th_o, double* __restrict__ ll_o, double* __restrict__ lp_o) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= P) return;
+  const int64_t src = (p / N) * N + idx[p];
+  for (int d = 0; d < D; ++d) th_o[p * D + d] = th[src * D + d];
+  ll_o[p] = ll[src];
+  lp_o[p] = lp[src];
+}
+
+// ------------------------------------------------------------------------------ M phase
+
+constexpr int kMaxD = 155;   // covariance kernel: <= 48 lower-triangle entries per thread
+
+// Column means of theta [P x D] in FP64 (one block per group of 32 columns).
+__global__ void col_mean_kernel(const double* __restrict__ th, int64_t P, int D, double* __restrict__ mean) {
+  __shared__ double sh[8][33];
+  const int d = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int r = threadIdx.x >> 5;   // 8 row groups
+  double s = 0.0;
+  if (d < D)
+    for (int64_t p = r; p < P; p += 8) s += th[p * D + d];
+  sh[r][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (r == 0 && d < D) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x & 31];
+    mean[d] = t / static_cast<double>(P);
+  }
+}
+
+constexpr int kCovSub = 64;        // particles staged per shared-memory pass
+constexpr int kCovThreads = 256;
+constexpr int kCovMaxEnt = 48;     // lower-triangle entries per thread (D <= 155)
+
+// Centred cross products: block b sums over its particle range in FP32 (products of FP32
+// centred values), writes the lower triangle as FP64 partials [blocks][T].
+__global__ void __launch_bounds__(kCovThreads)
+cov_partial_kernel(const double* __restrict__ th, int64_t P, int D, const double* __restrict__ mean,
+                   int64_t per_block, double* __restrict__ partial) {
+  extern __shared__ float cs[];   // [kCovSub][D]
+  const int T = D * (D + 1) / 2;
+  const int64_t p_lo = blockIdx.x * per_block;
+  const int64_t p_hi = min(P, p_lo + per_block);
+  float acc[kCovMaxEnt];
+  int ei[kCovMaxEnt], ej[kCovMaxEnt];
+  int ne = 0;
+  for (int e = threadIdx.x; e < T && ne < kCovMaxEnt; e += blockDim.x, ++ne) {
+    // e -> (i, j), i >= j, row-major lower triangle
+    int i = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > e) --i;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    ei[ne] = i;
+    ej[ne] = e - i * (i + 1) / 2;
+    acc[ne] = 0.f;
+  }
+  for (int64_t p0 = p_lo; p0 < p_hi; p0 += kCovSub) {
+    const int np = static_cast<int>(p_hi - p0 < kCovSub ? p_hi - p0 : kCovSub);
+    __syncthreads();
+    for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
+      const int pp = q / D, d = q - pp * D;
+      cs[pp * D + d] = static_cast<float>(th[(p0 + pp) * D + d] - mean[d]);
+    }
+    __syncthreads();
+    for (int q = 0; q < ne; ++q) {
+      float a = 0.f;
+      for (int pp = 0; pp < np; ++pp) a = fmaf(cs[pp * D + ei[q]], cs[pp * D + ej[q]], a);
+      acc[q] += a;
+    }
+  }
+  for (int q = 0; q < ne; ++q) partial[static_cast<int64_t>(blockIdx.x) * T + threadIdx.x + q * blockDim.x] = acc[q];
+}
+
+// V = sum over blocks (fixed order) / (P - 1), full symmetric [D x D]; Sigma = scale V.
+__global__ void cov_final_kernel(const double* __restrict__ partial, int blocks, int D, int64_t P, double scale,
+                                 double* __restrict__ V, double* __restrict__ Sigma) {
+  const int T = D * (D + 1) / 2;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= T) return;
+  int i = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > e) --i;
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  const int j = e - i * (i + 1) / 2;
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += partial[static_cast<int64_t>(b) * T + e];
+  const double v = s / static_cast<double>(P - 1);
+  if (V) {
+    V[i * D + j] = v;
+    V[j * D + i] = v;
+  }
+  if (Sigma) {
+    Sigma[i * D + j] = scale * v;
+    Sigma[j * D + i] = scale * v;
+  }
+}
+
+// Lower Cholesky factor of A [D x D] (FP64, one block, right-looking on the packed lower
+// triangle in shared memory). On failure (non-positive or non-finite pivot) sets *flag.
+// Writes L in FP64 (full, zero upper part) and the packed lower triangle in FP32.
+__global__ void cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
+                                float* __restrict__ L32, int* __restrict__ flag) {
+  extern __shared__ double a[];   // packed lower triangle, row-major
+  __shared__ int bad;
+  const int T = D * (D + 1) / 2;
+  for (int e = threadIdx.x; e < T; e += blockDim.x) {
+    int i = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > e) --i;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    a[e] = A[i * D + (e - i * (i + 1) / 2)];
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < D; ++j) {
+    if (threadIdx.x == 0) {
+      const double piv = a[j * (j + 1) / 2 + j];
+      if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
+      else a[j * (j + 1) / 2 + j] = sqrt(piv);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double djj = a[j * (j + 1) / 2 + j];
+    for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) a[i * (i + 1) / 2 + j] /= djj;
+    __syncthreads();
+    // trailing update: a[i][k] -= l[i][j] l[k][j] for j < k <= i
+    const int m = D - j - 1;
+    const int Tm = m * (m + 1) / 2;
+    for (int e = threadIdx.x; e < Tm; e += blockDim.x) {
+      int ii = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while (ii * (ii + 1) / 2 > e) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      const int kk = e - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      a[i * (i + 1) / 2 + k] -= a[i * (i + 1) / 2 + j] * a[k * (k + 1) / 2 + j];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(flag, 1);
+    return;
+  }
+  for (int q = threadIdx.x; q < D * D; q += blockDim.x) {
+    const int i = q / D, k = q - i * D;
+    L[q] = (k <= i) ? a[i * (i + 1) / 2 + k] : 0.0;
+  }
+  for (int e = threadIdx.x; e < T; e += blockDim.x) L32[e] = static_cast<float>(a[e]);
+}
+
+constexpr int kPropThreads = 128;
+
+// theta' = theta + L z (L packed lower triangle FP32; z FP32 normals from Philox, or given FP64),
+// plus the prior log kernel of theta'. Skipped when the factorisation failed.
+__global__ void __launch_bounds__(kPropThreads)
+propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __restrict__ L32,
+               const double* __restrict__ z_given, uint64_t seed, uint64_t step, const double* __restrict__ mu,
+               const double* __restrict__ prec, bool full, const int* __restrict__ flag,
+               double* __restrict__ th_o, double* __restrict__ lp_o) {
+  if (*flag) return;
+  extern __shared__ float ps[];
+  const int T = D * (D + 1) / 2;
+  float* Ls = ps;                              // [T]
+  float* zs = ps + ((T + 3) & ~3);             // [D][128]
+  for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
+  const int64_t p = blockIdx.x * static_cast<int64_t>(kPropThreads) + threadIdx.x;
+  const bool live = p < P;
+  if (live) {
+    if (z_given) {
+      for (int d = 0; d < D; ++d) zs[d * kPropThreads + threadIdx.x] = static_cast<float>(z_given[p * D + d]);
+    } else {
+      const int per = (D + 3) / 4;
+      for (int q = 0; q < per; ++q) {
+        const uint4 r = draw(seed, static_cast<uint32_t>(p * per + q), kStreamPropose, step);
+        const float2 a = normals2(r.x, r.y), b = normals2(r.z, r.w);
+        const float v[4] = {a.x, a.y, b.x, b.y};
+        for (int u = 0; u < 4; ++u)
+          if (4 * q + u < D) zs[(4 * q + u) * kPropThreads + threadIdx.x] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  const double* t = th + p * D;
+  double* o = th_o + p * D;
+  for (int i = 0; i < D; ++i) {
+    const float* Li = Ls + i * (i + 1) / 2;
+    float dlt = 0.f;
+    for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], zs[j * kPropThreads + threadIdx.x], dlt);
+    o[i] = t[i] + static_cast<double>(dlt);
+  }
+  lp_o[p] = prior_log_kernel(o, mu, prec, D, full);
+}
+
+// Metropolis accept (Algorithm 2 step 2(c)i): log alpha = ll' - ll + lp' - lp, accept when
+// log u < log alpha; accepted rows are copied into the state. Counts accepts per block.
+__global__ void accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restrict__ lp,
+                              const double* __restrict__ th_p, const double* __restrict__ ll_p,
+                              const double* __restrict__ lp_p, int64_t P, int D, const double* __restrict__ u_given,
+                              uint64_t seed, uint64_t step, const int* __restrict__ flag,
+                              unsigned long long* __restrict__ n_acc, int* __restrict__ nonfinite,
+                              double* __restrict__ log_alpha_out, int* __restrict__ acc_out) {
+  if (*flag) return;
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  bool acc = false;
+  if (p < P) {
+    const double lpp = ll_p[p];
+    if (!isfinite(lpp)) atomicOr(nonfinite, 1);
+    const double la = (lpp - ll[p]) + (lp_p[p] - lp[p]);
+    double u;
+    if (u_given) {
+      u = u_given[p];
+    } else {
+      const uint4 r = draw(seed, static_cast<uint32_t>(p), kStreamAccept, step);
+      u = uniform53(r.x, r.y);
+    }
+    acc = log(u) < la;
+    if (acc) {
+      for (int d = 0; d < D; ++d) th[p * D + d] = th_p[p * D + d];
+      ll[p] = lpp;
+      lp[p] = lp_p[p];
+    }
+    if (log_alpha_out) log_alpha_out[p] = la;
+    if (acc_out) acc_out[p] = acc ? 1 : 0;
+  }
+  const unsigned ballot = __ballot_sync(0xffffffffu, acc);
+  if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, static_cast<unsigned long long>(__popc(ballot)));
+}
+
+// Group sums of monitoring or output functions: functions are theta coordinates f < nth
+// (if with_theta), then ll (if with_ll), then the log-odds theta_c' xbar. Per group j and
+// function f: sums of (g - ref_f) and (g - ref_f)^2, ref_f the value at particle 0.
+__device__ __forceinline__ double fn_value(const double* th, const double* ll, const double* xbar, int64_t p,
+                                           int f, int D, int k, bool with_theta, bool with_ll) {
+  if (with_theta) {
+    if (f < D) return th[p * D + f];
+    f -= D;
+  }
+  if (with_ll) {
+    if (f == 0) return ll[p];
+    f -= 1;
+  }
+  const double* t = th + p * D + f * k;
+  double a = 0.0;
+  for (int i = 0; i < k; ++i) a = fma(t[i], xbar[i], a);
+  return a;
+}
+
+__global__ void group_moments_kernel(const double* __restrict__ th, const double* __restrict__ ll,
+                                     const double* __restrict__ xbar, int N, int D, int k, int F, bool with_theta,
+                                     bool with_ll, double* __restrict__ sums) {
+  __shared__ double sh[33];
+  const int j = blockIdx.x;
+  for (int f = 0; f < F; ++f) {
+    const double ref = fn_value(th, ll, xbar, 0, f, D, k, with_theta, with_ll);
+    double s1 = 0.0, s2 = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      const double g = fn_value(th, ll, xbar, static_cast<int64_t>(j) * N + n, f, D, k, with_theta, with_ll) - ref;
+      s1 += g;
+      s2 = fma(g, g, s2);
+    }
+    s1 = block_sum(s1, sh);
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+      sums[(static_cast<int64_t>(j) * F + f) * 3 + 0] = s1;
+      sums[(static_cast<int64_t>(j) * F + f) * 3 + 1] = s2;
+      sums[(static_cast<int64_t>(j) * F + f) * 3 + 2] = ref;
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ host helpers
+
+struct Moments {
+  std::vector<double> mean, sd, nse, rne;
+};
+
+// Eqs. (3), (5), (6), (7) as read (NSE = sqrt(vhat / (J N))), (10) from group sums.
+static Moments moments_from_sums(const std::vector<double>& sums, int J, int N, int F) {
+  Moments m;
+  m.mean.resize(F);
+  m.sd.resize(F);
+  m.nse.resize(F);
+  m.rne.resize(F);
+  for (int f = 0; f < F; ++f) {
+    const double ref = sums[(0 * F + f) * 3 + 2];
+    double gbar = 0.0, s2 = 0.0;
+    std::vector<double> gj(J);
+    for (int j = 0; j < J; ++j) {
+      gj[j] = sums[(j * F + f) * 3 + 0] / N;
+      gbar += gj[j];
+      s2 += sums[(j * F + f) * 3 + 1];
+    }
+    gbar /= J;
+    double vh = 0.0;
+    for (int j = 0; j < J; ++j) vh += (gj[j] - gbar) * (gj[j] - gbar);
+    vh *= static_cast<double>(N) / (J - 1.0);
+    const double var = std::max(0.0, s2 / (static_cast<double>(J) * N) - gbar * gbar);
+    m.mean[f] = ref + gbar;
+    m.sd[f] = std::sqrt(var);
+    m.nse[f] = std::sqrt(vh / (static_cast<double>(J) * N));
+    m.rne[f] = vh > 0.0 ? var / vh : INFINITY;
+  }
+  return m;
+}
+
+static void swapbuf(DevBuf& a, DevBuf& b) {
+  std::swap(a.ptr, b.ptr);
+  std::swap(a.bytes, b.bytes);
+}
+
+static bool prior_full(const sps_ctx* ctx) { return ctx->prior_kind == SPS_PRIOR_FULL; }
+
+static int cov_blocks(int64_t P) { return static_cast<int>(std::min<int64_t>(148, (P + kCovSub - 1) / kCovSub)); }
+
+// V (and Sigma = h V unless sigma_in) then its Cholesky factor into st->chol / scratch L32.
+static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_theta, double h,
+                                  const double* sigma_host, double* sigma_out, int* d_flag) {
+  const int D = ctx->D;
+  const int T = D * (D + 1) / 2;
+  double* d_sigma = st->cov.as<double>();
+  if (sigma_host) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma_host, sizeof(double) * D * D, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    col_mean_kernel<<<(D + 31) / 32, 256, 0, ctx->stream>>>(d_theta, st->P, D, st->mean.as<double>()); ++ctx->launches;
+    const int blocks = cov_blocks(st->P);
+    const int64_t per = (st->P + blocks - 1) / blocks;
+    cov_partial_kernel<<<blocks, kCovThreads, sizeof(float) * kCovSub * D, ctx->stream>>>(
+        d_theta, st->P, D, st->mean.as<double>(), per, st->scratch.as<double>()); ++ctx->launches;
+    cov_final_kernel<<<(T + 255) / 256, 256, 0, ctx->stream>>>(st->scratch.as<double>(), blocks, D, st->P, h,
+                                                                nullptr, d_sigma); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+  }
+  if (sigma_out)
+    SPS_CUDA_TRY(cudaMemcpyAsync(sigma_out, d_sigma, sizeof(double) * D * D, cudaMemcpyDeviceToHost, ctx->stream));
+  float* L32 = reinterpret_cast<float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
+  SPS_CUDA_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(sizeof(double) * T)));
+  cholesky_kernel<<<1, 256, sizeof(double) * T, ctx->stream>>>(d_sigma, D, st->chol.as<double>(), L32, d_flag); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
+static size_t propose_smem(int D) {
+  const int T = D * (D + 1) / 2;
+  return sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kPropThreads);
+}
+
+static sps_status launch_propose(sps_ctx* ctx, sps_state* st, const double* d_theta, int64_t P, const double* z,
+                                 uint64_t step, int* d_flag, double* th_o, double* lp_o) {
+  const int D = ctx->D;
+  const size_t smem = propose_smem(D);
+  SPS_CUDA_TRY(cudaFuncSetAttribute(propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
+  propose_kernel<<<static_cast<unsigned>((P + kPropThreads - 1) / kPropThreads), kPropThreads, smem, ctx->stream>>>(
+      d_theta, P, D, L32, z, st->seed, step, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(),
+      prior_full(ctx), d_flag, th_o, lp_o); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
+// Per-state buffers of the given size (theta etc.), counters and scratch.
+static sps_status state_buffers(sps_ctx* ctx, sps_state* st) {
+  const int64_t P = st->P;
+  const int D = ctx->D;
+  const size_t pd = static_cast<size_t>(P) * D * sizeof(double);
+  SPS_CUDA_TRY(st->theta.reserve(pd));
+  SPS_CUDA_TRY(st->theta_prop.reserve(pd));
+  SPS_CUDA_TRY(st->ll.reserve(P * sizeof(double)));
+  SPS_CUDA_TRY(st->ll_prop.reserve(P * sizeof(double)));
+  SPS_CUDA_TRY(st->lp.reserve(P * sizeof(double)));
+  SPS_CUDA_TRY(st->lp_prop.reserve(P * sizeof(double)));
+  SPS_CUDA_TRY(st->logw.reserve(P * sizeof(double)));
+  SPS_CUDA_TRY(st->logml.reserve(st->J * sizeof(double)));
+  SPS_CUDA_TRY(st->idx.reserve(P * sizeof(int)));
+  SPS_CUDA_TRY(st->cov.reserve(sizeof(double) * D * D));
+  SPS_CUDA_TRY(st->chol.reserve(sizeof(double) * D * D + sizeof(float) * (D * (D + 1) / 2 + 4)));
+  SPS_CUDA_TRY(st->mean.reserve(sizeof(double) * D));
+  const size_t T = static_cast<size_t>(D) * (D + 1) / 2;
+  const int F = D + ctx->NC + 1;
+  SPS_CUDA_TRY(st->scratch.reserve(std::max(sizeof(double) * T * cov_blocks(P),
+                                            sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64)));
+  // counters: [0] accepts (u64), then int flags: [2] chol failure, [3] non-finite, [4] resample
+  SPS_CUDA_TRY(st->counters.reserve(64));
+  return SPS_OK;
+}
+
+}  // namespace sps
+
+using namespace sps;
+
+namespace {
+
+struct Counters {
+  unsigned long long accepts;
+  int chol_bad, nonfinite, res_bad, pad;
+};
+
+sps_status read_counters(sps_ctx* ctx, sps_state* st, Counters* c) {
+  SPS_CUDA_TRY(cudaMemcpyAsync(c, st->counters.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+int* flag_ptr(sps_state* st, int which) { return reinterpret_cast<int*>(st->counters.as<char>() + 8) + which; }
+
+sps_status check_state(sps_ctx* ctx, const sps_state* st) {
+  if (!ctx || !st || st->ctx != ctx) return fail(ctx, SPS_ERR_INVALID_ARG, "state does not belong to this context");
+  return SPS_OK;
+}
+
+// Monitoring moments (ll, theta_c' xbar) after an M step: returns min RNE over the set.
+sps_status monitoring_rne(sps_ctx* ctx, sps_state* st, double* rne_min) {
+  const int F = 1 + ctx->NC;
+  group_moments_kernel<<<st->J, 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
+                                                       ctx->xbar.as<double>(), st->N, ctx->D, ctx->k, F, false,
+                                                       true, st->scratch.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> sums(static_cast<size_t>(st->J) * F * 3);
+  SPS_CUDA_TRY(cudaMemcpyAsync(sums.data(), st->scratch.ptr, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  Moments m = moments_from_sums(sums, st->J, st->N, F);
+  double r = INFINITY;
+  for (double v : m.rne) r = std::min(r, v);
+  *rne_min = r;
+  return SPS_OK;
+}
+
+// One M step; recomputes the cached log-likelihood with the M-phase kernel first when the C
+// phase has updated it (so that both sides of the Metropolis ratio use one function).
+sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sigma, double* sigma_used,
+                      sps_mstep_info* info) {
+  if (kernel != SPS_MKERNEL_RW) return fail(ctx, SPS_ERR_UNSUPPORTED, "only the random-walk M kernel is built");
+  const int precision = ctx->opt.precision;
+  if (st->ll_stale) {
+    SPS_TRY(loglik_dispatch(ctx, st->theta.as<double>(), st->P, st->t, st->ll.as<double>(), precision));
+    st->ll_stale = false;
+  }
+  SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
+  const double h = st->h;
+  SPS_TRY(factor_proposal(ctx, st, st->theta.as<double>(), h, sigma, sigma_used, flag_ptr(st, 0)));
+  const uint64_t step = ++st->step_counter;
+  SPS_TRY(launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, flag_ptr(st, 0),
+                         st->theta_prop.as<double>(), st->lp_prop.as<double>()));
+  SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(), precision));
+  accept_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
+      st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->theta_prop.as<double>(),
+      st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, flag_ptr(st, 0),
+      st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  Counters c;
+  SPS_TRY(read_counters(ctx, st, &c));
+  if (c.chol_bad)
+    return fail(ctx, SPS_ERR_DEGENERATE, "proposal covariance h V is not positive definite");
+  if (c.nonfinite) return fail(ctx, SPS_ERR_NONFINITE, "non-finite log-likelihood of a proposal");
+  const double alpha = static_cast<double>(c.accepts) / static_cast<double>(st->P);
+  double rmin = 0.0;
+  SPS_TRY(monitoring_rne(ctx, st, &rmin));
+  const sps_options& o = ctx->opt;
+  double hn = h;
+  if (!sigma) {
+    const double target = (kernel == SPS_MKERNEL_MALA) ? o.mala_target_accept : o.target_accept;
+    hn = (alpha > target) ? std::min(h + o.h_step, o.h_max) : std::max(h - o.h_step, o.h_min);
+    st->h = hn;
+  }
+  if (info) {
+    info->h = h;
+    info->accept_rate = alpha;
+    info->rne_min = rmin;
+    info->h_next = hn;
+  }
+  return SPS_OK;
+}
+
+sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new, double* ess_out,
+                       double* lme_out) {
+  const int64_t n = ctx->n, P = st->P;
+  if (st->t >= n) return fail(ctx, SPS_ERR_STATE, "C phase: no observations left");
+  if (t_target > 0 && (t_target <= st->t || t_target > n)) return fail(ctx, SPS_ERR_INVALID_ARG, "C phase: bad t_target");
+  const int64_t max_rows = std::max<int64_t>(1, std::min<int64_t>(1024, (int64_t{1} << 25) / P));
+  int64_t block = std::max<int64_t>(1, std::min<int64_t>(ctx->opt.cphase_block > 0 ? ctx->opt.cphase_block : 64, max_rows));
+  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(double) * max_rows * P));
+  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * max_rows));
+  SPS_CUDA_TRY(cudaMemsetAsync(st->logw.ptr, 0, sizeof(double) * P, ctx->stream));
+  int64_t s = st->t;
+  std::vector<double> ess(max_rows);
+  int64_t found = -1;
+  double ess_found = 0.0;
+  while (s < n) {
+    const int64_t b = std::min<int64_t>(block, n - s);
+    SPS_TRY(cphase_increments(ctx, st->theta.as<double>(), P, s, s + b, st->logw.as<double>(),
+                              st->lwbuf.as<double>()));
+    ess_rows_kernel<<<static_cast<unsigned>(b), 1024, 0, ctx->stream>>>(st->lwbuf.as<double>(), P,
+                                                                       st->ess_buf.as<double>()); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+    SPS_CUDA_TRY(cudaMemcpyAsync(ess.data(), st->ess_buf.ptr, sizeof(double) * b, cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int64_t j = 0; j < b; ++j) {
+      const int64_t sj = s + j + 1;
+      const bool stop = (t_target > 0) ? (sj == t_target)
+                                       : (ess[j] / static_cast<double>(P) < ctx->opt.ess_fraction || sj == n);
+      if (stop) {
+        found = j;
+        ess_found = ess[j];
+        break;
+      }
+    }
+    const int64_t row = (found >= 0) ? found : b - 1;
+    SPS_CUDA_TRY(cudaMemcpyAsync(st->logw.ptr, st->lwbuf.as<double>() + row * P, sizeof(double) * P,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+    if (found >= 0) {
+      s = s + found + 1;
+      break;
+    }
+    s += b;
+    block = std::min<int64_t>(block * 2, max_rows);
+  }
+  // log marginal likelihood increment per group, cached log-likelihood at the new t
+  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * std::max<int64_t>(max_rows, st->J)));
+  group_lme_kernel<<<st->J, 256, 0, ctx->stream>>>(st->logw.as<double>(), st->N, st->ess_buf.as<double>(),
+                                                  st->logml.as<double>()); ++ctx->launches;
+  add_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(st->ll.as<double>(),
+                                                                               st->logw.as<double>(), P); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> lme(st->J);
+  SPS_CUDA_TRY(cudaMemcpyAsync(lme.data(), st->ess_buf.ptr, sizeof(double) * st->J, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  st->t = s;
+  st->have_weights = true;
+  st->ll_stale = true;
+  if (t_new) *t_new = s;
+  if (ess_out) *ess_out = ess_found;
+  if (lme_out) std::memcpy(lme_out, lme.data(), sizeof(double) * st->J);
+  return SPS_OK;
+}
+
+sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_idx_out) {
+  if (!st->have_weights) return fail(ctx, SPS_ERR_STATE, "S phase before a C phase");
+  SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
+  const uint64_t step = ++st->cycle_counter;
+  resample_kernel<<<st->J, kResThreads, 0, ctx->stream>>>(st->logw.as<double>(), 0, st->N, d_u, st->seed, step,
+                                                          st->idx.as<int>(), flag_ptr(st, 2)); ++ctx->launches;
+  gather_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
+      st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->idx.as<int>(), st->P, st->N, ctx->D,
+      st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  if (d_idx_out)
+    SPS_CUDA_TRY(cudaMemcpyAsync(d_idx_out, st->idx.ptr, sizeof(int) * st->P, cudaMemcpyDeviceToDevice, ctx->stream));
+  Counters c;
+  SPS_TRY(read_counters(ctx, st, &c));
+  if (c.res_bad) return fail(ctx, SPS_ERR_DEGENERATE, "all resampling weights of a group vanished");
+  swapbuf(st->theta, st->theta_prop);
+  swapbuf(st->ll, st->ll_prop);
+  swapbuf(st->lp, st->lp_prop);
+  st->have_weights = false;
+  return SPS_OK;
+}
+
+sps_status mphase_impl(sps_ctx* ctx, sps_state* st, int kernel, int fixed_steps, const double* sigmas,
+                       sps_schedule* rec, int64_t rec_step0, int* steps, double* last_acc, double* last_rne) {
+  const double K = (st->t >= ctx->n) ? ctx->opt.rne_final : ctx->opt.rne_cycle;
+  const int D = ctx->D;
+  int r = 0;
+  sps_mstep_info info{};
+  while (true) {
+    const int64_t rs = rec_step0 + r;
+    double* sig_out = nullptr;
+    if (rec && rec->sigma && rs < rec->cap_steps) sig_out = rec->sigma + rs * D * D;
+    const double* sig_in = sigmas ? sigmas + static_cast<int64_t>(r) * D * D : nullptr;
+    SPS_TRY(mstep_impl(ctx, st, kernel, sig_in, sig_out, &info));
+    if (rec && rs < rec->cap_steps) {
+      if (rec->h) rec->h[rs] = info.h;
+      if (rec->accept) rec->accept[rs] = info.accept_rate;
+    }
+    ++r;
+    if (fixed_steps > 0) {
+      if (r >= fixed_steps) break;
+    } else if (info.rne_min >= K || r >= ctx->opt.r_max) {
+      break;
+    }
+  }
+  if (steps) *steps = r;
+  if (last_acc) *last_acc = info.accept_rate;
+  if (last_rne) *last_rne = info.rne_min;
+  return SPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sps_status sps_state_create(sps_ctx* ctx, int32_t J, int32_t N, uint64_t seed, sps_state** out) {
+  if (!out) return SPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (J < 2 || N < 2 || N > kMaxN) return fail(ctx, SPS_ERR_INVALID_ARG, "need 2 <= J and 2 <= N <= 4096");
+  if (ctx->D > kMaxD) return fail(ctx, SPS_ERR_UNSUPPORTED, "the simulator supports at most 155 parameters");
+  sps_state* st = new sps_state();
+  st->ctx = ctx;
+  st->J = J;
+  st->N = N;
+  st->P = static_cast<int64_t>(J) * N;
+  st->seed = seed;
+  st->h = ctx->opt.h_init;
+  sps_status s = state_buffers(ctx, st);
+  if (s != SPS_OK) {
+    delete st;
+    return s;
+  }
+  const int D = ctx->D;
+  DevBuf z;
+  if (z.reserve(static_cast<size_t>(st->P) * D * sizeof(double)) != cudaSuccess) {
+    delete st;
+    return fail(ctx, SPS_ERR_OOM, "state: out of device memory");
+  }
+  (void)cudaGetLastError();   // clear a stale error of an earlier, unrelated runtime call
+  prior_init_kernel<<<static_cast<unsigned>((st->P + 127) / 128), 128, 0, ctx->stream>>>(
+      seed, st->P, D, ctx->d_prior_mean.as<double>(), ctx->d_prior_chol.as<double>(), ctx->d_prior_prec.as<double>(),
+      prior_full(ctx), st->theta.as<double>(), st->lp.as<double>(), z.as<double>()); ++ctx->launches;
+  cudaMemsetAsync(st->ll.ptr, 0, sizeof(double) * st->P, ctx->stream);
+  cudaMemsetAsync(st->logw.ptr, 0, sizeof(double) * st->P, ctx->stream);
+  cudaMemsetAsync(st->logml.ptr, 0, sizeof(double) * J, ctx->stream);
+  const cudaError_t e_launch = cudaGetLastError();
+  const cudaError_t e_sync = cudaStreamSynchronize(ctx->stream);
+  if (e_launch != cudaSuccess || e_sync != cudaSuccess) {
+    delete st;
+    return fail(ctx, SPS_ERR_CUDA, std::string("state: prior draw failed: launch ") + cudaGetErrorString(e_launch) +
+                                       ", sync " + cudaGetErrorString(e_sync));
+  }
+  *out = st;
+  return SPS_OK;
+}
+
+void sps_state_destroy(sps_state* st) {
+  if (!st) return;
+  if (st->ctx) cudaStreamSynchronize(st->ctx->stream);
+  delete st;
+}
+
+sps_status sps_state_get(sps_ctx* ctx, const sps_state* st, double* theta, double* ll, double* logw, int64_t* t,
+                         double* h) {
+  SPS_TRY(check_state(ctx, st));
+  if (theta)
+    SPS_CUDA_TRY(cudaMemcpyAsync(theta, st->theta.ptr, sizeof(double) * st->P * ctx->D, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  if (ll) SPS_CUDA_TRY(cudaMemcpyAsync(ll, st->ll.ptr, sizeof(double) * st->P, cudaMemcpyDeviceToHost, ctx->stream));
+  if (logw)
+    SPS_CUDA_TRY(cudaMemcpyAsync(logw, st->logw.ptr, sizeof(double) * st->P, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (t) *t = st->t;
+  if (h) *h = st->h;
+  return SPS_OK;
+}
+
+sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const double* ll, int64_t t) {
+  SPS_TRY(check_state(ctx, st));
+  if (!theta || t < 0 || t > ctx->n) return fail(ctx, SPS_ERR_INVALID_ARG, "state_set: bad arguments");
+  SPS_CUDA_TRY(cudaMemcpyAsync(st->theta.ptr, theta, sizeof(double) * st->P * ctx->D, cudaMemcpyHostToDevice,
+                               ctx->stream));
+  prior_lp_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
+      st->theta.as<double>(), st->P, ctx->D, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(),
+      prior_full(ctx), st->lp.as<double>()); ++ctx->launches;
+  st->t = t;
+  if (ll) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(st->ll.ptr, ll, sizeof(double) * st->P, cudaMemcpyHostToDevice, ctx->stream));
+    st->ll_stale = false;
+  } else {
+    st->ll_stale = true;
+  }
+  st->have_weights = false;
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+sps_status sps_cphase(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new, double* ess,
+                      double* logml_inc) {
+  SPS_TRY(check_state(ctx, st));
+  return cphase_impl(ctx, st, t_target, t_new, ess, logml_inc);
+}
+
+sps_status sps_sphase(sps_ctx* ctx, sps_state* st, const double* uniforms, int32_t* idx_out, int32_t mem) {
+  SPS_TRY(check_state(ctx, st));
+  if (mem == SPS_MEM_DEVICE) return sphase_impl(ctx, st, uniforms, idx_out);
+  DevBuf du, di;
+  if (uniforms) {
+    SPS_CUDA_TRY(du.reserve(sizeof(double) * st->P));
+    SPS_CUDA_TRY(cudaMemcpyAsync(du.ptr, uniforms, sizeof(double) * st->P, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (idx_out) SPS_CUDA_TRY(di.reserve(sizeof(int) * st->P));
+  SPS_TRY(sphase_impl(ctx, st, uniforms ? du.as<double>() : nullptr, idx_out ? di.as<int>() : nullptr));
+  if (idx_out) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(idx_out, di.ptr, sizeof(int) * st->P, cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  return SPS_OK;
+}
+
+sps_status sps_mstep(sps_ctx* ctx, sps_state* st, int32_t kernel, const double* sigma, double* sigma_used,
+                     sps_mstep_info* info) {
+  SPS_TRY(check_state(ctx, st));
+  if (st->t <= 0) return fail(ctx, SPS_ERR_STATE, "M step before any observation was added");
+  SPS_TRY(mstep_impl(ctx, st, kernel, sigma, sigma_used, info));
+  if (sigma_used) SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+sps_status sps_mphase(sps_ctx* ctx, sps_state* st, int32_t kernel, int32_t fixed_steps, int32_t* steps,
+                      double* accept_rate, double* rne_min) {
+  SPS_TRY(check_state(ctx, st));
+  if (st->t <= 0) return fail(ctx, SPS_ERR_STATE, "M phase before any observation was added");
+  return mphase_impl(ctx, st, kernel, fixed_steps, nullptr, nullptr, 0, steps, accept_rate, rne_min);
+}
+
+sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, const sps_schedule* schedule,
+                   sps_schedule* record, sps_result* out) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!out || !out->mean || !out->sd || !out->nse || !out->rne || !out->log_ml_group)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_run: result arrays missing");
+  const auto t0 = std::chrono::steady_clock::now();
+  sps_state* st = nullptr;
+  SPS_TRY(sps_state_create(ctx, groups, particles_per_group, ctx->opt.seed, &st));
+  struct Guard {
+    sps_state* s;
+    ~Guard() { sps_state_destroy(s); }
+  } guard{st};
+  const int D = ctx->D;
+  const bool replay = schedule && schedule->n_cycles > 0;
+  int32_t L = 0;
+  int64_t total_steps = 0;
+  while (st->t < ctx->n) {
+    if (replay && L >= schedule->n_cycles) return fail(ctx, SPS_ERR_INVALID_ARG, "schedule ends before T");
+    const int64_t target = replay ? schedule->t[L] : 0;
+    int64_t tn = 0;
+    SPS_TRY(cphase_impl(ctx, st, target, &tn, nullptr, nullptr));
+    SPS_TRY(sphase_impl(ctx, st, nullptr, nullptr));
+    int steps = 0;
+    double acc = 0.0, rne = 0.0;
+    if (replay) {
+      const int R = schedule->R[L];
+      if (!schedule->sigma) return fail(ctx, SPS_ERR_INVALID_ARG, "replayed schedule has no Sigma matrices");
+      int64_t before = 0;
+      for (int q = 0; q < L; ++q) before += schedule->R[q];
+      SPS_TRY(mphase_impl(ctx, st, ctx->opt.mkernel, R, schedule->sigma + before * D * D, record, total_steps,
+                          &steps, &acc, &rne));
+    } else {
+      SPS_TRY(mphase_impl(ctx, st, ctx->opt.mkernel, 0, nullptr, record, total_steps, &steps, &acc, &rne));
+    }
+    if (record) {
+      if (L >= record->cap_cycles) return fail(ctx, SPS_ERR_INVALID_ARG, "schedule record: too many cycles");
+      record->t[L] = tn;
+      record->R[L] = steps;
+      if (total_steps + steps > record->cap_steps)
+        return fail(ctx, SPS_ERR_INVALID_ARG, "schedule record: too many M steps");
+    }
+    total_steps += steps;
+    ++L;
+  }
+  if (record) record->n_cycles = L;
+  // outputs: moments of theta and of the log-odds theta_c' xbar (Eq. 15), and the log ML
+  const int F = D + ctx->NC;
+  SPS_CUDA_TRY(st->scratch.reserve(sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64));
+  group_moments_kernel<<<st->J, 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
+                                                       ctx->xbar.as<double>(), st->N, D, ctx->k, F, true, false,
+                                                       st->scratch.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> sums(static_cast<size_t>(st->J) * F * 3), lml(st->J);
+  SPS_CUDA_TRY(cudaMemcpyAsync(sums.data(), st->scratch.ptr, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(lml.data(), st->logml.ptr, sizeof(double) * st->J, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  Moments m = moments_from_sums(sums, st->J, st->N, F);
+  for (int f = 0; f < F; ++f) {
+    out->mean[f] = m.mean[f];
+    out->sd[f] = m.sd[f];
+    out->nse[f] = m.nse[f];
+    out->rne[f] = m.rne[f];
+  }
+  double mean = 0.0, mx = -INFINITY;
+  for (int j = 0; j < st->J; ++j) {
+    out->log_ml_group[j] = lml[j];
+    mean += lml[j];
+    mx = std::max(mx, lml[j]);
+  }
+  mean /= st->J;
+  double var = 0.0, se = 0.0;
+  for (int j = 0; j < st->J; ++j) {
+    var += (lml[j] - mean) * (lml[j] - mean);
+    se += std::exp(lml[j] - mx);
+  }
+  out->log_ml = mean;
+  out->log_ml_nse = std::sqrt(var / (st->J - 1.0)) / std::sqrt(static_cast<double>(st->J));
+  out->log_ml_pooled = mx + std::log(se / st->J);
+  out->n_cycles = L;
+  out->m_steps = total_steps;
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return SPS_OK;
+}
+
+// ------------------------------------------------------------------------------ building blocks
+
+sps_status sps_resample(sps_ctx* ctx, const double* w, const double* u, int32_t J, int32_t N, int32_t* idx,
+                        int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!w || !u || !idx || J < 1 || N < 1 || N > kMaxN) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_resample: bad arguments");
+  const size_t P = static_cast<size_t>(J) * N;
+  DevBuf dw, du, di, df;
+  SPS_CUDA_TRY(df.reserve(sizeof(int)));
+  SPS_CUDA_TRY(cudaMemsetAsync(df.ptr, 0, sizeof(int), ctx->stream));
+  const double* pw = w;
+  const double* pu = u;
+  int* pi = idx;
+  if (mem == SPS_MEM_HOST) {
+    SPS_CUDA_TRY(dw.reserve(P * sizeof(double)));
+    SPS_CUDA_TRY(du.reserve(P * sizeof(double)));
+    SPS_CUDA_TRY(di.reserve(P * sizeof(int)));
+    SPS_CUDA_TRY(cudaMemcpyAsync(dw.ptr, w, P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    SPS_CUDA_TRY(cudaMemcpyAsync(du.ptr, u, P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    pw = dw.as<double>();
+    pu = du.as<double>();
+    pi = di.as<int>();
+  }
+  resample_kernel<<<J, kResThreads, 0, ctx->stream>>>(pw, 1, N, pu, 0, 0, pi, df.as<int>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  if (mem == SPS_MEM_HOST) {
+    int bad = 0;
+    SPS_CUDA_TRY(cudaMemcpyAsync(idx, di.ptr, P * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA_TRY(cudaMemcpyAsync(&bad, df.ptr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (bad) return fail(ctx, SPS_ERR_DEGENERATE, "all weights of a group quantise to zero");
+  } else {
+    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));   // the flag buffer is local to this call
+  }
+  return SPS_OK;
+}
+
+sps_status sps_philox(sps_ctx* ctx, uint32_t key0, uint32_t key1, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2,
+                      uint32_t ctr3, int64_t count, uint32_t* out, int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!out || count < 1) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_philox: bad arguments");
+  DevBuf d;
+  uint4* po = reinterpret_cast<uint4*>(out);
+  if (mem == SPS_MEM_HOST) {
+    SPS_CUDA_TRY(d.reserve(static_cast<size_t>(count) * 16));
+    po = d.as<uint4>();
+  }
+  philox_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, ctx->stream>>>(
+      key0, key1, make_uint4(ctr0, ctr1, ctr2, ctr3), count, po); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  if (mem == SPS_MEM_HOST) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(out, d.ptr, static_cast<size_t>(count) * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  return SPS_OK;
+}
+
+sps_status sps_ess(sps_ctx* ctx, const double* logw, int64_t P, int32_t J, double* ess, double* lme, int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!logw || P < 1 || J < 1 || P % J != 0) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_ess: bad arguments");
+  DevBuf dl, de, dm;
+  const double* pl = logw;
+  if (mem == SPS_MEM_HOST) {
+    SPS_CUDA_TRY(dl.reserve(P * sizeof(double)));
+    SPS_CUDA_TRY(cudaMemcpyAsync(dl.ptr, logw, P * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    pl = dl.as<double>();
+  }
+  SPS_CUDA_TRY(de.reserve(sizeof(double)));
+  SPS_CUDA_TRY(dm.reserve(sizeof(double) * J));
+  double* pe = (mem == SPS_MEM_DEVICE && ess) ? ess : de.as<double>();
+  double* pm = (mem == SPS_MEM_DEVICE && lme) ? lme : dm.as<double>();
+  ess_rows_kernel<<<1, 1024, 0, ctx->stream>>>(pl, P, pe); ++ctx->launches;
+  group_lme_kernel<<<J, 256, 0, ctx->stream>>>(pl, static_cast<int>(P / J), pm, nullptr); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  if (mem == SPS_MEM_HOST) {
+    if (ess) SPS_CUDA_TRY(cudaMemcpyAsync(ess, pe, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (lme) SPS_CUDA_TRY(cudaMemcpyAsync(lme, pm, sizeof(double) * J, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+sps_status sps_particle_cov(sps_ctx* ctx, const double* theta, int64_t P, double* V, int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!theta || !V || P < 2) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_particle_cov: bad arguments");
+  const int D = ctx->D;
+  if (D > 155) return fail(ctx, SPS_ERR_UNSUPPORTED, "sps_particle_cov: at most 155 parameters");
+  const int T = D * (D + 1) / 2;
+  const int blocks = cov_blocks(P);
+  DevBuf dt, dv, dmean, dpart;
+  const double* pt = theta;
+  if (mem == SPS_MEM_HOST) {
+    SPS_CUDA_TRY(dt.reserve(sizeof(double) * P * D));
+    SPS_CUDA_TRY(cudaMemcpyAsync(dt.ptr, theta, sizeof(double) * P * D, cudaMemcpyHostToDevice, ctx->stream));
+    pt = dt.as<double>();
+  }
+  SPS_CUDA_TRY(dv.reserve(sizeof(double) * D * D));
+  SPS_CUDA_TRY(dmean.reserve(sizeof(double) * D));
+  SPS_CUDA_TRY(dpart.reserve(sizeof(double) * T * blocks));
+  double* pv = (mem == SPS_MEM_DEVICE) ? V : dv.as<double>();
+  col_mean_kernel<<<(D + 31) / 32, 256, 0, ctx->stream>>>(pt, P, D, dmean.as<double>()); ++ctx->launches;
+  const int64_t per = (P + blocks - 1) / blocks;
+  cov_partial_kernel<<<blocks, kCovThreads, sizeof(float) * kCovSub * D, ctx->stream>>>(pt, P, D, dmean.as<double>(),
+                                                                                      per, dpart.as<double>()); ++ctx->launches;
+  cov_final_kernel<<<(T + 255) / 256, 256, 0, ctx->stream>>>(dpart.as<double>(), blocks, D, P, 1.0, pv, nullptr); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  if (mem == SPS_MEM_HOST)
+    SPS_CUDA_TRY(cudaMemcpyAsync(V, pv, sizeof(double) * D * D, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return SPS_OK;
+}
+
+sps_status sps_rw_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P, int64_t t, const double* sigma,
+                             const double* z, const double* u, int32_t precision, double* log_alpha,
+                             int32_t* accepted, int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!theta || !ll || !sigma || !z || !u || P < 1 || t < 0 || t > ctx->n)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_rw_step_given: bad arguments");
+  const int D = ctx->D;
+  if (D > kMaxD) return fail(ctx, SPS_ERR_UNSUPPORTED, "at most 155 parameters");
+  // a temporary state holds the buffers; its particles are the caller's
+  sps_state tmp;
+  tmp.ctx = ctx;
+  tmp.J = 1;
+  tmp.N = 2;
+  tmp.P = P;
+  SPS_TRY(state_buffers(ctx, &tmp));
+  DevBuf dz, du, dla, dacc;
+  const size_t pd = sizeof(double) * P * D;
+  const double* pz = z;
+  const double* pu = u;
+  double* pla = log_alpha;
+  int* pacc = accepted;
+  if (mem == SPS_MEM_HOST) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(tmp.theta.ptr, theta, pd, cudaMemcpyHostToDevice, ctx->stream));
+    SPS_CUDA_TRY(cudaMemcpyAsync(tmp.ll.ptr, ll, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream));
+    SPS_CUDA_TRY(dz.reserve(pd));
+    SPS_CUDA_TRY(du.reserve(sizeof(double) * P));
+    SPS_CUDA_TRY(dla.reserve(sizeof(double) * P));
+    SPS_CUDA_TRY(dacc.reserve(sizeof(int) * P));
+    SPS_CUDA_TRY(cudaMemcpyAsync(dz.ptr, z, pd, cudaMemcpyHostToDevice, ctx->stream));
+    SPS_CUDA_TRY(cudaMemcpyAsync(du.ptr, u, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream));
+    pz = dz.as<double>();
+    pu = du.as<double>();
+    pla = dla.as<double>();
+    pacc = dacc.as<int>();
+  } else {
+    SPS_CUDA_TRY(cudaMemcpyAsync(tmp.theta.ptr, theta, pd, cudaMemcpyDeviceToDevice, ctx->stream));
+    SPS_CUDA_TRY(cudaMemcpyAsync(tmp.ll.ptr, ll, sizeof(double) * P, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  SPS_CUDA_TRY(cudaMemsetAsync(tmp.counters.ptr, 0, sizeof(Counters), ctx->stream));
+  prior_lp_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+      tmp.theta.as<double>(), P, D, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(), prior_full(ctx),
+      tmp.lp.as<double>()); ++ctx->launches;
+  SPS_TRY(factor_proposal(ctx, &tmp, tmp.theta.as<double>(), 1.0, sigma, nullptr, flag_ptr(&tmp, 0)));
+  SPS_TRY(launch_propose(ctx, &tmp, tmp.theta.as<double>(), P, pz, 0, flag_ptr(&tmp, 0), tmp.theta_prop.as<double>(),
+                         tmp.lp_prop.as<double>()));
+  SPS_TRY(loglik_dispatch(ctx, tmp.theta_prop.as<double>(), P, t, tmp.ll_prop.as<double>(), precision));
+  accept_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+      tmp.theta.as<double>(), tmp.ll.as<double>(), tmp.lp.as<double>(), tmp.theta_prop.as<double>(),
+      tmp.ll_prop.as<double>(), tmp.lp_prop.as<double>(), P, D, pu, 0, 0, flag_ptr(&tmp, 0),
+      tmp.counters.as<unsigned long long>(), flag_ptr(&tmp, 1), pla, pacc); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  Counters c;
+  SPS_TRY(read_counters(ctx, &tmp, &c));
+  if (c.chol_bad) return fail(ctx, SPS_ERR_DEGENERATE, "sigma is not positive definite");
+  const cudaMemcpyKind k = (mem == SPS_MEM_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  SPS_CUDA_TRY(cudaMemcpyAsync(theta, tmp.theta.ptr, pd, k, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(ll, tmp.ll.ptr, sizeof(double) * P, k, ctx->stream));
+  if (mem == SPS_MEM_HOST) {
+    if (log_alpha) SPS_CUDA_TRY(cudaMemcpyAsync(log_alpha, pla, sizeof(double) * P, k, ctx->stream));
+    if (accepted) SPS_CUDA_TRY(cudaMemcpyAsync(accepted, pacc, sizeof(int) * P, k, ctx->stream));
+  }
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (c.nonfinite) return fail(ctx, SPS_ERR_NONFINITE, "non-finite log-likelihood of a proposal");
+  return SPS_OK;
+}
+
+}  // extern "C"

@@ -183,6 +183,25 @@ sps_status sps_counters(sps_ctx* ctx, int32_t reset, int64_t* launches, int64_t*
 sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
                       int32_t precision, int32_t mem);
 
+/* Allocation-free form of sps_loglik (split precision, device pointers only). The paper has no
+ * counterpart: it serves callers that cannot let the library call cudaMalloc during a call,
+ * for example code whose device memory is owned by another allocator (a framework's memory
+ * pool or a fixed arena) or loops that cannot accept the device synchronisation that cudaMalloc
+ * and cudaFree may cause. Its per-call scratch (theta operand rows, partial sums, a flag) lives in
+ * one 32 MiB device array that every GPU loading the library holds until the process exits;
+ * the call allocates nothing.
+ *   theta: [P x D] device FP64; ll: [P] device FP64 output; work is enqueued on the context's
+ *   stream (the call returns before it completes). Same results as sps_loglik(SPS_PREC_SPLIT).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * the context's device current; make that first call before any stream capture. All calls share
+ * the array: calls whose GPU work overlaps race and must be serialised by the caller.
+ * Limit: the call needs 4 (C-1) P' k64 bytes of operand rows (P' = P rounded up to 128, k64 = k
+ * rounded up to 64) plus 16 P' ceil(t / (128 m)) bytes of partial sums (m = observation tiles
+ * per work item, at most 32) and must fit in 32 MiB: the binary workload with 65 536 particles,
+ * k = 30 and n = 20 000 needs about 21 MiB. Larger calls return SPS_ERR_INVALID_ARG, with the
+ * required size in sps_last_error, and launch nothing; other errors as sps_loglik. */
+sps_status sps_loglik_noalloc(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll);
+
 /* Log-likelihood and its gradient d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s
  * (the derivative of Eq. 1; the paper prints no gradient).
  *   grad: [P x D] FP64 output, class-major like theta (mem). FP32 products and residuals,

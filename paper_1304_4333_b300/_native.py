@@ -65,6 +65,7 @@ SIGNATURES = {
     "sps_set_timing": (C.c_int, [_P, C.c_int32]),
     "sps_counters": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "sps_loglik": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, C.c_int32, C.c_int32]),
+    "sps_loglik_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P]),
     "sps_loglik_grad": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P, C.c_int32]),
     "sps_state_create": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P)]),
     "sps_state_destroy": (None, [_P]),

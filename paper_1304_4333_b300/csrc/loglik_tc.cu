@@ -508,3 +508,168 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
 }
 
 }  // namespace sps
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of the split-precision log-likelihood (sps_loglik_noalloc).
+//
+// Some callers cannot let the library call cudaMalloc during a call: code whose device memory
+// is owned entirely by another allocator (a framework's pool, a fixed arena of an embedded
+// application), or latency-critical loops that cannot accept cudaMalloc/cudaFree, which may
+// synchronise the device. For them this variant keeps its per-call scratch (the theta operand
+// rows, the partial sums and the timeout flag) in one file-scope device array of fixed size
+// instead of buffers grown with cudaMalloc. The array exists once per GPU that loads the
+// library and stays allocated until the process exits. Every call shares it: calls whose work
+// overlaps on the GPU (other streams, other host threads) race on it and must be serialised by
+// the caller. Its contents persist from the last call; everything that must start at zero is
+// cleared by each call.
+
+#include <mutex>
+
+namespace sps {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t{32} << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch array on the current device. The host-side name of the
+// array is only a stand-in: its device address comes from cudaGetSymbolAddress, looked up once
+// per device (with that device current) on the first call there.
+sps_status static_scratch_address(sps_ctx* ctx, unsigned char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != ctx->device) return fail(ctx, SPS_ERR_INVALID_ARG, "the context's device is not current");
+  if (dev < 0 || dev >= kMaxDevices) return fail(ctx, SPS_ERR_UNSUPPORTED, "device index beyond 63");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(ctx, SPS_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_static_ptr[dev]);
+  return SPS_OK;
+}
+
+template <int NC, int BN>
+sps_status launch_tc_maps(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_bytes,
+                          const CUtensorMap& mapTH, const CUtensorMap& mapTL) {
+  auto kern = loglik_tc_kernel<NC, BN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem_bytes));
+  if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+  const XEncoding& enc = ctx->enc;
+  const CUtensorMap& mxl = enc.kcpad > 0 ? enc.mapXl : enc.mapXh;
+  kern<<<grid, kThreads, smem_bytes, ctx->stream>>>(enc.mapXh, mxl, mapTH, mapTL, prm); ++ctx->launches;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("loglik_tc launch: ") + cudaGetErrorString(e));
+  return SPS_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll) {
+  const int NC = ctx->NC;
+  if (NC > 3) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision supports at most 4 outcomes");
+  const XEncoding& enc = ctx->enc;
+  const int ppad = static_cast<int>((P + kBM - 1) / kBM * kBM);
+  const int BN = enc.bn;
+  TcParams prm{};
+  prm.ppad = ppad;
+  prm.n_ptiles = ppad / kBM;
+  prm.t = static_cast<int>(t);
+  prm.n_tiles = static_cast<int>((t + BN - 1) / BN);
+  prm.kb_h = enc.kpad / kKB;
+  prm.kb_l = enc.kcpad / kKB;
+  prm.ksteps_h = (enc.k + 15) / 16;
+  prm.ksteps_l = (enc.kc + 15) / 16;
+  prm.th_row_stride = ppad;
+  const int grid_max = ctx->num_sms;
+  int chunk_tiles = std::max(1, std::min(prm.n_tiles, 32));
+  {
+    const int64_t want_items = 8LL * grid_max;
+    while (chunk_tiles > 4 &&
+           static_cast<int64_t>(prm.n_ptiles) * ((prm.n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
+      chunk_tiles /= 2;
+  }
+  prm.chunk_tiles = chunk_tiles;
+  prm.n_chunks = std::max(1, (prm.n_tiles + chunk_tiles - 1) / chunk_tiles);
+  prm.n_items = prm.n_tiles > 0 ? prm.n_ptiles * prm.n_chunks : 0;
+  const uint32_t budget = 227 * 1024 - 1024;
+  int th_bufs = 2, stages = 0;
+  for (int tb = 2; tb >= 1 && stages < 2; --tb) {
+    th_bufs = tb;
+    for (int st = 8; st >= 2; --st) {
+      if (smem_layout(NC, BN, prm.kb_h, prm.kb_l, st, tb).total <= budget) { stages = st; break; }
+    }
+  }
+  if (stages < 2) return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
+  prm.stages = stages;
+  prm.th_bufs = th_bufs;
+  // carve the static area: theta hi rows, theta lo rows, partial sums, flag
+  const size_t slices = static_cast<size_t>(prm.n_chunks) * kNWG;
+  const size_t op_bytes = round256(static_cast<size_t>(NC) * ppad * enc.kpad * sizeof(__nv_bfloat16));
+  const size_t part_bytes = round256(slices * ppad * sizeof(double));
+  const size_t need = 2 * op_bytes + part_bytes + 256;
+  if (need > kStaticScratchBytes) {
+    char msg[160];
+    snprintf(msg, sizeof msg,
+             "sps_loglik_noalloc: this call needs %zu bytes of scratch, the static area holds %zu; use sps_loglik",
+             need, kStaticScratchBytes);
+    return fail(ctx, SPS_ERR_INVALID_ARG, msg);
+  }
+  unsigned char* base = nullptr;
+  SPS_TRY(static_scratch_address(ctx, &base));
+  __nv_bfloat16* th_hi = reinterpret_cast<__nv_bfloat16*>(base);
+  __nv_bfloat16* th_lo = reinterpret_cast<__nv_bfloat16*>(base + op_bytes);
+  double* partial = reinterpret_cast<double*>(base + 2 * op_bytes);
+  int* flag = reinterpret_cast<int*>(base + 2 * op_bytes + part_bytes);
+  CUtensorMap mapTH, mapTL;
+  SPS_TRY(make_map_bf16(ctx, &mapTH, th_hi, static_cast<uint64_t>(NC) * ppad, enc.kpad, kBM));
+  SPS_TRY(make_map_bf16(ctx, &mapTL, th_lo, static_cast<uint64_t>(NC) * ppad, enc.kpad, kBM));
+  {
+    const int64_t total = static_cast<int64_t>(NC) * ppad * enc.kpad;
+    const int threads = 256;
+    encode_theta_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.kpad, ppad, th_hi, th_lo); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+  }
+  SPS_TRY(ensure_lin(ctx, t));
+  prm.partial = partial;
+  prm.flag = flag;
+  prm.timeout_ns = 2000000000ull;
+  SPS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));   // the flag must start at zero
+  const uint32_t smem_bytes = smem_layout(NC, BN, prm.kb_h, prm.kb_l, stages, th_bufs).total + 1024;
+  if (prm.n_items > 0) {
+    const int grid = std::min(grid_max, prm.n_items);
+    sps_status s;
+    if (NC == 1) s = launch_tc_maps<1, 128>(ctx, prm, grid, smem_bytes, mapTH, mapTL);
+    else if (NC == 2) s = launch_tc_maps<2, 128>(ctx, prm, grid, smem_bytes, mapTH, mapTL);
+    else s = launch_tc_maps<3, 64>(ctx, prm, grid, smem_bytes, mapTH, mapTL);
+    if (s != SPS_OK) return s;
+  }
+  {
+    const int threads = 256;
+    loglik_finalize_kernel<<<static_cast<unsigned>((P + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        d_theta, P, ctx->D, ctx->lin.as<double>(), partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad,
+        d_ll); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+  }
+  return SPS_OK;
+}
+
+}  // namespace sps
+
+extern "C" sps_status sps_loglik_noalloc(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!theta || !ll || P < 1 || t < 0 || t > ctx->n || P > (1LL << 28))
+    return sps::fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik_noalloc: bad arguments");
+  return sps::loglik_split_static(ctx, theta, P, t, ll);
+}

@@ -7,6 +7,7 @@ SPS_MEM_DEVICE on torch's current stream.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 from dataclasses import dataclass, field
 from typing import List, Optional
 
@@ -131,6 +132,7 @@ class Sps:
             self._prior_arrays.append(m)
             pr.mean = m.ctypes.data_as(C.POINTER(C.c_double))
         self.options = default_options(**options)
+        self._states = weakref.WeakSet()   # states are destroyed before the context
         ctx = C.c_void_p()
         st = self.lib.sps_init(C.byref(ctx), _ptr(X), n, k, _ptr(y), self.C, C.byref(pr), C.byref(self.options))
         if st != N.SPS_OK:
@@ -139,6 +141,8 @@ class Sps:
 
     def close(self):
         if getattr(self, "ctx", None):
+            for st in list(getattr(self, "_states", ())):
+                st.close()
             self.lib.sps_destroy(self.ctx)
             self.ctx = None
 
@@ -298,10 +302,12 @@ class State:
         st = C.c_void_p()
         sps._call("sps_state_create", J, N_, seed, C.byref(st))
         self.st = st
+        sps._states.add(self)
 
     def close(self):
         if getattr(self, "st", None):
-            self.sps.lib.sps_state_destroy(self.st)
+            if getattr(self.sps, "ctx", None):   # a destroyed context already released its device
+                self.sps.lib.sps_state_destroy(self.st)
             self.st = None
 
     def __del__(self):

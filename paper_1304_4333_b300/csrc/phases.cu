@@ -172,23 +172,51 @@ __global__ void prior_lp_kernel(const double* __restrict__ theta, int64_t P, int
 
 // ------------------------------------------------------------------------------ C phase
 
-// ESS(s) of one row of running log weights per block (Eq. 14), with exp of the FP64 difference
-// to the row maximum in FP32 and FP64 sums.
-__global__ void ess_rows_kernel(const double* __restrict__ lw, int64_t P, double* __restrict__ ess) {
+// ESS(s) of rows of running log weights (Eq. 14). Block (row, part) reduces its slice of the
+// row to (max, sum e, sum e^2) with e = exp of the FP64 difference to the slice maximum taken in
+// FP32 and FP64 sums; the merge rescales the parts to the row maximum in FP64.
+constexpr int kEssParts = 8;
+
+__global__ void ess_part_kernel(const double* __restrict__ lw, int64_t P, double* __restrict__ parts) {
   __shared__ double sh[33];
   const double* row = lw + static_cast<int64_t>(blockIdx.x) * P;
+  const int64_t per = (P + gridDim.y - 1) / gridDim.y;
+  const int64_t lo = blockIdx.y * per, hi = min(P, lo + per);
   double m = -INFINITY;
-  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) m = fmax(m, row[p]);
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) m = fmax(m, row[p]);
   m = block_max(m, sh);
   double s1 = 0.0, s2 = 0.0;
-  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) {
-    const double w = static_cast<double>(expf(static_cast<float>(row[p] - m)));
-    s1 += w;
-    s2 += w * w;
+  if (m > -INFINITY) {
+    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+      const double w = static_cast<double>(expf(static_cast<float>(row[p] - m)));
+      s1 += w;
+      s2 += w * w;
+    }
   }
   s1 = block_sum(s1, sh);
   s2 = block_sum(s2, sh);
-  if (threadIdx.x == 0) ess[blockIdx.x] = (s2 > 0.0) ? s1 * s1 / s2 : 0.0;
+  if (threadIdx.x == 0) {
+    double* o = parts + (static_cast<int64_t>(blockIdx.x) * gridDim.y + blockIdx.y) * 3;
+    o[0] = m;
+    o[1] = s1;
+    o[2] = s2;
+  }
+}
+
+__global__ void ess_merge_kernel(const double* __restrict__ parts, int rows, int nparts, double* __restrict__ ess) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const double* q = parts + static_cast<int64_t>(r) * nparts * 3;
+  double M = -INFINITY;
+  for (int i = 0; i < nparts; ++i) M = fmax(M, q[3 * i]);
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = 0; i < nparts; ++i) {
+    if (q[3 * i] == -INFINITY) continue;
+    const double f = exp(q[3 * i] - M);
+    s1 += f * q[3 * i + 1];
+    s2 += f * f * q[3 * i + 2];
+  }
+  ess[r] = (s2 > 0.0) ? s1 * s1 / s2 : 0.0;
 }
 
 // Per-group log N^-1 sum_n exp(logw_jn) in FP64 (one block per group).
@@ -305,21 +333,35 @@ __global__ void gather_kernel(const double* __restrict__ th, const double* __res
 
 constexpr int kMaxD = 155;   // covariance kernel: <= 48 lower-triangle entries per thread
 
-// Column means of theta [P x D] in FP64 (one block per group of 32 columns).
-__global__ void col_mean_kernel(const double* __restrict__ th, int64_t P, int D, double* __restrict__ mean) {
-  __shared__ double sh[8][33];
-  const int d = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int r = threadIdx.x >> 5;   // 8 row groups
+// Column sums of theta [P x D] in FP64, two stages: block b sums its particle range
+// [b * per_block, (b+1) * per_block) into partial[b][D] (thread = (column, row group)), then
+// mean[d] = sum over blocks in fixed order / P.
+__global__ void col_sum_partial_kernel(const double* __restrict__ th, int64_t P, int D, int64_t per_block,
+                                       double* __restrict__ partial) {
+  __shared__ double sh[256];
+  const int rg = max(1, static_cast<int>(blockDim.x) / D);   // row groups
+  const int d = threadIdx.x % D, g = threadIdx.x / D;
+  const int64_t p_lo = blockIdx.x * per_block;
+  const int64_t p_hi = min(P, p_lo + per_block);
   double s = 0.0;
-  if (d < D)
-    for (int64_t p = r; p < P; p += 8) s += th[p * D + d];
-  sh[r][threadIdx.x & 31] = s;
+  if (g < rg)
+    for (int64_t p = p_lo + g; p < p_hi; p += rg) s += th[p * D + d];
+  sh[threadIdx.x] = (g < rg) ? s : 0.0;
   __syncthreads();
-  if (r == 0 && d < D) {
+  for (int dd = threadIdx.x; dd < D; dd += blockDim.x) {
     double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x & 31];
-    mean[d] = t / static_cast<double>(P);
+    for (int q = 0; q < rg; ++q) t += sh[q * D + dd];
+    partial[static_cast<int64_t>(blockIdx.x) * D + dd] = t;
   }
+}
+
+__global__ void col_mean_final_kernel(const double* __restrict__ partial, int blocks, int D, int64_t P,
+                                      double* __restrict__ mean) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= D) return;
+  double t = 0.0;
+  for (int b = 0; b < blocks; ++b) t += partial[static_cast<int64_t>(b) * D + d];
+  mean[d] = t / static_cast<double>(P);
 }
 
 constexpr int kCovSub = 64;        // particles staged per shared-memory pass
@@ -540,22 +582,20 @@ __global__ void group_moments_kernel(const double* __restrict__ th, const double
                                      const double* __restrict__ xbar, int N, int D, int k, int F, bool with_theta,
                                      bool with_ll, double* __restrict__ sums) {
   __shared__ double sh[33];
-  const int j = blockIdx.x;
-  for (int f = 0; f < F; ++f) {
-    const double ref = fn_value(th, ll, xbar, 0, f, D, k, with_theta, with_ll);
-    double s1 = 0.0, s2 = 0.0;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-      const double g = fn_value(th, ll, xbar, static_cast<int64_t>(j) * N + n, f, D, k, with_theta, with_ll) - ref;
-      s1 += g;
-      s2 = fma(g, g, s2);
-    }
-    s1 = block_sum(s1, sh);
-    s2 = block_sum(s2, sh);
-    if (threadIdx.x == 0) {
-      sums[(static_cast<int64_t>(j) * F + f) * 3 + 0] = s1;
-      sums[(static_cast<int64_t>(j) * F + f) * 3 + 1] = s2;
-      sums[(static_cast<int64_t>(j) * F + f) * 3 + 2] = ref;
-    }
+  const int j = blockIdx.x, f = blockIdx.y;
+  const double ref = fn_value(th, ll, xbar, 0, f, D, k, with_theta, with_ll);
+  double s1 = 0.0, s2 = 0.0;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const double g = fn_value(th, ll, xbar, static_cast<int64_t>(j) * N + n, f, D, k, with_theta, with_ll) - ref;
+    s1 += g;
+    s2 = fma(g, g, s2);
+  }
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    sums[(static_cast<int64_t>(j) * F + f) * 3 + 0] = s1;
+    sums[(static_cast<int64_t>(j) * F + f) * 3 + 1] = s2;
+    sums[(static_cast<int64_t>(j) * F + f) * 3 + 2] = ref;
   }
 }
 
@@ -614,9 +654,11 @@ static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_t
   if (sigma_host) {
     SPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma_host, sizeof(double) * D * D, cudaMemcpyHostToDevice, ctx->stream));
   } else {
-    col_mean_kernel<<<(D + 31) / 32, 256, 0, ctx->stream>>>(d_theta, st->P, D, st->mean.as<double>()); ++ctx->launches;
     const int blocks = cov_blocks(st->P);
     const int64_t per = (st->P + blocks - 1) / blocks;
+    col_sum_partial_kernel<<<blocks, 256, 0, ctx->stream>>>(d_theta, st->P, D, per, st->scratch.as<double>()); ++ctx->launches;
+    col_mean_final_kernel<<<(D + 127) / 128, 128, 0, ctx->stream>>>(st->scratch.as<double>(), blocks, D, st->P,
+                                                                    st->mean.as<double>()); ++ctx->launches;
     cov_partial_kernel<<<blocks, kCovThreads, sizeof(float) * kCovSub * D, ctx->stream>>>(
         d_theta, st->P, D, st->mean.as<double>(), per, st->scratch.as<double>()); ++ctx->launches;
     cov_final_kernel<<<(T + 255) / 256, 256, 0, ctx->stream>>>(st->scratch.as<double>(), blocks, D, st->P, h,
@@ -671,8 +713,11 @@ static sps_status state_buffers(sps_ctx* ctx, sps_state* st) {
   SPS_CUDA_TRY(st->mean.reserve(sizeof(double) * D));
   const size_t T = static_cast<size_t>(D) * (D + 1) / 2;
   const int F = D + ctx->NC + 1;
-  SPS_CUDA_TRY(st->scratch.reserve(std::max(sizeof(double) * T * cov_blocks(P),
-                                            sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64)));
+  const size_t ess_rows_max = static_cast<size_t>(std::max<int64_t>(1, std::min<int64_t>(1024, (int64_t{1} << 25) / P)));
+  SPS_CUDA_TRY(st->scratch.reserve(std::max({sizeof(double) * T * cov_blocks(P),
+                                             sizeof(double) * D * cov_blocks(P),
+                                             sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64,
+                                             sizeof(double) * 3 * kEssParts * ess_rows_max})));
   // counters: [0] accepts (u64), then int flags: [2] chol failure, [3] non-finite, [4] resample
   SPS_CUDA_TRY(st->counters.reserve(64));
   return SPS_OK;
@@ -705,7 +750,7 @@ sps_status check_state(sps_ctx* ctx, const sps_state* st) {
 // Monitoring moments (ll, theta_c' xbar) after an M step: returns min RNE over the set.
 sps_status monitoring_rne(sps_ctx* ctx, sps_state* st, double* rne_min) {
   const int F = 1 + ctx->NC;
-  group_moments_kernel<<<st->J, 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
+  group_moments_kernel<<<dim3(st->J, F), 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
                                                        ctx->xbar.as<double>(), st->N, ctx->D, ctx->k, F, false,
                                                        true, st->scratch.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
@@ -784,8 +829,10 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
     const int64_t b = std::min<int64_t>(block, n - s);
     SPS_TRY(cphase_increments(ctx, st->theta.as<double>(), P, s, s + b, st->logw.as<double>(),
                               st->lwbuf.as<double>()));
-    ess_rows_kernel<<<static_cast<unsigned>(b), 1024, 0, ctx->stream>>>(st->lwbuf.as<double>(), P,
-                                                                       st->ess_buf.as<double>()); ++ctx->launches;
+    ess_part_kernel<<<dim3(static_cast<unsigned>(b), kEssParts), 512, 0, ctx->stream>>>(
+        st->lwbuf.as<double>(), P, st->scratch.as<double>()); ++ctx->launches;
+    ess_merge_kernel<<<static_cast<unsigned>((b + 63) / 64), 64, 0, ctx->stream>>>(
+        st->scratch.as<double>(), static_cast<int>(b), kEssParts, st->ess_buf.as<double>()); ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
     SPS_CUDA_TRY(cudaMemcpyAsync(ess.data(), st->ess_buf.ptr, sizeof(double) * b, cudaMemcpyDeviceToHost, ctx->stream));
     SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -1053,7 +1100,7 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
   // outputs: moments of theta and of the log-odds theta_c' xbar (Eq. 15), and the log ML
   const int F = D + ctx->NC;
   SPS_CUDA_TRY(st->scratch.reserve(sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64));
-  group_moments_kernel<<<st->J, 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
+  group_moments_kernel<<<dim3(st->J, F), 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
                                                        ctx->xbar.as<double>(), st->N, D, ctx->k, F, true, false,
                                                        st->scratch.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
@@ -1161,7 +1208,10 @@ sps_status sps_ess(sps_ctx* ctx, const double* logw, int64_t P, int32_t J, doubl
   SPS_CUDA_TRY(dm.reserve(sizeof(double) * J));
   double* pe = (mem == SPS_MEM_DEVICE && ess) ? ess : de.as<double>();
   double* pm = (mem == SPS_MEM_DEVICE && lme) ? lme : dm.as<double>();
-  ess_rows_kernel<<<1, 1024, 0, ctx->stream>>>(pl, P, pe); ++ctx->launches;
+  DevBuf dparts;
+  SPS_CUDA_TRY(dparts.reserve(sizeof(double) * 3 * kEssParts));
+  ess_part_kernel<<<dim3(1, kEssParts), 512, 0, ctx->stream>>>(pl, P, dparts.as<double>()); ++ctx->launches;
+  ess_merge_kernel<<<1, 64, 0, ctx->stream>>>(dparts.as<double>(), 1, kEssParts, pe); ++ctx->launches;
   group_lme_kernel<<<J, 256, 0, ctx->stream>>>(pl, static_cast<int>(P / J), pm, nullptr); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   if (mem == SPS_MEM_HOST) {
@@ -1190,8 +1240,10 @@ sps_status sps_particle_cov(sps_ctx* ctx, const double* theta, int64_t P, double
   SPS_CUDA_TRY(dmean.reserve(sizeof(double) * D));
   SPS_CUDA_TRY(dpart.reserve(sizeof(double) * T * blocks));
   double* pv = (mem == SPS_MEM_DEVICE) ? V : dv.as<double>();
-  col_mean_kernel<<<(D + 31) / 32, 256, 0, ctx->stream>>>(pt, P, D, dmean.as<double>()); ++ctx->launches;
   const int64_t per = (P + blocks - 1) / blocks;
+  col_sum_partial_kernel<<<blocks, 256, 0, ctx->stream>>>(pt, P, D, per, dpart.as<double>()); ++ctx->launches;
+  col_mean_final_kernel<<<(D + 127) / 128, 128, 0, ctx->stream>>>(dpart.as<double>(), blocks, D, P,
+                                                                  dmean.as<double>()); ++ctx->launches;
   cov_partial_kernel<<<blocks, kCovThreads, sizeof(float) * kCovSub * D, ctx->stream>>>(pt, P, D, dmean.as<double>(),
                                                                                       per, dpart.as<double>()); ++ctx->launches;
   cov_final_kernel<<<(T + 255) / 256, 256, 0, ctx->stream>>>(dpart.as<double>(), blocks, D, P, 1.0, pv, nullptr); ++ctx->launches;

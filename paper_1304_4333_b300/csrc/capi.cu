@@ -79,23 +79,24 @@ __global__ void nonexact_columns_kernel(const double* __restrict__ X, int64_t n,
   if (h != v) atomicOr(&nonexact[col], 1);
 }
 
+// Packed operand rows of X: [Xh over k16 | Xl over kc16 | 0], internal column order; and the
+// FP32 copy in the original order.
 __global__ void encode_x_kernel(const double* __restrict__ X, int64_t n, int k,
-                                const int* __restrict__ perm, int kpad, int kc, int kcpad,
-                                __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl,
-                                float* __restrict__ Xf) {
+                                const int* __restrict__ perm, int k16, int kc, int kx,
+                                __nv_bfloat16* __restrict__ Xp, float* __restrict__ Xf) {
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (idx >= n * kpad) return;
-  const int64_t s = idx / kpad;
-  const int j = static_cast<int>(idx - s * kpad);
+  if (idx >= n * kx) return;
+  const int64_t s = idx / kx;
+  const int e = static_cast<int>(idx - s * kx);
   double v = 0.0;
-  if (j < k) v = X[s * k + perm[j]];
-  const __nv_bfloat16 h = __double2bfloat16(v);
-  Xh[idx] = h;
-  if (j < kcpad) {
-    const double rem = (j < kc) ? v - static_cast<double>(__bfloat162float(h)) : 0.0;
-    Xl[s * kcpad + j] = __double2bfloat16(rem);
+  if (e < k16) {
+    if (e < k) v = static_cast<double>(__bfloat162float(__double2bfloat16(X[s * k + perm[e]])));
+  } else if (e - k16 < kc) {
+    const double x = X[s * k + perm[e - k16]];
+    v = x - static_cast<double>(__bfloat162float(__double2bfloat16(x)));
   }
-  if (j < k) Xf[s * k + j] = static_cast<float>(X[s * k + j]);
+  Xp[idx] = __double2bfloat16(v);
+  if (e < k) Xf[s * k + e] = static_cast<float>(X[s * k + e]);
 }
 
 // lin[c*k + i] = prefix[tile] + sum over the remaining rows s in [128*tile, t) of w_c(y_s) x_{s,i}.
@@ -399,21 +400,21 @@ sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const 
     enc.kc = static_cast<int>(enc.perm.size());
     for (int j = 0; j < k; ++j)
       if (!h[j]) enc.perm.push_back(j);
-    enc.kpad = (k + 63) / 64 * 64;
-    enc.kcpad = (enc.kc + 63) / 64 * 64;
-    enc.bn = (NC <= 2) ? 128 : 64;
+    enc.k16 = (k + 15) / 16 * 16;
+    enc.kc16 = (enc.kc + 15) / 16 * 16;
+    enc.kx = (enc.k16 + enc.kc16 + 63) / 64 * 64;
+    enc.kt = (2 * enc.k16 + 63) / 64 * 64;
+    enc.bn = (NC <= 3) ? tc_tile_rows(NC, enc.kx, enc.kt) : 0;
     if ((st = to_device(ctx, enc.perm_dev, enc.perm.data(), k * sizeof(int))) != SPS_OK) return bail(st);
-    if (enc.Xh.reserve(static_cast<size_t>(n) * enc.kpad * 2) != cudaSuccess ||
-        enc.Xl.reserve(static_cast<size_t>(n) * std::max(enc.kcpad, 64) * 2) != cudaSuccess ||
+    if (enc.Xp.reserve(static_cast<size_t>(n) * enc.kx * 2) != cudaSuccess ||
         ctx->Xf.reserve(static_cast<size_t>(n) * k * 4) != cudaSuccess)
       return bail(SPS_ERR_OOM);
-    const int64_t tot2 = n * enc.kpad;
+    const int64_t tot2 = n * enc.kx;
     encode_x_kernel<<<static_cast<unsigned>((tot2 + 255) / 256), 256>>>(
-        ctx->Xd.as<double>(), n, k, enc.perm_dev.as<int>(), enc.kpad, enc.kc, enc.kcpad,
-        enc.Xh.as<__nv_bfloat16>(), enc.Xl.as<__nv_bfloat16>(), ctx->Xf.as<float>()); ++ctx->launches;
+        ctx->Xd.as<double>(), n, k, enc.perm_dev.as<int>(), enc.k16, enc.kc, enc.kx,
+        enc.Xp.as<__nv_bfloat16>(), ctx->Xf.as<float>()); ++ctx->launches;
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(SPS_ERR_CUDA);
-    if ((st = make_map_bf16(ctx, &enc.mapXh, enc.Xh.ptr, n, enc.kpad, enc.bn)) != SPS_OK) return bail(st);
-    if (enc.kcpad > 0 && (st = make_map_bf16(ctx, &enc.mapXl, enc.Xl.ptr, n, enc.kcpad, enc.bn)) != SPS_OK)
+    if (enc.bn > 0 && (st = make_map_bf16(ctx, &enc.mapX, enc.Xp.ptr, n, enc.kx, enc.bn)) != SPS_OK)
       return bail(st);
   }
   // covariate means and prefix sums of the linear term, host FP64 in observation order

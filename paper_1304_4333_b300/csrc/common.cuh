@@ -44,26 +44,28 @@ struct DevBuf {
   template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
 
-// Encoding of X for the tensor-core path: columns permuted so that the columns that are not
-// exact in BF16 ("continuous") come first. Xh = bf16(X), Xl = bf16(X - Xh) for the first kc
-// columns (zero for the exact ones). Row pitch kpad / kcpad elements (multiples of 64).
+// Encoding of X for the tensor-core path. Columns are permuted so that the columns that are not
+// exact in BF16 ("continuous") come first. Each observation row holds [Xh | Xl]:
+// Xh = bf16(x) in elements [0, k16), Xl = bf16(x - Xh) of the continuous columns in
+// [k16, k16 + kc16) (k16, kc16: k and kc rounded up to 16), zero padding up to kx (a multiple of
+// 64, the 128-byte swizzle row). Theta operand rows hold [bf16(theta log2 e) | low part] in
+// [0, k16) and [k16, 2 k16), padded to kt.
 struct XEncoding {
   int k = 0, kc = 0;          // covariates, continuous covariates
-  int kpad = 0, kcpad = 0;    // padded widths of Xh and Xl (64-element K blocks)
-  int bn = 128;               // observation rows per TMA box of X
+  int k16 = 0, kc16 = 0;      // k and kc rounded up to 16 (MMA K step)
+  int kx = 0, kt = 0;         // row widths of the X and theta operands (multiples of 64)
+  int bn = 0;                 // observation rows per tile (TMA box of X); 0: no tile fits
   std::vector<int> perm;      // internal column j holds original column perm[j]
   DevBuf perm_dev;            // int [k]
-  DevBuf Xh, Xl;              // bf16 [n x kpad], [n x kcpad]
-  CUtensorMap mapXh;
-  CUtensorMap mapXl;
+  DevBuf Xp;                  // bf16 [n x kx]
+  CUtensorMap mapX;
 };
 
 // Per-call scratch of the likelihood kernels.
 struct LoglikScratch {
-  DevBuf thetaH, thetaL;      // bf16 [NC * Ppad x kpad] operand rows (class-major row blocks)
-  int64_t ppad_cap = 0;       // particle capacity of thetaH/thetaL
-  CUtensorMap mapTH;
-  CUtensorMap mapTL;
+  DevBuf thetaP;              // bf16 [NC * Ppad x kt] operand rows (class-major row blocks)
+  int64_t ppad_cap = 0;       // particle capacity of thetaP
+  CUtensorMap mapT;
   DevBuf partial;             // FP64 partial sums [slices x Ppad]
   DevBuf flag;                // int error/timeout flag
   DevBuf theta_in, ll_out, grad_out, aux;   // staging for host-memory calls
@@ -157,6 +159,8 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
 sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                            int precision);
 sps_status ensure_lin(sps_ctx* ctx, int64_t t);
+// Observation rows per tensor-core tile for NC = C - 1 outcomes and operand widths kx, kt.
+int tc_tile_rows(int NC, int kx, int kt);
 // Start/stop event of one timed launch of the fused kernel (no-ops when timing is off).
 void hot_begin(sps_ctx* ctx);
 void hot_end(sps_ctx* ctx);

@@ -9,38 +9,49 @@
 //                    (softplus(eta) - eta/2 = |eta|/2 + log(1 + e^{-|eta|}) is even in eta);
 //   C > 2:           ll = sum_c theta_c' sum_{s: y_s = c} x_s - sum_s LSE_s(0, eta_{s,1..C-1}).
 // The linear terms are FP64 dot products with FP64 prefix sums of X (finalize kernel); this
-// kernel produces the FP64 sums of the non-linear terms.
+// kernel produces the FP64 sums of the non-linear terms. Theta enters the tensor cores scaled by
+// log2(e), so the accumulators hold u = eta log2(e) and each exponential is one ex2. Logarithms
+// are taken once per tile, of running products of the (1 + 2^{-|u|}) factors (binary) or of the
+// shifted sums of exponentials (C > 2), kept in four independent chains whose binary exponents
+// are moved to an integer as they grow.
+//
+// Operands (128-byte-swizzled BF16, K blocks of 64 elements): an X row holds [Xh | Xl] with
+// Xh = bf16(x) over k16 columns and Xl = bf16(x - Xh) over the kc16 continuous columns; a theta
+// row holds [Th | Tl] of theta log2(e) over k16 columns. Per tile and class the MMA warp issues
+//     u_c[128 particles x BN obs] = Th_c Xh' + Tl_c Xh' + Th_c Xl'
+// (the Tl Xl' product, relative size 2^-16, is dropped).
 //
 // Kernel structure (one CTA per SM, persistent over work items):
-//   warp 0      TMA producer: theta operand tiles (double-buffered) and X tiles (stage ring),
-//               128-byte-swizzled bf16, cp.async.bulk.tensor with mbarrier transaction counts;
-//   warp 1      allocates TMEM, then one thread issues tcgen05.mma:
-//                 eta_c[128 particles x BN obs] = Th_c Xh' + Tl_c Xh' + Th_c Xl'
-//               (split BF16: theta = Th + Tl, X = Xh + Xl, the Tl Xl' product dropped),
-//               FP32 accumulators in TMEM, two accumulator buffers;
-//   warps 4..11 two epilogue warpgroups; TMEM lane = particle, so each thread reduces its own
-//               particle's row: FP32 per tile, FP64 across tiles.
+//   warp 0      TMA producer: theta tiles (double-buffered) and X tiles (stage ring),
+//               cp.async.bulk.tensor with mbarrier transaction counts;
+//   warp 1      allocates TMEM, then one thread issues tcgen05.mma into two TMEM accumulators;
+//   warps 2..9  two epilogue groups of four warps; warp w reads TMEM lane quadrant w % 4, so a
+//               group covers the 128 lanes (lane = particle) and owns one accumulator, i.e.
+//               every second observation tile; each thread reduces its own particle's row:
+//               FP32 within a tile, FP64 across tiles.
 // Work item = (observation chunk, particle tile), chunk-major so that concurrent CTAs read the
-// same X chunk through L2. Partial sums go to a [chunk][warpgroup][particle] FP64 buffer that
-// the finalize kernel sums in a fixed order: the result is deterministic.
+// same X chunk through L2. Partial sums go to a [chunk][group][particle] FP64 buffer that the
+// finalize kernel sums in a fixed order: the result is deterministic.
 //
 // Every mbarrier wait is bounded (wall-clock limit); on a timeout the CTA raises a flag, drains
-// its own copies and MMAs with bounded waits, frees TMEM and returns.
+// its own copies and MMAs with bounded waits, frees TMEM and returns. Warps reconverge before
+// every .sync.aligned tcgen05 instruction, and the producer waits for every stage it filled to be
+// released before the CTA exits, so no asynchronous arrive is still in flight at exit.
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "common.cuh"
 
 namespace sps {
 namespace {
 
-constexpr int kBM = 128;          // particles per tile = TMEM lanes
-constexpr int kNWG = 2;           // epilogue warpgroups
-constexpr int kNBUF = 2;          // TMEM accumulator buffers (one per epilogue warpgroup)
-constexpr int kThreads = 128 * (2 + kNWG);   // warps 0-3 (producer, MMA, 2 idle) + epilogue
-constexpr int kKB = 64;           // K-block width (elements): one 128-byte swizzle row
-constexpr uint32_t kTileA = kBM * 128;       // bytes of one 128-row K block
+constexpr int kBM = 128;                        // particles per tile = TMEM lanes
+constexpr int kNWG = 2;                         // epilogue groups = TMEM accumulators
+constexpr int kThreads = 32 * (2 + 4 * kNWG);   // producer, MMA, 8 epilogue warps
+constexpr int kKB = 64;                         // K-block width (elements): one 128-byte swizzle row
+constexpr uint32_t kTileA = kBM * 128;          // bytes of one 128-row K block
 
 struct TcParams {
   int ppad;            // padded particle count (multiple of 128)
@@ -50,63 +61,89 @@ struct TcParams {
   int chunk_tiles;     // observation tiles per work item
   int n_chunks;
   int n_items;
-  int kb_h;            // K blocks of Xh / theta operands
-  int kb_l;            // K blocks of Xl
-  int ksteps_h;        // 16-wide MMA K steps over Xh (ceil(k/16))
-  int ksteps_l;        // over Xl (ceil(kc/16)); 0 when every column is exact
+  int kbx;             // K blocks of an X row
+  int kbt;             // K blocks of a theta row
+  int k16;             // element offset of the low parts in both rows
+  int ksh;             // 16-wide MMA K steps over Xh (k16 / 16)
+  int ksl;             // over Xl (kc16 / 16); 0 when every column is exact
   int stages;          // X ring depth
   int th_bufs;         // theta buffers (1 or 2)
-  int th_row_stride;   // rows between classes in the theta operand maps (= ppad)
+  int th_row_stride;   // rows between classes in the theta operand map (= ppad)
   double* partial;     // [n_chunks][kNWG][ppad]
   int* flag;           // set to 1 on a timeout
   unsigned long long timeout_ns;
 };
 
 struct SmemLayout {
-  uint32_t th_bytes;   // one theta buffer (hi + lo, all classes)
-  uint32_t x_bytes;    // one X stage (Xh + Xl blocks)
+  uint32_t th_bytes;   // one theta buffer (all classes)
+  uint32_t x_bytes;    // one X stage
   uint32_t off_th, off_x, off_bar;
   uint32_t total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int NC, int BN, int kb_h, int kb_l, int stages,
-                                                  int th_bufs) {
+__host__ __device__ inline SmemLayout smem_layout(int NC, int BN, int kbx, int kbt, int stages, int th_bufs) {
   SmemLayout L;
-  L.th_bytes = static_cast<uint32_t>(2 * NC * kb_h) * kTileA;
-  L.x_bytes = static_cast<uint32_t>(kb_h + kb_l) * static_cast<uint32_t>(BN) * 128u;
+  L.th_bytes = static_cast<uint32_t>(NC * kbt) * kTileA;
+  L.x_bytes = static_cast<uint32_t>(kbx) * static_cast<uint32_t>(BN) * 128u;
   L.off_th = 0;
   L.off_x = L.off_th + th_bufs * L.th_bytes;
   L.off_bar = L.off_x + stages * L.x_bytes;
-  // barriers: x_full[st], x_empty[st], th_full[2], th_empty[2], acc_full[NBUF], acc_empty[NBUF],
+  // barriers: x_full[st], x_empty[st], th_full[2], th_empty[2], acc_full[2], acc_empty[2],
   // drain; then tmem base (u32) and abort flag (int)
-  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * kNBUF + 1) + 16;
+  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * kNWG + 1) + 16;
   return L;
+}
+
+constexpr uint32_t kSmemBudget = 227 * 1024 - 1024;
+
+// Pipeline depth for a tile shape: prefer double-buffered theta with at least 4 X stages, then
+// single-buffered theta; false when fewer than 2 stages fit.
+bool pick_stages(int NC, int BN, int kbx, int kbt, int* stages, int* th_bufs) {
+  for (int tb = 2; tb >= 1; --tb) {
+    int st = 0;
+    for (int s = 8; s >= 2; --s)
+      if (smem_layout(NC, BN, kbx, kbt, s, tb).total <= kSmemBudget) { st = s; break; }
+    if (st >= 4 || (tb == 1 && st >= 2)) {
+      *stages = st;
+      *th_bufs = tb;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Descriptor of the 16-element K slice starting at element `e` of an operand tile made of
+// 64-element K blocks of `rows` rows each.
+__device__ __forceinline__ uint64_t kslice_desc(uint32_t base, int rows, int e) {
+  return ptx::sdesc_sw128(base + static_cast<uint32_t>((e >> 6) * rows * 128)) +
+         static_cast<uint64_t>(((e & 63) * 2) >> 4);
 }
 
 template <int NC, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
-loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constant__ CUtensorMap mapXl,
-                 const __grid_constant__ CUtensorMap mapTH, const __grid_constant__ CUtensorMap mapTL,
+loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                  const TcParams prm) {
+  constexpr int NBUF = kNWG;
+  static_assert(NBUF * NC * BN <= 512, "TMEM has 512 columns");
+  constexpr uint32_t kTmemCols = (NBUF * NC * BN <= 256) ? 256u : 512u;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the 128B-swizzle atoms
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const SmemLayout L = smem_layout(NC, BN, prm.kb_h, prm.kb_l, prm.stages, prm.th_bufs);
+  const SmemLayout L = smem_layout(NC, BN, prm.kbx, prm.kbt, prm.stages, prm.th_bufs);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar);
   uint64_t* x_full = bars;
   uint64_t* x_empty = x_full + prm.stages;
   uint64_t* th_full = x_empty + prm.stages;
   uint64_t* th_empty = th_full + 2;
   uint64_t* acc_full = th_empty + 2;
-  uint64_t* acc_empty = acc_full + kNBUF;
-  uint64_t* drain = acc_empty + kNBUF;
+  uint64_t* acc_empty = acc_full + NBUF;
+  uint64_t* drain = acc_empty + NBUF;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  constexpr uint32_t kTmemCols = (kNBUF * NC * BN <= 256) ? 256u : 512u;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < prm.stages; ++i) {
@@ -117,9 +154,9 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
       ptx::mbar_init(&th_full[i], 1);
       ptx::mbar_init(&th_empty[i], 1);
     }
-    for (int i = 0; i < kNBUF; ++i) {
+    for (int i = 0; i < NBUF; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
-      ptx::mbar_init(&acc_empty[i], 4);   // one arrive per epilogue warp of the owning group
+      ptx::mbar_init(&acc_empty[i], 4);   // one arrive per warp of the owning group
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -138,50 +175,40 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      ptx::prefetch_map(&mapXh);
-      ptx::prefetch_map(&mapTH);
-      ptx::prefetch_map(&mapTL);
-      if (prm.kb_l > 0) ptx::prefetch_map(&mapXl);
+      ptx::prefetch_map(&mapX);
+      ptx::prefetch_map(&mapT);
       int st = 0;
       uint32_t xph = 0;
       int tb = 0;
       uint32_t tph = 0;
       bool ok = true;
-      // parity of the last fill issued on each stage / theta buffer, for the drain on abort
-      uint32_t issued_x = 0, issued_t = 0;
-      uint32_t last_par_x[16];
-      uint32_t last_par_t[2] = {0, 0};
+      // bit s: stage / theta buffer s was filled; parity of its last fill
+      uint32_t issued_x = 0, issued_t = 0, par_x = 0, par_t = 0;
       for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
         const int chunk = item / prm.n_ptiles;
         const int ptile = item - chunk * prm.n_ptiles;
         const int tile_lo = chunk * prm.chunk_tiles;
         const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
-        // theta operand tiles of this particle tile
         if (!ptx::mbar_wait_bounded(&th_empty[tb], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
         uint8_t* thb = smem + L.off_th + tb * L.th_bytes;
         ptx::mbar_arrive_expect_tx(&th_full[tb], L.th_bytes);
         for (int c = 0; c < NC; ++c) {
           const int row = c * prm.th_row_stride + ptile * kBM;
-          for (int kb = 0; kb < prm.kb_h; ++kb) {
-            ptx::tma_load_2d(thb + (c * prm.kb_h + kb) * kTileA, &mapTH, &th_full[tb], kb * kKB, row);
-            ptx::tma_load_2d(thb + ((NC + c) * prm.kb_h + kb) * kTileA, &mapTL, &th_full[tb], kb * kKB, row);
-          }
+          for (int kb = 0; kb < prm.kbt; ++kb)
+            ptx::tma_load_2d(thb + (c * prm.kbt + kb) * kTileA, &mapT, &th_full[tb], kb * kKB, row);
         }
         issued_t |= 1u << tb;
-        last_par_t[tb] = tph;
+        par_t = (par_t & ~(1u << tb)) | (tph << tb);
         if (++tb == prm.th_bufs) { tb = 0; tph ^= 1u; }
-        // observation tiles
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
           if (!ptx::mbar_wait_bounded(&x_empty[st], xph ^ 1u, abort_flag, limit)) { ok = false; break; }
           uint8_t* xb = smem + L.off_x + st * L.x_bytes;
           ptx::mbar_arrive_expect_tx(&x_full[st], L.x_bytes);
           const int obs = tile * BN;
-          for (int kb = 0; kb < prm.kb_h; ++kb)
-            ptx::tma_load_2d(xb + kb * BN * 128, &mapXh, &x_full[st], kb * kKB, obs);
-          for (int kb = 0; kb < prm.kb_l; ++kb)
-            ptx::tma_load_2d(xb + (prm.kb_h + kb) * BN * 128, &mapXl, &x_full[st], kb * kKB, obs);
+          for (int kb = 0; kb < prm.kbx; ++kb)
+            ptx::tma_load_2d(xb + kb * BN * 128, &mapX, &x_full[st], kb * kKB, obs);
           issued_x |= 1u << st;
-          last_par_x[st] = xph;
+          par_x = (par_x & ~(1u << st)) | (xph << st);
           if (++st == prm.stages) { st = 0; xph ^= 1u; }
         }
       }
@@ -189,9 +216,16 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
         // drain: wait (bounded) for every copy this thread issued before the CTA exits
         volatile int no_abort = 0;
         for (int s = 0; s < prm.stages; ++s)
-          if (issued_x & (1u << s)) ptx::mbar_wait_bounded(&x_full[s], last_par_x[s], &no_abort, limit);
+          if (issued_x & (1u << s)) ptx::mbar_wait_bounded(&x_full[s], (par_x >> s) & 1u, &no_abort, limit);
         for (int b = 0; b < 2; ++b)
-          if (issued_t & (1u << b)) ptx::mbar_wait_bounded(&th_full[b], last_par_t[b], &no_abort, limit);
+          if (issued_t & (1u << b)) ptx::mbar_wait_bounded(&th_full[b], (par_t >> b) & 1u, &no_abort, limit);
+      } else {
+        // tail: stages are released by asynchronous tcgen05.commit arrives; wait until every
+        // stage and theta buffer filled here has been released
+        for (int s = 0; s < prm.stages; ++s)
+          if (issued_x & (1u << s)) ptx::mbar_wait_bounded(&x_empty[s], (par_x >> s) & 1u, abort_flag, limit);
+        for (int b = 0; b < 2; ++b)
+          if (issued_t & (1u << b)) ptx::mbar_wait_bounded(&th_empty[b], (par_t >> b) & 1u, abort_flag, limit);
       }
     }
   } else if (warp == 1) {
@@ -213,8 +247,8 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
         ptx::tc_fence_after();
         const uint32_t thb = ptx::smem_u32(smem + L.off_th + tb * L.th_bytes);
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
-          const int buf = acc_count % kNBUF;
-          const uint32_t aph = (acc_count / kNBUF) & 1u;
+          const int buf = acc_count % NBUF;
+          const uint32_t aph = (acc_count / NBUF) & 1u;
           if (!ptx::mbar_wait_bounded(&acc_empty[buf], aph ^ 1u, abort_flag, limit)) { ok = false; break; }
           if (!ptx::mbar_wait_bounded(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
           ptx::tc_fence_after();
@@ -222,29 +256,13 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const uint32_t d = tmem_base + static_cast<uint32_t>((buf * NC + c) * BN);
-            uint32_t accum = 0;
-            // Th_c * Xh'
-            for (int ks = 0; ks < prm.ksteps_h; ++ks) {
-              const int kb = ks >> 2, kk = ks & 3;
-              const uint64_t a = ptx::sdesc_sw128(thb + (c * prm.kb_h + kb) * kTileA) + 2 * kk;
-              const uint64_t b = ptx::sdesc_sw128(xb + kb * BN * 128) + 2 * kk;
-              ptx::mma_bf16(d, a, b, idesc, accum);
-              accum = 1;
-            }
-            // Tl_c * Xh'
-            for (int ks = 0; ks < prm.ksteps_h; ++ks) {
-              const int kb = ks >> 2, kk = ks & 3;
-              const uint64_t a = ptx::sdesc_sw128(thb + ((NC + c) * prm.kb_h + kb) * kTileA) + 2 * kk;
-              const uint64_t b = ptx::sdesc_sw128(xb + kb * BN * 128) + 2 * kk;
-              ptx::mma_bf16(d, a, b, idesc, 1);
-            }
-            // Th_c * Xl' over the continuous columns
-            for (int ks = 0; ks < prm.ksteps_l; ++ks) {
-              const int kb = ks >> 2, kk = ks & 3;
-              const uint64_t a = ptx::sdesc_sw128(thb + (c * prm.kb_h + kb) * kTileA) + 2 * kk;
-              const uint64_t b = ptx::sdesc_sw128(xb + (prm.kb_h + kb) * BN * 128) + 2 * kk;
-              ptx::mma_bf16(d, a, b, idesc, 1);
-            }
+            const uint32_t tc = thb + static_cast<uint32_t>(c * prm.kbt) * kTileA;
+            for (int i = 0; i < prm.ksh; ++i)   // Th_c Xh'
+              ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, 16 * i), idesc, i > 0);
+            for (int i = 0; i < prm.ksh; ++i)   // Tl_c Xh'
+              ptx::mma_bf16(d, kslice_desc(tc, kBM, prm.k16 + 16 * i), kslice_desc(xb, BN, 16 * i), idesc, 1);
+            for (int i = 0; i < prm.ksl; ++i)   // Th_c Xl' over the continuous columns
+              ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, prm.k16 + 16 * i), idesc, 1);
           }
           issued_any = true;
           ptx::mma_commit(&x_empty[st]);
@@ -256,20 +274,19 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
         if (++tb == prm.th_bufs) { tb = 0; tph ^= 1u; }
       }
       if (*abort_flag && issued_any) {
-        // wait (bounded) until every MMA this thread issued has completed
         ptx::mma_commit(drain);
         volatile int no_abort = 0;
         ptx::mbar_wait_bounded(drain, 0, &no_abort, limit);
       }
     }
-  } else if (warp >= 4) {
+  } else {
     // ------------------------------------------------------------------ epilogue
-    const int wg = (warp - 4) >> 2;
+    const int wg = (warp - 2) >> 2;
     const int quad = warp & 3;
     const int row = quad * 32 + lane;                 // particle within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
-    constexpr float kLog2e = 1.4426950408889634f;
     constexpr float kLn2 = 0.6931471805599453f;
+    constexpr int NCH = BN / 32;                      // 32-column chunks per tile
     uint32_t acc_count = 0;
     bool ok = true;
     for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
@@ -279,77 +296,104 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
       const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
       double acc64 = 0.0;
       for (int tile = tile_lo; tile < tile_hi; ++tile, ++acc_count) {
-        const int buf = acc_count % kNBUF;
-        if ((buf % kNWG) != wg) continue;
-        const uint32_t aph = (acc_count / kNBUF) & 1u;
-        if (!ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit)) { ok = false; break; }
+        const int buf = acc_count % NBUF;
+        if (buf != wg) continue;
+        const uint32_t aph = (acc_count / NBUF) & 1u;
+        // every lane waits; the vote reconverges the warp before the .sync.aligned TMEM loads
+        ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit));
+        if (!ok) break;
         ptx::tc_fence_after();
         const int valid = min(BN, prm.t - tile * BN);
-        float lin_acc = 0.f;     // sum of |eta|/2 (binary) or of the LSE shifts m (C > 2)
-        float prod = 1.f;        // running product of the log arguments, renormalised
-        int pexp = 0;            // binary exponent taken out of prod
-        const uint32_t col0 = static_cast<uint32_t>(buf * NC * BN);
-#pragma unroll 1
-        for (int j0 = 0; j0 < BN; j0 += 32) {
-          if constexpr (NC == 1) {
-            float v[32];
-            ptx::tmem_ld_32x32b_x32(tmem_base + lane_base + col0 + j0, v);
-            ptx::tmem_wait_ld();
+        // four independent chains: sums of |u| (binary) or of the shifts m (C > 2), and products
+        // of the log arguments, each factor below 2 (binary) or NC + 1 (C > 2)
+        float la[4] = {0.f, 0.f, 0.f, 0.f};
+        float pr[4] = {1.f, 1.f, 1.f, 1.f};
+        int pexp = 0;
+        const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN);
+        auto renorm = [&]() {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int bits = __float_as_int(pr[q]);
+            pexp += (bits >> 23) - 127;
+            pr[q] = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
+          }
+        };
+        if constexpr (NC == 1) {
+          // double-buffered TMEM loads: the next 32 columns are in flight while the current
+          // ones are reduced
+          static_assert(NCH % 2 == 0, "chunk pairs");
+          float va[32], vb[32];
+          auto reduce = [&](const float (&v)[32], int j0) {
             if (j0 + 32 <= valid) {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 const float a = fabsf(v[j]);
-                lin_acc += a;
-                const float e = ptx::ex2_approx(-a * kLog2e);
-                prod = fmaf(prod, e, prod);
+                la[j & 3] += a;
+                pr[j & 3] = fmaf(pr[j & 3], ptx::ex2_approx(-a), pr[j & 3]);
               }
             } else {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                const bool in = (j0 + j) < valid;
+                const bool in = (j0 + j < valid);
                 const float a = in ? fabsf(v[j]) : 0.f;
-                lin_acc += a;
-                const float e = in ? ptx::ex2_approx(-a * kLog2e) : 0.f;
-                prod = fmaf(prod, e, prod);
+                const float e = in ? ptx::ex2_approx(-a) : 0.f;
+                la[j & 3] += a;
+                pr[j & 3] = fmaf(pr[j & 3], e, pr[j & 3]);
               }
             }
-          } else {
+          };
+          ptx::tmem_ld_32x32b_x32(tbase, va);
+          ptx::tmem_wait_ld();
+#pragma unroll 1
+          for (int ch = 0; ch < NCH; ch += 2) {
+            ptx::tmem_ld_32x32b_x32(tbase + (ch + 1) * 32, vb);
+            reduce(va, ch * 32);
+            ptx::tmem_wait_ld();
+            if (ch + 2 < NCH) {
+              ptx::tmem_ld_32x32b_x32(tbase + (ch + 2) * 32, va);
+            } else {
+              // every column of the accumulator is in registers: hand it back to the MMA warp
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+            }
+            reduce(vb, (ch + 1) * 32);
+            if (ch + 2 < NCH) ptx::tmem_wait_ld();
+            if ((ch & 6) == 6) renorm();   // every 8 chunks: at most 64 factors below 2 per chain
+          }
+        } else {
+#pragma unroll 1
+          for (int ch = 0; ch < NCH; ++ch) {
             float v[NC][32];
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-              ptx::tmem_ld_32x32b_x32(tmem_base + lane_base + col0 + c * BN + j0, v[c]);
+            for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
             ptx::tmem_wait_ld();
+            if (ch == NCH - 1) {
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+            }
+            const int j0 = ch * 32;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               float m = 0.f;
 #pragma unroll
               for (int c = 0; c < NC; ++c) m = fmaxf(m, v[c][j]);
-              const float ms = m * kLog2e;
-              float s = ptx::ex2_approx(-ms);
+              float sx = ptx::ex2_approx(-m);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) s += ptx::ex2_approx(fmaf(v[c][j], kLog2e, -ms));
+              for (int c = 0; c < NC; ++c) sx += ptx::ex2_approx(v[c][j] - m);
               const bool in = (j0 + j) < valid;
-              lin_acc += in ? m : 0.f;
-              prod *= in ? s : 1.f;
-              if ((j & 15) == 15) {   // s < C <= 4: renormalise every 16 factors
-                const int bits = __float_as_int(prod);
-                pexp += (bits >> 23) - 127;
-                prod = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
-              }
+              la[j & 3] += in ? m : 0.f;
+              pr[j & 3] *= in ? sx : 1.f;
             }
-          }
-          if constexpr (NC == 1) {   // factors in [1, 2]: renormalise every 32
-            const int bits = __float_as_int(prod);
-            pexp += (bits >> 23) - 127;
-            prod = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
+            if ((ch & 3) == 3) renorm();   // every 4 chunks: at most 32 factors below 4 per chain
           }
         }
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
-        const float logpart = kLn2 * (static_cast<float>(pexp) + ptx::lg2_approx(prod));
+        renorm();
+        const float pm = (pr[0] * pr[1]) * (pr[2] * pr[3]);   // product of four mantissas < 16
+        const float lsum = (la[0] + la[1]) + (la[2] + la[3]);
         const float scale = (NC == 1) ? 0.5f : 1.0f;
-        acc64 += static_cast<double>(fmaf(scale, lin_acc, logpart));
+        acc64 += static_cast<double>(kLn2 * (fmaf(scale, lsum, static_cast<float>(pexp)) + ptx::lg2_approx(pm)));
       }
       if (!ok) break;
       prm.partial[(static_cast<size_t>(chunk) * kNWG + wg) * prm.ppad + ptile * kBM + row] = acc64;
@@ -360,12 +404,13 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapXh, const __grid_constan
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicExch(prm.flag, 1);
   if (warp == 1) {
+    __syncwarp();   // lane 0 ran the MMA role alone: reconverge before the aligned dealloc
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem_base, kTmemCols);
   }
 }
 
-// ll[p] = lin_p - sum over chunks and warpgroups of partial (fixed order), lin_p = theta_p . lin
+// ll[p] = lin_p - sum over chunks and groups of partial (fixed order), lin_p = theta_p . lin
 // with lin [NC x k] in the original column order.
 __global__ void loglik_finalize_kernel(const double* __restrict__ theta, int64_t P, int D,
                                        const double* __restrict__ lin, const double* __restrict__ partial,
@@ -380,134 +425,147 @@ __global__ void loglik_finalize_kernel(const double* __restrict__ theta, int64_t
   ll[p] = a - s;
 }
 
-// theta [P x D] FP64 (original order, class-major) -> Th, Tl bf16 rows [NC*ppad x kpad] with
-// internal (permuted) columns; padding rows/columns zero.
+// theta [P x D] FP64 (original order, class-major) -> operand rows [NC*ppad x kt] bf16 holding
+// [hi(theta log2 e) | lo(theta log2 e)] over the internal (permuted) columns; padding zero.
 __global__ void encode_theta_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
-                                    const int* __restrict__ perm, int kpad, int ppad,
-                                    __nv_bfloat16* __restrict__ th, __nv_bfloat16* __restrict__ tl) {
+                                    const int* __restrict__ perm, int k16, int kt, int ppad,
+                                    __nv_bfloat16* __restrict__ out) {
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  const int64_t total = static_cast<int64_t>(NC) * ppad * kpad;
+  const int64_t total = static_cast<int64_t>(NC) * ppad * k16;
   if (idx >= total) return;
-  const int j = static_cast<int>(idx % kpad);
-  const int64_t r = idx / kpad;
+  const int j = static_cast<int>(idx % k16);
+  const int64_t r = idx / k16;
   const int c = static_cast<int>(r / ppad);
   const int64_t p = r - static_cast<int64_t>(c) * ppad;
   double v = 0.0;
-  if (p < P && j < k) v = theta[p * (static_cast<int64_t>(NC) * k) + c * k + perm[j]];
+  if (p < P && j < k) v = theta[p * (static_cast<int64_t>(NC) * k) + c * k + perm[j]] * 1.4426950408889634;
   const __nv_bfloat16 h = __double2bfloat16(v);
   const double rem = v - static_cast<double>(__bfloat162float(h));
-  th[idx] = h;
-  tl[idx] = __double2bfloat16(rem);
+  __nv_bfloat16* rowp = out + r * kt;
+  rowp[j] = h;
+  rowp[k16 + j] = __double2bfloat16(rem);
+  for (int jj = 2 * k16 + j; jj < kt; jj += k16) rowp[jj] = __double2bfloat16(0.0);
 }
 
 template <int NC, int BN>
-sps_status launch_tc(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_bytes) {
+sps_status launch_tc(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_bytes, const CUtensorMap& mapT,
+                     bool timed) {
   auto kern = loglik_tc_kernel<NC, BN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem_bytes));
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
-  const XEncoding& enc = ctx->enc;
-  const CUtensorMap& mxl = enc.kcpad > 0 ? enc.mapXl : enc.mapXh;
-  hot_begin(ctx);
-  kern<<<grid, kThreads, smem_bytes, ctx->stream>>>(enc.mapXh, mxl, ctx->ll.mapTH, ctx->ll.mapTL, prm); ++ctx->launches;
-  hot_end(ctx);
+  if (timed) hot_begin(ctx);
+  kern<<<grid, kThreads, smem_bytes, ctx->stream>>>(ctx->enc.mapX, mapT, prm); ++ctx->launches;
+  if (timed) hot_end(ctx);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("loglik_tc launch: ") + cudaGetErrorString(e));
   return SPS_OK;
 }
 
-}  // namespace
+sps_status launch_any(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_bytes, const CUtensorMap& mapT,
+                      bool timed) {
+  const int NC = ctx->NC, BN = ctx->enc.bn;
+  if (NC == 1 && BN == 256) return launch_tc<1, 256>(ctx, prm, grid, smem_bytes, mapT, timed);
+  if (NC == 1 && BN == 128) return launch_tc<1, 128>(ctx, prm, grid, smem_bytes, mapT, timed);
+  if (NC == 2 && BN == 128) return launch_tc<2, 128>(ctx, prm, grid, smem_bytes, mapT, timed);
+  if (NC == 2 && BN == 64) return launch_tc<2, 64>(ctx, prm, grid, smem_bytes, mapT, timed);
+  if (NC == 3 && BN == 64) return launch_tc<3, 64>(ctx, prm, grid, smem_bytes, mapT, timed);
+  if (NC == 3 && BN == 32) return launch_tc<3, 32>(ctx, prm, grid, smem_bytes, mapT, timed);
+  return fail(ctx, SPS_ERR_UNSUPPORTED, "no tensor-core tile for this shape");
+}
 
-sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll) {
-  const int NC = ctx->NC;
-  if (NC > 3) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision supports at most 4 outcomes");
-  XEncoding& enc = ctx->enc;
-  LoglikScratch& S = ctx->ll;
+// Work decomposition and pipeline depth of one call; false when the tile does not fit.
+bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t* smem_bytes) {
+  const XEncoding& enc = ctx->enc;
+  const int NC = ctx->NC, BN = enc.bn;
   const int ppad = static_cast<int>((P + kBM - 1) / kBM * kBM);
-  // theta operands and their tensor maps
-  if (S.ppad_cap < ppad) {
-    const int64_t cap = std::max<int64_t>(ppad, S.ppad_cap * 3 / 2 / kBM * kBM);
-    const size_t bytes = static_cast<size_t>(NC) * cap * enc.kpad * sizeof(__nv_bfloat16);
-    SPS_CUDA_TRY(S.thetaH.reserve(bytes));
-    SPS_CUDA_TRY(S.thetaL.reserve(bytes));
-    S.ppad_cap = cap;
-  }
-  // maps are rebuilt for the row stride actually used (ppad)
-  SPS_TRY(make_map_bf16(ctx, &S.mapTH, S.thetaH.ptr, static_cast<uint64_t>(NC) * ppad, enc.kpad, kBM));
-  SPS_TRY(make_map_bf16(ctx, &S.mapTL, S.thetaL.ptr, static_cast<uint64_t>(NC) * ppad, enc.kpad, kBM));
-  {
-    const int64_t total = static_cast<int64_t>(NC) * ppad * enc.kpad;
-    const int threads = 256;
-    encode_theta_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.kpad, ppad, S.thetaH.as<__nv_bfloat16>(),
-        S.thetaL.as<__nv_bfloat16>()); ++ctx->launches;
-    SPS_CUDA_TRY(cudaGetLastError());
-  }
-  SPS_TRY(ensure_lin(ctx, t));
-
-  const int BN = enc.bn;
-  TcParams prm{};
-  prm.ppad = ppad;
-  prm.n_ptiles = ppad / kBM;
-  prm.t = static_cast<int>(t);
-  prm.n_tiles = static_cast<int>((t + BN - 1) / BN);
-  prm.kb_h = enc.kpad / kKB;
-  prm.kb_l = enc.kcpad / kKB;
-  prm.ksteps_h = (enc.k + 15) / 16;
-  prm.ksteps_l = (enc.kc + 15) / 16;
-  prm.th_row_stride = ppad;
+  *prm = TcParams{};
+  prm->ppad = ppad;
+  prm->n_ptiles = ppad / kBM;
+  prm->t = static_cast<int>(t);
+  prm->n_tiles = static_cast<int>((t + BN - 1) / BN);
+  prm->kbx = enc.kx / kKB;
+  prm->kbt = enc.kt / kKB;
+  prm->k16 = enc.k16;
+  prm->ksh = enc.k16 / 16;
+  prm->ksl = enc.kc16 / 16;
+  prm->th_row_stride = ppad;
   // chunking: enough work items to balance the persistent grid, items long enough to amortise
   // the theta loads
   const int grid_max = ctx->num_sms;
-  int chunk_tiles = std::max(1, std::min(prm.n_tiles, 32));
+  int chunk_tiles = std::max(1, std::min(prm->n_tiles, 4096 / BN));
+  const int64_t want_items = 8LL * grid_max;
+  while (chunk_tiles > 2 &&
+         static_cast<int64_t>(prm->n_ptiles) * ((prm->n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
+    chunk_tiles /= 2;
+  prm->chunk_tiles = chunk_tiles;
+  prm->n_chunks = std::max(1, (prm->n_tiles + chunk_tiles - 1) / chunk_tiles);
+  prm->n_items = prm->n_tiles > 0 ? prm->n_ptiles * prm->n_chunks : 0;
+  int stages = 0, th_bufs = 0;
+  if (!pick_stages(NC, BN, prm->kbx, prm->kbt, &stages, &th_bufs)) return false;
+  prm->stages = stages;
+  prm->th_bufs = th_bufs;
+  prm->timeout_ns = 2000000000ull;
+  *smem_bytes = smem_layout(NC, BN, prm->kbx, prm->kbt, stages, th_bufs).total + 1024;
+  return true;
+}
+
+}  // namespace
+
+// Observation rows per tensor-core tile: the widest tile for the outcome count that keeps at
+// least three X stages in shared memory (0 when none fits).
+int tc_tile_rows(int NC, int kx, int kt) {
+  const int cands[3][2] = {{256, 128}, {128, 64}, {64, 32}};
+  if (NC < 1 || NC > 3) return 0;
+  for (int q = 0; q < 2; ++q) {
+    const int BN = cands[NC - 1][q];
+    int st = 0, tb = 0;
+    if (pick_stages(NC, BN, kx / kKB, kt / kKB, &st, &tb) && st >= 3) return BN;
+  }
+  const int BN = cands[NC - 1][1];
+  int st = 0, tb = 0;
+  return pick_stages(NC, BN, kx / kKB, kt / kKB, &st, &tb) ? BN : 0;
+}
+
+sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll) {
+  const int NC = ctx->NC;
+  if (NC > 3 || ctx->enc.bn == 0) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision: unsupported shape");
+  XEncoding& enc = ctx->enc;
+  LoglikScratch& S = ctx->ll;
+  TcParams prm;
+  uint32_t smem_bytes = 0;
+  if (!plan_call(ctx, P, t, &prm, &smem_bytes))
+    return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
+  const int ppad = prm.ppad;
+  if (S.ppad_cap < ppad) {
+    const int64_t cap = std::max<int64_t>(ppad, S.ppad_cap * 3 / 2 / kBM * kBM);
+    SPS_CUDA_TRY(S.thetaP.reserve(static_cast<size_t>(NC) * cap * enc.kt * sizeof(__nv_bfloat16)));
+    S.ppad_cap = cap;
+  }
+  SPS_TRY(make_map_bf16(ctx, &S.mapT, S.thetaP.ptr, static_cast<uint64_t>(NC) * ppad, enc.kt, kBM));
   {
-    const int64_t want_items = 8LL * grid_max;
-    while (chunk_tiles > 4 &&
-           static_cast<int64_t>(prm.n_ptiles) * ((prm.n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
-      chunk_tiles /= 2;
+    const int64_t total = static_cast<int64_t>(NC) * ppad * enc.k16;
+    encode_theta_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, ctx->stream>>>(
+        d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, ppad, S.thetaP.as<__nv_bfloat16>());
+    ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
   }
-  prm.chunk_tiles = chunk_tiles;
-  prm.n_chunks = std::max(1, (prm.n_tiles + chunk_tiles - 1) / chunk_tiles);
-  prm.n_items = prm.n_tiles > 0 ? prm.n_ptiles * prm.n_chunks : 0;
-  // shared memory: as many X stages as fit with double-buffered theta, else single
-  const uint32_t budget = 227 * 1024 - 1024;
-  int th_bufs = 2, stages = 0;
-  for (int tb = 2; tb >= 1 && stages < 2; --tb) {
-    th_bufs = tb;
-    for (int st = 8; st >= 2; --st) {
-      if (smem_layout(NC, BN, prm.kb_h, prm.kb_l, st, tb).total <= budget) { stages = st; break; }
-    }
-  }
-  if (stages < 2) return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
-  prm.stages = stages;
-  prm.th_bufs = th_bufs;
+  SPS_TRY(ensure_lin(ctx, t));
   const size_t slices = static_cast<size_t>(prm.n_chunks) * kNWG;
   SPS_CUDA_TRY(S.partial.reserve(slices * ppad * sizeof(double)));
   SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
   prm.partial = S.partial.as<double>();
   prm.flag = S.flag.as<int>();
-  prm.timeout_ns = 2000000000ull;
   SPS_CUDA_TRY(cudaMemsetAsync(prm.flag, 0, sizeof(int), ctx->stream));
-  const uint32_t smem_bytes = smem_layout(NC, BN, prm.kb_h, prm.kb_l, stages, th_bufs).total + 1024;
-  if (prm.n_items > 0) {
-    const int grid = std::min(grid_max, prm.n_items);
-    sps_status s;
-    if (NC == 1) s = launch_tc<1, 128>(ctx, prm, grid, smem_bytes);
-    else if (NC == 2) s = launch_tc<2, 128>(ctx, prm, grid, smem_bytes);
-    else s = launch_tc<3, 64>(ctx, prm, grid, smem_bytes);
-    if (s != SPS_OK) return s;
-  }
-  {
-    const int threads = 256;
-    loglik_finalize_kernel<<<static_cast<unsigned>((P + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        d_theta, P, ctx->D, ctx->lin.as<double>(), prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0,
-        ppad, d_ll); ++ctx->launches;
-    SPS_CUDA_TRY(cudaGetLastError());
-  }
+  if (prm.n_items > 0)
+    SPS_TRY(launch_any(ctx, prm, std::min(ctx->num_sms, prm.n_items), smem_bytes, S.mapT, true));
+  loglik_finalize_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+      d_theta, P, ctx->D, ctx->lin.as<double>(), prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0,
+      ppad, d_ll);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
 }
-
-}  // namespace sps
 
 // ------------------------------------------------------------------------------------------
 // Allocation-free variant of the split-precision log-likelihood (sps_loglik_noalloc).
@@ -523,9 +581,6 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
 // the caller. Its contents persist from the last call; everything that must start at zero is
 // cleared by each call.
 
-#include <mutex>
-
-namespace sps {
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t{32} << 20;   // 32 MiB
@@ -556,68 +611,24 @@ sps_status static_scratch_address(sps_ctx* ctx, unsigned char** out) {
   return SPS_OK;
 }
 
-template <int NC, int BN>
-sps_status launch_tc_maps(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_bytes,
-                          const CUtensorMap& mapTH, const CUtensorMap& mapTL) {
-  auto kern = loglik_tc_kernel<NC, BN>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem_bytes));
-  if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
-  const XEncoding& enc = ctx->enc;
-  const CUtensorMap& mxl = enc.kcpad > 0 ? enc.mapXl : enc.mapXh;
-  kern<<<grid, kThreads, smem_bytes, ctx->stream>>>(enc.mapXh, mxl, mapTH, mapTL, prm); ++ctx->launches;
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("loglik_tc launch: ") + cudaGetErrorString(e));
-  return SPS_OK;
-}
-
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
 sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll) {
   const int NC = ctx->NC;
-  if (NC > 3) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision supports at most 4 outcomes");
+  if (NC > 3 || ctx->enc.bn == 0) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision: unsupported shape");
   const XEncoding& enc = ctx->enc;
-  const int ppad = static_cast<int>((P + kBM - 1) / kBM * kBM);
-  const int BN = enc.bn;
-  TcParams prm{};
-  prm.ppad = ppad;
-  prm.n_ptiles = ppad / kBM;
-  prm.t = static_cast<int>(t);
-  prm.n_tiles = static_cast<int>((t + BN - 1) / BN);
-  prm.kb_h = enc.kpad / kKB;
-  prm.kb_l = enc.kcpad / kKB;
-  prm.ksteps_h = (enc.k + 15) / 16;
-  prm.ksteps_l = (enc.kc + 15) / 16;
-  prm.th_row_stride = ppad;
-  const int grid_max = ctx->num_sms;
-  int chunk_tiles = std::max(1, std::min(prm.n_tiles, 32));
-  {
-    const int64_t want_items = 8LL * grid_max;
-    while (chunk_tiles > 4 &&
-           static_cast<int64_t>(prm.n_ptiles) * ((prm.n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
-      chunk_tiles /= 2;
-  }
-  prm.chunk_tiles = chunk_tiles;
-  prm.n_chunks = std::max(1, (prm.n_tiles + chunk_tiles - 1) / chunk_tiles);
-  prm.n_items = prm.n_tiles > 0 ? prm.n_ptiles * prm.n_chunks : 0;
-  const uint32_t budget = 227 * 1024 - 1024;
-  int th_bufs = 2, stages = 0;
-  for (int tb = 2; tb >= 1 && stages < 2; --tb) {
-    th_bufs = tb;
-    for (int st = 8; st >= 2; --st) {
-      if (smem_layout(NC, BN, prm.kb_h, prm.kb_l, st, tb).total <= budget) { stages = st; break; }
-    }
-  }
-  if (stages < 2) return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
-  prm.stages = stages;
-  prm.th_bufs = th_bufs;
-  // carve the static area: theta hi rows, theta lo rows, partial sums, flag
+  TcParams prm;
+  uint32_t smem_bytes = 0;
+  if (!plan_call(ctx, P, t, &prm, &smem_bytes))
+    return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
+  const int ppad = prm.ppad;
+  // carve the static area: theta operand rows, partial sums, flag
   const size_t slices = static_cast<size_t>(prm.n_chunks) * kNWG;
-  const size_t op_bytes = round256(static_cast<size_t>(NC) * ppad * enc.kpad * sizeof(__nv_bfloat16));
+  const size_t op_bytes = round256(static_cast<size_t>(NC) * ppad * enc.kt * sizeof(__nv_bfloat16));
   const size_t part_bytes = round256(slices * ppad * sizeof(double));
-  const size_t need = 2 * op_bytes + part_bytes + 256;
+  const size_t need = op_bytes + part_bytes + 256;
   if (need > kStaticScratchBytes) {
     char msg[160];
     snprintf(msg, sizeof msg,
@@ -627,41 +638,29 @@ sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, i
   }
   unsigned char* base = nullptr;
   SPS_TRY(static_scratch_address(ctx, &base));
-  __nv_bfloat16* th_hi = reinterpret_cast<__nv_bfloat16*>(base);
-  __nv_bfloat16* th_lo = reinterpret_cast<__nv_bfloat16*>(base + op_bytes);
-  double* partial = reinterpret_cast<double*>(base + 2 * op_bytes);
-  int* flag = reinterpret_cast<int*>(base + 2 * op_bytes + part_bytes);
-  CUtensorMap mapTH, mapTL;
-  SPS_TRY(make_map_bf16(ctx, &mapTH, th_hi, static_cast<uint64_t>(NC) * ppad, enc.kpad, kBM));
-  SPS_TRY(make_map_bf16(ctx, &mapTL, th_lo, static_cast<uint64_t>(NC) * ppad, enc.kpad, kBM));
+  __nv_bfloat16* ops = reinterpret_cast<__nv_bfloat16*>(base);
+  double* partial = reinterpret_cast<double*>(base + op_bytes);
+  int* flag = reinterpret_cast<int*>(base + op_bytes + part_bytes);
+  CUtensorMap mapT;
+  SPS_TRY(make_map_bf16(ctx, &mapT, ops, static_cast<uint64_t>(NC) * ppad, enc.kt, kBM));
   {
-    const int64_t total = static_cast<int64_t>(NC) * ppad * enc.kpad;
-    const int threads = 256;
-    encode_theta_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.kpad, ppad, th_hi, th_lo); ++ctx->launches;
+    const int64_t total = static_cast<int64_t>(NC) * ppad * enc.k16;
+    encode_theta_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, ctx->stream>>>(
+        d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, ppad, ops);
+    ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
   }
   SPS_TRY(ensure_lin(ctx, t));
   prm.partial = partial;
   prm.flag = flag;
-  prm.timeout_ns = 2000000000ull;
   SPS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));   // the flag must start at zero
-  const uint32_t smem_bytes = smem_layout(NC, BN, prm.kb_h, prm.kb_l, stages, th_bufs).total + 1024;
-  if (prm.n_items > 0) {
-    const int grid = std::min(grid_max, prm.n_items);
-    sps_status s;
-    if (NC == 1) s = launch_tc_maps<1, 128>(ctx, prm, grid, smem_bytes, mapTH, mapTL);
-    else if (NC == 2) s = launch_tc_maps<2, 128>(ctx, prm, grid, smem_bytes, mapTH, mapTL);
-    else s = launch_tc_maps<3, 64>(ctx, prm, grid, smem_bytes, mapTH, mapTL);
-    if (s != SPS_OK) return s;
-  }
-  {
-    const int threads = 256;
-    loglik_finalize_kernel<<<static_cast<unsigned>((P + threads - 1) / threads), threads, 0, ctx->stream>>>(
-        d_theta, P, ctx->D, ctx->lin.as<double>(), partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad,
-        d_ll); ++ctx->launches;
-    SPS_CUDA_TRY(cudaGetLastError());
-  }
+  if (prm.n_items > 0)
+    SPS_TRY(launch_any(ctx, prm, std::min(ctx->num_sms, prm.n_items), smem_bytes, mapT, false));
+  loglik_finalize_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+      d_theta, P, ctx->D, ctx->lin.as<double>(), partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad,
+      d_ll);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
 }
 

@@ -25,10 +25,11 @@
 //   warp 0      TMA producer: theta tiles (double-buffered) and X tiles (stage ring),
 //               cp.async.bulk.tensor with mbarrier transaction counts;
 //   warp 1      allocates TMEM, then one thread issues tcgen05.mma into two TMEM accumulators;
-//   warps 2..9  two epilogue groups of four warps; warp w reads TMEM lane quadrant w % 4, so a
-//               group covers the 128 lanes (lane = particle) and owns one accumulator, i.e.
-//               every second observation tile; each thread reduces its own particle's row:
-//               FP32 within a tile, FP64 across tiles.
+//   warps 2..   epilogue groups of four warps; warp w reads TMEM lane quadrant w % 4, so a
+//               group covers the 128 lanes (lane = particle). C = 2: four groups, two per
+//               accumulator, each taking half of its columns; C > 2: two groups, one per
+//               accumulator. Each thread reduces its own particle's row: FP32 within a tile,
+//               FP64 across tiles.
 // Work item = (observation chunk, particle tile), chunk-major so that concurrent CTAs read the
 // same X chunk through L2. Partial sums go to a [chunk][group][particle] FP64 buffer that the
 // finalize kernel sums in a fixed order: the result is deterministic.
@@ -48,8 +49,11 @@ namespace sps {
 namespace {
 
 constexpr int kBM = 128;                        // particles per tile = TMEM lanes
-constexpr int kNWG = 2;                         // epilogue groups = TMEM accumulators
-constexpr int kThreads = 32 * (2 + 4 * kNWG);   // producer, MMA, 8 epilogue warps
+constexpr int kNBUF = 2;                        // TMEM accumulators
+// Epilogue groups of four warps (warp w reads TMEM lane quadrant w % 4): four for C = 2, two
+// sharing each accumulator by halves of its columns; two for C > 2, one per accumulator.
+__host__ __device__ constexpr int nwg_for(int NC) { return NC == 1 ? 4 : 2; }
+__host__ __device__ constexpr int threads_for(int NC) { return 32 * (2 + 4 * nwg_for(NC)); }
 constexpr int kKB = 64;                         // K-block width (elements): one 128-byte swizzle row
 constexpr uint32_t kTileA = kBM * 128;          // bytes of one 128-row K block
 
@@ -69,7 +73,7 @@ struct TcParams {
   int stages;          // X ring depth
   int th_bufs;         // theta buffers (1 or 2)
   int th_row_stride;   // rows between classes in the theta operand map (= ppad)
-  double* partial;     // [n_chunks][kNWG][ppad]
+  double* partial;     // [n_chunks][nwg][ppad]
   int* flag;           // set to 1 on a timeout
   unsigned long long timeout_ns;
 };
@@ -90,7 +94,7 @@ __host__ __device__ inline SmemLayout smem_layout(int NC, int BN, int kbx, int k
   L.off_bar = L.off_x + stages * L.x_bytes;
   // barriers: x_full[st], x_empty[st], th_full[2], th_empty[2], acc_full[2], acc_empty[2],
   // drain; then tmem base (u32) and abort flag (int)
-  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * kNWG + 1) + 16;
+  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * kNBUF + 1) + 16;
   return L;
 }
 
@@ -120,10 +124,13 @@ __device__ __forceinline__ uint64_t kslice_desc(uint32_t base, int rows, int e) 
 }
 
 template <int NC, int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_for(NC), 1)
 loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                  const TcParams prm) {
-  constexpr int NBUF = kNWG;
+  constexpr int NBUF = kNBUF;
+  constexpr int NWG = nwg_for(NC);
+  constexpr int GPB = NWG / NBUF;                 // epilogue groups per accumulator
+  constexpr int COLS = BN / GPB;                  // columns of a tile per group
   static_assert(NBUF * NC * BN <= 512, "TMEM has 512 columns");
   constexpr uint32_t kTmemCols = (NBUF * NC * BN <= 256) ? 256u : 512u;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -156,7 +163,7 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     }
     for (int i = 0; i < NBUF; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
-      ptx::mbar_init(&acc_empty[i], 4);   // one arrive per warp of the owning group
+      ptx::mbar_init(&acc_empty[i], 4 * GPB);   // one arrive per warp of the owning groups
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
@@ -282,11 +289,13 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   } else {
     // ------------------------------------------------------------------ epilogue
     const int wg = (warp - 2) >> 2;
+    const int my_buf = wg / GPB;
+    const int col0 = (wg % GPB) * COLS;               // first column of this group in a tile
     const int quad = warp & 3;
     const int row = quad * 32 + lane;                 // particle within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
     constexpr float kLn2 = 0.6931471805599453f;
-    constexpr int NCH = BN / 32;                      // 32-column chunks per tile
+    constexpr int NCH = COLS / 32;                    // 32-column chunks per group and tile
     uint32_t acc_count = 0;
     bool ok = true;
     for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
@@ -297,19 +306,19 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       double acc64 = 0.0;
       for (int tile = tile_lo; tile < tile_hi; ++tile, ++acc_count) {
         const int buf = acc_count % NBUF;
-        if (buf != wg) continue;
+        if (buf != my_buf) continue;
         const uint32_t aph = (acc_count / NBUF) & 1u;
         // every lane waits; the vote reconverges the warp before the .sync.aligned TMEM loads
         ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit));
         if (!ok) break;
         ptx::tc_fence_after();
-        const int valid = min(BN, prm.t - tile * BN);
+        const int valid = prm.t - tile * BN - col0;   // columns of this group inside [0, t)
         // four independent chains: sums of |u| (binary) or of the shifts m (C > 2), and products
         // of the log arguments, each factor below 2 (binary) or NC + 1 (C > 2)
         float la[4] = {0.f, 0.f, 0.f, 0.f};
         float pr[4] = {1.f, 1.f, 1.f, 1.f};
         int pexp = 0;
-        const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN);
+        const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN + col0);
         auto renorm = [&]() {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -318,16 +327,24 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             pr[q] = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
           }
         };
-        if constexpr (NC == 1) {
-          // double-buffered TMEM loads: the next 32 columns are in flight while the current
-          // ones are reduced
-          static_assert(NCH % 2 == 0, "chunk pairs");
-          float va[32], vb[32];
-          auto reduce = [&](const float (&v)[32], int j0) {
+#pragma unroll 1
+        for (int ch = 0; ch < NCH; ++ch) {
+          float v[NC][32];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
+          ptx::tmem_wait_ld();
+          if (ch == NCH - 1) {
+            // this group's columns are in registers: release its share of the accumulator
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+          }
+          const int j0 = ch * 32;
+          if constexpr (NC == 1) {
             if (j0 + 32 <= valid) {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                const float a = fabsf(v[j]);
+                const float a = fabsf(v[0][j]);
                 la[j & 3] += a;
                 pr[j & 3] = fmaf(pr[j & 3], ptx::ex2_approx(-a), pr[j & 3]);
               }
@@ -335,45 +352,14 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 const bool in = (j0 + j < valid);
-                const float a = in ? fabsf(v[j]) : 0.f;
+                const float a = in ? fabsf(v[0][j]) : 0.f;
                 const float e = in ? ptx::ex2_approx(-a) : 0.f;
                 la[j & 3] += a;
                 pr[j & 3] = fmaf(pr[j & 3], e, pr[j & 3]);
               }
             }
-          };
-          ptx::tmem_ld_32x32b_x32(tbase, va);
-          ptx::tmem_wait_ld();
-#pragma unroll 1
-          for (int ch = 0; ch < NCH; ch += 2) {
-            ptx::tmem_ld_32x32b_x32(tbase + (ch + 1) * 32, vb);
-            reduce(va, ch * 32);
-            ptx::tmem_wait_ld();
-            if (ch + 2 < NCH) {
-              ptx::tmem_ld_32x32b_x32(tbase + (ch + 2) * 32, va);
-            } else {
-              // every column of the accumulator is in registers: hand it back to the MMA warp
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
-            }
-            reduce(vb, (ch + 1) * 32);
-            if (ch + 2 < NCH) ptx::tmem_wait_ld();
-            if ((ch & 6) == 6) renorm();   // every 8 chunks: at most 64 factors below 2 per chain
-          }
-        } else {
-#pragma unroll 1
-          for (int ch = 0; ch < NCH; ++ch) {
-            float v[NC][32];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
-            ptx::tmem_wait_ld();
-            if (ch == NCH - 1) {
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
-            }
-            const int j0 = ch * 32;
+            if ((ch & 7) == 7) renorm();   // every 8 chunks: at most 64 factors below 2 per chain
+          } else {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               float m = 0.f;
@@ -396,7 +382,7 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         acc64 += static_cast<double>(kLn2 * (fmaf(scale, lsum, static_cast<float>(pexp)) + ptx::lg2_approx(pm)));
       }
       if (!ok) break;
-      prm.partial[(static_cast<size_t>(chunk) * kNWG + wg) * prm.ppad + ptile * kBM + row] = acc64;
+      prm.partial[(static_cast<size_t>(chunk) * NWG + wg) * prm.ppad + ptile * kBM + row] = acc64;
     }
   }
 
@@ -455,7 +441,7 @@ sps_status launch_tc(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_
                                        static_cast<int>(smem_bytes));
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
   if (timed) hot_begin(ctx);
-  kern<<<grid, kThreads, smem_bytes, ctx->stream>>>(ctx->enc.mapX, mapT, prm); ++ctx->launches;
+  kern<<<grid, threads_for(NC), smem_bytes, ctx->stream>>>(ctx->enc.mapX, mapT, prm); ++ctx->launches;
   if (timed) hot_end(ctx);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("loglik_tc launch: ") + cudaGetErrorString(e));
@@ -551,7 +537,7 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
     SPS_CUDA_TRY(cudaGetLastError());
   }
   SPS_TRY(ensure_lin(ctx, t));
-  const size_t slices = static_cast<size_t>(prm.n_chunks) * kNWG;
+  const size_t slices = static_cast<size_t>(prm.n_chunks) * nwg_for(NC);
   SPS_CUDA_TRY(S.partial.reserve(slices * ppad * sizeof(double)));
   SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
   prm.partial = S.partial.as<double>();
@@ -625,7 +611,7 @@ sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, i
     return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
   const int ppad = prm.ppad;
   // carve the static area: theta operand rows, partial sums, flag
-  const size_t slices = static_cast<size_t>(prm.n_chunks) * kNWG;
+  const size_t slices = static_cast<size_t>(prm.n_chunks) * nwg_for(NC);
   const size_t op_bytes = round256(static_cast<size_t>(NC) * ppad * enc.kt * sizeof(__nv_bfloat16));
   const size_t part_bytes = round256(slices * ppad * sizeof(double));
   const size_t need = op_bytes + part_bytes + 256;

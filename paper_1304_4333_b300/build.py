@@ -20,6 +20,9 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsps.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# per-file extra flags: the fused kernel flushes FP32 denormals to zero (its exponentials of
+# non-positive arguments may underflow; 2^-126 relative to the other factor is below rounding)
+FILE_FLAGS = {"loglik_tc.cu": ["-ftz=true"]}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-O3", "-I", INCLUDE, "-I", CSRC]
 
@@ -39,7 +42,7 @@ def _headers_mtime() -> float:
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    hdr = _headers_mtime()
+    hdr = max(_headers_mtime(), os.path.getmtime(os.path.abspath(__file__)))
     objs = []
     flags = NVCC_FLAGS + list(extra_flags or [])
     for src in sources:
@@ -48,7 +51,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         if (not force and os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
                 and os.path.getmtime(obj) >= hdr):
             continue
-        cmd = [nvcc()] + ARCH + flags + ["-c", src, "-o", obj]
+        cmd = [nvcc()] + ARCH + flags + FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)

@@ -27,9 +27,9 @@
 //   warp 1      allocates TMEM, then one thread issues tcgen05.mma into two TMEM accumulators;
 //   warps 2..   epilogue groups of four warps; warp w reads TMEM lane quadrant w % 4, so a
 //               group covers the 128 lanes (lane = particle). C = 2: four groups, two per
-//               accumulator, each taking half of its columns; C > 2: two groups, one per
-//               accumulator. Each thread reduces its own particle's row: FP32 within a tile,
-//               FP64 across tiles.
+//               accumulator, each taking half of its columns; C > 2: two groups, each owning
+//               whole accumulators. Each thread reduces its own particle's row: FP32 within a
+//               tile, FP64 across tiles.
 // Work item = (observation chunk, particle tile), chunk-major so that concurrent CTAs read the
 // same X chunk through L2. Partial sums go to a [chunk][group][particle] FP64 buffer that the
 // finalize kernel sums in a fixed order: the result is deterministic.
@@ -49,9 +49,12 @@ namespace sps {
 namespace {
 
 constexpr int kBM = 128;                        // particles per tile = TMEM lanes
-constexpr int kNBUF = 2;                        // TMEM accumulators
-// Epilogue groups of four warps (warp w reads TMEM lane quadrant w % 4): four for C = 2, two
-// sharing each accumulator by halves of its columns; two for C > 2, one per accumulator.
+// TMEM accumulators of NC x BN columns: as many as the 512 columns hold, at most four.
+__host__ __device__ constexpr int nbuf_for(int NC, int BN) {
+  return (512 / (NC * BN)) >= 4 ? 4 : 512 / (NC * BN);
+}
+// Epilogue groups of four warps (warp w reads TMEM lane quadrant w % 4): four for C = 2, two for
+// C > 2; a group owns one accumulator, or half of one when there are fewer accumulators.
 __host__ __device__ constexpr int nwg_for(int NC) { return NC == 1 ? 4 : 2; }
 __host__ __device__ constexpr int threads_for(int NC) { return 32 * (2 + 4 * nwg_for(NC)); }
 constexpr int kKB = 64;                         // K-block width (elements): one 128-byte swizzle row
@@ -94,7 +97,7 @@ __host__ __device__ inline SmemLayout smem_layout(int NC, int BN, int kbx, int k
   L.off_bar = L.off_x + stages * L.x_bytes;
   // barriers: x_full[st], x_empty[st], th_full[2], th_empty[2], acc_full[2], acc_empty[2],
   // drain; then tmem base (u32) and abort flag (int)
-  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * kNBUF + 1) + 16;
+  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * nbuf_for(NC, BN) + 1) + 16;
   return L;
 }
 
@@ -127,9 +130,13 @@ template <int NC, int BN>
 __global__ void __launch_bounds__(threads_for(NC), 1)
 loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                  const TcParams prm) {
-  constexpr int NBUF = kNBUF;
+  constexpr int NBUF = nbuf_for(NC, BN);
   constexpr int NWG = nwg_for(NC);
-  constexpr int GPB = NWG / NBUF;                 // epilogue groups per accumulator
+  static_assert(NWG % NBUF == 0 || NBUF % NWG == 0, "groups and accumulators");
+  // Groups own whole accumulators, or GPB groups share one by columns. (Sharing every tile among
+  // all groups shortens the turnaround but makes all warps convoy on each tile: slower.)
+  constexpr bool kShareAll = false;
+  constexpr int GPB = kShareAll ? NWG : ((NWG >= NBUF) ? NWG / NBUF : 1);   // groups per accumulator
   constexpr int COLS = BN / GPB;                  // columns of a tile per group
   static_assert(NBUF * NC * BN <= 512, "TMEM has 512 columns");
   constexpr uint32_t kTmemCols = (NBUF * NC * BN <= 256) ? 256u : 512u;
@@ -289,8 +296,9 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   } else {
     // ------------------------------------------------------------------ epilogue
     const int wg = (warp - 2) >> 2;
-    const int my_buf = wg / GPB;
-    const int col0 = (wg % GPB) * COLS;               // first column of this group in a tile
+    // with fewer accumulators than groups, GPB groups share one by columns; with more, a group
+    // owns every NWG-th accumulator
+    const int col0 = (kShareAll || NWG >= NBUF) ? (wg % GPB) * COLS : 0;   // first column of this group
     const int quad = warp & 3;
     const int row = quad * 32 + lane;                 // particle within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
@@ -306,7 +314,7 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       double acc64 = 0.0;
       for (int tile = tile_lo; tile < tile_hi; ++tile, ++acc_count) {
         const int buf = acc_count % NBUF;
-        if (buf != my_buf) continue;
+        if (!kShareAll && ((NWG >= NBUF) ? (buf != wg / GPB) : (buf % NWG != wg))) continue;
         const uint32_t aph = (acc_count / NBUF) & 1u;
         // every lane waits; the vote reconverges the warp before the .sync.aligned TMEM loads
         ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit));

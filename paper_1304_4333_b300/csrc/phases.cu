@@ -430,42 +430,33 @@ __global__ void cov_final_kernel(const double* __restrict__ partial, int blocks,
 }
 
 // Lower Cholesky factor of A [D x D] (FP64, one block, right-looking on the packed lower
-// triangle in shared memory). On failure (non-positive or non-finite pivot) sets *flag.
-// Writes L in FP64 (full, zero upper part) and the packed lower triangle in FP32.
+// triangle in shared memory, one thread per row of the trailing update). On failure
+// (non-positive or non-finite pivot) sets *flag. Writes L in FP64 (full, zero upper part) and the
+// packed lower triangle in FP32.
+__device__ __forceinline__ int tri(int i, int k) { return i * (i + 1) / 2 + k; }
+
 __global__ void cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
                                 float* __restrict__ L32, int* __restrict__ flag) {
   extern __shared__ double a[];   // packed lower triangle, row-major
   __shared__ int bad;
-  const int T = D * (D + 1) / 2;
-  for (int e = threadIdx.x; e < T; e += blockDim.x) {
-    int i = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-    while (i * (i + 1) / 2 > e) --i;
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    a[e] = A[i * D + (e - i * (i + 1) / 2)];
-  }
+  for (int i = threadIdx.x; i < D; i += blockDim.x)
+    for (int k = 0; k <= i; ++k) a[tri(i, k)] = A[i * D + k];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < D; ++j) {
     if (threadIdx.x == 0) {
-      const double piv = a[j * (j + 1) / 2 + j];
+      const double piv = a[tri(j, j)];
       if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
-      else a[j * (j + 1) / 2 + j] = sqrt(piv);
+      else a[tri(j, j)] = sqrt(piv);
     }
     __syncthreads();
     if (bad) break;
-    const double djj = a[j * (j + 1) / 2 + j];
-    for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) a[i * (i + 1) / 2 + j] /= djj;
+    const double djj = a[tri(j, j)];
+    for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) a[tri(i, j)] /= djj;
     __syncthreads();
-    // trailing update: a[i][k] -= l[i][j] l[k][j] for j < k <= i
-    const int m = D - j - 1;
-    const int Tm = m * (m + 1) / 2;
-    for (int e = threadIdx.x; e < Tm; e += blockDim.x) {
-      int ii = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-      while (ii * (ii + 1) / 2 > e) --ii;
-      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-      const int kk = e - ii * (ii + 1) / 2;
-      const int i = j + 1 + ii, k = j + 1 + kk;
-      a[i * (i + 1) / 2 + k] -= a[i * (i + 1) / 2 + j] * a[k * (k + 1) / 2 + j];
+    for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) {
+      const double lij = a[tri(i, j)];
+      for (int k = j + 1; k <= i; ++k) a[tri(i, k)] -= lij * a[tri(k, j)];
     }
     __syncthreads();
   }
@@ -475,8 +466,9 @@ __global__ void cholesky_kernel(const double* __restrict__ A, int D, double* __r
   }
   for (int q = threadIdx.x; q < D * D; q += blockDim.x) {
     const int i = q / D, k = q - i * D;
-    L[q] = (k <= i) ? a[i * (i + 1) / 2 + k] : 0.0;
+    L[q] = (k <= i) ? a[tri(i, k)] : 0.0;
   }
+  const int T = D * (D + 1) / 2;
   for (int e = threadIdx.x; e < T; e += blockDim.x) L32[e] = static_cast<float>(a[e]);
 }
 
@@ -582,10 +574,12 @@ __global__ void group_moments_kernel(const double* __restrict__ th, const double
                                      const double* __restrict__ xbar, int N, int D, int k, int F, bool with_theta,
                                      bool with_ll, double* __restrict__ sums) {
   __shared__ double sh[33];
-  const int j = blockIdx.x, f = blockIdx.y;
+  const int j = blockIdx.x, f = blockIdx.y, z = blockIdx.z, S = gridDim.z;
+  const int per = (N + S - 1) / S;
+  const int n_lo = z * per, n_hi = min(N, n_lo + per);
   const double ref = fn_value(th, ll, xbar, 0, f, D, k, with_theta, with_ll);
   double s1 = 0.0, s2 = 0.0;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+  for (int n = n_lo + threadIdx.x; n < n_hi; n += blockDim.x) {
     const double g = fn_value(th, ll, xbar, static_cast<int64_t>(j) * N + n, f, D, k, with_theta, with_ll) - ref;
     s1 += g;
     s2 = fma(g, g, s2);
@@ -593,9 +587,10 @@ __global__ void group_moments_kernel(const double* __restrict__ th, const double
   s1 = block_sum(s1, sh);
   s2 = block_sum(s2, sh);
   if (threadIdx.x == 0) {
-    sums[(static_cast<int64_t>(j) * F + f) * 3 + 0] = s1;
-    sums[(static_cast<int64_t>(j) * F + f) * 3 + 1] = s2;
-    sums[(static_cast<int64_t>(j) * F + f) * 3 + 2] = ref;
+    double* o = sums + ((static_cast<int64_t>(j) * F + f) * S + z) * 3;
+    o[0] = s1;
+    o[1] = s2;
+    o[2] = ref;
   }
 }
 
@@ -606,6 +601,24 @@ __global__ void group_moments_kernel(const double* __restrict__ th, const double
 struct Moments {
   std::vector<double> mean, sd, nse, rne;
 };
+
+constexpr int kMomParts = 8;   // blocks per group and function in the monitoring moments
+
+// Sum the S partial blocks of each (group, function) in a fixed order: [J][F][S][3] -> [J][F][3].
+static std::vector<double> reduce_parts(const std::vector<double>& parts, int J, int F, int S) {
+  std::vector<double> out(static_cast<size_t>(J) * F * 3, 0.0);
+  for (int q = 0; q < J * F; ++q) {
+    double a = 0.0, b = 0.0;
+    for (int z = 0; z < S; ++z) {
+      a += parts[(static_cast<size_t>(q) * S + z) * 3 + 0];
+      b += parts[(static_cast<size_t>(q) * S + z) * 3 + 1];
+    }
+    out[q * 3 + 0] = a;
+    out[q * 3 + 1] = b;
+    out[q * 3 + 2] = parts[static_cast<size_t>(q) * S * 3 + 2];
+  }
+  return out;
+}
 
 // Eqs. (3), (5), (6), (7) as read (NSE = sqrt(vhat / (J N))), (10) from group sums.
 static Moments moments_from_sums(const std::vector<double>& sums, int J, int N, int F) {
@@ -670,7 +683,9 @@ static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_t
   float* L32 = reinterpret_cast<float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
   SPS_CUDA_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(sizeof(double) * T)));
-  cholesky_kernel<<<1, 256, sizeof(double) * T, ctx->stream>>>(d_sigma, D, st->chol.as<double>(), L32, d_flag); ++ctx->launches;
+  const int chol_threads = std::min(256, (D + 31) / 32 * 32);
+  cholesky_kernel<<<1, chol_threads, sizeof(double) * T, ctx->stream>>>(d_sigma, D, st->chol.as<double>(), L32,
+                                                                       d_flag); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
 }
@@ -717,6 +732,7 @@ static sps_status state_buffers(sps_ctx* ctx, sps_state* st) {
   SPS_CUDA_TRY(st->scratch.reserve(std::max({sizeof(double) * T * cov_blocks(P),
                                              sizeof(double) * D * cov_blocks(P),
                                              sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64,
+                                             sizeof(double) * 3 * static_cast<size_t>(st->J) * (1 + ctx->NC) * kMomParts,
                                              sizeof(double) * 3 * kEssParts * ess_rows_max})));
   // counters: [0] accepts (u64), then int flags: [2] chol failure, [3] non-finite, [4] resample
   SPS_CUDA_TRY(st->counters.reserve(64));
@@ -747,18 +763,24 @@ sps_status check_state(sps_ctx* ctx, const sps_state* st) {
   return SPS_OK;
 }
 
-// Monitoring moments (ll, theta_c' xbar) after an M step: returns min RNE over the set.
-sps_status monitoring_rne(sps_ctx* ctx, sps_state* st, double* rne_min) {
+// Monitoring moments (ll, theta_c' xbar) after an M step: launch the group sums, then read them
+// with the step's counters in one synchronisation; min RNE over the set.
+void launch_monitoring(sps_ctx* ctx, sps_state* st) {
   const int F = 1 + ctx->NC;
-  group_moments_kernel<<<dim3(st->J, F), 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
-                                                       ctx->xbar.as<double>(), st->N, ctx->D, ctx->k, F, false,
-                                                       true, st->scratch.as<double>()); ++ctx->launches;
+  group_moments_kernel<<<dim3(st->J, F, kMomParts), 256, 0, ctx->stream>>>(
+      st->theta.as<double>(), st->ll.as<double>(), ctx->xbar.as<double>(), st->N, ctx->D, ctx->k, F, false, true,
+      st->scratch.as<double>()); ++ctx->launches;
+}
+
+sps_status read_step(sps_ctx* ctx, sps_state* st, Counters* c, double* rne_min) {
+  const int F = 1 + ctx->NC;
+  std::vector<double> parts(static_cast<size_t>(st->J) * F * kMomParts * 3);
   SPS_CUDA_TRY(cudaGetLastError());
-  std::vector<double> sums(static_cast<size_t>(st->J) * F * 3);
-  SPS_CUDA_TRY(cudaMemcpyAsync(sums.data(), st->scratch.ptr, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
+  SPS_CUDA_TRY(cudaMemcpyAsync(parts.data(), st->scratch.ptr, parts.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(c, st->counters.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  Moments m = moments_from_sums(sums, st->J, st->N, F);
+  Moments m = moments_from_sums(reduce_parts(parts, st->J, F, kMomParts), st->J, st->N, F);
   double r = INFINITY;
   for (double v : m.rne) r = std::min(r, v);
   *rne_min = r;
@@ -787,14 +809,14 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
       st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, flag_ptr(st, 0),
       st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
+  launch_monitoring(ctx, st);
   Counters c;
-  SPS_TRY(read_counters(ctx, st, &c));
+  double rmin = 0.0;
+  SPS_TRY(read_step(ctx, st, &c, &rmin));
   if (c.chol_bad)
     return fail(ctx, SPS_ERR_DEGENERATE, "proposal covariance h V is not positive definite");
   if (c.nonfinite) return fail(ctx, SPS_ERR_NONFINITE, "non-finite log-likelihood of a proposal");
   const double alpha = static_cast<double>(c.accepts) / static_cast<double>(st->P);
-  double rmin = 0.0;
-  SPS_TRY(monitoring_rne(ctx, st, &rmin));
   const sps_options& o = ctx->opt;
   double hn = h;
   if (!sigma) {
@@ -1100,9 +1122,9 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
   // outputs: moments of theta and of the log-odds theta_c' xbar (Eq. 15), and the log ML
   const int F = D + ctx->NC;
   SPS_CUDA_TRY(st->scratch.reserve(sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64));
-  group_moments_kernel<<<dim3(st->J, F), 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
-                                                       ctx->xbar.as<double>(), st->N, D, ctx->k, F, true, false,
-                                                       st->scratch.as<double>()); ++ctx->launches;
+  group_moments_kernel<<<dim3(st->J, F, 1), 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
+                                                          ctx->xbar.as<double>(), st->N, D, ctx->k, F, true, false,
+                                                          st->scratch.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   std::vector<double> sums(static_cast<size_t>(st->J) * F * 3), lml(st->J);
   SPS_CUDA_TRY(cudaMemcpyAsync(sums.data(), st->scratch.ptr, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,

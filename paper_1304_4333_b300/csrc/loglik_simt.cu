@@ -1,4 +1,5 @@
-// Plain FP32 SIMT log-likelihood (the baseline path) and the C-phase increment kernel.
+// Plain FP32 SIMT log-likelihood (the baseline path) and the C-phase increment kernel; a
+// register-resident variant serves models with k <= 64 and C <= 4 (k <= 32 for C > 2).
 //
 // Both evaluate, per particle and observation, the log probability of the observed outcome of
 // the multinomial logit (Eq. 1, Sec. 2.1) in FP32: eta_c = theta_c' x_s (eta_0 = 0),
@@ -88,6 +89,88 @@ fp32_terms_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
   if (mode == 0 && p < P) out[static_cast<int64_t>(blockIdx.y) * P + p] = acc;
 }
 
+// Register-resident variant for small models (k <= KMAX, NC = C - 1 fixed): each thread keeps
+// its particle's theta in registers; X rows are staged in shared memory padded with zeros to KMAX
+// and read as broadcast float4. Same arithmetic and outputs as fp32_terms_kernel.
+template <int KMAX, int NC>
+__global__ void __launch_bounds__(kP)
+fp32_terms_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const float* __restrict__ X,
+                      const int* __restrict__ y, int64_t s_begin, int64_t s_end, int64_t chunk, int mode,
+                      double* __restrict__ out, const double* __restrict__ logw_in) {
+  __shared__ __align__(16) float xs[kTS][KMAX];
+  __shared__ int ys[kTS];
+  const int D = k * NC;
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * kP + threadIdx.x;
+  const int64_t s_lo = s_begin + static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t s_hi = (s_lo + chunk < s_end) ? s_lo + chunk : s_end;
+  float th[NC][KMAX];
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) th[c][i] = (p < P && i < k) ? static_cast<float>(theta[p * D + c * k + i]) : 0.f;
+  double acc = (mode == 1 && p < P) ? logw_in[p] : 0.0;
+  for (int64_t s0 = s_lo; s0 < s_hi; s0 += kTS) {
+    const int ns = static_cast<int>(s_hi - s0 < kTS ? s_hi - s0 : kTS);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTS * KMAX; idx += blockDim.x) {
+      const int j = idx / KMAX, i = idx - j * KMAX;
+      xs[j][i] = (j < ns && i < k) ? X[(s0 + j) * k + i] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < ns; idx += blockDim.x) ys[idx] = y[s0 + idx];
+    __syncthreads();
+    float tile = 0.f;
+    for (int j = 0; j < ns; ++j) {
+      float eta[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) eta[c] = 0.f;
+#pragma unroll
+      for (int i = 0; i < KMAX; i += 4) {
+        const float4 xv = *reinterpret_cast<const float4*>(&xs[j][i]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          eta[c] = fmaf(th[c][i], xv.x, eta[c]);
+          eta[c] = fmaf(th[c][i + 1], xv.y, eta[c]);
+          eta[c] = fmaf(th[c][i + 2], xv.z, eta[c]);
+          eta[c] = fmaf(th[c][i + 3], xv.w, eta[c]);
+        }
+      }
+      const float term = logit_term(eta, NC, ys[j]);
+      if (mode == 1) {
+        acc += static_cast<double>(term);
+        if (p < P) out[(s0 - s_lo + j) * P + p] = acc;
+      } else {
+        tile += term;
+      }
+    }
+    if (mode == 0) acc += static_cast<double>(tile);
+  }
+  if (mode == 0 && p < P) out[static_cast<int64_t>(blockIdx.y) * P + p] = acc;
+}
+
+// Launch the register variant when the model fits one of its instantiations.
+bool launch_reg(sps_ctx* ctx, dim3 grid, const double* theta, int64_t P, int64_t s_begin, int64_t s_end,
+                int64_t chunk, int mode, double* out, const double* logw_in) {
+  const int k = ctx->k, NC = ctx->NC;
+  const float* X = ctx->Xf.as<float>();
+  const int* y = ctx->y.as<int>();
+#define SPS_REG_CASE(KM, NCM)                                                                          \
+  if (NC == NCM && k <= KM) {                                                                          \
+    fp32_terms_reg_kernel<KM, NCM><<<grid, kP, 0, ctx->stream>>>(theta, P, k, X, y, s_begin, s_end, chunk, \
+                                                                 mode, out, logw_in);                  \
+    ++ctx->launches;                                                                                   \
+    return true;                                                                                       \
+  }
+  SPS_REG_CASE(8, 1)
+  SPS_REG_CASE(32, 1)
+  SPS_REG_CASE(64, 1)
+  SPS_REG_CASE(8, 2)
+  SPS_REG_CASE(32, 2)
+  SPS_REG_CASE(8, 3)
+  SPS_REG_CASE(32, 3)
+#undef SPS_REG_CASE
+  return false;
+}
+
 __global__ void sum_slices_kernel(const double* __restrict__ partial, int64_t P, int slices,
                                   double* __restrict__ ll) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -119,11 +202,13 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
   chunks = std::max<int64_t>(1, (t + chunk - 1) / chunk);
   SPS_CUDA_TRY(ctx->ll.partial.reserve(static_cast<size_t>(chunks) * P * sizeof(double)));
   double* partial = ctx->ll.partial.as<double>();
-  SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
   dim3 grid(static_cast<unsigned>(ptiles), static_cast<unsigned>(chunks));
-  fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
-                                                     ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr); ++ctx->launches;
+  if (!launch_reg(ctx, grid, d_theta, P, 0, t, chunk, 0, partial, nullptr)) {
+    SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+    fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
+                                                       ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr); ++ctx->launches;
+  }
   SPS_CUDA_TRY(cudaGetLastError());
   sum_slices_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
       partial, P, t > 0 ? static_cast<int>(chunks) : 0, d_ll); ++ctx->launches;
@@ -136,13 +221,15 @@ sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int
   const size_t smem = fp32_smem(ctx->k, ctx->NC);
   if (ctx->NC > kMaxNC || smem > 200 * 1024)
     return fail(ctx, SPS_ERR_UNSUPPORTED, "C phase: k*(C-1) too large");
-  SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
   const int64_t ptiles = (P + kP - 1) / kP;
   dim3 grid(static_cast<unsigned>(ptiles), 1);
-  fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
-                                                     ctx->y.as<int>(), s_lo, s_hi, s_hi - s_lo, 1, d_lw,
-                                                     d_logw_in); ++ctx->launches;
+  if (!launch_reg(ctx, grid, d_theta, P, s_lo, s_hi, s_hi - s_lo, 1, d_lw, d_logw_in)) {
+    SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+    fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
+                                                       ctx->y.as<int>(), s_lo, s_hi, s_hi - s_lo, 1, d_lw,
+                                                       d_logw_in); ++ctx->launches;
+  }
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
 }

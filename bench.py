@@ -286,9 +286,30 @@ def run_ours(args, world, rank, local):
                      "bounds_ms_full_t": {"sfu": sfu_ms, "tensor_split": tensor_ms, "hbm": hbm_ms},
                      "peak_source": "148 SMs x 32 ex2/clk/SM x sm_max_mhz of MEASURED_PEAKS (ex2 rate from a probe)"},
     }
+    if not args.no_sps:
+        line["sps"] = sps_wall(w, rank)
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_throughput(w)
     print(json.dumps(line), flush=True)
+
+
+def sps_wall(w, rank):
+    """Second half of the metric: wall time of the whole simulator (sps_run, Algorithm 2) on c2
+    with the split-BF16 path and with the plain FP32 path, the log-ML NSE each reaches at the
+    configured 16 x 4096 particles, and the projected wall time to NSE <= 0.05 (NSE scales as
+    particles^-1/2 and the time as particles, so time x (NSE / 0.05)^2; labelled as projected)."""
+    from paper_1304_4333_b300 import Sps
+    out = {}
+    for prec in ("split", "fp32"):
+        s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=11 + rank, precision=prec)
+        r = s.run(w.J, w.N, record=False)
+        out[prec] = {"wall_s": r.seconds, "log_ml": r.log_ml, "log_ml_nse": r.log_ml_nse,
+                     "cycles": r.n_cycles, "m_steps": r.m_steps,
+                     "projected_wall_s_to_nse_0.05": r.seconds * max(1.0, (r.log_ml_nse / 0.05) ** 2)}
+        s.close()
+    out["speedup_vs_fp32"] = out["fp32"]["wall_s"] / out["split"]["wall_s"]
+    out["particles"] = f"{w.J} groups x {w.N}"
+    return out
 
 
 def main():
@@ -299,6 +320,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split", choices=["split", "fp32"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sps", action="store_true", help="skip the whole-simulator wall-time runs")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     args = ap.parse_args()

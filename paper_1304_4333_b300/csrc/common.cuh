@@ -121,6 +121,8 @@ struct sps_state {
   double h = 0.5;
   bool have_weights = false;      // a C phase has run since the last S phase
   bool ll_stale = false;          // ll holds C-phase sums: recompute with the M-phase kernel
+  int ll_kind = -1;               // function that produced ll: 0 split, 1 FP32, 2 gradient kernel
+  bool grad_valid = false;        // grad holds the log-likelihood gradient of theta at t
   uint64_t step_counter = 0;      // Philox counter word for per-step streams
   uint64_t cycle_counter = 0;
   sps::DevBuf theta, theta_prop;  // FP64 [P x D]
@@ -137,6 +139,8 @@ struct sps_state {
   sps::DevBuf mean;               // FP64 [D]
   sps::DevBuf counters;           // int/unsigned counters (accepts, error flags)
   sps::DevBuf grad, grad_prop;    // FP64 [P x D] (MALA)
+  sps::DevBuf zq;                 // FP32 [P x D] MALA: 1/2 L' g(theta) + z of the current proposal
+  sps::DevBuf z2;                 // FP64 [P] MALA: |z|^2 of the current proposal
   std::vector<double> host_tmp;
 };
 

@@ -551,6 +551,129 @@ __global__ void accept_kernel(double* __restrict__ th, double* __restrict__ ll, 
   if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, static_cast<unsigned long long>(__popc(ballot)));
 }
 
+// ------------------------------------------------------------------------------ MALA
+// Metropolis-adjusted Langevin M kernel (not in the paper; an exact MH kernel for the same
+// posterior). With Sigma = h V = L L' and g the gradient of the log posterior,
+//   theta' = theta + L v,  v = (1/2) L' g(theta) + z,   z ~ N(0, I),
+// i.e. mean theta + (h/2) V g(theta) and covariance h V. The reverse move has residual
+// L^{-1}(theta - theta' - (1/2) L L' g(theta')) = -(v + (1/2) L' g(theta')) =: w, so
+//   log alpha = ll' - ll + lp' - lp - |w|^2 / 2 + |z|^2 / 2.
+
+constexpr int kMalaThreads = 64;
+
+// Gradient of the prior log density, -Prec (theta - mu), component i (FP64).
+__device__ __forceinline__ double prior_grad(const double* th, const double* mu, const double* prec, int D,
+                                             bool full, int i) {
+  if (!full) return -prec[i] * (th[i] - mu[i]);
+  double a = 0.0;
+  for (int j = 0; j < D; ++j) a = fma(prec[i * D + j], th[j] - mu[j], a);
+  return -a;
+}
+
+__global__ void __launch_bounds__(kMalaThreads)
+mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gll, int64_t P, int D,
+                    const float* __restrict__ L32, uint64_t seed, uint64_t step, const double* __restrict__ mu,
+                    const double* __restrict__ prec, bool full, const int* __restrict__ flag,
+                    double* __restrict__ th_o, double* __restrict__ lp_o, float* __restrict__ zq_o,
+                    double* __restrict__ z2_o) {
+  if (*flag) return;
+  extern __shared__ float ms[];
+  const int T = D * (D + 1) / 2;
+  float* Ls = ms;                                  // [T] packed lower triangle
+  float* vs = ms + ((T + 3) & ~3);                 // [D][64] gradient, then v
+  float* zs = vs + D * kMalaThreads;               // [D][64]
+  for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
+  const int64_t p = blockIdx.x * static_cast<int64_t>(kMalaThreads) + threadIdx.x;
+  const bool live = p < P;
+  const int c = threadIdx.x;
+  double z2 = 0.0;
+  if (live) {
+    const double* t = th + p * D;
+    for (int i = 0; i < D; ++i)
+      vs[i * kMalaThreads + c] = static_cast<float>(gll[p * D + i] + prior_grad(t, mu, prec, D, full, i));
+    const int per = (D + 3) / 4;
+    for (int q = 0; q < per; ++q) {
+      const uint4 r = draw(seed, static_cast<uint32_t>(p * per + q), kStreamPropose, step);
+      const float2 a = normals2(r.x, r.y), b = normals2(r.z, r.w);
+      const float v[4] = {a.x, a.y, b.x, b.y};
+      for (int u = 0; u < 4; ++u)
+        if (4 * q + u < D) {
+          zs[(4 * q + u) * kMalaThreads + c] = v[u];
+          z2 += static_cast<double>(v[u]) * v[u];
+        }
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  // v_j = (1/2) (L' g)_j + z_j, in place: (L' g)_j reads g_i for i >= j only
+  for (int j = 0; j < D; ++j) {
+    float a = 0.f;
+    for (int i = j; i < D; ++i) a = fmaf(Ls[i * (i + 1) / 2 + j], vs[i * kMalaThreads + c], a);
+    vs[j * kMalaThreads + c] = fmaf(0.5f, a, zs[j * kMalaThreads + c]);
+  }
+  const double* t = th + p * D;
+  double* o = th_o + p * D;
+  for (int i = 0; i < D; ++i) {
+    const float* Li = Ls + i * (i + 1) / 2;
+    float dlt = 0.f;
+    for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], vs[j * kMalaThreads + c], dlt);
+    o[i] = t[i] + static_cast<double>(dlt);
+    zq_o[p * D + i] = vs[i * kMalaThreads + c];
+  }
+  z2_o[p] = z2;
+  lp_o[p] = prior_log_kernel(o, mu, prec, D, full);
+}
+
+__global__ void __launch_bounds__(kMalaThreads)
+mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restrict__ lp,
+                   double* __restrict__ g, const double* __restrict__ th_p, const double* __restrict__ ll_p,
+                   const double* __restrict__ lp_p, const double* __restrict__ g_p, const float* __restrict__ zq,
+                   const double* __restrict__ z2, const float* __restrict__ L32, int64_t P, int D,
+                   const double* __restrict__ mu, const double* __restrict__ prec, bool full, uint64_t seed,
+                   uint64_t step, const int* __restrict__ flag, unsigned long long* __restrict__ n_acc,
+                   int* __restrict__ nonfinite) {
+  if (*flag) return;
+  extern __shared__ float ms[];
+  const int T = D * (D + 1) / 2;
+  float* Ls = ms;
+  float* gs = ms + ((T + 3) & ~3);   // [D][64]
+  for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
+  const int64_t p = blockIdx.x * static_cast<int64_t>(kMalaThreads) + threadIdx.x;
+  const bool live = p < P;
+  const int c = threadIdx.x;
+  if (live) {
+    const double* tp = th_p + p * D;
+    for (int i = 0; i < D; ++i)
+      gs[i * kMalaThreads + c] = static_cast<float>(g_p[p * D + i] + prior_grad(tp, mu, prec, D, full, i));
+  }
+  __syncthreads();
+  bool acc = false;
+  if (live) {
+    double w2 = 0.0;
+    for (int j = 0; j < D; ++j) {
+      float b = 0.f;
+      for (int i = j; i < D; ++i) b = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaThreads + c], b);
+      const double w = static_cast<double>(zq[p * D + j]) + 0.5 * static_cast<double>(b);
+      w2 = fma(w, w, w2);
+    }
+    const double lpp = ll_p[p];
+    if (!isfinite(lpp)) atomicOr(nonfinite, 1);
+    const double la = (lpp - ll[p]) + (lp_p[p] - lp[p]) - 0.5 * w2 + 0.5 * z2[p];
+    const uint4 r = draw(seed, static_cast<uint32_t>(p), kStreamAccept, step);
+    acc = log(uniform53(r.x, r.y)) < la;
+    if (acc) {
+      for (int d = 0; d < D; ++d) {
+        th[p * D + d] = th_p[p * D + d];
+        g[p * D + d] = g_p[p * D + d];
+      }
+      ll[p] = lpp;
+      lp[p] = lp_p[p];
+    }
+  }
+  const unsigned ballot = __ballot_sync(0xffffffffu, acc);
+  if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, static_cast<unsigned long long>(__popc(ballot)));
+}
+
 // Group sums of monitoring or output functions: functions are theta coordinates f < nth
 // (if with_theta), then ll (if with_ll), then the log-odds theta_c' xbar. Per group j and
 // function f: sums of (g - ref_f) and (g - ref_f)^2, ref_f the value at particle 0.
@@ -791,24 +914,70 @@ sps_status read_step(sps_ctx* ctx, sps_state* st, Counters* c, double* rne_min) 
 // phase has updated it (so that both sides of the Metropolis ratio use one function).
 sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sigma, double* sigma_used,
                       sps_mstep_info* info) {
-  if (kernel != SPS_MKERNEL_RW) return fail(ctx, SPS_ERR_UNSUPPORTED, "only the random-walk M kernel is built");
+  if (kernel != SPS_MKERNEL_RW && kernel != SPS_MKERNEL_MALA)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "unknown M kernel");
   const int precision = ctx->opt.precision;
-  if (st->ll_stale) {
+  const int D = ctx->D;
+  const bool mala = (kernel == SPS_MKERNEL_MALA);
+  // the cached log-likelihood (and, for MALA, its gradient) must come from the function the
+  // proposals are evaluated with
+  const int kind = mala ? 2 : (precision == SPS_PREC_FP32 ? 1 : 0);
+  if (mala) {
+    SPS_CUDA_TRY(st->grad.reserve(sizeof(double) * st->P * D));
+    SPS_CUDA_TRY(st->grad_prop.reserve(sizeof(double) * st->P * D));
+    SPS_CUDA_TRY(st->zq.reserve(sizeof(float) * st->P * D));
+    SPS_CUDA_TRY(st->z2.reserve(sizeof(double) * st->P));
+    if (st->ll_stale || st->ll_kind != kind || !st->grad_valid) {
+      SPS_TRY(loglik_grad_fp32(ctx, st->theta.as<double>(), st->P, st->t, st->ll.as<double>(),
+                               st->grad.as<double>()));
+      st->ll_stale = false;
+      st->ll_kind = kind;
+      st->grad_valid = true;
+    }
+  } else if (st->ll_stale || st->ll_kind != kind) {
     SPS_TRY(loglik_dispatch(ctx, st->theta.as<double>(), st->P, st->t, st->ll.as<double>(), precision));
     st->ll_stale = false;
+    st->ll_kind = kind;
   }
   SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
   const double h = st->h;
   SPS_TRY(factor_proposal(ctx, st, st->theta.as<double>(), h, sigma, sigma_used, flag_ptr(st, 0)));
   const uint64_t step = ++st->step_counter;
-  SPS_TRY(launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, flag_ptr(st, 0),
-                         st->theta_prop.as<double>(), st->lp_prop.as<double>()));
-  SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(), precision));
-  accept_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
-      st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->theta_prop.as<double>(),
-      st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, flag_ptr(st, 0),
-      st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
-  SPS_CUDA_TRY(cudaGetLastError());
+  if (mala) {
+    const int T = D * (D + 1) / 2;
+    const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kMalaThreads);
+    const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kMalaThreads);
+    SPS_CUDA_TRY(cudaFuncSetAttribute(mala_propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem_p)));
+    SPS_CUDA_TRY(cudaFuncSetAttribute(mala_accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem_a)));
+    const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
+    const unsigned blocks = static_cast<unsigned>((st->P + kMalaThreads - 1) / kMalaThreads);
+    mala_propose_kernel<<<blocks, kMalaThreads, smem_p, ctx->stream>>>(
+        st->theta.as<double>(), st->grad.as<double>(), st->P, D, L32, st->seed, step, ctx->d_prior_mean.as<double>(),
+        ctx->d_prior_prec.as<double>(), prior_full(ctx), flag_ptr(st, 0), st->theta_prop.as<double>(),
+        st->lp_prop.as<double>(), st->zq.as<float>(), st->z2.as<double>()); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+    SPS_TRY(loglik_grad_fp32(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
+                             st->grad_prop.as<double>()));
+    mala_accept_kernel<<<blocks, kMalaThreads, smem_a, ctx->stream>>>(
+        st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->grad.as<double>(),
+        st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->grad_prop.as<double>(),
+        st->zq.as<float>(), st->z2.as<double>(), L32, st->P, D, ctx->d_prior_mean.as<double>(),
+        ctx->d_prior_prec.as<double>(), prior_full(ctx), st->seed, step, flag_ptr(st, 0),
+        st->counters.as<unsigned long long>(), flag_ptr(st, 1)); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+  } else {
+    SPS_TRY(launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, flag_ptr(st, 0),
+                           st->theta_prop.as<double>(), st->lp_prop.as<double>()));
+    SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(), precision));
+    accept_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
+        st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->theta_prop.as<double>(),
+        st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, flag_ptr(st, 0),
+        st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+    st->grad_valid = false;
+  }
   launch_monitoring(ctx, st);
   Counters c;
   double rmin = 0.0;
@@ -916,6 +1085,7 @@ sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_id
   swapbuf(st->ll, st->ll_prop);
   swapbuf(st->lp, st->lp_prop);
   st->have_weights = false;
+  st->grad_valid = false;   // gradients are not gathered
   return SPS_OK;
 }
 
@@ -1027,10 +1197,12 @@ sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const
   if (ll) {
     SPS_CUDA_TRY(cudaMemcpyAsync(st->ll.ptr, ll, sizeof(double) * st->P, cudaMemcpyHostToDevice, ctx->stream));
     st->ll_stale = false;
+    st->ll_kind = (ctx->opt.precision == SPS_PREC_FP32) ? 1 : 0;   // taken as the RW kernel's values
   } else {
     st->ll_stale = true;
   }
   st->have_weights = false;
+  st->grad_valid = false;
   SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return SPS_OK;
 }

@@ -257,3 +257,34 @@ def test_two_pass_replay(cuda):
     np.testing.assert_array_equal(p2.schedule.R, p1.schedule.R)
     np.testing.assert_allclose(p2.schedule.sigma, p1.schedule.sigma)
     assert abs(p1.log_ml - p2.log_ml) < 5 * max(math.hypot(p1.log_ml_nse, p2.log_ml_nse), 1e-3)
+
+
+def test_mala_leaves_the_prior_invariant_when_x_is_zero(cuda):
+    # X = 0: the likelihood is constant, the posterior is the N(0, 25 I) prior and the MALA drift
+    # comes from the prior alone. An exact MH kernel keeps prior draws distributed as the prior;
+    # an error in the proposal-density ratio shows up as a drift of the variance.
+    n, k = 40, 3
+    X = np.zeros((n, k))
+    y = (np.arange(n) % 2).astype(np.int32)
+    s = _ctx(X, y, 2, seed=5)
+    st = s.state(16, 1024, seed=7)
+    t_new, _, _ = st.cphase()
+    assert t_new == n
+    st.sphase()
+    accs = [st.mstep("mala")["accept"] for _ in range(60)]
+    th = st.get()["theta"]
+    assert 0.2 < np.mean(accs) < 0.99
+    P = th.shape[0]
+    # after resampling particles are duplicated; 60 steps decorrelate them, allow 6 sigma
+    np.testing.assert_allclose(th.mean(axis=0), 0.0, atol=6 * 5.0 / np.sqrt(P / 4))
+    np.testing.assert_allclose(th.var(axis=0), 25.0, rtol=0.1)
+
+
+def test_sps_run_mala_against_quadrature(cuda):
+    X, y, quad = _quad_case()
+    s = _ctx(X, y, 2, seed=23, mkernel="mala")
+    r = s.run(16, 1024)
+    z = (r.mean[:2] - quad["mean"]) / r.nse[:2]
+    assert np.all(np.abs(z) < 4), (r.mean[:2], quad["mean"], r.nse[:2])
+    np.testing.assert_allclose(r.sd[:2], quad["sd"], rtol=0.05)
+    assert abs(r.log_ml - quad["log_ml"]) < 4 * max(r.log_ml_nse, 1e-3)

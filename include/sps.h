@@ -145,6 +145,9 @@ void sps_options_default(sps_options* opt);
  *   n >= 1, 1 <= k <= 256, 2 <= n_outcomes <= 4 for the tensor-core path (the FP32 path
  *   accepts up to 16 outcomes). prior: Gaussian on the D = k*(n_outcomes-1) free coefficients.
  *   opt may be NULL (defaults). Copies and encodes X and y to the current CUDA device.
+ *   The fused split-precision kernel runs in clusters of two CTAs that share X tiles when the
+ *   device can co-schedule them; the environment variable SPS_TC_CLUSTER=1, read here, keeps it
+ *   to single CTAs (same results, for comparison).
  * Errors: SPS_ERR_INVALID_ARG for bad sizes, y out of range, non-finite X or a prior covariance
  * that is not positive definite; SPS_ERR_OOM; SPS_ERR_CUDA. *out is NULL on failure. */
 sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const int32_t* y,
@@ -195,11 +198,12 @@ sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, d
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  * the context's device current; make that first call before any stream capture. All calls share
  * the array: calls whose GPU work overlaps race and must be serialised by the caller.
- * Limit: the call needs 4 (C-1) P' k64 bytes of operand rows (P' = P rounded up to 128, k64 = k
- * rounded up to 64) plus 16 P' ceil(t / (128 m)) bytes of partial sums (m = observation tiles
- * per work item, at most 32) and must fit in 32 MiB: the binary workload with 65 536 particles,
- * k = 30 and n = 20 000 needs about 21 MiB. Larger calls return SPS_ERR_INVALID_ARG, with the
- * required size in sps_last_error, and launch nothing; other errors as sps_loglik. */
+ * Limit: the call needs 4 (C-1) P' k64 bytes of operand rows (P' = P rounded up to 256, k64 = k
+ * rounded up to 64) plus 8 W P' c bytes of partial sums (W = 4 for C = 2, 2 for C > 2; c = the
+ * call's observation chunks, at most ceil(t / 64)) and must fit in 32 MiB: the binary workload
+ * with 65 536 particles, k = 30 and n = 20 000 (c = 5) needs about 26 MiB. Larger calls return
+ * SPS_ERR_INVALID_ARG, with the required size in sps_last_error, and launch nothing; other
+ * errors as sps_loglik. */
 sps_status sps_loglik_noalloc(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll);
 
 /* Log-likelihood and its gradient d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s

@@ -414,7 +414,8 @@ sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const 
         ctx->Xd.as<double>(), n, k, enc.perm_dev.as<int>(), enc.k16, enc.kc, enc.kx,
         enc.Xp.as<__nv_bfloat16>(), ctx->Xf.as<float>()); ++ctx->launches;
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(SPS_ERR_CUDA);
-    if (enc.bn > 0 && (st = make_map_bf16(ctx, &enc.mapX, enc.Xp.ptr, n, enc.kx, enc.bn)) != SPS_OK)
+    if (enc.bn > 0 && (st = tc_configure_cluster(ctx)) != SPS_OK) return bail(st);
+    if (enc.bn > 0 && (st = make_map_bf16(ctx, &enc.mapX, enc.Xp.ptr, n, enc.kx, enc.bn / enc.cl)) != SPS_OK)
       return bail(st);
   }
   // covariate means and prefix sums of the linear term, host FP64 in observation order

@@ -54,7 +54,10 @@ struct XEncoding {
   int k = 0, kc = 0;          // covariates, continuous covariates
   int k16 = 0, kc16 = 0;      // k and kc rounded up to 16 (MMA K step)
   int kx = 0, kt = 0;         // row widths of the X and theta operands (multiples of 64)
-  int bn = 0;                 // observation rows per tile (TMA box of X); 0: no tile fits
+  int bn = 0;                 // observation rows per tile; 0: no tile fits
+  int cl = 1;                 // CTAs per cluster sharing each X tile (each loads bn / cl rows of
+                              // it, multicast to all); the TMA box of X is {64, bn / cl}
+  int max_clusters = 0;       // co-resident clusters of the fused kernel at this shape
   std::vector<int> perm;      // internal column j holds original column perm[j]
   DevBuf perm_dev;            // int [k]
   DevBuf Xp;                  // bf16 [n x kx]
@@ -165,6 +168,9 @@ sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64
 sps_status ensure_lin(sps_ctx* ctx, int64_t t);
 // Observation rows per tensor-core tile for NC = C - 1 outcomes and operand widths kx, kt.
 int tc_tile_rows(int NC, int kx, int kt);
+// Cluster size of the fused kernel for the context's tile shape (sets enc.cl, enc.max_clusters):
+// 2 when clusters of two fit on the device, else 1; SPS_TC_CLUSTER=1 in the environment forces 1.
+sps_status tc_configure_cluster(sps_ctx* ctx);
 // Start/stop event of one timed launch of the fused kernel (no-ops when timing is off).
 void hot_begin(sps_ctx* ctx);
 void hot_end(sps_ctx* ctx);
@@ -249,6 +255,28 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// The same tile, written at the same shared-memory offset of every CTA of the cluster named in
+// `cta_mask`; each destination CTA's mbarrier at the offset of `bar` receives the bytes it got.
+__device__ __forceinline__ void tma_load_2d_multicast(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                                      int32_t x, int32_t y, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(cta_mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of every CTA of the cluster: arrive (release) and wait (acquire).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -291,6 +319,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+
+// As mma_commit, but the arrive lands on the mbarrier at the offset of `bar` in every CTA of the
+// cluster named in `cta_mask`.
+__device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)), "h"(cta_mask)
       : "memory");
 }
 

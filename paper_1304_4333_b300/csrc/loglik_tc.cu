@@ -11,9 +11,10 @@
 // The linear terms are FP64 dot products with FP64 prefix sums of X (finalize kernel); this
 // kernel produces the FP64 sums of the non-linear terms. Theta enters the tensor cores scaled by
 // log2(e), so the accumulators hold u = eta log2(e) and each exponential is one ex2. Logarithms
-// are taken once per tile, of running products of the (1 + 2^{-|u|}) factors (binary) or of the
-// shifted sums of exponentials (C > 2), kept in four independent chains whose binary exponents
-// are moved to an integer as they grow.
+// are taken once per tile, of running products of the (1 + 2^{-|u|}) factors (binary: four
+// chains, at most 32 factors in [1, 2] each, no rescaling needed; packed FP32x2 adds and FMAs)
+// or of the shifted sums of exponentials (C > 2: four chains whose binary exponents are moved to
+// an integer as they grow).
 //
 // Operands (128-byte-swizzled BF16, K blocks of 64 elements): an X row holds [Xh | Xl] with
 // Xh = bf16(x) over k16 columns and Xl = bf16(x - Xh) over the kc16 continuous columns; a theta
@@ -28,16 +29,23 @@
 //   warps 2..   epilogue groups of four warps; warp w reads TMEM lane quadrant w % 4, so a
 //               group covers the 128 lanes (lane = particle). C = 2: four groups, two per
 //               accumulator, each taking half of its columns; C > 2: two groups, each owning
-//               whole accumulators. Each thread reduces its own particle's row: FP32 within a
-//               tile, FP64 across tiles.
-// Work item = (observation chunk, particle tile), chunk-major so that concurrent CTAs read the
-// same X chunk through L2. Partial sums go to a [chunk][group][particle] FP64 buffer that the
-// finalize kernel sums in a fixed order: the result is deterministic.
+//               whole accumulators; a group visits only the tiles of its accumulator. Each
+//               thread reduces its own particle's row: FP32 within a tile, FP32 with Kahan
+//               compensation across the tiles of a work item, FP64 across work items.
+// Work item = (observation chunk, group of CL particle tiles), chunk-major so that concurrent
+// CTAs read the same X chunk through L2. With CL = 2 the two CTAs of a cluster take the two
+// particle tiles of an item and share its X tiles: each loads half of the rows of every X tile
+// and multicasts them to both, and each CTA's MMA completion releases the stage in both, so a
+// stage is refilled only when both have consumed it. This halves the X traffic out of L2.
+// Partial sums go to a [chunk][group][particle] FP64 buffer that the finalize kernel sums in a
+// fixed order: the result is deterministic.
 //
 // Every mbarrier wait is bounded (wall-clock limit); on a timeout the CTA raises a flag, drains
-// its own copies and MMAs with bounded waits, frees TMEM and returns. Warps reconverge before
-// every .sync.aligned tcgen05 instruction, and the producer waits for every stage it filled to be
-// released before the CTA exits, so no asynchronous arrive is still in flight at exit.
+// its own copies and MMAs with bounded waits, frees TMEM and returns (a stalled peer makes the
+// other CTA of its cluster time out as well; both meet at the final cluster barrier). Warps
+// reconverge before every .sync.aligned tcgen05 instruction, and the producer waits for every
+// stage it filled to be released before the CTA exits, so no asynchronous arrive is still in
+// flight at exit.
 
 #include <algorithm>
 #include <cstdio>
@@ -61,8 +69,9 @@ constexpr int kKB = 64;                         // K-block width (elements): one
 constexpr uint32_t kTileA = kBM * 128;          // bytes of one 128-row K block
 
 struct TcParams {
-  int ppad;            // padded particle count (multiple of 128)
+  int ppad;            // padded particle count (multiple of 128 x cluster size)
   int n_ptiles;
+  int n_pgroups;       // n_ptiles / cluster size
   int t;               // prefix length
   int n_tiles;         // observation tiles covering [0, t)
   int chunk_tiles;     // observation tiles per work item
@@ -128,17 +137,19 @@ __device__ __forceinline__ uint64_t kslice_desc(uint32_t base, int rows, int e) 
          static_cast<uint64_t>(((e & 63) * 2) >> 4);
 }
 
-template <int NC, int BN>
+template <int NC, int BN, int CL>
 __global__ void __launch_bounds__(threads_for(NC), 1)
 loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                  const TcParams prm) {
+  static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
+  constexpr int HR = BN / CL;                     // X rows of a tile loaded by this CTA
+  constexpr uint16_t kMask = (1u << CL) - 1u;     // every CTA of the cluster
   constexpr int NBUF = nbuf_for(NC, BN);
   constexpr int NWG = nwg_for(NC);
   static_assert(NWG % NBUF == 0 || NBUF % NWG == 0, "groups and accumulators");
   // Groups own whole accumulators, or GPB groups share one by columns. (Sharing every tile among
   // all groups shortens the turnaround but makes all warps convoy on each tile: slower.)
-  constexpr bool kShareAll = false;
-  constexpr int GPB = kShareAll ? NWG : ((NWG >= NBUF) ? NWG / NBUF : 1);   // groups per accumulator
+  constexpr int GPB = (NWG >= NBUF) ? NWG / NBUF : 1;   // groups per accumulator
   constexpr int COLS = BN / GPB;                  // columns of a tile per group
   static_assert(NBUF * NC * BN <= 512, "TMEM has 512 columns");
   constexpr uint32_t kTmemCols = (NBUF * NC * BN <= 256) ? 256u : 512u;
@@ -160,11 +171,14 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const int rank = (CL > 1) ? static_cast<int>(ptx::cluster_ctarank()) : 0;
+  const int cluster_id = blockIdx.x / CL;
+  const int n_clusters = gridDim.x / CL;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < prm.stages; ++i) {
       ptx::mbar_init(&x_full[i], 1);
-      ptx::mbar_init(&x_empty[i], 1);
+      ptx::mbar_init(&x_empty[i], CL);   // released by the MMA of every CTA of the cluster
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&th_full[i], 1);
@@ -184,6 +198,8 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   }
   ptx::tc_fence_before();
   __syncthreads();
+  // the peer's copies and arrives target this CTA's barriers: both must be initialised first
+  if constexpr (CL > 1) ptx::cluster_sync();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
   const uint64_t limit = prm.timeout_ns;
@@ -200,9 +216,9 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       bool ok = true;
       // bit s: stage / theta buffer s was filled; parity of its last fill
       uint32_t issued_x = 0, issued_t = 0, par_x = 0, par_t = 0;
-      for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
-        const int chunk = item / prm.n_ptiles;
-        const int ptile = item - chunk * prm.n_ptiles;
+      for (int item = cluster_id; ok && item < prm.n_items; item += n_clusters) {
+        const int chunk = item / prm.n_pgroups;
+        const int ptile = (item - chunk * prm.n_pgroups) * CL + rank;
         const int tile_lo = chunk * prm.chunk_tiles;
         const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
         if (!ptx::mbar_wait_bounded(&th_empty[tb], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
@@ -219,10 +235,15 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
           if (!ptx::mbar_wait_bounded(&x_empty[st], xph ^ 1u, abort_flag, limit)) { ok = false; break; }
           uint8_t* xb = smem + L.off_x + st * L.x_bytes;
-          ptx::mbar_arrive_expect_tx(&x_full[st], L.x_bytes);
-          const int obs = tile * BN;
-          for (int kb = 0; kb < prm.kbx; ++kb)
-            ptx::tma_load_2d(xb + kb * BN * 128, &mapX, &x_full[st], kb * kKB, obs);
+          ptx::mbar_arrive_expect_tx(&x_full[st], L.x_bytes);   // the whole tile, both halves
+          const int obs = tile * BN + rank * HR;
+          for (int kb = 0; kb < prm.kbx; ++kb) {
+            uint8_t* dst = xb + kb * BN * 128 + rank * HR * 128;
+            if constexpr (CL > 1)
+              ptx::tma_load_2d_multicast(dst, &mapX, &x_full[st], kb * kKB, obs, kMask);
+            else
+              ptx::tma_load_2d(dst, &mapX, &x_full[st], kb * kKB, obs);
+          }
           issued_x |= 1u << st;
           par_x = (par_x & ~(1u << st)) | (xph << st);
           if (++st == prm.stages) { st = 0; xph ^= 1u; }
@@ -255,8 +276,8 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       uint32_t acc_count = 0;
       bool ok = true;
       bool issued_any = false;
-      for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
-        const int chunk = item / prm.n_ptiles;
+      for (int item = cluster_id; ok && item < prm.n_items; item += n_clusters) {
+        const int chunk = item / prm.n_pgroups;
         const int tile_lo = chunk * prm.chunk_tiles;
         const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
         if (!ptx::mbar_wait_bounded(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
@@ -281,7 +302,8 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
               ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, prm.k16 + 16 * i), idesc, 1);
           }
           issued_any = true;
-          ptx::mma_commit(&x_empty[st]);
+          if constexpr (CL > 1) ptx::mma_commit_multicast(&x_empty[st], kMask);
+          else ptx::mma_commit(&x_empty[st]);
           ptx::mma_commit(&acc_full[buf]);
           ++acc_count;
           if (++st == prm.stages) { st = 0; xph ^= 1u; }
@@ -298,78 +320,112 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   } else {
     // ------------------------------------------------------------------ epilogue
     const int wg = (warp - 2) >> 2;
-    // with fewer accumulators than groups, GPB groups share one by columns; with more, a group
-    // owns every NWG-th accumulator
-    const int col0 = (kShareAll || NWG >= NBUF) ? (wg % GPB) * COLS : 0;   // first column of this group
+    // With at least as many groups as accumulators, GPB groups share accumulator wg / GPB by
+    // columns and take every NBUF-th tile; otherwise group wg owns the accumulators b with
+    // b % NWG == wg and takes every NWG-th tile.
+    constexpr int STEP = (NWG >= NBUF) ? NBUF : NWG;
+    const int own = (NWG >= NBUF) ? wg / GPB : wg;     // tiles with acc_count % STEP == own
+    const int col0 = (NWG >= NBUF) ? (wg % GPB) * COLS : 0;   // first column of this group
     const int quad = warp & 3;
     const int row = quad * 32 + lane;                 // particle within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
     constexpr float kLn2 = 0.6931471805599453f;
     constexpr int NCH = COLS / 32;                    // 32-column chunks per group and tile
-    uint32_t acc_count = 0;
+    uint32_t acc_base = 0;                            // accumulator uses before this item
     bool ok = true;
-    for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
-      const int chunk = item / prm.n_ptiles;
-      const int ptile = item - chunk * prm.n_ptiles;
+    for (int item = cluster_id; ok && item < prm.n_items; item += n_clusters) {
+      const int chunk = item / prm.n_pgroups;
+      const int ptile = (item - chunk * prm.n_pgroups) * CL + rank;
       const int tile_lo = chunk * prm.chunk_tiles;
       const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
-      double acc64 = 0.0;
-      for (int tile = tile_lo; tile < tile_hi; ++tile, ++acc_count) {
-        const int buf = acc_count % NBUF;
-        if (!kShareAll && ((NWG >= NBUF) ? (buf != wg / GPB) : (buf % NWG != wg))) continue;
+      // FP32 sum of this item's tiles with Kahan compensation (converted to FP64 once per item)
+      float ksum = 0.f, kcomp = 0.f;
+      const int first = tile_lo + static_cast<int>((static_cast<uint32_t>(own) + STEP - acc_base % STEP) % STEP);
+      for (int tile = first; tile < tile_hi; tile += STEP) {
+        const uint32_t acc_count = acc_base + static_cast<uint32_t>(tile - tile_lo);
+        const int buf = static_cast<int>(acc_count % NBUF);
         const uint32_t aph = (acc_count / NBUF) & 1u;
         // every lane waits; the vote reconverges the warp before the .sync.aligned TMEM loads
         ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit));
         if (!ok) break;
         ptx::tc_fence_after();
         const int valid = prm.t - tile * BN - col0;   // columns of this group inside [0, t)
-        // four independent chains: sums of |u| (binary) or of the shifts m (C > 2), and products
-        // of the log arguments, each factor below 2 (binary) or NC + 1 (C > 2)
-        float la[4] = {0.f, 0.f, 0.f, 0.f};
-        float pr[4] = {1.f, 1.f, 1.f, 1.f};
-        int pexp = 0;
+        const bool whole = valid >= COLS;
         const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN + col0);
-        auto renorm = [&]() {
+        float tile_val;                               // this tile's non-linear sum in log2 units
+        if constexpr (NC == 1) {
+          // four chains as two packed pairs (one FP32x2 add and one FP32x2 FMA per two terms):
+          // sums of |u| and products of the factors 1 + 2^-|u| in [1, 2]
+          float2 la = make_float2(0.f, 0.f), lb = make_float2(0.f, 0.f);
+          float2 pa = make_float2(1.f, 1.f), pb = make_float2(1.f, 1.f);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int bits = __float_as_int(pr[q]);
-            pexp += (bits >> 23) - 127;
-            pr[q] = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
-          }
-        };
-#pragma unroll 1
-        for (int ch = 0; ch < NCH; ++ch) {
-          float v[NC][32];
+          for (int ch = 0; ch < NCH; ++ch) {
+            float v[32];
+            ptx::tmem_ld_32x32b_x32(tbase + ch * 32, v);
+            ptx::tmem_wait_ld();
+            if (ch == NCH - 1) {
+              // this group's columns are in registers: release its share of the accumulator
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+            }
+            if (whole) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
-          ptx::tmem_wait_ld();
-          if (ch == NCH - 1) {
-            // this group's columns are in registers: release its share of the accumulator
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
-          }
-          const int j0 = ch * 32;
-          if constexpr (NC == 1) {
-            if (j0 + 32 <= valid) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const float a = fabsf(v[0][j]);
-                la[j & 3] += a;
-                pr[j & 3] = fmaf(pr[j & 3], ptx::ex2_approx(-a), pr[j & 3]);
+              for (int j = 0; j < 32; j += 4) {
+                const float a0 = fabsf(v[j]), a1 = fabsf(v[j + 1]), a2 = fabsf(v[j + 2]), a3 = fabsf(v[j + 3]);
+                la = __fadd2_rn(la, make_float2(a0, a1));
+                lb = __fadd2_rn(lb, make_float2(a2, a3));
+                pa = __ffma2_rn(pa, make_float2(ptx::ex2_approx(-a0), ptx::ex2_approx(-a1)), pa);
+                pb = __ffma2_rn(pb, make_float2(ptx::ex2_approx(-a2), ptx::ex2_approx(-a3)), pb);
               }
             } else {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const bool in = (j0 + j < valid);
-                const float a = in ? fabsf(v[0][j]) : 0.f;
-                const float e = in ? ptx::ex2_approx(-a) : 0.f;
-                la[j & 3] += a;
-                pr[j & 3] = fmaf(pr[j & 3], e, pr[j & 3]);
+              for (int j = 0; j < 32; j += 4) {
+                float a[4], e[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const bool in = (ch * 32 + j + q) < valid;
+                  a[q] = in ? fabsf(v[j + q]) : 0.f;
+                  e[q] = in ? ptx::ex2_approx(-a[q]) : 0.f;
+                }
+                la = __fadd2_rn(la, make_float2(a[0], a[1]));
+                lb = __fadd2_rn(lb, make_float2(a[2], a[3]));
+                pa = __ffma2_rn(pa, make_float2(e[0], e[1]), pa);
+                pb = __ffma2_rn(pb, make_float2(e[2], e[3]), pb);
               }
             }
-            if ((ch & 7) == 7) renorm();   // every 8 chunks: at most 64 factors below 2 per chain
-          } else {
+          }
+          // at most COLS / 4 <= 32 factors in [1, 2] per chain, so each pair's product is at
+          // most 2^64: no overflow within a tile
+          static_assert(COLS <= 128, "product chains must not overflow");
+          const float lsum = (la.x + la.y) + (lb.x + lb.y);
+          tile_val = fmaf(0.5f, lsum, ptx::lg2_approx(pa.x * pa.y) + ptx::lg2_approx(pb.x * pb.y));
+        } else {
+          // four chains: sums of the shifts m and products of the shifted sums (< NC + 1 each),
+          // binary exponents moved to an integer every four chunks
+          float la[4] = {0.f, 0.f, 0.f, 0.f};
+          float pr[4] = {1.f, 1.f, 1.f, 1.f};
+          int pexp = 0;
+          auto renorm = [&]() {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int bits = __float_as_int(pr[q]);
+              pexp += (bits >> 23) - 127;
+              pr[q] = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
+            }
+          };
+#pragma unroll 1
+          for (int ch = 0; ch < NCH; ++ch) {
+            float v[NC][32];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
+            ptx::tmem_wait_ld();
+            if (ch == NCH - 1) {
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+            }
+            const int j0 = ch * 32;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               float m = 0.f;
@@ -382,17 +438,22 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
               la[j & 3] += in ? m : 0.f;
               pr[j & 3] *= in ? sx : 1.f;
             }
-            if ((ch & 3) == 3) renorm();   // every 4 chunks: at most 32 factors below 4 per chain
+            if ((ch & 3) == 3) renorm();   // at most 32 factors below 4 per chain
           }
+          renorm();
+          const float pm = (pr[0] * pr[1]) * (pr[2] * pr[3]);   // product of four mantissas < 16
+          const float lsum = (la[0] + la[1]) + (la[2] + la[3]);
+          tile_val = (lsum + static_cast<float>(pexp)) + ptx::lg2_approx(pm);
         }
-        renorm();
-        const float pm = (pr[0] * pr[1]) * (pr[2] * pr[3]);   // product of four mantissas < 16
-        const float lsum = (la[0] + la[1]) + (la[2] + la[3]);
-        const float scale = (NC == 1) ? 0.5f : 1.0f;
-        acc64 += static_cast<double>(kLn2 * (fmaf(scale, lsum, static_cast<float>(pexp)) + ptx::lg2_approx(pm)));
+        const float y = kLn2 * tile_val - kcomp;
+        const float tsum = ksum + y;
+        kcomp = (tsum - ksum) - y;
+        ksum = tsum;
       }
       if (!ok) break;
-      prm.partial[(static_cast<size_t>(chunk) * NWG + wg) * prm.ppad + ptile * kBM + row] = acc64;
+      acc_base += static_cast<uint32_t>(tile_hi - tile_lo);
+      prm.partial[(static_cast<size_t>(chunk) * NWG + wg) * prm.ppad + ptile * kBM + row] =
+          static_cast<double>(ksum) - static_cast<double>(kcomp);
     }
   }
 
@@ -404,6 +465,8 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem_base, kTmemCols);
   }
+  // no CTA leaves while its peer may still arrive on its barriers or write its shared memory
+  if constexpr (CL > 1) ptx::cluster_sync();
 }
 
 // ll[p] = lin_p - sum over chunks and groups of partial (fixed order), lin_p = theta_p . lin
@@ -443,41 +506,88 @@ __global__ void encode_theta_kernel(const double* __restrict__ theta, int64_t P,
   for (int jj = 2 * k16 + j; jj < kt; jj += k16) rowp[jj] = __double2bfloat16(0.0);
 }
 
-template <int NC, int BN>
-sps_status launch_tc(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_bytes, const CUtensorMap& mapT,
-                     bool timed) {
-  auto kern = loglik_tc_kernel<NC, BN>;
+cudaLaunchConfig_t launch_config(int grid, int NC, uint32_t smem_bytes, cudaStream_t stream, int CL,
+                                 cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads_for(NC)));
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(CL);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Launch (launch = true) or query the co-resident clusters of one instance (launch = false).
+template <int NC, int BN, int CL>
+sps_status run_tc(sps_ctx* ctx, const TcParams* prm, int grid, uint32_t smem_bytes, const CUtensorMap* mapT,
+                  bool timed, int* max_clusters) {
+  auto kern = loglik_tc_kernel<NC, BN, CL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem_bytes));
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+  cudaLaunchAttribute attr[1];
+  if (!prm) {
+    cudaLaunchConfig_t cfg = launch_config(CL * ctx->num_sms, NC, smem_bytes, ctx->stream, CL, attr);
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    *max_clusters = n;
+    return SPS_OK;
+  }
+  cudaLaunchConfig_t cfg = launch_config(grid, NC, smem_bytes, ctx->stream, CL, attr);
   if (timed) hot_begin(ctx);
-  kern<<<grid, threads_for(NC), smem_bytes, ctx->stream>>>(ctx->enc.mapX, mapT, prm); ++ctx->launches;
+  e = cudaLaunchKernelEx(&cfg, kern, ctx->enc.mapX, *mapT, *prm); ++ctx->launches;
   if (timed) hot_end(ctx);
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("loglik_tc launch: ") + cudaGetErrorString(e));
   return SPS_OK;
 }
 
-sps_status launch_any(sps_ctx* ctx, const TcParams& prm, int grid, uint32_t smem_bytes, const CUtensorMap& mapT,
-                      bool timed) {
+template <int NC, int BN>
+sps_status run_cl(sps_ctx* ctx, int CL, const TcParams* prm, int grid, uint32_t smem_bytes, const CUtensorMap* mapT,
+                  bool timed, int* max_clusters) {
+  return CL == 2 ? run_tc<NC, BN, 2>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters)
+                 : run_tc<NC, BN, 1>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters);
+}
+
+sps_status run_any(sps_ctx* ctx, int CL, const TcParams* prm, int grid, uint32_t smem_bytes, const CUtensorMap* mapT,
+                   bool timed, int* max_clusters) {
   const int NC = ctx->NC, BN = ctx->enc.bn;
-  if (NC == 1 && BN == 256) return launch_tc<1, 256>(ctx, prm, grid, smem_bytes, mapT, timed);
-  if (NC == 1 && BN == 128) return launch_tc<1, 128>(ctx, prm, grid, smem_bytes, mapT, timed);
-  if (NC == 2 && BN == 128) return launch_tc<2, 128>(ctx, prm, grid, smem_bytes, mapT, timed);
-  if (NC == 2 && BN == 64) return launch_tc<2, 64>(ctx, prm, grid, smem_bytes, mapT, timed);
-  if (NC == 3 && BN == 64) return launch_tc<3, 64>(ctx, prm, grid, smem_bytes, mapT, timed);
-  if (NC == 3 && BN == 32) return launch_tc<3, 32>(ctx, prm, grid, smem_bytes, mapT, timed);
+  if (NC == 1 && BN == 256) return run_cl<1, 256>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  if (NC == 1 && BN == 128) return run_cl<1, 128>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  if (NC == 2 && BN == 128) return run_cl<2, 128>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  if (NC == 2 && BN == 64) return run_cl<2, 64>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  if (NC == 3 && BN == 64) return run_cl<3, 64>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  if (NC == 3 && BN == 32) return run_cl<3, 32>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
   return fail(ctx, SPS_ERR_UNSUPPORTED, "no tensor-core tile for this shape");
+}
+
+// Persistent grid of one call: CL CTAs per cluster, at most the co-resident clusters, at most
+// one cluster per work item.
+int grid_for(const sps_ctx* ctx, const TcParams& prm) {
+  const int CL = ctx->enc.cl;
+  const int cap = (CL > 1) ? ctx->enc.max_clusters : ctx->num_sms;
+  return CL * std::max(1, std::min(cap, prm.n_items));
 }
 
 // Work decomposition and pipeline depth of one call; false when the tile does not fit.
 bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t* smem_bytes) {
   const XEncoding& enc = ctx->enc;
   const int NC = ctx->NC, BN = enc.bn;
-  const int ppad = static_cast<int>((P + kBM - 1) / kBM * kBM);
+  const int prow = kBM * enc.cl;                  // particle rows of one work item
+  const int ppad = static_cast<int>((P + prow - 1) / prow * prow);
   *prm = TcParams{};
   prm->ppad = ppad;
   prm->n_ptiles = ppad / kBM;
+  prm->n_pgroups = prm->n_ptiles / enc.cl;
   prm->t = static_cast<int>(t);
   prm->n_tiles = static_cast<int>((t + BN - 1) / BN);
   prm->kbx = enc.kx / kKB;
@@ -488,15 +598,15 @@ bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t
   prm->th_row_stride = ppad;
   // chunking: enough work items to balance the persistent grid, items long enough to amortise
   // the theta loads
-  const int grid_max = ctx->num_sms;
+  const int grid_max = (enc.cl > 1) ? enc.max_clusters : ctx->num_sms;   // concurrent work items
   int chunk_tiles = std::max(1, std::min(prm->n_tiles, 4096 / BN));
   const int64_t want_items = 8LL * grid_max;
   while (chunk_tiles > 2 &&
-         static_cast<int64_t>(prm->n_ptiles) * ((prm->n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
+         static_cast<int64_t>(prm->n_pgroups) * ((prm->n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
     chunk_tiles /= 2;
   prm->chunk_tiles = chunk_tiles;
   prm->n_chunks = std::max(1, (prm->n_tiles + chunk_tiles - 1) / chunk_tiles);
-  prm->n_items = prm->n_tiles > 0 ? prm->n_ptiles * prm->n_chunks : 0;
+  prm->n_items = prm->n_tiles > 0 ? prm->n_pgroups * prm->n_chunks : 0;
   int stages = 0, th_bufs = 0;
   if (!pick_stages(NC, BN, prm->kbx, prm->kbt, &stages, &th_bufs)) return false;
   prm->stages = stages;
@@ -521,6 +631,25 @@ int tc_tile_rows(int NC, int kx, int kt) {
   const int BN = cands[NC - 1][1];
   int st = 0, tb = 0;
   return pick_stages(NC, BN, kx / kKB, kt / kKB, &st, &tb) ? BN : 0;
+}
+
+sps_status tc_configure_cluster(sps_ctx* ctx) {
+  XEncoding& enc = ctx->enc;
+  enc.cl = 1;
+  enc.max_clusters = 0;
+  if (enc.bn == 0) return SPS_OK;
+  const char* env = getenv("SPS_TC_CLUSTER");
+  if (env && env[0] == '1' && env[1] == 0) return SPS_OK;
+  int stages = 0, th_bufs = 0;
+  if (!pick_stages(ctx->NC, enc.bn, enc.kx / kKB, enc.kt / kKB, &stages, &th_bufs)) return SPS_OK;
+  const uint32_t smem_bytes = smem_layout(ctx->NC, enc.bn, enc.kx / kKB, enc.kt / kKB, stages, th_bufs).total + 1024;
+  int n = 0;
+  SPS_TRY(run_any(ctx, 2, nullptr, 0, smem_bytes, nullptr, false, &n));
+  if (n >= 1) {
+    enc.cl = 2;
+    enc.max_clusters = n;
+  }
+  return SPS_OK;
 }
 
 sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll) {
@@ -554,7 +683,7 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
   prm.flag = S.flag.as<int>();
   SPS_CUDA_TRY(cudaMemsetAsync(prm.flag, 0, sizeof(int), ctx->stream));
   if (prm.n_items > 0)
-    SPS_TRY(launch_any(ctx, prm, std::min(ctx->num_sms, prm.n_items), smem_bytes, S.mapT, true));
+    SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));
   loglik_finalize_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
       d_theta, P, ctx->D, ctx->lin.as<double>(), prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0,
       ppad, d_ll);
@@ -651,7 +780,7 @@ sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, i
   prm.flag = flag;
   SPS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));   // the flag must start at zero
   if (prm.n_items > 0)
-    SPS_TRY(launch_any(ctx, prm, std::min(ctx->num_sms, prm.n_items), smem_bytes, mapT, false));
+    SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &mapT, false, nullptr));
   loglik_finalize_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
       d_theta, P, ctx->D, ctx->lin.as<double>(), partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad,
       d_ll);

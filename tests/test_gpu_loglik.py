@@ -137,3 +137,21 @@ def test_c3_multinomial_sampled(torch_cuda, prec):
     ref = oracle_loglik(w.X, w.y, theta[idx], w.C, w.n)
     rtol = 1e-5 if prec == "split" else 1e-6
     np.testing.assert_allclose(got[idx], ref, rtol=rtol)
+
+
+@pytest.mark.parametrize("C,k,exact", [(2, 30, 10), (3, 12, 4), (4, 50, 10)])
+def test_cluster_pairs_match_single_ctas_bitwise(torch_cuda, C, k, exact, monkeypatch):
+    # the fused kernel's CTA pairs share X tiles by multicast; each tile's arithmetic and the
+    # order of the partial sums are those of single CTAs, so the results are identical
+    X, y = _mk(1000, k, C, 20 + k, exact)
+    g = np.random.Generator(np.random.PCG64(5))
+    s_pair = _sps(X, y, C)
+    monkeypatch.setenv("SPS_TC_CLUSTER", "1")
+    s_single = _sps(X, y, C)
+    for P, t in ((300, 1000), (1, 1), (129, 777), (2000, 513)):
+        theta = 0.2 * g.standard_normal((P, k * (C - 1)))
+        a = s_pair.loglik(theta, t, "split")
+        b = s_single.loglik(theta, t, "split")
+        np.testing.assert_array_equal(a, b)
+        ref = oracle_loglik(X, y, theta, C, t)
+        assert np.all(np.abs(a - ref) <= _tol(X, theta, C, t, ref, "split"))

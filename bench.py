@@ -45,48 +45,88 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clocks and throttle reasons sampled during the timed region.
 
-    def __init__(self, index: int = 0):
+    Samples come from NVML in a background thread (every 10 ms, a few microseconds per query, no
+    process started while the region runs); without NVML, from an `nvidia-smi -lms` process
+    started before the region and stopped after it. Reads only: no setting is changed."""
+
+    # clock-event reason bits (NVML): hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
+    # sw_power_cap
+    _BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
+
+    def __init__(self, index: int = 0, period_s: float = 0.01):
         self.index = index
-        self.samples = []
+        self.period = period_s
+        self.samples = []          # (sm_mhz, sm_max_mhz, reasons set)
         self._stop = threading.Event()
         self._t = None
+        self._proc = None
+        self._nvml = None
 
-    def _run(self):
-        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
-        while not self._stop.is_set():
+    def _run_nvml(self):
+        nv = self._nvml
+        h = nv.nvmlDeviceGetHandleByIndex(self.index)
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while True:
             try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([v.strip() for v in out.split(",")])
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                bits = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                self.samples.append((float(sm), float(mx), {k for k, b in self._BITS.items() if bits & b}))
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            if self._stop.wait(self.period):
+                break
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nvml = pynvml
+            self._t = threading.Thread(target=self._run_nvml, daemon=True)
+            self._t.start()
+        except Exception:
+            q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap")
+            try:
+                self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                               "--format=csv,noheader,nounits", "-lms", "50"],
+                                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                time.sleep(0.2)
+            except Exception:
+                self._proc = None
         return self
 
     def __exit__(self, *a):
         self._stop.set()
         if self._t:
             self._t.join(timeout=10)
+            try:
+                self._nvml.nvmlShutdown()
+            except Exception:
+                pass
+        if self._proc:
+            time.sleep(0.1)
+            self._proc.terminate()
+            try:
+                out, _ = self._proc.communicate(timeout=5)
+            except Exception:
+                out = ""
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in out.splitlines():
+                f = [v.strip() for v in line.split(",")]
+                if len(f) >= 6 and f[0].replace(".", "").isdigit():
+                    self.samples.append((float(f[0]), float(f[1]),
+                                         {names[i] for i in range(4) if f[2 + i] == "Active"}))
 
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples),
+                "sm_max_mhz": max(s[1] for s in self.samples),
+                "reasons": sorted(set().union(*(s[2] for s in self.samples))),
+                "samples": len(self.samples), "source": "nvml" if self._nvml else "nvidia-smi -lms 50"}
 
 
 def dist_setup():
@@ -343,7 +383,7 @@ def sps_wall(w, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split", choices=["split", "fp32"])

@@ -100,21 +100,25 @@ __global__ void encode_x_kernel(const double* __restrict__ X, int64_t n, int k,
 }
 
 // lin[c*k + i] = prefix[tile] + sum over the remaining rows s in [128*tile, t) of w_c(y_s) x_{s,i}.
+// One warp per output: lanes take every 32nd row, then a shuffle sum (FP64).
 __global__ void lin_tail_kernel(const double* __restrict__ prefix, const double* __restrict__ X,
                                 const int* __restrict__ y, int k, int NC, int64_t t,
                                 double* __restrict__ lin) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (idx >= NC * k) return;
   const int c = idx / k;
   const int i = idx - c * k;
   const int64_t tile = t / 128;
-  double a = prefix[tile * NC * k + idx];
-  for (int64_t s = tile * 128; s < t; ++s) {
+  double a = 0.0;
+  for (int64_t s = tile * 128 + lane; s < t; s += 32) {
     const int ys = y[s];
     const double w = (NC == 1) ? (ys == 1 ? 0.5 : -0.5) : (ys == c + 1 ? 1.0 : 0.0);
     a = fma(w, X[s * k + i], a);
   }
-  lin[idx] = a;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) lin[idx] = prefix[tile * NC * k + idx] + a;
 }
 
 sps_status to_device(sps_ctx* ctx, DevBuf& buf, const void* host, size_t bytes) {
@@ -165,7 +169,7 @@ sps_status make_map_bf16(sps_ctx* ctx, CUtensorMap* map, const void* base, uint6
 sps_status ensure_lin(sps_ctx* ctx, int64_t t) {
   if (ctx->lin_t == t) return SPS_OK;
   const int nk = ctx->NC * ctx->k;
-  lin_tail_kernel<<<(nk + 127) / 128, 128, 0, ctx->stream>>>(ctx->lin_prefix.as<double>(), ctx->Xd.as<double>(),
+  lin_tail_kernel<<<(nk + 3) / 4, 128, 0, ctx->stream>>>(ctx->lin_prefix.as<double>(), ctx->Xd.as<double>(),
                                                             ctx->y.as<int>(), ctx->k, ctx->NC, t,
                                                             ctx->lin.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());

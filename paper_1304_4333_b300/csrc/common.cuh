@@ -133,13 +133,14 @@ struct sps_state {
   sps::DevBuf lp, lp_prop;        // FP64 [P] prior log kernel
   sps::DevBuf logw;               // FP64 [P]
   sps::DevBuf logml;              // FP64 [J]
-  sps::DevBuf lwbuf;              // FP64 [block x P] C-phase running log weights
+  sps::DevBuf lwbuf;              // float2 [block x P] C-phase running log weights (Kahan pairs)
+  sps::DevBuf lwstate;            // float2 [P] running log weights at the start of a C-phase block
+  sps::DevBuf gmax;               // FP64 [J] group maxima of logw (S-phase weight scale)
   sps::DevBuf ess_buf;            // FP64 [block] ESS per observation of a block
   sps::DevBuf idx;                // int32 [P]
   sps::DevBuf scratch;            // moments, covariance partials, counters
   sps::DevBuf cov;                // FP64 [D x D]
   sps::DevBuf chol;               // FP64 [D x D]
-  sps::DevBuf mean;               // FP64 [D]
   sps::DevBuf counters;           // int/unsigned counters (accepts, error flags)
   sps::DevBuf grad, grad_prop;    // FP64 [P x D] (MALA)
   sps::DevBuf zq;                 // FP32 [P x D] MALA: 1/2 L' g(theta) + z of the current proposal
@@ -174,12 +175,50 @@ sps_status tc_configure_cluster(sps_ctx* ctx);
 // Start/stop event of one timed launch of the fused kernel (no-ops when timing is off).
 void hot_begin(sps_ctx* ctx);
 void hot_end(sps_ctx* ctx);
-// C-phase running log weights for observations [s_lo, s_hi): d_lw[j*P + p] (FP64).
+// C-phase running log weights for observations [s_lo, s_hi): d_lw[j*P + p] = d_lw_in[p] plus the
+// terms of observations s_lo..s_lo+j, as Kahan pairs (s, c) of value s - c.
 sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
-                             int64_t s_hi, const double* d_logw_in, double* d_lw);
+                             int64_t s_hi, const float2* d_lw_in, float2* d_lw);
 // Log-likelihood and gradient (FP32 products, FP64 sums across 32-observation tiles).
 sps_status loglik_grad_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                             double* d_grad);
+
+}  // namespace sps
+
+// ------------------------------------------------------------------------------------------
+// FP64 <-> FP32 conversions by integer operations. FP64 arithmetic and conversion instructions
+// run at about 1.5-1.8 per clock per SM on this GPU (FP32: 128), so element-wise code converts
+// with these and keeps FP64 instructions for reductions.
+
+namespace sps {
+
+// double -> float, rounding toward zero (relative error < 2^-23). Zero and values below the
+// float normal range give a signed zero, values above it a signed infinity, NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  if (e <= 896u) return __uint_as_float(sign);                          // |d| < 2^-126
+  if (e >= 1151u)                                                        // |d| >= 2^128, inf, NaN
+    return __uint_as_float(sign | 0x7F800000u | ((e == 0x7FFu && ((hi & 0xFFFFFu) | lo)) ? 0x400000u : 0u));
+  return __uint_as_float(sign | ((e - 896u) << 23) | m);
+}
+
+// float -> double, exact (float subnormals give a signed zero).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  unsigned hi;
+  if (e == 0u) hi = sign;
+  else if (e == 0xFFu) hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  else hi = sign | ((e + 896u) << 20) | (m >> 3);
+  const unsigned lo = (e == 0u || e == 0xFFu) ? 0u : (m << 29);
+  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(hi) << 32) | lo));
+}
 
 }  // namespace sps
 

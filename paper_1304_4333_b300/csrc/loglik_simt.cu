@@ -25,7 +25,7 @@ __device__ __forceinline__ void load_theta_t(float* sm, const double* __restrict
     const int pp = idx / D;
     const int d = idx - pp * D;
     const int64_t p = p0 + pp;
-    sm[d * kP + pp] = (p < P) ? static_cast<float>(theta[p * D + d]) : 0.f;
+    sm[d * kP + pp] = (p < P) ? f64_to_f32(theta[p * D + d]) : 0.f;
   }
 }
 
@@ -41,14 +41,25 @@ __device__ __forceinline__ float logit_term(const float* eta, int NC, int yo) {
 
 constexpr int kMaxNC = 15;
 
+// Running C-phase log weight kept as a Kahan pair (s, c), value s - c: one FP32 add of the term
+// and three FP32 operations of compensation per observation, about FP64-accumulation accuracy
+// for FP32 terms without FP64 instructions.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 // Each thread: particle p0 + threadIdx.x; observations [s_lo, s_hi).
-// mode 0: partial[blockIdx.y * P + p] = sum of terms (FP64 across tiles);
-// mode 1: C-phase increments: lw[j * P + p] = logw_in[p] + sum_{s_lo <= s' <= s_lo + j} term.
+// mode 0: out[blockIdx.y * P + p] = sum of terms (FP64 across tiles);
+// mode 1: C-phase increments: lw_out[j * P + p] = lw_in[p] + sum_{s_lo <= s' <= s_lo + j} term,
+//         as Kahan pairs.
 __global__ void __launch_bounds__(kP)
 fp32_terms_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
                   const float* __restrict__ X, const int* __restrict__ y, int64_t s_begin,
                   int64_t s_end, int64_t chunk, int mode, double* __restrict__ out,
-                  const double* __restrict__ logw_in) {
+                  float2* __restrict__ lw_out, const float2* __restrict__ lw_in) {
   extern __shared__ float smf[];
   const int D = k * NC;
   float* th = smf;                          // [D][128]
@@ -59,7 +70,13 @@ fp32_terms_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
   const int64_t s_lo = s_begin + static_cast<int64_t>(blockIdx.y) * chunk;
   const int64_t s_hi = (s_lo + chunk < s_end) ? s_lo + chunk : s_end;
   load_theta_t(th, theta, P, D, p0);
-  double acc = (mode == 1 && p < P) ? logw_in[p] : 0.0;
+  double acc = 0.0;
+  float ks = 0.f, kc = 0.f;
+  if (mode == 1 && p < P) {
+    const float2 v = lw_in[p];
+    ks = v.x;
+    kc = v.y;
+  }
   float eta[kMaxNC];
   for (int64_t s0 = s_lo; s0 < s_hi; s0 += kTS) {
     const int ns = static_cast<int>(s_hi - s0 < kTS ? s_hi - s0 : kTS);
@@ -78,13 +95,13 @@ fp32_terms_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
       }
       const float term = logit_term(eta, NC, ys[j]);
       if (mode == 1) {
-        acc += static_cast<double>(term);
-        if (p < P) out[(s0 - s_lo + j) * P + p] = acc;
+        kahan_add(ks, kc, term);
+        if (p < P) lw_out[(s0 - s_lo + j) * P + p] = make_float2(ks, kc);
       } else {
         tile += term;
       }
     }
-    if (mode == 0) acc += static_cast<double>(tile);
+    if (mode == 0) acc += f32_to_f64(tile);
   }
   if (mode == 0 && p < P) out[static_cast<int64_t>(blockIdx.y) * P + p] = acc;
 }
@@ -96,7 +113,7 @@ template <int KMAX, int NC>
 __global__ void __launch_bounds__(kP)
 fp32_terms_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const float* __restrict__ X,
                       const int* __restrict__ y, int64_t s_begin, int64_t s_end, int64_t chunk, int mode,
-                      double* __restrict__ out, const double* __restrict__ logw_in) {
+                      double* __restrict__ out, float2* __restrict__ lw_out, const float2* __restrict__ lw_in) {
   __shared__ __align__(16) float xs[kTS][KMAX];
   __shared__ int ys[kTS];
   const int D = k * NC;
@@ -107,8 +124,14 @@ fp32_terms_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const 
 #pragma unroll
   for (int c = 0; c < NC; ++c)
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i) th[c][i] = (p < P && i < k) ? static_cast<float>(theta[p * D + c * k + i]) : 0.f;
-  double acc = (mode == 1 && p < P) ? logw_in[p] : 0.0;
+    for (int i = 0; i < KMAX; ++i) th[c][i] = (p < P && i < k) ? f64_to_f32(theta[p * D + c * k + i]) : 0.f;
+  double acc = 0.0;
+  float ks = 0.f, kc = 0.f;
+  if (mode == 1 && p < P) {
+    const float2 v = lw_in[p];
+    ks = v.x;
+    kc = v.y;
+  }
   for (int64_t s0 = s_lo; s0 < s_hi; s0 += kTS) {
     const int ns = static_cast<int>(s_hi - s0 < kTS ? s_hi - s0 : kTS);
     __syncthreads();
@@ -136,27 +159,27 @@ fp32_terms_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const 
       }
       const float term = logit_term(eta, NC, ys[j]);
       if (mode == 1) {
-        acc += static_cast<double>(term);
-        if (p < P) out[(s0 - s_lo + j) * P + p] = acc;
+        kahan_add(ks, kc, term);
+        if (p < P) lw_out[(s0 - s_lo + j) * P + p] = make_float2(ks, kc);
       } else {
         tile += term;
       }
     }
-    if (mode == 0) acc += static_cast<double>(tile);
+    if (mode == 0) acc += f32_to_f64(tile);
   }
   if (mode == 0 && p < P) out[static_cast<int64_t>(blockIdx.y) * P + p] = acc;
 }
 
 // Launch the register variant when the model fits one of its instantiations.
 bool launch_reg(sps_ctx* ctx, dim3 grid, const double* theta, int64_t P, int64_t s_begin, int64_t s_end,
-                int64_t chunk, int mode, double* out, const double* logw_in) {
+                int64_t chunk, int mode, double* out, float2* lw_out, const float2* lw_in) {
   const int k = ctx->k, NC = ctx->NC;
   const float* X = ctx->Xf.as<float>();
   const int* y = ctx->y.as<int>();
 #define SPS_REG_CASE(KM, NCM)                                                                          \
   if (NC == NCM && k <= KM) {                                                                          \
     fp32_terms_reg_kernel<KM, NCM><<<grid, kP, 0, ctx->stream>>>(theta, P, k, X, y, s_begin, s_end, chunk, \
-                                                                 mode, out, logw_in);                  \
+                                                                 mode, out, lw_out, lw_in);            \
     ++ctx->launches;                                                                                   \
     return true;                                                                                       \
   }
@@ -203,11 +226,12 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
   SPS_CUDA_TRY(ctx->ll.partial.reserve(static_cast<size_t>(chunks) * P * sizeof(double)));
   double* partial = ctx->ll.partial.as<double>();
   dim3 grid(static_cast<unsigned>(ptiles), static_cast<unsigned>(chunks));
-  if (!launch_reg(ctx, grid, d_theta, P, 0, t, chunk, 0, partial, nullptr)) {
+  if (!launch_reg(ctx, grid, d_theta, P, 0, t, chunk, 0, partial, nullptr, nullptr)) {
     SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem)));
     fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
-                                                       ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr); ++ctx->launches;
+                                                       ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr,
+                                                       nullptr); ++ctx->launches;
   }
   SPS_CUDA_TRY(cudaGetLastError());
   sum_slices_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
@@ -217,18 +241,18 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
 }
 
 sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
-                             int64_t s_hi, const double* d_logw_in, double* d_lw) {
+                             int64_t s_hi, const float2* d_lw_in, float2* d_lw) {
   const size_t smem = fp32_smem(ctx->k, ctx->NC);
   if (ctx->NC > kMaxNC || smem > 200 * 1024)
     return fail(ctx, SPS_ERR_UNSUPPORTED, "C phase: k*(C-1) too large");
   const int64_t ptiles = (P + kP - 1) / kP;
   dim3 grid(static_cast<unsigned>(ptiles), 1);
-  if (!launch_reg(ctx, grid, d_theta, P, s_lo, s_hi, s_hi - s_lo, 1, d_lw, d_logw_in)) {
+  if (!launch_reg(ctx, grid, d_theta, P, s_lo, s_hi, s_hi - s_lo, 1, nullptr, d_lw, d_lw_in)) {
     SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem)));
     fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
-                                                       ctx->y.as<int>(), s_lo, s_hi, s_hi - s_lo, 1, d_lw,
-                                                       d_logw_in); ++ctx->launches;
+                                                       ctx->y.as<int>(), s_lo, s_hi, s_hi - s_lo, 1, nullptr,
+                                                       d_lw, d_lw_in); ++ctx->launches;
   }
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;

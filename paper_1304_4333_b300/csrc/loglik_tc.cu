@@ -470,40 +470,69 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 }
 
 // ll[p] = lin_p - sum over chunks and groups of partial (fixed order), lin_p = theta_p . lin
-// with lin [NC x k] in the original column order.
-__global__ void loglik_finalize_kernel(const double* __restrict__ theta, int64_t P, int D,
-                                       const double* __restrict__ lin, const double* __restrict__ partial,
-                                       int slices, int ppad, double* __restrict__ ll) {
+// with lin [NC x k] in the original column order (FP64, four interleaved partial sums each).
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads)
+loglik_finalize_kernel(const double* __restrict__ theta, int64_t P, int D,
+                       const double* __restrict__ lin, const double* __restrict__ partial,
+                       int slices, int ppad, double* __restrict__ ll) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= P) return;
-  double a = 0.0;
   const double* th = theta + p * D;
-  for (int i = 0; i < D; ++i) a = fma(th[i], lin[i], a);
-  double s = 0.0;
-  for (int q = 0; q < slices; ++q) s += partial[static_cast<size_t>(q) * ppad + p];
-  ll[p] = a - s;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int i = 0;
+  for (; i + 4 <= D; i += 4) {
+    a0 = fma(th[i], lin[i], a0);
+    a1 = fma(th[i + 1], lin[i + 1], a1);
+    a2 = fma(th[i + 2], lin[i + 2], a2);
+    a3 = fma(th[i + 3], lin[i + 3], a3);
+  }
+  for (; i < D; ++i) a0 = fma(th[i], lin[i], a0);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const double* q = partial + p;
+  int j = 0;
+  for (; j + 4 <= slices; j += 4) {
+    s0 += q[static_cast<size_t>(j) * ppad];
+    s1 += q[static_cast<size_t>(j + 1) * ppad];
+    s2 += q[static_cast<size_t>(j + 2) * ppad];
+    s3 += q[static_cast<size_t>(j + 3) * ppad];
+  }
+  for (; j < slices; ++j) s0 += q[static_cast<size_t>(j) * ppad];
+  ll[p] = ((a0 + a1) + (a2 + a3)) - ((s0 + s1) + (s2 + s3));
+}
+
+sps_status launch_finalize(sps_ctx* ctx, const double* theta, int64_t P, const double* partial, int slices,
+                           int ppad, double* ll) {
+  loglik_finalize_kernel<<<static_cast<unsigned>((P + kFinThreads - 1) / kFinThreads), kFinThreads, 0,
+                           ctx->stream>>>(theta, P, ctx->D, ctx->lin.as<double>(), partial, slices, ppad, ll);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
 }
 
 // theta [P x D] FP64 (original order, class-major) -> operand rows [NC*ppad x kt] bf16 holding
 // [hi(theta log2 e) | lo(theta log2 e)] over the internal (permuted) columns; padding zero.
+// FP32 arithmetic: v = f32(theta) log2(e) carries 23 bits, of which hi + lo keep 16. One warp
+// per operand row (rows = NC * ppad < 2^31), lanes over its columns.
 __global__ void encode_theta_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
                                     const int* __restrict__ perm, int k16, int kt, int ppad,
                                     __nv_bfloat16* __restrict__ out) {
-  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  const int64_t total = static_cast<int64_t>(NC) * ppad * k16;
-  if (idx >= total) return;
-  const int j = static_cast<int>(idx % k16);
-  const int64_t r = idx / k16;
-  const int c = static_cast<int>(r / ppad);
-  const int64_t p = r - static_cast<int64_t>(c) * ppad;
-  double v = 0.0;
-  if (p < P && j < k) v = theta[p * (static_cast<int64_t>(NC) * k) + c * k + perm[j]] * 1.4426950408889634;
-  const __nv_bfloat16 h = __double2bfloat16(v);
-  const double rem = v - static_cast<double>(__bfloat162float(h));
-  __nv_bfloat16* rowp = out + r * kt;
-  rowp[j] = h;
-  rowp[k16 + j] = __double2bfloat16(rem);
-  for (int jj = 2 * k16 + j; jj < kt; jj += k16) rowp[jj] = __double2bfloat16(0.0);
+  const int r = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= NC * ppad) return;
+  const int c = r / ppad;
+  const int p = r - c * ppad;
+  const double* src = theta + static_cast<int64_t>(p) * (NC * k) + c * k;
+  __nv_bfloat16* rowp = out + static_cast<int64_t>(r) * kt;
+  for (int j = lane; j < k16; j += 32) {
+    float v = 0.f;
+    if (p < P && j < k) v = f64_to_f32(src[perm[j]]) * 1.44269504f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    rowp[j] = h;
+    rowp[k16 + j] = __float2bfloat16_rn(v - __bfloat162float(h));   // v - h is exact
+  }
+  for (int jj = 2 * k16 + lane; jj < kt; jj += 32) rowp[jj] = __float2bfloat16_rn(0.f);
 }
 
 cudaLaunchConfig_t launch_config(int grid, int NC, uint32_t smem_bytes, cudaStream_t stream, int CL,
@@ -669,8 +698,8 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
   }
   SPS_TRY(make_map_bf16(ctx, &S.mapT, S.thetaP.ptr, static_cast<uint64_t>(NC) * ppad, enc.kt, kBM));
   {
-    const int64_t total = static_cast<int64_t>(NC) * ppad * enc.k16;
-    encode_theta_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, ctx->stream>>>(
+    const int64_t rows = static_cast<int64_t>(NC) * ppad;   // one warp per row, 8 rows per block
+    encode_theta_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
         d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, ppad, S.thetaP.as<__nv_bfloat16>());
     ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
@@ -684,12 +713,7 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
   SPS_CUDA_TRY(cudaMemsetAsync(prm.flag, 0, sizeof(int), ctx->stream));
   if (prm.n_items > 0)
     SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));
-  loglik_finalize_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
-      d_theta, P, ctx->D, ctx->lin.as<double>(), prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0,
-      ppad, d_ll);
-  ++ctx->launches;
-  SPS_CUDA_TRY(cudaGetLastError());
-  return SPS_OK;
+  return launch_finalize(ctx, d_theta, P, prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad, d_ll);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -769,8 +793,8 @@ sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, i
   CUtensorMap mapT;
   SPS_TRY(make_map_bf16(ctx, &mapT, ops, static_cast<uint64_t>(NC) * ppad, enc.kt, kBM));
   {
-    const int64_t total = static_cast<int64_t>(NC) * ppad * enc.k16;
-    encode_theta_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, ctx->stream>>>(
+    const int64_t rows = static_cast<int64_t>(NC) * ppad;   // one warp per row, 8 rows per block
+    encode_theta_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
         d_theta, P, ctx->k, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, ppad, ops);
     ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
@@ -781,12 +805,7 @@ sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, i
   SPS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));   // the flag must start at zero
   if (prm.n_items > 0)
     SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &mapT, false, nullptr));
-  loglik_finalize_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
-      d_theta, P, ctx->D, ctx->lin.as<double>(), partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad,
-      d_ll);
-  ++ctx->launches;
-  SPS_CUDA_TRY(cudaGetLastError());
-  return SPS_OK;
+  return launch_finalize(ctx, d_theta, P, partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad, d_ll);
 }
 
 }  // namespace sps

@@ -115,22 +115,25 @@ __device__ double block_max(double v, double* sh) {
 // ------------------------------------------------------------------------------ prior
 
 // Prior log kernel -(1/2) (theta - mu)' Prec (theta - mu); prec is diagonal [D] unless full.
+// FP32 element-wise (d = f32(theta) - f32(mu)) and FP32 sums: the same deterministic function
+// for every particle and proposal, so Metropolis ratios stay exact for it; its relative error
+// (about 1e-7) is far below the posterior's scale.
 __device__ double prior_log_kernel(const double* th, const double* mu, const double* prec, int D, bool full) {
-  double a = 0.0;
+  float a = 0.f;
   if (!full) {
     for (int i = 0; i < D; ++i) {
-      const double d = th[i] - mu[i];
-      a = fma(d * d, prec[i], a);
+      const float d = f64_to_f32(th[i]) - f64_to_f32(mu[i]);
+      a = fmaf(d * d, f64_to_f32(prec[i]), a);
     }
   } else {
     for (int i = 0; i < D; ++i) {
-      const double di = th[i] - mu[i];
-      double r = 0.0;
-      for (int j = 0; j < D; ++j) r = fma(prec[i * D + j], th[j] - mu[j], r);
-      a = fma(di, r, a);
+      const float di = f64_to_f32(th[i]) - f64_to_f32(mu[i]);
+      float r = 0.f;
+      for (int j = 0; j < D; ++j) r = fmaf(f64_to_f32(prec[i * D + j]), f64_to_f32(th[j]) - f64_to_f32(mu[j]), r);
+      a = fmaf(di, r, a);
     }
   }
-  return -0.5 * a;
+  return -0.5 * f32_to_f64(a);
 }
 
 // Algorithm 1 step 1: theta_p = mu + L0 z, z iid N(0, 1) (FP64 Box-Muller from Philox).
@@ -172,34 +175,74 @@ __global__ void prior_lp_kernel(const double* __restrict__ theta, int64_t P, int
 
 // ------------------------------------------------------------------------------ C phase
 
-// ESS(s) of rows of running log weights (Eq. 14). Block (row, part) reduces its slice of the
-// row to (max, sum e, sum e^2) with e = exp of the FP64 difference to the slice maximum taken in
-// FP32 and FP64 sums; the merge rescales the parts to the row maximum in FP64.
+// A running log weight as a pair (s, c) of value s - c: the C phase's Kahan pairs, or an FP64
+// value split into its FP32 truncation and the FP32 remainder.
+struct LwPair {
+  float s, c;
+};
+__device__ __forceinline__ LwPair load_lw(const float2* __restrict__ r, int64_t p) {
+  const float2 v = r[p];
+  return {v.x, v.y};
+}
+__device__ __forceinline__ LwPair load_lw(const double* __restrict__ r, int64_t p) {
+  const double v = r[p];
+  const float hi = f64_to_f32(v);
+  return {hi, f64_to_f32(f32_to_f64(hi) - v)};
+}
+
+__device__ float block_max_f(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  float t = (threadIdx.x < nw) ? sh[threadIdx.x] : -INFINITY;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (l == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// ESS(s) of rows of running log weights (Eq. 14), in two kernels. Block (row, part) reads its
+// slice of the row once: each thread keeps an online maximum m of s and the FP32 sums of
+// e = exp((s - m) - c) and e^2, rescaled when m grows (s - m is exact near the maximum, where
+// the weights matter); the block rescales its threads to the block maximum and sums in FP64.
+// The merge rescales the parts to the row maximum and returns (sum e)^2 / sum e^2.
 constexpr int kEssParts = 8;
 
-__global__ void ess_part_kernel(const double* __restrict__ lw, int64_t P, double* __restrict__ parts) {
+template <class InT>
+__global__ void ess_part_kernel(const InT* __restrict__ lw, int64_t P, double* __restrict__ parts) {
+  __shared__ float shf[33];
   __shared__ double sh[33];
-  const double* row = lw + static_cast<int64_t>(blockIdx.x) * P;
+  const InT* row = lw + static_cast<int64_t>(blockIdx.x) * P;
   const int64_t per = (P + gridDim.y - 1) / gridDim.y;
   const int64_t lo = blockIdx.y * per, hi = min(P, lo + per);
-  double m = -INFINITY;
-  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) m = fmax(m, row[p]);
-  m = block_max(m, sh);
-  double s1 = 0.0, s2 = 0.0;
-  if (m > -INFINITY) {
-    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-      const double w = static_cast<double>(expf(static_cast<float>(row[p] - m)));
-      s1 += w;
-      s2 += w * w;
+  float m = -INFINITY, s1 = 0.f, s2 = 0.f;
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+    const LwPair v = load_lw(row, p);
+    if (v.s > m) {
+      const float f = (m > -INFINITY) ? __expf(m - v.s) : 0.f;
+      s1 *= f;
+      s2 *= f * f;
+      m = v.s;
     }
+    const float e = __expf((v.s - m) - v.c);
+    s1 += e;
+    s2 = fmaf(e, e, s2);
   }
-  s1 = block_sum(s1, sh);
-  s2 = block_sum(s2, sh);
+  const float M = block_max_f(m, shf);
+  const float f = (m > -INFINITY) ? __expf(m - M) : 0.f;
+  const double t1 = block_sum(f32_to_f64(s1 * f), sh);
+  const double t2 = block_sum(f32_to_f64(s2 * f * f), sh);
   if (threadIdx.x == 0) {
     double* o = parts + (static_cast<int64_t>(blockIdx.x) * gridDim.y + blockIdx.y) * 3;
-    o[0] = m;
-    o[1] = s1;
-    o[2] = s2;
+    o[0] = f32_to_f64(M);
+    o[1] = t1;
+    o[2] = t2;
   }
 }
 
@@ -207,34 +250,66 @@ __global__ void ess_merge_kernel(const double* __restrict__ parts, int rows, int
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const double* q = parts + static_cast<int64_t>(r) * nparts * 3;
-  double M = -INFINITY;
-  for (int i = 0; i < nparts; ++i) M = fmax(M, q[3 * i]);
+  float M = -INFINITY;
+  for (int i = 0; i < nparts; ++i) M = fmaxf(M, f64_to_f32(q[3 * i]));   // the part maxima are FP32 values
   double s1 = 0.0, s2 = 0.0;
   for (int i = 0; i < nparts; ++i) {
-    if (q[3 * i] == -INFINITY) continue;
-    const double f = exp(q[3 * i] - M);
+    const float mi = f64_to_f32(q[3 * i]);
+    if (mi == -INFINITY) continue;
+    const double f = f32_to_f64(__expf(mi - M));
     s1 += f * q[3 * i + 1];
     s2 += f * f * q[3 * i + 2];
   }
   ess[r] = (s2 > 0.0) ? s1 * s1 / s2 : 0.0;
 }
 
-// Per-group log N^-1 sum_n exp(logw_jn) in FP64 (one block per group).
-__global__ void group_lme_kernel(const double* __restrict__ logw, int N, double* __restrict__ lme,
-                                 double* __restrict__ logml) {
+// logw[p] = value of the Kahan pair row[p] in FP64.
+__global__ void lw_to_f64_kernel(const float2* __restrict__ row, int64_t P, double* __restrict__ logw) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= P) return;
+  const float2 v = row[p];
+  logw[p] = f32_to_f64(v.x) - f32_to_f64(v.y);
+}
+
+// Per-group log N^-1 sum_n exp(logw_jn) in FP64, in two kernels: block (group, part) writes its
+// slice's maximum and sum of exp(logw - maximum); the merge (thread per group) rescales the
+// parts, writes lme_j, adds it to logml_j and records the group maximum.
+constexpr int kLmeParts = 8;
+
+__global__ void group_lme_part_kernel(const double* __restrict__ logw, int N, double* __restrict__ parts) {
   __shared__ double sh[33];
   const double* row = logw + static_cast<int64_t>(blockIdx.x) * N;
+  const int per = (N + gridDim.y - 1) / gridDim.y;
+  const int lo = blockIdx.y * per, hi = min(N, lo + per);
   double m = -INFINITY;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) m = fmax(m, row[n]);
+  for (int n = lo + threadIdx.x; n < hi; n += blockDim.x) m = fmax(m, row[n]);
   m = block_max(m, sh);
   double s = 0.0;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) s += exp(row[n] - m);
+  if (m > -INFINITY)
+    for (int n = lo + threadIdx.x; n < hi; n += blockDim.x) s += exp(row[n] - m);
   s = block_sum(s, sh);
   if (threadIdx.x == 0) {
-    const double v = m + log(s / static_cast<double>(N));
-    lme[blockIdx.x] = v;
-    if (logml) logml[blockIdx.x] += v;
+    double* o = parts + (static_cast<int64_t>(blockIdx.x) * gridDim.y + blockIdx.y) * 2;
+    o[0] = m;
+    o[1] = s;
   }
+}
+
+__global__ void group_lme_merge_kernel(const double* __restrict__ parts, int J, int nparts, int N,
+                                       double* __restrict__ lme, double* __restrict__ logml,
+                                       double* __restrict__ gmax) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  const double* q = parts + static_cast<int64_t>(j) * nparts * 2;
+  double M = -INFINITY;
+  for (int i = 0; i < nparts; ++i) M = fmax(M, q[2 * i]);
+  double S = 0.0;
+  for (int i = 0; i < nparts; ++i)
+    if (q[2 * i] > -INFINITY) S += q[2 * i + 1] * exp(q[2 * i] - M);
+  const double v = M + log(S / static_cast<double>(N));
+  lme[j] = v;
+  if (logml) logml[j] += v;
+  if (gmax) gmax[j] = M;
 }
 
 __global__ void add_kernel(double* __restrict__ a, const double* __restrict__ b, int64_t n) {
@@ -246,34 +321,37 @@ __global__ void add_kernel(double* __restrict__ a, const double* __restrict__ b,
 
 constexpr int kMaxN = 4096;
 constexpr int kResThreads = 1024;
+constexpr int kResBlocks = 4;   // blocks per group, each drawing N / kResBlocks of the indices
 
-// Multinomial resampling of one group per block by an integer CDF (S phase, Algorithm 1):
-// q_n = floor(w_n 2^40) with w_n = exp(logw_n - max) (mode 0) or the given w_n (mode 1),
-// c = inclusive uint64 prefix sums, tau_i = min(floor(u_i Q), Q - 1), idx_i = first n with c_n > tau.
+// Multinomial resampling within groups by an integer CDF (S phase, Algorithm 1), two kernels.
+// q_p = floor(w_p 2^40) with w_p = exp(logw_p - max of its group) (mode 0, FP64) or the given
+// w_p (mode 1).
+__global__ void resample_q_kernel(const double* __restrict__ src, int mode, int N, int64_t P,
+                                  const double* __restrict__ gmax, unsigned long long* __restrict__ q) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= P) return;
+  const double w = (mode == 0) ? exp(src[p] - gmax[p / N]) : src[p];
+  q[p] = static_cast<unsigned long long>(floor(ldexp(w, 40)));
+}
+
+// Block (group j, slice b): c = inclusive uint64 prefix sums of the group's q (every block of the
+// group builds the same table), then for the draws i of its slice tau_i = min(floor(u_i Q), Q - 1)
+// and idx_i = first n with c_n > tau_i. Sets *flag when the group's Q is zero.
 __global__ void __launch_bounds__(kResThreads)
-resample_kernel(const double* __restrict__ src, int mode, int N, const double* __restrict__ u_given,
+resample_kernel(const unsigned long long* __restrict__ qv, int N, const double* __restrict__ u_given,
                 uint64_t seed, uint64_t step, int* __restrict__ idx, int* __restrict__ flag) {
   __shared__ unsigned long long c[kMaxN];
   __shared__ unsigned long long part[kResThreads];
-  __shared__ double sh[33];
   const int j = blockIdx.x;
-  const double* row = src + static_cast<int64_t>(j) * N;
-  double m = 0.0;
-  if (mode == 0) {
-    m = -INFINITY;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) m = fmax(m, row[n]);
-    m = block_max(m, sh);
-  }
+  const unsigned long long* q = qv + static_cast<int64_t>(j) * N;
   // each thread owns a contiguous run of ceil(N / threads) elements
   const int per = (N + blockDim.x - 1) / blockDim.x;
   const int n0 = threadIdx.x * per;
   unsigned long long run = 0;
-  for (int q = 0; q < per; ++q) {
-    const int n = n0 + q;
+  for (int k = 0; k < per; ++k) {
+    const int n = n0 + k;
     if (n < N) {
-      const double w = (mode == 0) ? exp(row[n] - m) : row[n];
-      const unsigned long long qn = static_cast<unsigned long long>(floor(ldexp(w, 40)));
-      run += qn;
+      run += q[n];
       c[n] = run;
     }
   }
@@ -287,8 +365,8 @@ resample_kernel(const double* __restrict__ src, int mode, int N, const double* _
     __syncthreads();
   }
   const unsigned long long off = (threadIdx.x > 0) ? part[threadIdx.x - 1] : 0ull;
-  for (int q = 0; q < per; ++q) {
-    const int n = n0 + q;
+  for (int k = 0; k < per; ++k) {
+    const int n = n0 + k;
     if (n < N) c[n] += off;
   }
   __syncthreads();
@@ -297,7 +375,9 @@ resample_kernel(const double* __restrict__ src, int mode, int N, const double* _
     if (threadIdx.x == 0) atomicOr(flag, 1);
     return;
   }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  const int slice = (N + gridDim.y - 1) / gridDim.y;
+  const int i_hi = min(N, static_cast<int>(blockIdx.y + 1) * slice);
+  for (int i = blockIdx.y * slice + threadIdx.x; i < i_hi; i += blockDim.x) {
     double u;
     if (u_given) {
       u = u_given[static_cast<int64_t>(j) * N + i];
@@ -317,108 +397,131 @@ resample_kernel(const double* __restrict__ src, int mode, int N, const double* _
   }
 }
 
-// dst[p] = src[group(p) * N + idx[p]] for theta rows and the per-particle scalars.
+// dst[p] = src[group(p) * N + idx[p]] for theta rows and the per-particle scalars. A block of
+// 256 threads moves ppb = 256 / D whole rows, one thread per element (coalesced writes); the
+// first thread of a row also moves ll and lp.
 __global__ void gather_kernel(const double* __restrict__ th, const double* __restrict__ ll,
                               const double* __restrict__ lp, const int* __restrict__ idx, int64_t P, int N, int D,
                               double* __restrict__ th_o, double* __restrict__ ll_o, double* __restrict__ lp_o) {
-  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (p >= P) return;
+  const int ppb = static_cast<int>(blockDim.x) / D;
+  const int pp = static_cast<int>(threadIdx.x) / D;
+  const int d = static_cast<int>(threadIdx.x) - pp * D;
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * ppb + pp;
+  if (pp >= ppb || p >= P) return;
   const int64_t src = (p / N) * N + idx[p];
-  for (int d = 0; d < D; ++d) th_o[p * D + d] = th[src * D + d];
-  ll_o[p] = ll[src];
-  lp_o[p] = lp[src];
+  th_o[p * D + d] = th[src * D + d];
+  if (d == 0) {
+    ll_o[p] = ll[src];
+    lp_o[p] = lp[src];
+  }
 }
 
 // ------------------------------------------------------------------------------ M phase
 
-constexpr int kMaxD = 155;   // covariance kernel: <= 48 lower-triangle entries per thread
-
-// Column sums of theta [P x D] in FP64, two stages: block b sums its particle range
-// [b * per_block, (b+1) * per_block) into partial[b][D] (thread = (column, row group)), then
-// mean[d] = sum over blocks in fixed order / P.
-__global__ void col_sum_partial_kernel(const double* __restrict__ th, int64_t P, int D, int64_t per_block,
-                                       double* __restrict__ partial) {
-  __shared__ double sh[256];
-  const int rg = max(1, static_cast<int>(blockDim.x) / D);   // row groups
-  const int d = threadIdx.x % D, g = threadIdx.x / D;
-  const int64_t p_lo = blockIdx.x * per_block;
-  const int64_t p_hi = min(P, p_lo + per_block);
-  double s = 0.0;
-  if (g < rg)
-    for (int64_t p = p_lo + g; p < p_hi; p += rg) s += th[p * D + d];
-  sh[threadIdx.x] = (g < rg) ? s : 0.0;
-  __syncthreads();
-  for (int dd = threadIdx.x; dd < D; dd += blockDim.x) {
-    double t = 0.0;
-    for (int q = 0; q < rg; ++q) t += sh[q * D + dd];
-    partial[static_cast<int64_t>(blockIdx.x) * D + dd] = t;
-  }
-}
-
-__global__ void col_mean_final_kernel(const double* __restrict__ partial, int blocks, int D, int64_t P,
-                                      double* __restrict__ mean) {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= D) return;
-  double t = 0.0;
-  for (int b = 0; b < blocks; ++b) t += partial[static_cast<int64_t>(b) * D + d];
-  mean[d] = t / static_cast<double>(P);
-}
+constexpr int kMaxD = 155;   // covariance kernel: <= 48 moment entries per thread
 
 constexpr int kCovSub = 64;        // particles staged per shared-memory pass
 constexpr int kCovThreads = 256;
-constexpr int kCovMaxEnt = 48;     // lower-triangle entries per thread (D <= 155)
+constexpr int kCovMaxEnt = 48;     // moment entries per thread: T + D <= 256 x 48 for D <= 155
 
-// Centred cross products: block b sums over its particle range in FP32 (products of FP32
-// centred values), writes the lower triangle as FP64 partials [blocks][T].
+// Lower-triangle index e -> (i, j), i >= j, row-major.
+__device__ __forceinline__ void tri_ij(int e, int* i, int* j) {
+  int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > e) --r;
+  while ((r + 1) * (r + 2) / 2 <= e) ++r;
+  *i = r;
+  *j = e - r * (r + 1) / 2;
+}
+
+// First and second moments of theta about a shift (particle 0): block b sums, over its particle
+// range, d = f32(theta_p) - f32(theta_0) and the lower triangle of d d', in FP32 within a
+// 64-particle pass and with Kahan compensation across passes, and writes E = T + D FP64
+// partials: [0, T) sum d_i d_j, [T, T + D) sum d_i. The covariance is shift-invariant; centring
+// on a particle keeps the products at the scale of the spread, not of the location.
+// ENT: compile-time bound on the entries of one thread (E <= 256 ENT), so that the per-entry
+// state stays in registers.
+template <int ENT>
 __global__ void __launch_bounds__(kCovThreads)
-cov_partial_kernel(const double* __restrict__ th, int64_t P, int D, const double* __restrict__ mean,
-                   int64_t per_block, double* __restrict__ partial) {
-  extern __shared__ float cs[];   // [kCovSub][D]
-  const int T = D * (D + 1) / 2;
+cov_moments_kernel(const double* __restrict__ th, int64_t P, int D, int64_t per_block,
+                   double* __restrict__ partial) {
+  extern __shared__ float cs[];   // [kCovSub][D], then the shift [D]
+  float* shift = cs + kCovSub * D;
+  const int T = D * (D + 1) / 2, E = T + D;
   const int64_t p_lo = blockIdx.x * per_block;
   const int64_t p_hi = min(P, p_lo + per_block);
-  float acc[kCovMaxEnt];
-  int ei[kCovMaxEnt], ej[kCovMaxEnt];
-  int ne = 0;
-  for (int e = threadIdx.x; e < T && ne < kCovMaxEnt; e += blockDim.x, ++ne) {
-    // e -> (i, j), i >= j, row-major lower triangle
-    int i = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-    while (i * (i + 1) / 2 > e) --i;
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    ei[ne] = i;
-    ej[ne] = e - i * (i + 1) / 2;
-    acc[ne] = 0.f;
+  for (int d = threadIdx.x; d < D; d += blockDim.x) shift[d] = f64_to_f32(th[d]);
+  float acc[ENT], comp[ENT];
+  int ei[ENT], ej[ENT];
+#pragma unroll
+  for (int q = 0; q < ENT; ++q) {
+    const int e = threadIdx.x + q * kCovThreads;
+    ei[q] = 0;
+    ej[q] = -2;   // no entry
+    if (e < T) {
+      tri_ij(e, &ei[q], &ej[q]);
+    } else if (e < E) {
+      ei[q] = e - T;
+      ej[q] = -1;   // first moment
+    }
+    acc[q] = 0.f;
+    comp[q] = 0.f;
   }
   for (int64_t p0 = p_lo; p0 < p_hi; p0 += kCovSub) {
     const int np = static_cast<int>(p_hi - p0 < kCovSub ? p_hi - p0 : kCovSub);
     __syncthreads();
     for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
       const int pp = q / D, d = q - pp * D;
-      cs[pp * D + d] = static_cast<float>(th[(p0 + pp) * D + d] - mean[d]);
+      cs[pp * D + d] = f64_to_f32(th[(p0 + pp) * D + d]) - shift[d];
     }
     __syncthreads();
-    for (int q = 0; q < ne; ++q) {
+#pragma unroll
+    for (int q = 0; q < ENT; ++q) {
+      if (ej[q] == -2) continue;
       float a = 0.f;
-      for (int pp = 0; pp < np; ++pp) a = fmaf(cs[pp * D + ei[q]], cs[pp * D + ej[q]], a);
-      acc[q] += a;
+      if (ej[q] >= 0) {
+        for (int pp = 0; pp < np; ++pp) a = fmaf(cs[pp * D + ei[q]], cs[pp * D + ej[q]], a);
+      } else {
+        for (int pp = 0; pp < np; ++pp) a += cs[pp * D + ei[q]];
+      }
+      const float y = a - comp[q];
+      const float t = acc[q] + y;
+      comp[q] = (t - acc[q]) - y;
+      acc[q] = t;
     }
   }
-  for (int q = 0; q < ne; ++q) partial[static_cast<int64_t>(blockIdx.x) * T + threadIdx.x + q * blockDim.x] = acc[q];
+#pragma unroll
+  for (int q = 0; q < ENT; ++q) {
+    const int e = threadIdx.x + q * kCovThreads;
+    if (e < E) partial[static_cast<int64_t>(blockIdx.x) * E + e] = f32_to_f64(acc[q]) - f32_to_f64(comp[q]);
+  }
 }
 
-// V = sum over blocks (fixed order) / (P - 1), full symmetric [D x D]; Sigma = scale V.
+// V = (S2 - S1 S1' / P) / (P - 1) from the block partials, one warp per lower-triangle entry
+// (lanes take every 32nd block, FP64); writes the full symmetric V and Sigma = scale V.
 __global__ void cov_final_kernel(const double* __restrict__ partial, int blocks, int D, int64_t P, double scale,
                                  double* __restrict__ V, double* __restrict__ Sigma) {
-  const int T = D * (D + 1) / 2;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int T = D * (D + 1) / 2, E = T + D;
+  const int e = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (e >= T) return;
-  int i = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-  while (i * (i + 1) / 2 > e) --i;
-  while ((i + 1) * (i + 2) / 2 <= e) ++i;
-  const int j = e - i * (i + 1) / 2;
-  double s = 0.0;
-  for (int b = 0; b < blocks; ++b) s += partial[static_cast<int64_t>(b) * T + e];
-  const double v = s / static_cast<double>(P - 1);
+  int i, j;
+  tri_ij(e, &i, &j);
+  double s2 = 0.0, si = 0.0, sj = 0.0;
+  for (int b = lane; b < blocks; b += 32) {
+    const double* q = partial + static_cast<int64_t>(b) * E;
+    s2 += q[e];
+    si += q[T + i];
+    sj += q[T + j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+    sj += __shfl_xor_sync(0xffffffffu, sj, o);
+  }
+  if (lane != 0) return;
+  const double n = static_cast<double>(P);
+  const double v = (s2 - si * sj / n) / (n - 1.0);
   if (V) {
     V[i * D + j] = v;
     V[j * D + i] = v;
@@ -430,33 +533,67 @@ __global__ void cov_final_kernel(const double* __restrict__ partial, int blocks,
 }
 
 // Lower Cholesky factor of A [D x D] (FP64, one block, right-looking on the packed lower
-// triangle in shared memory, one thread per row of the trailing update). On failure
-// (non-positive or non-finite pivot) sets *flag. Writes L in FP64 (full, zero upper part) and the
-// packed lower triangle in FP32.
+// triangle in shared memory). FP64 instructions have about 64 cycles of latency on this GPU (a
+// square root about 600, a division about 400), so the critical path is kept short: per column
+// one Newton reciprocal square root, the scaled column copied to a separate buffer, and the
+// trailing update spread over all threads by triangle entry (about two independent FMAs per
+// thread for D = 30). On failure (pivot not positive, or outside (1e-37, 1e37)) sets *flag.
+// Writes L in FP64 (full, zero upper part) and the packed lower triangle in FP32.
 __device__ __forceinline__ int tri(int i, int k) { return i * (i + 1) / 2 + k; }
 
-__global__ void cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
-                                float* __restrict__ L32, int* __restrict__ flag) {
+// 1/sqrt(a) for a in the float normal range: an FP32 seed refined by two Newton steps in FP64
+// (y <- y (3 - a y^2) / 2; the error squares each step, 2^-22 -> 2^-43 -> below 2^-53).
+__device__ __forceinline__ double rsqrt_f64(double a) {
+  double y = f32_to_f64(rsqrtf(f64_to_f32(a)));
+  const double h = 0.5 * a;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+constexpr int kCholThreads = 256;
+
+__global__ void __launch_bounds__(kCholThreads)
+cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
+                float* __restrict__ L32, int* __restrict__ flag) {
   extern __shared__ double a[];   // packed lower triangle, row-major
+  __shared__ double col[kMaxD];   // scaled column j
+  __shared__ double rinv;
   __shared__ int bad;
-  for (int i = threadIdx.x; i < D; i += blockDim.x)
-    for (int k = 0; k <= i; ++k) a[tri(i, k)] = A[i * D + k];
+  const int T = D * (D + 1) / 2;
+  for (int e = threadIdx.x; e < T; e += blockDim.x) {
+    int i, k;
+    tri_ij(e, &i, &k);
+    a[e] = A[i * D + k];
+  }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < D; ++j) {
     if (threadIdx.x == 0) {
       const double piv = a[tri(j, j)];
-      if (!(piv > 0.0) || !isfinite(piv)) bad = 1;
-      else a[tri(j, j)] = sqrt(piv);
+      if (!(piv > 1e-37) || !(piv < 1e37)) {
+        bad = 1;
+      } else {
+        const double y = rsqrt_f64(piv);
+        a[tri(j, j)] = piv * y;   // sqrt(piv)
+        rinv = y;
+      }
     }
     __syncthreads();
     if (bad) break;
-    const double djj = a[tri(j, j)];
-    for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) a[tri(i, j)] /= djj;
-    __syncthreads();
+    const double r = rinv;
     for (int i = j + 1 + threadIdx.x; i < D; i += blockDim.x) {
-      const double lij = a[tri(i, j)];
-      for (int k = j + 1; k <= i; ++k) a[tri(i, k)] -= lij * a[tri(k, j)];
+      const double v = a[tri(i, j)] * r;
+      a[tri(i, j)] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    // trailing update a[i][k] -= l_ij l_kj for j < k <= i, entries of the rows below j
+    const int e0 = tri(j + 1, 0);
+    for (int e = e0 + threadIdx.x; e < T; e += blockDim.x) {
+      int i, k;
+      tri_ij(e, &i, &k);
+      if (k > j) a[e] = fma(-col[i], col[k], a[e]);
     }
     __syncthreads();
   }
@@ -468,26 +605,57 @@ __global__ void cholesky_kernel(const double* __restrict__ A, int D, double* __r
     const int i = q / D, k = q - i * D;
     L[q] = (k <= i) ? a[tri(i, k)] : 0.0;
   }
-  const int T = D * (D + 1) / 2;
-  for (int e = threadIdx.x; e < T; e += blockDim.x) L32[e] = static_cast<float>(a[e]);
+  for (int e = threadIdx.x; e < T; e += blockDim.x) L32[e] = f64_to_f32(a[e]);
 }
 
-constexpr int kPropThreads = 128;
+// Particle rows [p0, p0 + np) of a [P x D] FP64 matrix to / from shared memory with row stride
+// Dp (odd, so that one row per lane reads without bank conflicts); global accesses coalesced.
+__device__ __forceinline__ void stage_rows(const double* __restrict__ src, int64_t p0, int np, int D, int Dp,
+                                           double* sm) {
+  const double* g = src + p0 * D;
+  for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
+    const int r = q / D;
+    sm[r * Dp + (q - r * D)] = g[q];
+  }
+}
+__device__ __forceinline__ void unstage_rows(double* __restrict__ dst, int64_t p0, int np, int D, int Dp,
+                                             const double* sm) {
+  double* g = dst + p0 * D;
+  for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
+    const int r = q / D;
+    g[q] = sm[r * Dp + (q - r * D)];
+  }
+}
+
+constexpr int kPropThreads = 64;   // particles per block
 
 // theta' = theta + L z (L packed lower triangle FP32; z FP32 normals from Philox, or given FP64),
-// plus the prior log kernel of theta'. Skipped when the factorisation failed.
+// plus the prior log kernel of theta'. The block's theta rows go through shared memory (coalesced
+// reads and writes); each thread updates its own row there. Skipped when the factorisation failed.
 __global__ void __launch_bounds__(kPropThreads)
 propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __restrict__ L32,
                const double* __restrict__ z_given, uint64_t seed, uint64_t step, const double* __restrict__ mu,
                const double* __restrict__ prec, bool full, const int* __restrict__ flag,
                double* __restrict__ th_o, double* __restrict__ lp_o) {
   if (*flag) return;
-  extern __shared__ float ps[];
+  extern __shared__ double pd[];
   const int T = D * (D + 1) / 2;
-  float* Ls = ps;                              // [T]
-  float* zs = ps + ((T + 3) & ~3);             // [D][128]
+  const int Dp = D | 1;
+  double* rows = pd;                                                  // [64][Dp]
+  float* Ls = reinterpret_cast<float*>(rows + kPropThreads * Dp);     // [T]
+  float* zs = Ls + ((T + 3) & ~3);                                    // [D][64]
+  float* mus = zs + D * kPropThreads;                                 // [D] f32(mu), [D] f32(prec)
+  float* prs = mus + D;
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
-  const int64_t p = blockIdx.x * static_cast<int64_t>(kPropThreads) + threadIdx.x;
+  if (!full)
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      mus[i] = f64_to_f32(mu[i]);
+      prs[i] = f64_to_f32(prec[i]);
+    }
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kPropThreads;
+  const int np = static_cast<int>(P - p0 < kPropThreads ? P - p0 : kPropThreads);
+  stage_rows(th, p0, np, D, Dp, rows);
+  const int64_t p = p0 + threadIdx.x;
   const bool live = p < P;
   if (live) {
     if (z_given) {
@@ -504,28 +672,42 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
     }
   }
   __syncthreads();
-  if (!live) return;
-  const double* t = th + p * D;
-  double* o = th_o + p * D;
-  for (int i = 0; i < D; ++i) {
-    const float* Li = Ls + i * (i + 1) / 2;
-    float dlt = 0.f;
-    for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], zs[j * kPropThreads + threadIdx.x], dlt);
-    o[i] = t[i] + static_cast<double>(dlt);
+  if (live) {
+    double* row = rows + threadIdx.x * Dp;
+    float a = 0.f;   // diagonal prior: the arithmetic of prior_log_kernel, on the new row
+    for (int i = 0; i < D; ++i) {
+      const float* Li = Ls + i * (i + 1) / 2;
+      float dlt = 0.f;
+      for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], zs[j * kPropThreads + threadIdx.x], dlt);
+      const double v = row[i] + f32_to_f64(dlt);
+      row[i] = v;
+      if (!full) {
+        const float d = f64_to_f32(v) - mus[i];
+        a = fmaf(d * d, prs[i], a);
+      }
+    }
+    lp_o[p] = full ? prior_log_kernel(row, mu, prec, D, full) : -0.5 * f32_to_f64(a);
   }
-  lp_o[p] = prior_log_kernel(o, mu, prec, D, full);
+  __syncthreads();
+  unstage_rows(th_o, p0, np, D, Dp, rows);
 }
 
+constexpr int kAccThreads = 256;
+
 // Metropolis accept (Algorithm 2 step 2(c)i): log alpha = ll' - ll + lp' - lp, accept when
-// log u < log alpha; accepted rows are copied into the state. Counts accepts per block.
-__global__ void accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restrict__ lp,
-                              const double* __restrict__ th_p, const double* __restrict__ ll_p,
-                              const double* __restrict__ lp_p, int64_t P, int D, const double* __restrict__ u_given,
-                              uint64_t seed, uint64_t step, const int* __restrict__ flag,
-                              unsigned long long* __restrict__ n_acc, int* __restrict__ nonfinite,
-                              double* __restrict__ log_alpha_out, int* __restrict__ acc_out) {
+// log u < log alpha; the block then copies its accepted rows into the state element by element
+// (coalesced). Counts accepts per warp.
+__global__ void __launch_bounds__(kAccThreads)
+accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restrict__ lp,
+              const double* __restrict__ th_p, const double* __restrict__ ll_p,
+              const double* __restrict__ lp_p, int64_t P, int D, const double* __restrict__ u_given,
+              uint64_t seed, uint64_t step, const int* __restrict__ flag,
+              unsigned long long* __restrict__ n_acc, int* __restrict__ nonfinite,
+              double* __restrict__ log_alpha_out, int* __restrict__ acc_out) {
+  __shared__ unsigned char take[kAccThreads];
   if (*flag) return;
-  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kAccThreads;
+  const int64_t p = p0 + threadIdx.x;
   bool acc = false;
   if (p < P) {
     const double lpp = ll_p[p];
@@ -540,15 +722,21 @@ __global__ void accept_kernel(double* __restrict__ th, double* __restrict__ ll, 
     }
     acc = log(u) < la;
     if (acc) {
-      for (int d = 0; d < D; ++d) th[p * D + d] = th_p[p * D + d];
       ll[p] = lpp;
       lp[p] = lp_p[p];
     }
     if (log_alpha_out) log_alpha_out[p] = la;
     if (acc_out) acc_out[p] = acc ? 1 : 0;
   }
+  take[threadIdx.x] = acc ? 1 : 0;
   const unsigned ballot = __ballot_sync(0xffffffffu, acc);
   if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, static_cast<unsigned long long>(__popc(ballot)));
+  __syncthreads();
+  const int np = static_cast<int>(P - p0 < kAccThreads ? P - p0 : kAccThreads);
+  for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
+    const int r = q / D;
+    if (take[r]) th[p0 * D + q] = th_p[p0 * D + q];
+  }
 }
 
 // ------------------------------------------------------------------------------ MALA
@@ -687,10 +875,11 @@ __device__ __forceinline__ double fn_value(const double* th, const double* ll, c
     if (f == 0) return ll[p];
     f -= 1;
   }
+  // theta_c' xbar: FP32 products and sum (a monitoring function; 1e-7 relative is ample)
   const double* t = th + p * D + f * k;
-  double a = 0.0;
-  for (int i = 0; i < k; ++i) a = fma(t[i], xbar[i], a);
-  return a;
+  float a = 0.f;
+  for (int i = 0; i < k; ++i) a = fmaf(f64_to_f32(t[i]), f64_to_f32(xbar[i]), a);
+  return f32_to_f64(a);
 }
 
 __global__ void group_moments_kernel(const double* __restrict__ th, const double* __restrict__ ll,
@@ -717,6 +906,69 @@ __global__ void group_moments_kernel(const double* __restrict__ th, const double
   }
 }
 
+// Monitoring moments after an M step (Algorithm 2 step 2(c)iii): functions f = 0: ll, f = c:
+// theta_c' xbar (c = 1..NC), F = NC + 1 <= 4. Block (group j, part z) stages its particles'
+// theta rows in shared memory (coalesced), each thread evaluates all F functions of its particle
+// and the block writes, per function, the sums of (g - ref_f) and (g - ref_f)^2 with ref_f the
+// value at particle 0, in the [J][F][S][3] layout of group_moments_kernel.
+constexpr int kMonThreads = 128;
+
+template <int F>
+__global__ void __launch_bounds__(kMonThreads)
+monitor_moments_kernel(const double* __restrict__ th, const double* __restrict__ ll,
+                       const double* __restrict__ xbar, int N, int D, int k, double* __restrict__ sums) {
+  extern __shared__ double mrow[];   // [128][Dp]
+  __shared__ double sh[33];
+  __shared__ float xb[kMaxD];
+  const int Dp = D | 1;
+  const int j = blockIdx.x, z = blockIdx.y, S = gridDim.y;
+  const int per = (N + S - 1) / S;
+  const int n_lo = z * per, n_hi = min(N, n_lo + per);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) xb[i] = f64_to_f32(xbar[i]);
+  __syncthreads();
+  auto value = [&](const double* row, double llv, int f) -> double {
+    if (f == 0) return llv;
+    float a = 0.f;
+    const double* t = row + (f - 1) * k;
+    for (int i = 0; i < k; ++i) a = fmaf(f64_to_f32(t[i]), xb[i], a);
+    return f32_to_f64(a);
+  };
+  double ref[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) ref[f] = value(th, ll[0], f);
+  double s1[F], s2[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) s1[f] = s2[f] = 0.0;
+  for (int n0 = n_lo; n0 < n_hi; n0 += kMonThreads) {
+    const int np = min(kMonThreads, n_hi - n0);
+    const int64_t p0 = static_cast<int64_t>(j) * N + n0;
+    __syncthreads();
+    stage_rows(th, p0, np, D, Dp, mrow);
+    __syncthreads();
+    if (static_cast<int>(threadIdx.x) < np) {
+      const double* row = mrow + threadIdx.x * Dp;
+      const double llv = ll[p0 + threadIdx.x];
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        const double g = value(row, llv, f) - ref[f];
+        s1[f] += g;
+        s2[f] = fma(g, g, s2[f]);
+      }
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    const double a = block_sum(s1[f], sh);
+    const double b = block_sum(s2[f], sh);
+    if (threadIdx.x == 0) {
+      double* o = sums + ((static_cast<int64_t>(j) * F + f) * S + z) * 3;
+      o[0] = a;
+      o[1] = b;
+      o[2] = ref[f];
+    }
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ host helpers
@@ -725,7 +977,7 @@ struct Moments {
   std::vector<double> mean, sd, nse, rne;
 };
 
-constexpr int kMomParts = 8;   // blocks per group and function in the monitoring moments
+constexpr int kMomParts = 32;  // blocks per group in the monitoring moments (128 particles each at N = 4096)
 
 // Sum the S partial blocks of each (group, function) in a fixed order: [J][F][S][3] -> [J][F][3].
 static std::vector<double> reduce_parts(const std::vector<double>& parts, int J, int F, int S) {
@@ -779,7 +1031,31 @@ static void swapbuf(DevBuf& a, DevBuf& b) {
 
 static bool prior_full(const sps_ctx* ctx) { return ctx->prior_kind == SPS_PRIOR_FULL; }
 
-static int cov_blocks(int64_t P) { return static_cast<int>(std::min<int64_t>(148, (P + kCovSub - 1) / kCovSub)); }
+static int cov_blocks(int64_t P) { return static_cast<int>(std::min<int64_t>(296, (P + kCovSub - 1) / kCovSub)); }
+
+// V = pooled covariance of theta [P x D] (divisor P - 1) into V and/or Sigma = scale V (device,
+// full symmetric); partial: cov_blocks(P) x (T + D) doubles of scratch.
+static sps_status launch_cov(sps_ctx* ctx, const double* theta, int64_t P, int D, double scale, double* partial,
+                             double* V, double* Sigma) {
+  const int T = D * (D + 1) / 2;
+  const int blocks = cov_blocks(P);
+  const int64_t per = (P + blocks - 1) / blocks;
+  const int E = T + D;
+  const size_t smem = sizeof(float) * (kCovSub + 1) * D;
+  if (E <= 2 * kCovThreads)
+    cov_moments_kernel<2><<<blocks, kCovThreads, smem, ctx->stream>>>(theta, P, D, per, partial);
+  else if (E <= 8 * kCovThreads)
+    cov_moments_kernel<8><<<blocks, kCovThreads, smem, ctx->stream>>>(theta, P, D, per, partial);
+  else if (E <= 16 * kCovThreads)
+    cov_moments_kernel<16><<<blocks, kCovThreads, smem, ctx->stream>>>(theta, P, D, per, partial);
+  else
+    cov_moments_kernel<kCovMaxEnt><<<blocks, kCovThreads, smem, ctx->stream>>>(theta, P, D, per, partial);
+  ++ctx->launches;
+  cov_final_kernel<<<static_cast<unsigned>((T + 7) / 8), 256, 0, ctx->stream>>>(partial, blocks, D, P, scale, V,
+                                                                                 Sigma); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
 
 // V (and Sigma = h V unless sigma_in) then its Cholesky factor into st->chol / scratch L32.
 static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_theta, double h,
@@ -790,32 +1066,23 @@ static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_t
   if (sigma_host) {
     SPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma_host, sizeof(double) * D * D, cudaMemcpyHostToDevice, ctx->stream));
   } else {
-    const int blocks = cov_blocks(st->P);
-    const int64_t per = (st->P + blocks - 1) / blocks;
-    col_sum_partial_kernel<<<blocks, 256, 0, ctx->stream>>>(d_theta, st->P, D, per, st->scratch.as<double>()); ++ctx->launches;
-    col_mean_final_kernel<<<(D + 127) / 128, 128, 0, ctx->stream>>>(st->scratch.as<double>(), blocks, D, st->P,
-                                                                    st->mean.as<double>()); ++ctx->launches;
-    cov_partial_kernel<<<blocks, kCovThreads, sizeof(float) * kCovSub * D, ctx->stream>>>(
-        d_theta, st->P, D, st->mean.as<double>(), per, st->scratch.as<double>()); ++ctx->launches;
-    cov_final_kernel<<<(T + 255) / 256, 256, 0, ctx->stream>>>(st->scratch.as<double>(), blocks, D, st->P, h,
-                                                                nullptr, d_sigma); ++ctx->launches;
-    SPS_CUDA_TRY(cudaGetLastError());
+    SPS_TRY(launch_cov(ctx, d_theta, st->P, D, h, st->scratch.as<double>(), nullptr, d_sigma));
   }
   if (sigma_out)
     SPS_CUDA_TRY(cudaMemcpyAsync(sigma_out, d_sigma, sizeof(double) * D * D, cudaMemcpyDeviceToHost, ctx->stream));
   float* L32 = reinterpret_cast<float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
   SPS_CUDA_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(sizeof(double) * T)));
-  const int chol_threads = std::min(256, (D + 31) / 32 * 32);
-  cholesky_kernel<<<1, chol_threads, sizeof(double) * T, ctx->stream>>>(d_sigma, D, st->chol.as<double>(), L32,
-                                                                       d_flag); ++ctx->launches;
+  cholesky_kernel<<<1, kCholThreads, sizeof(double) * T, ctx->stream>>>(d_sigma, D, st->chol.as<double>(), L32,
+                                                                        d_flag); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
 }
 
 static size_t propose_smem(int D) {
   const int T = D * (D + 1) / 2;
-  return sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kPropThreads);
+  return sizeof(double) * kPropThreads * static_cast<size_t>(D | 1) +
+         sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kPropThreads + 2 * static_cast<size_t>(D));
 }
 
 static sps_status launch_propose(sps_ctx* ctx, sps_state* st, const double* d_theta, int64_t P, const double* z,
@@ -848,13 +1115,12 @@ static sps_status state_buffers(sps_ctx* ctx, sps_state* st) {
   SPS_CUDA_TRY(st->idx.reserve(P * sizeof(int)));
   SPS_CUDA_TRY(st->cov.reserve(sizeof(double) * D * D));
   SPS_CUDA_TRY(st->chol.reserve(sizeof(double) * D * D + sizeof(float) * (D * (D + 1) / 2 + 4)));
-  SPS_CUDA_TRY(st->mean.reserve(sizeof(double) * D));
   const size_t T = static_cast<size_t>(D) * (D + 1) / 2;
   const int F = D + ctx->NC + 1;
   const size_t ess_rows_max = static_cast<size_t>(std::max<int64_t>(1, std::min<int64_t>(1024, (int64_t{1} << 25) / P)));
-  SPS_CUDA_TRY(st->scratch.reserve(std::max({sizeof(double) * T * cov_blocks(P),
-                                             sizeof(double) * D * cov_blocks(P),
+  SPS_CUDA_TRY(st->scratch.reserve(std::max({sizeof(double) * (T + D) * cov_blocks(P),
                                              sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64,
+                                             sizeof(double) * 2 * static_cast<size_t>(st->J) * kLmeParts,
                                              sizeof(double) * 3 * static_cast<size_t>(st->J) * (1 + ctx->NC) * kMomParts,
                                              sizeof(double) * 3 * kEssParts * ess_rows_max})));
   // counters: [0] accepts (u64), then int flags: [2] chol failure, [3] non-finite, [4] resample
@@ -890,9 +1156,26 @@ sps_status check_state(sps_ctx* ctx, const sps_state* st) {
 // with the step's counters in one synchronisation; min RNE over the set.
 void launch_monitoring(sps_ctx* ctx, sps_state* st) {
   const int F = 1 + ctx->NC;
-  group_moments_kernel<<<dim3(st->J, F, kMomParts), 256, 0, ctx->stream>>>(
-      st->theta.as<double>(), st->ll.as<double>(), ctx->xbar.as<double>(), st->N, ctx->D, ctx->k, F, false, true,
-      st->scratch.as<double>()); ++ctx->launches;
+  const size_t smem = sizeof(double) * kMonThreads * (ctx->D | 1);
+  const dim3 grid(st->J, kMomParts);
+  double* out = st->scratch.as<double>();
+  const double* th = st->theta.as<double>();
+  const double* ll = st->ll.as<double>();
+  const double* xb = ctx->xbar.as<double>();
+#define SPS_MON_CASE(FF)                                                                                  \
+  if (F == FF) {                                                                                          \
+    cudaFuncSetAttribute(monitor_moments_kernel<FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                         static_cast<int>(smem));                                                         \
+    monitor_moments_kernel<FF><<<grid, kMonThreads, smem, ctx->stream>>>(th, ll, xb, st->N, ctx->D, ctx->k, out); \
+  }
+  SPS_MON_CASE(2)
+  SPS_MON_CASE(3)
+  SPS_MON_CASE(4)
+#undef SPS_MON_CASE
+  if (F > 4)
+    group_moments_kernel<<<dim3(st->J, F, kMomParts), 256, 0, ctx->stream>>>(th, ll, xb, st->N, ctx->D, ctx->k, F,
+                                                                            false, true, out);
+  ++ctx->launches;
 }
 
 sps_status read_step(sps_ctx* ctx, sps_state* st, Counters* c, double* rne_min) {
@@ -971,7 +1254,7 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
     SPS_TRY(launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, flag_ptr(st, 0),
                            st->theta_prop.as<double>(), st->lp_prop.as<double>()));
     SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(), precision));
-    accept_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
+    accept_kernel<<<static_cast<unsigned>((st->P + kAccThreads - 1) / kAccThreads), kAccThreads, 0, ctx->stream>>>(
         st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->theta_prop.as<double>(),
         st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, flag_ptr(st, 0),
         st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
@@ -1002,6 +1285,11 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
   return SPS_OK;
 }
 
+// C phase (Algorithm 1 step 2(a)): running log weights over blocks of observations (doubling
+// from the configured block), the ESS of every observation of a block read back at once, stop at
+// the first s with ESS / P below the threshold (or at t_target / n); then the per-group log
+// marginal-likelihood increments and the cached log-likelihood at the new t. One synchronisation
+// per block, plus one to return the increments when lme_out is given.
 sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new, double* ess_out,
                        double* lme_out) {
   const int64_t n = ctx->n, P = st->P;
@@ -1009,19 +1297,21 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
   if (t_target > 0 && (t_target <= st->t || t_target > n)) return fail(ctx, SPS_ERR_INVALID_ARG, "C phase: bad t_target");
   const int64_t max_rows = std::max<int64_t>(1, std::min<int64_t>(1024, (int64_t{1} << 25) / P));
   int64_t block = std::max<int64_t>(1, std::min<int64_t>(ctx->opt.cphase_block > 0 ? ctx->opt.cphase_block : 64, max_rows));
-  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(double) * max_rows * P));
-  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * max_rows));
-  SPS_CUDA_TRY(cudaMemsetAsync(st->logw.ptr, 0, sizeof(double) * P, ctx->stream));
+  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(float2) * max_rows * P));
+  SPS_CUDA_TRY(st->lwstate.reserve(sizeof(float2) * P));
+  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * std::max<int64_t>(max_rows, st->J)));
+  SPS_CUDA_TRY(st->gmax.reserve(sizeof(double) * st->J));
+  SPS_CUDA_TRY(cudaMemsetAsync(st->lwstate.ptr, 0, sizeof(float2) * P, ctx->stream));
+  float2* rows = st->lwbuf.as<float2>();
   int64_t s = st->t;
   std::vector<double> ess(max_rows);
   int64_t found = -1;
   double ess_found = 0.0;
   while (s < n) {
     const int64_t b = std::min<int64_t>(block, n - s);
-    SPS_TRY(cphase_increments(ctx, st->theta.as<double>(), P, s, s + b, st->logw.as<double>(),
-                              st->lwbuf.as<double>()));
-    ess_part_kernel<<<dim3(static_cast<unsigned>(b), kEssParts), 512, 0, ctx->stream>>>(
-        st->lwbuf.as<double>(), P, st->scratch.as<double>()); ++ctx->launches;
+    SPS_TRY(cphase_increments(ctx, st->theta.as<double>(), P, s, s + b, st->lwstate.as<float2>(), rows));
+    ess_part_kernel<float2><<<dim3(static_cast<unsigned>(b), kEssParts), 512, 0, ctx->stream>>>(
+        rows, P, st->scratch.as<double>()); ++ctx->launches;
     ess_merge_kernel<<<static_cast<unsigned>((b + 63) / 64), 64, 0, ctx->stream>>>(
         st->scratch.as<double>(), static_cast<int>(b), kEssParts, st->ess_buf.as<double>()); ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
@@ -1037,42 +1327,52 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
         break;
       }
     }
-    const int64_t row = (found >= 0) ? found : b - 1;
-    SPS_CUDA_TRY(cudaMemcpyAsync(st->logw.ptr, st->lwbuf.as<double>() + row * P, sizeof(double) * P,
-                                 cudaMemcpyDeviceToDevice, ctx->stream));
     if (found >= 0) {
+      lw_to_f64_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(rows + found * P, P,
+                                                                                       st->logw.as<double>()); ++ctx->launches;
+      SPS_CUDA_TRY(cudaGetLastError());
       s = s + found + 1;
       break;
     }
+    SPS_CUDA_TRY(cudaMemcpyAsync(st->lwstate.ptr, rows + (b - 1) * P, sizeof(float2) * P, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
     s += b;
     block = std::min<int64_t>(block * 2, max_rows);
   }
-  // log marginal likelihood increment per group, cached log-likelihood at the new t
-  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * std::max<int64_t>(max_rows, st->J)));
-  group_lme_kernel<<<st->J, 256, 0, ctx->stream>>>(st->logw.as<double>(), st->N, st->ess_buf.as<double>(),
-                                                  st->logml.as<double>()); ++ctx->launches;
+  // log marginal likelihood increment per group, group maxima, cached log-likelihood at the new t
+  group_lme_part_kernel<<<dim3(st->J, kLmeParts), 256, 0, ctx->stream>>>(st->logw.as<double>(), st->N,
+                                                                         st->scratch.as<double>()); ++ctx->launches;
+  group_lme_merge_kernel<<<(st->J + 63) / 64, 64, 0, ctx->stream>>>(st->scratch.as<double>(), st->J, kLmeParts, st->N,
+                                                                    st->ess_buf.as<double>(), st->logml.as<double>(),
+                                                                    st->gmax.as<double>()); ++ctx->launches;
   add_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(st->ll.as<double>(),
                                                                                st->logw.as<double>(), P); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
-  std::vector<double> lme(st->J);
-  SPS_CUDA_TRY(cudaMemcpyAsync(lme.data(), st->ess_buf.ptr, sizeof(double) * st->J, cudaMemcpyDeviceToHost, ctx->stream));
-  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (lme_out) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(lme_out, st->ess_buf.ptr, sizeof(double) * st->J, cudaMemcpyDeviceToHost, ctx->stream));
+    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
   st->t = s;
   st->have_weights = true;
   st->ll_stale = true;
   if (t_new) *t_new = s;
   if (ess_out) *ess_out = ess_found;
-  if (lme_out) std::memcpy(lme_out, lme.data(), sizeof(double) * st->J);
   return SPS_OK;
 }
 
+// S phase (Algorithm 1 step 2(b)): quantised weights, per-group integer-CDF draws, gather.
+// The C-phase row buffer holds the quantised weights (uint64 [P]) here.
 sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_idx_out) {
   if (!st->have_weights) return fail(ctx, SPS_ERR_STATE, "S phase before a C phase");
   SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
   const uint64_t step = ++st->cycle_counter;
-  resample_kernel<<<st->J, kResThreads, 0, ctx->stream>>>(st->logw.as<double>(), 0, st->N, d_u, st->seed, step,
-                                                          st->idx.as<int>(), flag_ptr(st, 2)); ++ctx->launches;
-  gather_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
+  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(unsigned long long) * st->P));
+  unsigned long long* q = st->lwbuf.as<unsigned long long>();
+  resample_q_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
+      st->logw.as<double>(), 0, st->N, st->P, st->gmax.as<double>(), q); ++ctx->launches;
+  resample_kernel<<<dim3(st->J, kResBlocks), kResThreads, 0, ctx->stream>>>(q, st->N, d_u, st->seed, step,
+                                                                            st->idx.as<int>(), flag_ptr(st, 2)); ++ctx->launches;
+  gather_kernel<<<static_cast<unsigned>((st->P + 256 / ctx->D - 1) / (256 / ctx->D)), 256, 0, ctx->stream>>>(
       st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->idx.as<int>(), st->P, st->N, ctx->D,
       st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
@@ -1354,7 +1654,12 @@ sps_status sps_resample(sps_ctx* ctx, const double* w, const double* u, int32_t 
     pu = du.as<double>();
     pi = di.as<int>();
   }
-  resample_kernel<<<J, kResThreads, 0, ctx->stream>>>(pw, 1, N, pu, 0, 0, pi, df.as<int>()); ++ctx->launches;
+  DevBuf dq;
+  SPS_CUDA_TRY(dq.reserve(P * sizeof(unsigned long long)));
+  resample_q_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+      pw, 1, N, static_cast<int64_t>(P), nullptr, dq.as<unsigned long long>()); ++ctx->launches;
+  resample_kernel<<<dim3(J, kResBlocks), kResThreads, 0, ctx->stream>>>(dq.as<unsigned long long>(), N, pu, 0, 0, pi,
+                                                                        df.as<int>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   if (mem == SPS_MEM_HOST) {
     int bad = 0;
@@ -1403,10 +1708,14 @@ sps_status sps_ess(sps_ctx* ctx, const double* logw, int64_t P, int32_t J, doubl
   double* pe = (mem == SPS_MEM_DEVICE && ess) ? ess : de.as<double>();
   double* pm = (mem == SPS_MEM_DEVICE && lme) ? lme : dm.as<double>();
   DevBuf dparts;
-  SPS_CUDA_TRY(dparts.reserve(sizeof(double) * 3 * kEssParts));
-  ess_part_kernel<<<dim3(1, kEssParts), 512, 0, ctx->stream>>>(pl, P, dparts.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(dparts.reserve(sizeof(double) * std::max<size_t>(3 * kEssParts, 2 * static_cast<size_t>(J) * kLmeParts)));
+  ess_part_kernel<double><<<dim3(1, kEssParts), 512, 0, ctx->stream>>>(pl, P, dparts.as<double>()); ++ctx->launches;
   ess_merge_kernel<<<1, 64, 0, ctx->stream>>>(dparts.as<double>(), 1, kEssParts, pe); ++ctx->launches;
-  group_lme_kernel<<<J, 256, 0, ctx->stream>>>(pl, static_cast<int>(P / J), pm, nullptr); ++ctx->launches;
+  group_lme_part_kernel<<<dim3(J, kLmeParts), 256, 0, ctx->stream>>>(pl, static_cast<int>(P / J),
+                                                                     dparts.as<double>()); ++ctx->launches;
+  group_lme_merge_kernel<<<(J + 63) / 64, 64, 0, ctx->stream>>>(dparts.as<double>(), J, kLmeParts,
+                                                                static_cast<int>(P / J), pm, nullptr,
+                                                                nullptr); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   if (mem == SPS_MEM_HOST) {
     if (ess) SPS_CUDA_TRY(cudaMemcpyAsync(ess, pe, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1423,7 +1732,7 @@ sps_status sps_particle_cov(sps_ctx* ctx, const double* theta, int64_t P, double
   if (D > 155) return fail(ctx, SPS_ERR_UNSUPPORTED, "sps_particle_cov: at most 155 parameters");
   const int T = D * (D + 1) / 2;
   const int blocks = cov_blocks(P);
-  DevBuf dt, dv, dmean, dpart;
+  DevBuf dt, dv, dpart;
   const double* pt = theta;
   if (mem == SPS_MEM_HOST) {
     SPS_CUDA_TRY(dt.reserve(sizeof(double) * P * D));
@@ -1431,17 +1740,9 @@ sps_status sps_particle_cov(sps_ctx* ctx, const double* theta, int64_t P, double
     pt = dt.as<double>();
   }
   SPS_CUDA_TRY(dv.reserve(sizeof(double) * D * D));
-  SPS_CUDA_TRY(dmean.reserve(sizeof(double) * D));
-  SPS_CUDA_TRY(dpart.reserve(sizeof(double) * T * blocks));
+  SPS_CUDA_TRY(dpart.reserve(sizeof(double) * (T + D) * blocks));
   double* pv = (mem == SPS_MEM_DEVICE) ? V : dv.as<double>();
-  const int64_t per = (P + blocks - 1) / blocks;
-  col_sum_partial_kernel<<<blocks, 256, 0, ctx->stream>>>(pt, P, D, per, dpart.as<double>()); ++ctx->launches;
-  col_mean_final_kernel<<<(D + 127) / 128, 128, 0, ctx->stream>>>(dpart.as<double>(), blocks, D, P,
-                                                                  dmean.as<double>()); ++ctx->launches;
-  cov_partial_kernel<<<blocks, kCovThreads, sizeof(float) * kCovSub * D, ctx->stream>>>(pt, P, D, dmean.as<double>(),
-                                                                                      per, dpart.as<double>()); ++ctx->launches;
-  cov_final_kernel<<<(T + 255) / 256, 256, 0, ctx->stream>>>(dpart.as<double>(), blocks, D, P, 1.0, pv, nullptr); ++ctx->launches;
-  SPS_CUDA_TRY(cudaGetLastError());
+  SPS_TRY(launch_cov(ctx, pt, P, D, 1.0, dpart.as<double>(), pv, nullptr));
   if (mem == SPS_MEM_HOST)
     SPS_CUDA_TRY(cudaMemcpyAsync(V, pv, sizeof(double) * D * D, cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -1494,7 +1795,7 @@ sps_status sps_rw_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P,
   SPS_TRY(launch_propose(ctx, &tmp, tmp.theta.as<double>(), P, pz, 0, flag_ptr(&tmp, 0), tmp.theta_prop.as<double>(),
                          tmp.lp_prop.as<double>()));
   SPS_TRY(loglik_dispatch(ctx, tmp.theta_prop.as<double>(), P, t, tmp.ll_prop.as<double>(), precision));
-  accept_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+  accept_kernel<<<static_cast<unsigned>((P + kAccThreads - 1) / kAccThreads), kAccThreads, 0, ctx->stream>>>(
       tmp.theta.as<double>(), tmp.ll.as<double>(), tmp.lp.as<double>(), tmp.theta_prop.as<double>(),
       tmp.ll_prop.as<double>(), tmp.lp_prop.as<double>(), P, D, pu, 0, 0, flag_ptr(&tmp, 0),
       tmp.counters.as<unsigned long long>(), flag_ptr(&tmp, 1), pla, pacc); ++ctx->launches;

@@ -30,6 +30,13 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
 * ess: bounds, equal weights, a single non-zero weight, shift invariance.
 * resample_multinomial: offspring counts sum to N, degenerate weights, exact hand cases,
   unbiasedness of offspring counts over replications (chi-square).
+* resample_residual: exact deterministic copies for weights with integral N w, copies never
+  below floor(N w) (up to the 2^-40 quantisation), unbiasedness over replications.
+* log predictive likelihoods (cphase / sps_run): the first observation's value against the
+  direct formula log mean_n p(y_1 | theta_n), X = 0 (each equals -log C exactly), their sum over
+  a cycle against the log-ML increment.
+* normalise_prior / gprior_covariance: the normalised prior against Monte Carlo draws of the
+  class differences; the paper's identity T^-1 sum_t x_t' (2 g T (X'X)^-1) x_t = 2 g.
 * group_moments: hand-computed small arrays; calibration of NSE is statistical.
 * sps_run: X = 0 (posterior = prior, log ML = -n log C exactly), a dogmatic prior
   (log ML -> loglik at the prior mean), grid quadrature on 1-2 parameter logits.

@@ -71,6 +71,37 @@ class GaussianPrior:
         return self.mean[None, :] + rng.standard_normal((P, self.D)) @ self.chol.T
 
 
+def normalise_prior(mu: np.ndarray, Sigma: np.ndarray):
+    """Prior of the normalised parameters from independent class priors (Sec. 3.1, Eq. 17).
+
+    mu: [C, k], Sigma: [C, k, k] for theta_c ~ N(mu_c, Sigma_c), c = 0..C-1 independent. With
+    outcome 0 as the base (theta_j replaced by theta_j - theta_0, j = 1..C-1) the D = k (C-1)
+    vector is Gaussian with block mean mu_j - mu_0, diagonal blocks Sigma_j + Sigma_0 and
+    off-diagonal blocks Sigma_0. Returns (mean [D], cov [D, D]).
+    """
+    mu = np.asarray(mu, dtype=np.float64)
+    Sigma = np.asarray(Sigma, dtype=np.float64)
+    C, k = mu.shape
+    mean = np.concatenate([mu[j] - mu[0] for j in range(1, C)])
+    cov = np.zeros((k * (C - 1), k * (C - 1)))
+    for a in range(1, C):
+        for b in range(1, C):
+            blk = Sigma[0].copy()
+            if a == b:
+                blk = blk + Sigma[a]
+            cov[(a - 1) * k:a * k, (b - 1) * k:b * k] = blk
+    return mean, cov
+
+
+def gprior_covariance(X: np.ndarray, C: int, g: float):
+    """Zellner's g-prior of the paper (Sec. 3.1, Eq. 18): mu_c = 0 and Sigma_c = g T (X'X)^-1 for
+    every outcome, then normalised on outcome 0 (normalise_prior). Returns (mean, cov)."""
+    X = np.asarray(X, dtype=np.float64)
+    T, k = X.shape
+    S = g * T * np.linalg.inv(X.T @ X)
+    return normalise_prior(np.zeros((C, k)), np.broadcast_to(S, (C, k, k)))
+
+
 # ----------------------------------------------------------------------------- statistics
 
 def ess(logw: np.ndarray) -> float:
@@ -147,6 +178,41 @@ def resample_multinomial(w: np.ndarray, u: np.ndarray) -> np.ndarray:
     return np.searchsorted(c, tau, side="right").astype(np.int32)
 
 
+RESIDUAL_SHIFT = 12
+
+
+def resample_residual(w: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Residual resampling of one group (the alternative to multinomial resampling that the S
+    phase allows, Sec. 2.2; Chopin's condition holds for it), in integers.
+
+    w: [N] weights with max(w) = 1; u: [N] FP64 uniforms on [0, 1), of which the first R are
+    used. q_n = floor(w_n 2^40), Q = sum q. Particle n gets c_n = floor(N q_n / Q) copies
+    (exact: N q_n < 2^64), placed first in particle order; the remaining R = N - sum c draws are
+    multinomial on the residuals r_n = (N q_n mod Q) >> 12 (so that sum r < 2^52 stays exact in
+    FP64), by the integer CDF of resample_multinomial: tau = min(floor(u_i sum r), sum r - 1),
+    index = first n with cumulative r > tau. Returns [N] int32 indices.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    N = w.shape[0]
+    q = [int(v) for v in np.floor(np.ldexp(w, WEIGHT_BITS))]
+    Q = sum(q)
+    if Q == 0:
+        raise DegenerateError("all resampling weights quantise to zero")
+    counts = [(N * qn) // Q for qn in q]
+    resid = [((N * qn) % Q) >> RESIDUAL_SHIFT for qn in q]
+    out = []
+    for n, c in enumerate(counts):
+        out.extend([n] * c)
+    R = N - len(out)
+    if R > 0:
+        cr = np.cumsum(np.array(resid, dtype=np.uint64), dtype=np.uint64)
+        S = cr[-1]
+        tau = np.floor(np.asarray(u[:R], dtype=np.float64) * np.float64(S)).astype(np.uint64)
+        tau = np.minimum(tau, S - np.uint64(1))
+        out.extend(np.searchsorted(cr, tau, side="right").tolist())
+    return np.array(out, dtype=np.int32)
+
+
 def normalised_weights(logw: np.ndarray) -> np.ndarray:
     """exp(logw - max logw) for one group."""
     lw = np.asarray(logw, dtype=np.float64)
@@ -167,6 +233,7 @@ class SpsOptions:
     rne_cycle: float = 0.35        # step 2(b)i: K = 0.35 if s < T
     rne_final: float = 0.9         # step 2(b)ii: K = 0.9 if s = T
     r_max: int = 200               # cap on M steps per cycle (not in the paper)
+    resampling: str = "multinomial"   # or "residual" (S phase, Sec. 2.2)
 
 
 @dataclass
@@ -179,6 +246,7 @@ class CycleRecord:
     rne_min: List[float] = field(default_factory=list)
     ess_end: float = 0.0
     logml_inc: Optional[np.ndarray] = None   # [J]
+    log_pred: Optional[np.ndarray] = None    # [t_l - t_{l-1}, J] per-observation log predictive
 
 
 @dataclass
@@ -191,6 +259,9 @@ class SpsResult:
     log_ml_groups: np.ndarray   # [J]
     log_ml_pooled: float        # log of the mean of ML_j over groups
     cycles: List[CycleRecord]
+    log_pred_groups: Optional[np.ndarray] = None   # [T, J] log p(y_s | y_1:s-1) per group
+    log_pred: Optional[np.ndarray] = None          # [T] mean over groups
+    log_pred_nse: Optional[np.ndarray] = None      # [T] sd over groups / sqrt(J)
 
     @property
     def n_cycles(self) -> int:
@@ -204,16 +275,22 @@ class SpsResult:
 # ----------------------------------------------------------------------------- phases
 
 def cphase(X, y, C, theta, t0: int, J: int, N: int, ess_fraction: float = 0.5,
-           t_fixed: Optional[int] = None):
+           t_fixed: Optional[int] = None, log_pred: Optional[list] = None):
     """C phase (Algorithm 1 step 2(a), Eq. 11; end rule Algorithm 2 step 1, Eq. 14).
 
     Starting from w_jn(t0) = 1, multiply in p(y_s | theta_jn) for s = t0+1, t0+2, ... and stop at
     the first s with ESS(s)/(J N) < ess_fraction, or at s = T. With t_fixed given (a recorded
     schedule), stop at s = t_fixed instead. Returns (t_new, logw [J*N], ess at t_new).
+
+    With a list given as log_pred, appends for each s the [J] log predictive likelihoods
+    log p(y_s | y_1:s-1) of the groups (Sec. 6 calls them a by-product of SPS):
+    log sum_n w_jn(s) - log sum_n w_jn(s-1), the weighted mean of p(y_s | theta_jn) under the
+    weights before observation s. Over a cycle they sum to the log-ML increment.
     """
     T = X.shape[0]
     P = theta.shape[0]
     logw = np.zeros(P)
+    prev = np.zeros(J)                       # log mean_n w_jn(t0) = 0
     s = t0
     e = float(P)
     # evaluate observation terms a block at a time; the stopping rule is still applied at each s
@@ -224,6 +301,10 @@ def cphase(X, y, C, theta, t0: int, J: int, N: int, ess_fraction: float = 0.5,
         for j in range(hi - s):
             logw = logw + terms[:, j]
             s += 1
+            if log_pred is not None:
+                cur = np.array([log_mean_exp(logw[g * N:(g + 1) * N]) for g in range(J)])
+                log_pred.append(cur - prev)
+                prev = cur
             e = ess(logw)
             if t_fixed is not None:
                 if s == t_fixed:
@@ -233,13 +314,15 @@ def cphase(X, y, C, theta, t0: int, J: int, N: int, ess_fraction: float = 0.5,
     return s, logw, e
 
 
-def sphase(theta, ll, logw, J: int, N: int, rng: np.random.Generator):
-    """S phase (Algorithm 1 step 2(b)): multinomial resampling of each group independently."""
+def sphase(theta, ll, logw, J: int, N: int, rng: np.random.Generator, scheme: str = "multinomial"):
+    """S phase (Algorithm 1 step 2(b)): multinomial (or residual) resampling of each group
+    independently."""
     idx = np.empty(J * N, dtype=np.int64)
     for j in range(J):
         w = normalised_weights(logw[j * N:(j + 1) * N])
         u = rng.random(N)
-        idx[j * N:(j + 1) * N] = j * N + resample_multinomial(w, u)
+        pick = resample_residual(w, u) if scheme == "residual" else resample_multinomial(w, u)
+        idx[j * N:(j + 1) * N] = j * N + pick
     return theta[idx].copy(), ll[idx].copy(), idx
 
 
@@ -312,14 +395,15 @@ def sps_run(X: np.ndarray, y: np.ndarray, C: int, prior: GaussianPrior, J: int, 
     ell_idx = 0
     while t < T:
         fixed = schedule[ell_idx] if schedule is not None else None
+        lp: list = []
         t_new, logw, e = cphase(X, y, C, theta, t, J, N, opt.ess_fraction,
-                                t_fixed=None if fixed is None else fixed.t)
+                                t_fixed=None if fixed is None else fixed.t, log_pred=lp)
         inc = np.array([log_mean_exp(logw[j * N:(j + 1) * N]) for j in range(J)])
         logml += inc
         ll = ll + logw
-        rec = CycleRecord(t=t_new, ess_end=e, logml_inc=inc)
+        rec = CycleRecord(t=t_new, ess_end=e, logml_inc=inc, log_pred=np.array(lp))
         t = t_new
-        theta, ll, _ = sphase(theta, ll, logw, J, N, rng)
+        theta, ll, _ = sphase(theta, ll, logw, J, N, rng, opt.resampling)
         K = opt.rne_final if t == T else opt.rne_cycle
         r = 0
         while True:
@@ -354,4 +438,6 @@ def sps_run(X: np.ndarray, y: np.ndarray, C: int, prior: GaussianPrior, J: int, 
     lm_nse = float(logml.std(ddof=1) / np.sqrt(J)) if J > 1 else float("nan")
     mx = logml.max()
     pooled = float(mx + np.log(np.mean(np.exp(logml - mx))))
-    return SpsResult(theta, ll, mom, lm, lm_nse, logml, pooled, cycles)
+    lpg = np.concatenate([c.log_pred for c in cycles], axis=0)   # [T, J]
+    lp_nse = lpg.std(axis=1, ddof=1) / np.sqrt(J) if J > 1 else np.full(T, np.nan)
+    return SpsResult(theta, ll, mom, lm, lm_nse, logml, pooled, cycles, lpg, lpg.mean(axis=1), lp_nse)

@@ -64,6 +64,9 @@ typedef enum sps_precision { SPS_PREC_SPLIT = 0, SPS_PREC_FP32 = 1 } sps_precisi
  * MALA adds the drift (h/2) V grad log p(theta | y) and the matching proposal-density ratio. */
 typedef enum sps_mkernel { SPS_MKERNEL_RW = 0, SPS_MKERNEL_MALA = 1 } sps_mkernel;
 
+/* S-phase resampling scheme (Sec. 2.2 allows multinomial or residual resampling). */
+typedef enum sps_resampling { SPS_RESAMPLE_MULTINOMIAL = 0, SPS_RESAMPLE_RESIDUAL = 1 } sps_resampling;
+
 typedef enum sps_prior_kind {
   SPS_PRIOR_ISO = 0,   /* cov = sd^2 I, cov_or_sd points to 1 value (sd) */
   SPS_PRIOR_DIAG = 1,  /* cov = diag(sd^2), cov_or_sd points to D values (sd) */
@@ -95,6 +98,7 @@ typedef struct sps_options {
   int32_t cphase_block;    /* observations per C-phase block launch, default 64 */
   double mala_target_accept; /* 0.5: step-size target when mkernel == MALA (not in the paper) */
   uint64_t seed;           /* Philox key for sps_run's random numbers */
+  int32_t resampling;      /* sps_resampling, default SPS_RESAMPLE_MULTINOMIAL */
 } sps_options;
 
 typedef struct sps_ctx sps_ctx;
@@ -133,12 +137,25 @@ typedef struct sps_result {
   int32_t n_cycles;        /* L */
   int64_t m_steps;         /* sum of R_l */
   double seconds;          /* wall time of the run on the host clock */
+  double* log_pred;        /* [n] or NULL: log predictive likelihoods log p(y_s | y_1:s-1), the
+                              mean over groups of log sum_n w_jn(s) - log sum_n w_jn(s-1) within
+                              the cycle containing s (Sec. 6 calls them a by-product of SPS);
+                              over a cycle they sum to the log-ML increment */
+  double* log_pred_nse;    /* [n] or NULL: their sd over groups / sqrt(J) */
 } sps_result;
 
 /* ------------------------------------------------------------------ lifecycle */
 
 /* Fill *opt with the paper's Algorithm 2 constants and the library defaults. */
 void sps_options_default(sps_options* opt);
+
+/* Prior of the normalised parameters from independent class priors (Sec. 3.1, Eq. 17):
+ * theta_c ~ N(mu_c, Sigma_c), c = 0..C-1; with outcome 0 as the base the D = k (C-1) vector of
+ * theta_j - theta_0 has block mean mu_j - mu_0, diagonal blocks Sigma_j + Sigma_0 and
+ * off-diagonal blocks Sigma_0. Host arrays: mu [C x k], Sigma [C x k x k] row-major;
+ * mean_out [D], cov_out [D x D]. Pure host arithmetic (setup, not on the simulator's path). */
+sps_status sps_prior_normalize(int32_t k, int32_t n_outcomes, const double* mu, const double* Sigma,
+                               double* mean_out, double* cov_out);
 
 /* Create a context for the data (X, y) and prior (Sec. 2.1, Eq. 1; Sec. 3.1, Eq. 16).
  *   X: host FP64 [n x k] row-major covariates; y: host int32 [n], values 0..n_outcomes-1.
@@ -166,6 +183,16 @@ const char* sps_last_error(const sps_ctx* ctx);
 
 /* Sizes of the context: n, k, C, D. Any pointer may be NULL. */
 sps_status sps_get_dims(const sps_ctx* ctx, int64_t* n, int32_t* k, int32_t* C, int32_t* D);
+
+/* Replace the context's prior (same rules as sps_init); states created later draw from it. */
+sps_status sps_set_prior(sps_ctx* ctx, const sps_prior* prior);
+
+/* Zellner's g-prior of the paper for the context's data (Sec. 3.1, Eq. 18): Sigma_c = g n (X'X)^-1
+ * and mu_c = 0 for every outcome, normalised on outcome 0 (sps_prior_normalize). X'X is summed
+ * on the device in FP64; its inverse (k x k) is taken on the host by Cholesky. mean_out [D]
+ * (zeros) and cov_out [D x D] are host arrays; pass them to sps_set_prior as SPS_PRIOR_FULL.
+ * SPS_ERR_DEGENERATE when X'X is singular. */
+sps_status sps_gprior(sps_ctx* ctx, double g, double* mean_out, double* cov_out);
 
 /* Instrumentation (the paper has no counterpart). sps_set_timing(ctx, 1) records CUDA events on
  * the context's stream around every launch of the fused log-likelihood kernel from then on.
@@ -234,12 +261,15 @@ sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const
  * ESS(s)/(J N) < ess_fraction or s = n; with t_target > 0 stop at s = t_target instead
  * (a recorded schedule). Adds log N^-1 sum_n w_jn to each group's log marginal likelihood,
  * updates the cached log-likelihoods and sets t. Outputs (host, may be NULL): t_new, ess at
- * t_new, logml_inc [J]. */
+ * t_new, logml_inc [J], log_pred [(t_new - t) x J] row-major: the per-group log predictive
+ * likelihoods of the observations taken in (capacity (n - t) x J; FP32 exponentials of the
+ * running log weights, FP64 sums). */
 sps_status sps_cphase(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new,
-                      double* ess, double* logml_inc);
+                      double* ess, double* logml_inc, double* log_pred);
 
-/* S phase (Algorithm 1 step 2(b)): multinomial resampling of each group from its C-phase
- * weights, then the gather of particles and cached log-likelihoods.
+/* S phase (Algorithm 1 step 2(b)): resampling of each group from its C-phase weights (the
+ * context's sps_options.resampling scheme, see sps_resample), then the gather of particles and
+ * cached log-likelihoods.
  *   uniforms: [J*N] FP64 on [0,1) (mem) to use instead of the state's Philox stream, or NULL.
  *   idx_out: [J*N] int32 (mem) receives the selected index within the group, or NULL. */
 sps_status sps_sphase(sps_ctx* ctx, sps_state* st, const double* uniforms, int32_t* idx_out,
@@ -276,14 +306,18 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
 
 /* ------------------------------------------------------------------ building blocks */
 
-/* Multinomial resampling by an integer CDF, each of J groups of N independently (the S phase
- * of Algorithm 1): q_n = floor(w_n 2^40) with w the group's FP64 weights divided by their
- * maximum (w is given already divided: max w_n = 1 in each group), cumulative sums in uint64,
- * tau = min(floor(u_i * Q), Q - 1), idx_i = first n with cumulative q > tau.
+/* Resampling by integer CDFs, each of J groups of N independently (the S phase of Algorithm 1):
+ * q_n = floor(w_n 2^40) with w the group's FP64 weights divided by their maximum (w is given
+ * already divided: max w_n = 1 in each group), Q = sum q.
+ *   SPS_RESAMPLE_MULTINOMIAL: cumulative sums of q in uint64, tau_i = min(floor(u_i * Q), Q - 1),
+ *     idx_i = first n with cumulative q > tau_i.
+ *   SPS_RESAMPLE_RESIDUAL: c_n = floor(N q_n / Q) copies of n placed first in particle order,
+ *     then R = N - sum c draws i = 0..R-1 multinomial as above on r_n = (N q_n mod Q) >> 12,
+ *     using u_i.
  *   w, u: [J*N] FP64 (mem); idx: [J*N] int32 within-group indices (mem). N <= 4096.
  * SPS_ERR_DEGENERATE (host memory only) when a group's weights all quantise to zero. */
 sps_status sps_resample(sps_ctx* ctx, const double* w, const double* u, int32_t J, int32_t N,
-                        int32_t* idx, int32_t mem);
+                        int32_t scheme, int32_t* idx, int32_t mem);
 
 /* Philox4x32-10 blocks (Salmon et al., SC'11) for counters (ctr0 + i, ctr1, ctr2, ctr3),
  * i = 0..count-1, key (key0, key1): out [count x 4] uint32 (mem). */

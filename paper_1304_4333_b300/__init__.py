@@ -5,6 +5,6 @@ Posterior Simulation". The compute path is the in-tree CUDA library libsps.so (C
 include/sps.h); this package is its Python binding. Importing the binding loads the library and
 raises if it is missing: there is no CPU fallback.
 """
-from .api import Sps, State, RunResult, Schedule, SpsError, default_options  # noqa: F401
+from .api import Sps, State, RunResult, Schedule, SpsError, default_options, prior_normalize  # noqa: F401
 
 __all__ = ["Sps", "State", "RunResult", "Schedule", "SpsError", "default_options"]

@@ -17,6 +17,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 PREC_SPLIT, PREC_FP32 = 0, 1
 MKERNEL_RW, MKERNEL_MALA = 0, 1
 PRIOR_ISO, PRIOR_DIAG, PRIOR_FULL = 0, 1, 2
+RESAMPLE_MULTINOMIAL, RESAMPLE_RESIDUAL = 0, 1
 
 
 class SpsPrior(C.Structure):
@@ -28,7 +29,7 @@ class SpsOptions(C.Structure):
                 ("h_min", C.c_double), ("h_max", C.c_double), ("target_accept", C.c_double),
                 ("rne_cycle", C.c_double), ("rne_final", C.c_double), ("r_max", C.c_int32),
                 ("precision", C.c_int32), ("mkernel", C.c_int32), ("cphase_block", C.c_int32),
-                ("mala_target_accept", C.c_double), ("seed", C.c_uint64)]
+                ("mala_target_accept", C.c_double), ("seed", C.c_uint64), ("resampling", C.c_int32)]
 
 
 class SpsSchedule(C.Structure):
@@ -41,7 +42,8 @@ class SpsResult(C.Structure):
     _fields_ = [("mean", C.POINTER(C.c_double)), ("sd", C.POINTER(C.c_double)), ("nse", C.POINTER(C.c_double)),
                 ("rne", C.POINTER(C.c_double)), ("log_ml_group", C.POINTER(C.c_double)),
                 ("log_ml", C.c_double), ("log_ml_nse", C.c_double), ("log_ml_pooled", C.c_double),
-                ("n_cycles", C.c_int32), ("m_steps", C.c_int64), ("seconds", C.c_double)]
+                ("n_cycles", C.c_int32), ("m_steps", C.c_int64), ("seconds", C.c_double),
+                ("log_pred", C.POINTER(C.c_double)), ("log_pred_nse", C.POINTER(C.c_double))]
 
 
 class SpsMstepInfo(C.Structure):
@@ -71,14 +73,17 @@ SIGNATURES = {
     "sps_state_destroy": (None, [_P]),
     "sps_state_get": (C.c_int, [_P, _P, _P, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "sps_state_set": (C.c_int, [_P, _P, _P, _P, C.c_int64]),
-    "sps_cphase": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double), _P]),
+    "sps_cphase": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P]),
     "sps_sphase": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
     "sps_mstep": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.POINTER(SpsMstepInfo)]),
     "sps_mphase": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                              C.POINTER(C.c_double)]),
     "sps_run": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(SpsSchedule), C.POINTER(SpsSchedule),
                           C.POINTER(SpsResult)]),
-    "sps_resample": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, _P, C.c_int32]),
+    "sps_resample": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32]),
+    "sps_set_prior": (C.c_int, [_P, C.POINTER(SpsPrior)]),
+    "sps_gprior": (C.c_int, [_P, C.c_double, _P, _P]),
+    "sps_prior_normalize": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P]),
     "sps_philox": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                              C.c_int64, _P, C.c_int32]),
     "sps_ess": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P, C.c_int32]),

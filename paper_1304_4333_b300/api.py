@@ -18,6 +18,7 @@ from ._native import SpsError
 
 PRECISIONS = {"split": N.PREC_SPLIT, "fp32": N.PREC_FP32}
 MKERNELS = {"rw": N.MKERNEL_RW, "mala": N.MKERNEL_MALA}
+RESAMPLING = {"multinomial": N.RESAMPLE_MULTINOMIAL, "residual": N.RESAMPLE_RESIDUAL}
 
 
 def _check(lib, ctx, status: int):
@@ -55,8 +56,26 @@ def default_options(**over) -> N.SpsOptions:
             v = PRECISIONS[v]
         if k == "mkernel" and isinstance(v, str):
             v = MKERNELS[v]
+        if k == "resampling" and isinstance(v, str):
+            v = RESAMPLING[v]
         setattr(o, k, v)
     return o
+
+
+def prior_normalize(mu, Sigma):
+    """Prior of theta_j - theta_0 (j = 1..C-1) from independent class priors N(mu_c, Sigma_c)
+    (sps_prior_normalize): mu [C, k], Sigma [C, k, k] -> (mean [D], cov [D, D])."""
+    lib = N.load()
+    mu = _f64(mu)
+    Sig = _f64(Sigma)
+    Cn, k = mu.shape
+    D = k * (Cn - 1)
+    mean = np.empty(D)
+    cov = np.empty((D, D))
+    st = lib.sps_prior_normalize(k, Cn, _ptr(mu), _ptr(Sig), _ptr(mean), _ptr(cov))
+    if st != N.SPS_OK:
+        raise SpsError(st, lib.sps_status_string(st).decode())
+    return mean, cov
 
 
 @dataclass
@@ -73,6 +92,8 @@ class RunResult:
     m_steps: int
     seconds: float
     schedule: Optional["Schedule"] = None
+    log_pred: Optional[np.ndarray] = None       # [n] log p(y_s | y_1:s-1), mean over groups
+    log_pred_nse: Optional[np.ndarray] = None   # [n] sd over groups / sqrt(J)
 
 
 @dataclass
@@ -115,22 +136,7 @@ class Sps:
         n, k = X.shape
         self.n, self.k, self.C = int(n), int(k), int(C_outcomes)
         self.D = self.k * (self.C - 1)
-        pr = N.SpsPrior()
-        self._prior_arrays = []
-        if prior_cov is not None:
-            cov = _f64(prior_cov).reshape(self.D, self.D)
-            pr.kind, self._prior_arrays = N.PRIOR_FULL, [cov]
-        elif prior_diag_sd is not None:
-            sd = _f64(prior_diag_sd).reshape(self.D)
-            pr.kind, self._prior_arrays = N.PRIOR_DIAG, [sd]
-        else:
-            sd = np.array([float(prior_sd)])
-            pr.kind, self._prior_arrays = N.PRIOR_ISO, [sd]
-        pr.cov_or_sd = self._prior_arrays[0].ctypes.data_as(C.POINTER(C.c_double))
-        if prior_mean is not None:
-            m = _f64(prior_mean).reshape(self.D)
-            self._prior_arrays.append(m)
-            pr.mean = m.ctypes.data_as(C.POINTER(C.c_double))
+        pr = self._prior_struct(prior_sd, prior_mean, prior_cov, prior_diag_sd)
         self.options = default_options(**options)
         self._states = weakref.WeakSet()   # states are destroyed before the context
         ctx = C.c_void_p()
@@ -209,17 +215,50 @@ class Sps:
         self._call("sps_loglik_grad", _ptr(th), th.shape[0], t, _ptr(ll), _ptr(g), N.MEM_HOST)
         return ll, g
 
+    # ------------------------------------------------------------------ priors
+    def _prior_struct(self, prior_sd=5.0, prior_mean=None, prior_cov=None, prior_diag_sd=None) -> N.SpsPrior:
+        pr = N.SpsPrior()
+        if prior_cov is not None:
+            cov = _f64(prior_cov).reshape(self.D, self.D)
+            pr.kind, self._prior_arrays = N.PRIOR_FULL, [cov]
+        elif prior_diag_sd is not None:
+            sd = _f64(prior_diag_sd).reshape(self.D)
+            pr.kind, self._prior_arrays = N.PRIOR_DIAG, [sd]
+        else:
+            sd = np.array([float(prior_sd)])
+            pr.kind, self._prior_arrays = N.PRIOR_ISO, [sd]
+        pr.cov_or_sd = self._prior_arrays[0].ctypes.data_as(C.POINTER(C.c_double))
+        if prior_mean is not None:
+            m = _f64(prior_mean).reshape(self.D)
+            self._prior_arrays.append(m)
+            pr.mean = m.ctypes.data_as(C.POINTER(C.c_double))
+        return pr
+
+    def set_prior(self, prior_sd: float = 5.0, prior_mean=None, prior_cov=None, prior_diag_sd=None):
+        """Replace the prior (sps_set_prior); states created afterwards draw from it."""
+        pr = self._prior_struct(prior_sd, prior_mean, prior_cov, prior_diag_sd)
+        self._call("sps_set_prior", C.byref(pr))
+
+    def gprior(self, g: float):
+        """Zellner's g-prior for this data, normalised on outcome 0 (sps_gprior): (mean, cov)."""
+        mean = np.empty(self.D)
+        cov = np.empty((self.D, self.D))
+        self._call("sps_gprior", float(g), _ptr(mean), _ptr(cov))
+        return mean, cov
+
     # ------------------------------------------------------------------ building blocks
-    def resample(self, w, u, J: int, N_: int):
+    def resample(self, w, u, J: int, N_: int, scheme: str = "multinomial"):
+        sch = RESAMPLING[scheme]
         if _is_device(w):
             torch = _torch()
             idx = torch.empty(J * N_, dtype=torch.int32, device=w.device)
             self._sync_stream()
-            self._call("sps_resample", _ptr(w.contiguous()), _ptr(u.contiguous()), J, N_, _ptr(idx), N.MEM_DEVICE)
+            self._call("sps_resample", _ptr(w.contiguous()), _ptr(u.contiguous()), J, N_, sch, _ptr(idx),
+                       N.MEM_DEVICE)
             return idx
         w = _f64(w); u = _f64(u)
         idx = np.empty(J * N_, dtype=np.int32)
-        self._call("sps_resample", _ptr(w), _ptr(u), J, N_, _ptr(idx), N.MEM_HOST)
+        self._call("sps_resample", _ptr(w), _ptr(u), J, N_, sch, _ptr(idx), N.MEM_HOST)
         return idx
 
     def philox(self, key, ctr, count: int):
@@ -257,7 +296,7 @@ class Sps:
         return State(self, J, N_, seed)
 
     def run(self, J: int, N_: int, schedule: Optional[Schedule] = None, record: bool = True,
-            cap_cycles: int = 4096, cap_steps: int = 20000) -> RunResult:
+            cap_cycles: int = 4096, cap_steps: int = 20000, log_pred: bool = False) -> RunResult:
         m = self.D + self.C - 1
         arrs = {k: np.zeros(m) for k in ("mean", "sd", "nse", "rne")}
         lmg = np.zeros(J)
@@ -265,6 +304,11 @@ class Sps:
         for k_, a in arrs.items():
             setattr(res, k_, a.ctypes.data_as(C.POINTER(C.c_double)))
         res.log_ml_group = lmg.ctypes.data_as(C.POINTER(C.c_double))
+        lp = np.zeros(self.n) if log_pred else None
+        lpn = np.zeros(self.n) if log_pred else None
+        if log_pred:
+            res.log_pred = lp.ctypes.data_as(C.POINTER(C.c_double))
+            res.log_pred_nse = lpn.ctypes.data_as(C.POINTER(C.c_double))
         sched_in = schedule.as_struct() if schedule is not None else None
         rec = None
         if record:
@@ -291,7 +335,7 @@ class Sps:
                              rs[:S].copy() if rs is not None else np.zeros((0, self.D, self.D)),
                              rh[:S].copy(), ra[:S].copy())
         return RunResult(arrs["mean"], arrs["sd"], arrs["nse"], arrs["rne"], lmg, res.log_ml, res.log_ml_nse,
-                         res.log_ml_pooled, res.n_cycles, res.m_steps, res.seconds, sched)
+                         res.log_ml_pooled, res.n_cycles, res.m_steps, res.seconds, sched, lp, lpn)
 
 
 class State:
@@ -333,10 +377,16 @@ class State:
         l = _f64(ll) if ll is not None else None
         self.sps._call("sps_state_set", self.st, _ptr(th), _ptr(l) if l is not None else None, int(t))
 
-    def cphase(self, t_target: int = 0):
+    def cphase(self, t_target: int = 0, log_pred: bool = False):
+        """C phase; returns (t_new, ess, logml_inc[J]) and, with log_pred, the per-group log
+        predictive likelihoods [t_new - t, J] of the observations taken in."""
         tn = C.c_int64(); e = C.c_double(); inc = np.empty(self.J)
-        self.sps._call("sps_cphase", self.st, int(t_target), C.byref(tn), C.byref(e), _ptr(inc))
-        return tn.value, e.value, inc
+        lp = np.empty((self.sps.n - self.get_t(), self.J)) if log_pred else None
+        self.sps._call("sps_cphase", self.st, int(t_target), C.byref(tn), C.byref(e), _ptr(inc),
+                       _ptr(lp) if lp is not None else None)
+        if lp is None:
+            return tn.value, e.value, inc
+        return tn.value, e.value, inc, lp[:tn.value - (self.sps.n - lp.shape[0])].copy()
 
     def sphase(self, uniforms=None):
         idx = np.empty(self.J * self.N, dtype=np.int32)

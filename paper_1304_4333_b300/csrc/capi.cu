@@ -145,6 +145,85 @@ bool cholesky_host(const std::vector<double>& A, int D, std::vector<double>& L) 
   return true;
 }
 
+// Validate a prior for the context's D and install it: mean, covariance, host Cholesky factor,
+// device mean, precision (diagonal for ISO/DIAG, full inverse for FULL) and factor. Nothing of
+// the context changes when the prior is rejected.
+sps_status apply_prior(sps_ctx* ctx, const sps_prior* prior) {
+  const int D = ctx->D;
+  if (!prior || !prior->cov_or_sd) return fail(ctx, SPS_ERR_INVALID_ARG, "prior: covariance missing");
+  std::vector<double> mean(D, 0.0), cov(static_cast<size_t>(D) * D, 0.0), chol;
+  if (prior->mean)
+    for (int i = 0; i < D; ++i) mean[i] = prior->mean[i];
+  if (prior->kind == SPS_PRIOR_ISO) {
+    const double sd = prior->cov_or_sd[0];
+    if (!(sd > 0.0) || !std::isfinite(sd)) return fail(ctx, SPS_ERR_INVALID_ARG, "prior: bad sd");
+    for (int i = 0; i < D; ++i) cov[i * D + i] = sd * sd;
+  } else if (prior->kind == SPS_PRIOR_DIAG) {
+    for (int i = 0; i < D; ++i) {
+      const double sd = prior->cov_or_sd[i];
+      if (!(sd > 0.0) || !std::isfinite(sd)) return fail(ctx, SPS_ERR_INVALID_ARG, "prior: bad sd");
+      cov[i * D + i] = sd * sd;
+    }
+  } else if (prior->kind == SPS_PRIOR_FULL) {
+    for (int i = 0; i < D * D; ++i) cov[i] = prior->cov_or_sd[i];
+  } else {
+    return fail(ctx, SPS_ERR_INVALID_ARG, "prior: unknown kind");
+  }
+  for (double v : mean)
+    if (!std::isfinite(v)) return fail(ctx, SPS_ERR_INVALID_ARG, "prior: non-finite mean");
+  if (!cholesky_host(cov, D, chol)) return fail(ctx, SPS_ERR_INVALID_ARG, "prior covariance is not positive definite");
+  std::vector<double> prec;
+  if (prior->kind == SPS_PRIOR_FULL) {
+    std::vector<double> Linv(static_cast<size_t>(D) * D, 0.0);
+    for (int j = 0; j < D; ++j) {
+      Linv[j * D + j] = 1.0 / chol[j * D + j];
+      for (int i = j + 1; i < D; ++i) {
+        double a = 0.0;
+        for (int m = j; m < i; ++m) a += chol[i * D + m] * Linv[m * D + j];
+        Linv[i * D + j] = -a / chol[i * D + i];
+      }
+    }
+    prec.assign(static_cast<size_t>(D) * D, 0.0);
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        double a = 0.0;
+        for (int m = std::max(i, j); m < D; ++m) a += Linv[m * D + i] * Linv[m * D + j];
+        prec[i * D + j] = a;
+      }
+  } else {
+    prec.resize(D);
+    for (int i = 0; i < D; ++i) prec[i] = 1.0 / cov[i * D + i];
+  }
+  SPS_TRY(to_device(ctx, ctx->d_prior_prec, prec.data(), prec.size() * sizeof(double)));
+  SPS_TRY(to_device(ctx, ctx->d_prior_mean, mean.data(), D * sizeof(double)));
+  SPS_TRY(to_device(ctx, ctx->d_prior_chol, chol.data(), chol.size() * sizeof(double)));
+  ctx->prior_kind = prior->kind;
+  ctx->prior_mean = mean;
+  ctx->prior_cov = cov;
+  ctx->prior_chol = chol;
+  return SPS_OK;
+}
+
+// X'X [k x k] in FP64: one block per lower-triangle entry (i >= j), threads over observations.
+__global__ void xtx_kernel(const double* __restrict__ X, int64_t n, int k, double* __restrict__ out) {
+  __shared__ double sh[32];
+  int i = 0, e = blockIdx.x;
+  while ((i + 1) * (i + 2) / 2 <= e) ++i;
+  const int j = e - i * (i + 1) / 2;
+  double a = 0.0;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) a = fma(X[t * k + i], X[t * k + j], a);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += sh[w];
+    out[i * k + j] = s;
+    out[j * k + i] = s;
+  }
+}
+
 }  // namespace
 
 sps_status make_map_bf16(sps_ctx* ctx, CUtensorMap* map, const void* base, uint64_t rows,
@@ -225,6 +304,7 @@ void sps_options_default(sps_options* o) {
   o->cphase_block = 64;
   o->mala_target_accept = 0.5;
   o->seed = 0;
+  o->resampling = SPS_RESAMPLE_MULTINOMIAL;
 }
 
 const char* sps_status_string(sps_status s) {
@@ -251,6 +331,64 @@ sps_status sps_get_dims(const sps_ctx* ctx, int64_t* n, int32_t* k, int32_t* C, 
   if (C) *C = ctx->C;
   if (D) *D = ctx->D;
   return SPS_OK;
+}
+
+sps_status sps_set_prior(sps_ctx* ctx, const sps_prior* prior) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  return apply_prior(ctx, prior);
+}
+
+sps_status sps_prior_normalize(int32_t k, int32_t n_outcomes, const double* mu, const double* Sigma,
+                               double* mean_out, double* cov_out) {
+  if (k < 1 || n_outcomes < 2 || !mu || !Sigma || !mean_out || !cov_out) return SPS_ERR_INVALID_ARG;
+  const int C = n_outcomes, D = k * (C - 1);
+  for (int a = 1; a < C; ++a)
+    for (int i = 0; i < k; ++i) mean_out[(a - 1) * k + i] = mu[a * k + i] - mu[i];
+  const size_t kk = static_cast<size_t>(k) * k;
+  for (int a = 1; a < C; ++a)
+    for (int b = 1; b < C; ++b)
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+          double v = Sigma[i * k + j];                       // Sigma_0
+          if (a == b) v += Sigma[a * kk + i * k + j];        // + Sigma_a on the diagonal blocks
+          cov_out[static_cast<size_t>((a - 1) * k + i) * D + (b - 1) * k + j] = v;
+        }
+  return SPS_OK;
+}
+
+sps_status sps_gprior(sps_ctx* ctx, double g, double* mean_out, double* cov_out) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!(g > 0.0) || !std::isfinite(g) || !mean_out || !cov_out)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_gprior: bad arguments");
+  const int k = ctx->k, C = ctx->C;
+  DevBuf d;
+  SPS_CUDA_TRY(d.reserve(sizeof(double) * k * k));
+  xtx_kernel<<<k * (k + 1) / 2, 256, 0, ctx->stream>>>(ctx->Xd.as<double>(), ctx->n, k, d.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> A(static_cast<size_t>(k) * k), L;
+  SPS_CUDA_TRY(cudaMemcpyAsync(A.data(), d.ptr, sizeof(double) * k * k, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (!cholesky_host(A, k, L)) return fail(ctx, SPS_ERR_DEGENERATE, "sps_gprior: X'X is singular");
+  // (X'X)^-1 = L^-T L^-1 from the inverse of the Cholesky factor
+  std::vector<double> Linv(static_cast<size_t>(k) * k, 0.0), S(static_cast<size_t>(k) * k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    Linv[j * k + j] = 1.0 / L[j * k + j];
+    for (int i = j + 1; i < k; ++i) {
+      double a = 0.0;
+      for (int m = j; m < i; ++m) a += L[i * k + m] * Linv[m * k + j];
+      Linv[i * k + j] = -a / L[i * k + i];
+    }
+  }
+  const double scale = g * static_cast<double>(ctx->n);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      double a = 0.0;
+      for (int m = std::max(i, j); m < k; ++m) a += Linv[m * k + i] * Linv[m * k + j];
+      S[i * k + j] = scale * a;
+    }
+  std::vector<double> mu(static_cast<size_t>(C) * k, 0.0), Sig(static_cast<size_t>(C) * k * k);
+  for (int c = 0; c < C; ++c) std::copy(S.begin(), S.end(), Sig.begin() + static_cast<size_t>(c) * k * k);
+  return sps_prior_normalize(k, C, mu.data(), Sig.data(), mean_out, cov_out);
 }
 
 sps_status sps_set_stream(sps_ctx* ctx, void* stream) {
@@ -318,65 +456,7 @@ sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const 
   ctx->num_sms = prop.multiProcessorCount;
 
   // ---- prior
-  ctx->prior_kind = prior->kind;
-  ctx->prior_mean.assign(D, 0.0);
-  if (prior->mean)
-    for (int i = 0; i < D; ++i) ctx->prior_mean[i] = prior->mean[i];
-  ctx->prior_cov.assign(static_cast<size_t>(D) * D, 0.0);
-  if (!prior->cov_or_sd) return bail(SPS_ERR_INVALID_ARG);
-  if (prior->kind == SPS_PRIOR_ISO) {
-    const double sd = prior->cov_or_sd[0];
-    if (!(sd > 0.0) || !std::isfinite(sd)) return bail(SPS_ERR_INVALID_ARG);
-    for (int i = 0; i < D; ++i) ctx->prior_cov[i * D + i] = sd * sd;
-  } else if (prior->kind == SPS_PRIOR_DIAG) {
-    for (int i = 0; i < D; ++i) {
-      const double sd = prior->cov_or_sd[i];
-      if (!(sd > 0.0) || !std::isfinite(sd)) return bail(SPS_ERR_INVALID_ARG);
-      ctx->prior_cov[i * D + i] = sd * sd;
-    }
-  } else if (prior->kind == SPS_PRIOR_FULL) {
-    for (int i = 0; i < D * D; ++i) ctx->prior_cov[i] = prior->cov_or_sd[i];
-  } else {
-    return bail(SPS_ERR_INVALID_ARG);
-  }
-  for (double v : ctx->prior_mean)
-    if (!std::isfinite(v)) return bail(SPS_ERR_INVALID_ARG);
-  if (!cholesky_host(ctx->prior_cov, D, ctx->prior_chol)) {
-    ctx->last_error = "prior covariance is not positive definite";
-    return bail(SPS_ERR_INVALID_ARG);
-  }
-  {
-    // precision: diagonal for ISO/DIAG, full inverse (via the Cholesky factor) for FULL
-    std::vector<double> prec;
-    if (prior->kind == SPS_PRIOR_FULL) {
-      std::vector<double> Linv(static_cast<size_t>(D) * D, 0.0);
-      const auto& L = ctx->prior_chol;
-      for (int j = 0; j < D; ++j) {
-        Linv[j * D + j] = 1.0 / L[j * D + j];
-        for (int i = j + 1; i < D; ++i) {
-          double s = 0.0;
-          for (int m = j; m < i; ++m) s += L[i * D + m] * Linv[m * D + j];
-          Linv[i * D + j] = -s / L[i * D + i];
-        }
-      }
-      prec.assign(static_cast<size_t>(D) * D, 0.0);
-      for (int i = 0; i < D; ++i)
-        for (int j = 0; j < D; ++j) {
-          double s = 0.0;
-          for (int m = std::max(i, j); m < D; ++m) s += Linv[m * D + i] * Linv[m * D + j];
-          prec[i * D + j] = s;
-        }
-    } else {
-      prec.resize(D);
-      for (int i = 0; i < D; ++i) prec[i] = 1.0 / ctx->prior_cov[i * D + i];
-    }
-    if (to_device(ctx, ctx->d_prior_prec, prec.data(), prec.size() * sizeof(double)) != SPS_OK)
-      return bail(SPS_ERR_OOM);
-    if (to_device(ctx, ctx->d_prior_mean, ctx->prior_mean.data(), D * sizeof(double)) != SPS_OK ||
-        to_device(ctx, ctx->d_prior_chol, ctx->prior_chol.data(), ctx->prior_chol.size() * sizeof(double)) !=
-            SPS_OK)
-      return bail(SPS_ERR_OOM);
-  }
+  if (const sps_status ps = apply_prior(ctx, prior); ps != SPS_OK) return bail(ps);
 
   // ---- data
   sps_status st;

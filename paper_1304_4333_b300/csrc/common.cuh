@@ -136,6 +136,7 @@ struct sps_state {
   sps::DevBuf lwbuf;              // float2 [block x P] C-phase running log weights (Kahan pairs)
   sps::DevBuf lwstate;            // float2 [P] running log weights at the start of a C-phase block
   sps::DevBuf gmax;               // FP64 [J] group maxima of logw (S-phase weight scale)
+  sps::DevBuf lpl_dev;            // FP64 [block x J] per-group log-mean-exp of C-phase rows
   sps::DevBuf ess_buf;            // FP64 [block] ESS per observation of a block
   sps::DevBuf idx;                // int32 [P]
   sps::DevBuf scratch;            // moments, covariance partials, counters

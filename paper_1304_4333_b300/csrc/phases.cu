@@ -271,6 +271,28 @@ __global__ void lw_to_f64_kernel(const float2* __restrict__ row, int64_t P, doub
   logw[p] = f32_to_f64(v.x) - f32_to_f64(v.y);
 }
 
+// Per-group log N^-1 sum_n exp(lw_jn) of each row of C-phase running log weights (Kahan pairs):
+// out[r * J + j]; block (row, group), FP32 exponentials of (s - m) - c with an online maximum,
+// FP64 block sums. Differences of consecutive rows are the log predictive likelihoods.
+__global__ void row_group_lme_kernel(const float2* __restrict__ rows, int64_t P, int N, double* __restrict__ out) {
+  __shared__ float shf[33];
+  __shared__ double sh[33];
+  const float2* g = rows + static_cast<int64_t>(blockIdx.x) * P + static_cast<int64_t>(blockIdx.y) * N;
+  float m = -INFINITY, s1 = 0.f;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    const float2 v = g[n];
+    if (v.x > m) {
+      s1 *= (m > -INFINITY) ? __expf(m - v.x) : 0.f;
+      m = v.x;
+    }
+    s1 += __expf((v.x - m) - v.y);
+  }
+  const float M = block_max_f(m, shf);
+  const double t = block_sum(f32_to_f64(s1 * ((m > -INFINITY) ? __expf(m - M) : 0.f)), sh);
+  if (threadIdx.x == 0)
+    out[static_cast<int64_t>(blockIdx.x) * gridDim.y + blockIdx.y] = f32_to_f64(M) + log(t / static_cast<double>(N));
+}
+
 // Per-group log N^-1 sum_n exp(logw_jn) in FP64, in two kernels: block (group, part) writes its
 // slice's maximum and sum of exp(logw - maximum); the merge (thread per group) rescales the
 // parts, writes lme_j, adds it to logml_j and records the group maximum.
@@ -395,6 +417,129 @@ resample_kernel(const unsigned long long* __restrict__ qv, int N, const double* 
     }
     idx[static_cast<int64_t>(j) * N + i] = lo;
   }
+}
+
+constexpr int kResidualShift = 12;
+
+// Residual resampling of group j (block (j, slice)): with Q = sum q, particle n gets
+// c_n = floor(N q_n / Q) copies, placed first in particle order (positions given by the
+// inclusive scan of c), and the R = N - sum c remaining positions i = 0..R-1 take multinomial
+// draws on the residuals r_n = (N q_n mod Q) >> 12 by the integer CDF (u_i as in
+// resample_kernel). N q_n <= 2^52 and sum r < 2^52: all exact. Every block of the group builds
+// the same tables and fills its slice of the N positions. Sets *flag when Q is zero.
+__global__ void __launch_bounds__(kResThreads)
+resample_residual_kernel(const unsigned long long* __restrict__ qv, int N, const double* __restrict__ u_given,
+                         uint64_t seed, uint64_t step, int* __restrict__ idx, int* __restrict__ flag) {
+  extern __shared__ unsigned long long rs[];
+  unsigned long long* cr = rs;                // [N] inclusive scan of residuals
+  unsigned long long* cc = rs + kMaxN;        // [N] inclusive scan of copies
+  unsigned long long* part = rs + 2 * kMaxN;  // [threads]
+  __shared__ unsigned long long Qs;
+  const int j = blockIdx.x;
+  const unsigned long long* q = qv + static_cast<int64_t>(j) * N;
+  const int per = (N + blockDim.x - 1) / blockDim.x;
+  const int n0 = threadIdx.x * per;
+  // Q
+  unsigned long long run = 0;
+  for (int k = 0; k < per; ++k)
+    if (n0 + k < N) run += q[n0 + k];
+  part[threadIdx.x] = run;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x); ++w) t += part[w];
+    Qs = t;
+  }
+  __syncthreads();
+  const unsigned long long Q = Qs;
+  if (Q == 0ull) {
+    if (threadIdx.x == 0) atomicOr(flag, 1);
+    return;
+  }
+  const unsigned long long NN = static_cast<unsigned long long>(N);
+  // per-thread runs of copies and residuals, then block scans of both
+  unsigned long long rc = 0, rr = 0;
+  for (int k = 0; k < per; ++k) {
+    const int n = n0 + k;
+    if (n < N) {
+      const unsigned long long a = NN * q[n];
+      rc += a / Q;
+      rr += (a % Q) >> kResidualShift;
+      cc[n] = rc;
+      cr[n] = rr;
+    }
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    part[threadIdx.x] = (pass == 0) ? rc : rr;
+    __syncthreads();
+    for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {
+      const unsigned long long v = (threadIdx.x >= static_cast<unsigned>(o)) ? part[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    const unsigned long long off = (threadIdx.x > 0) ? part[threadIdx.x - 1] : 0ull;
+    unsigned long long* c = (pass == 0) ? cc : cr;
+    for (int k = 0; k < per; ++k)
+      if (n0 + k < N) c[n0 + k] += off;
+    __syncthreads();
+  }
+  const int copies = static_cast<int>(cc[N - 1]);
+  const unsigned long long S = cr[N - 1];
+  if (copies < N && S == 0ull) {   // only with weights not scaled to a maximum of 1
+    if (threadIdx.x == 0) atomicOr(flag, 1);
+    return;
+  }
+  const int slice = (N + gridDim.y - 1) / gridDim.y;
+  const int i_hi = min(N, static_cast<int>(blockIdx.y + 1) * slice);
+  for (int pos = blockIdx.y * slice + threadIdx.x; pos < i_hi; pos += blockDim.x) {
+    const unsigned long long* cdf;
+    unsigned long long tau;
+    if (pos < copies) {
+      cdf = cc;
+      tau = static_cast<unsigned long long>(pos);
+    } else {
+      const int i = pos - copies;
+      double u;
+      if (u_given) {
+        u = u_given[static_cast<int64_t>(j) * N + i];
+      } else {
+        const uint4 r = draw(seed, static_cast<uint32_t>(j * N + i), kStreamResample, step);
+        u = uniform53(r.x, r.y);
+      }
+      cdf = cr;
+      tau = static_cast<unsigned long long>(floor(__dmul_rn(u, static_cast<double>(S))));
+      if (tau > S - 1) tau = S - 1;
+    }
+    int lo = 0, hi = N - 1;   // first n with cdf[n] > tau
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cdf[mid] > tau) hi = mid;
+      else lo = mid + 1;
+    }
+    idx[static_cast<int64_t>(j) * N + pos] = lo;
+  }
+}
+
+constexpr size_t kResidualSmem = sizeof(unsigned long long) * (2 * kMaxN + kResThreads);
+
+// Launch the scan/search kernel of a resampling scheme on quantised weights q [J*N].
+sps_status launch_resample(sps_ctx* ctx, int scheme, const unsigned long long* q, int J, int N, const double* u,
+                           uint64_t seed, uint64_t step, int* idx, int* flag) {
+  if (scheme == SPS_RESAMPLE_RESIDUAL) {
+    SPS_CUDA_TRY(cudaFuncSetAttribute(resample_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kResidualSmem)));
+    resample_residual_kernel<<<dim3(J, kResBlocks), kResThreads, kResidualSmem, ctx->stream>>>(q, N, u, seed, step,
+                                                                                                idx, flag);
+  } else if (scheme == SPS_RESAMPLE_MULTINOMIAL) {
+    resample_kernel<<<dim3(J, kResBlocks), kResThreads, 0, ctx->stream>>>(q, N, u, seed, step, idx, flag);
+  } else {
+    return fail(ctx, SPS_ERR_INVALID_ARG, "unknown resampling scheme");
+  }
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
 }
 
 // dst[p] = src[group(p) * N + idx[p]] for theta rows and the per-particle scalars. A block of
@@ -1291,7 +1436,7 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
 // marginal-likelihood increments and the cached log-likelihood at the new t. One synchronisation
 // per block, plus one to return the increments when lme_out is given.
 sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new, double* ess_out,
-                       double* lme_out) {
+                       double* lme_out, double* lpl_out) {
   const int64_t n = ctx->n, P = st->P;
   if (st->t >= n) return fail(ctx, SPS_ERR_STATE, "C phase: no observations left");
   if (t_target > 0 && (t_target <= st->t || t_target > n)) return fail(ctx, SPS_ERR_INVALID_ARG, "C phase: bad t_target");
@@ -1301,10 +1446,12 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
   SPS_CUDA_TRY(st->lwstate.reserve(sizeof(float2) * P));
   SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * std::max<int64_t>(max_rows, st->J)));
   SPS_CUDA_TRY(st->gmax.reserve(sizeof(double) * st->J));
+  if (lpl_out) SPS_CUDA_TRY(st->lpl_dev.reserve(sizeof(double) * max_rows * st->J));
   SPS_CUDA_TRY(cudaMemsetAsync(st->lwstate.ptr, 0, sizeof(float2) * P, ctx->stream));
   float2* rows = st->lwbuf.as<float2>();
   int64_t s = st->t;
   std::vector<double> ess(max_rows);
+  std::vector<double> lme_rows, lme_prev(st->J, 0.0);   // log mean of the weights before s
   int64_t found = -1;
   double ess_found = 0.0;
   while (s < n) {
@@ -1314,6 +1461,13 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
         rows, P, st->scratch.as<double>()); ++ctx->launches;
     ess_merge_kernel<<<static_cast<unsigned>((b + 63) / 64), 64, 0, ctx->stream>>>(
         st->scratch.as<double>(), static_cast<int>(b), kEssParts, st->ess_buf.as<double>()); ++ctx->launches;
+    if (lpl_out) {
+      row_group_lme_kernel<<<dim3(static_cast<unsigned>(b), st->J), 256, 0, ctx->stream>>>(
+          rows, P, st->N, st->lpl_dev.as<double>()); ++ctx->launches;
+      lme_rows.resize(static_cast<size_t>(b) * st->J);
+      SPS_CUDA_TRY(cudaMemcpyAsync(lme_rows.data(), st->lpl_dev.ptr, sizeof(double) * b * st->J,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    }
     SPS_CUDA_TRY(cudaGetLastError());
     SPS_CUDA_TRY(cudaMemcpyAsync(ess.data(), st->ess_buf.ptr, sizeof(double) * b, cudaMemcpyDeviceToHost, ctx->stream));
     SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -1321,6 +1475,15 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
       const int64_t sj = s + j + 1;
       const bool stop = (t_target > 0) ? (sj == t_target)
                                        : (ess[j] / static_cast<double>(P) < ctx->opt.ess_fraction || sj == n);
+      if (lpl_out) {
+        // log predictive likelihood of observation sj per group (row j of this block)
+        double* o = lpl_out + (sj - 1 - st->t) * st->J;
+        for (int g = 0; g < st->J; ++g) {
+          const double cur = lme_rows[static_cast<size_t>(j) * st->J + g];
+          o[g] = cur - lme_prev[g];
+          lme_prev[g] = cur;
+        }
+      }
       if (stop) {
         found = j;
         ess_found = ess[j];
@@ -1370,8 +1533,8 @@ sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_id
   unsigned long long* q = st->lwbuf.as<unsigned long long>();
   resample_q_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
       st->logw.as<double>(), 0, st->N, st->P, st->gmax.as<double>(), q); ++ctx->launches;
-  resample_kernel<<<dim3(st->J, kResBlocks), kResThreads, 0, ctx->stream>>>(q, st->N, d_u, st->seed, step,
-                                                                            st->idx.as<int>(), flag_ptr(st, 2)); ++ctx->launches;
+  SPS_TRY(launch_resample(ctx, ctx->opt.resampling, q, st->J, st->N, d_u, st->seed, step, st->idx.as<int>(),
+                          flag_ptr(st, 2)));
   gather_kernel<<<static_cast<unsigned>((st->P + 256 / ctx->D - 1) / (256 / ctx->D)), 256, 0, ctx->stream>>>(
       st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->idx.as<int>(), st->P, st->N, ctx->D,
       st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>()); ++ctx->launches;
@@ -1508,9 +1671,9 @@ sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const
 }
 
 sps_status sps_cphase(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new, double* ess,
-                      double* logml_inc) {
+                      double* logml_inc, double* log_pred) {
   SPS_TRY(check_state(ctx, st));
-  return cphase_impl(ctx, st, t_target, t_new, ess, logml_inc);
+  return cphase_impl(ctx, st, t_target, t_new, ess, logml_inc, log_pred);
 }
 
 sps_status sps_sphase(sps_ctx* ctx, sps_state* st, const double* uniforms, int32_t* idx_out, int32_t mem) {
@@ -1562,11 +1725,15 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
   const bool replay = schedule && schedule->n_cycles > 0;
   int32_t L = 0;
   int64_t total_steps = 0;
+  const bool want_lpl = out->log_pred || out->log_pred_nse;
+  std::vector<double> lpl(want_lpl ? static_cast<size_t>(ctx->n) * groups : 0);
   while (st->t < ctx->n) {
     if (replay && L >= schedule->n_cycles) return fail(ctx, SPS_ERR_INVALID_ARG, "schedule ends before T");
     const int64_t target = replay ? schedule->t[L] : 0;
     int64_t tn = 0;
-    SPS_TRY(cphase_impl(ctx, st, target, &tn, nullptr, nullptr));
+    const int64_t t_before = st->t;
+    SPS_TRY(cphase_impl(ctx, st, target, &tn, nullptr, nullptr,
+                        want_lpl ? lpl.data() + t_before * groups : nullptr));
     SPS_TRY(sphase_impl(ctx, st, nullptr, nullptr));
     int steps = 0;
     double acc = 0.0, rne = 0.0;
@@ -1627,14 +1794,25 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
   out->log_ml_pooled = mx + std::log(se / st->J);
   out->n_cycles = L;
   out->m_steps = total_steps;
+  if (want_lpl)
+    for (int64_t q = 0; q < ctx->n; ++q) {
+      const double* row = lpl.data() + q * groups;
+      double m = 0.0;
+      for (int j = 0; j < groups; ++j) m += row[j];
+      m /= groups;
+      double v = 0.0;
+      for (int j = 0; j < groups; ++j) v += (row[j] - m) * (row[j] - m);
+      if (out->log_pred) out->log_pred[q] = m;
+      if (out->log_pred_nse) out->log_pred_nse[q] = std::sqrt(v / (groups - 1.0)) / std::sqrt(static_cast<double>(groups));
+    }
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return SPS_OK;
 }
 
 // ------------------------------------------------------------------------------ building blocks
 
-sps_status sps_resample(sps_ctx* ctx, const double* w, const double* u, int32_t J, int32_t N, int32_t* idx,
-                        int32_t mem) {
+sps_status sps_resample(sps_ctx* ctx, const double* w, const double* u, int32_t J, int32_t N, int32_t scheme,
+                        int32_t* idx, int32_t mem) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
   if (!w || !u || !idx || J < 1 || N < 1 || N > kMaxN) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_resample: bad arguments");
   const size_t P = static_cast<size_t>(J) * N;
@@ -1658,9 +1836,7 @@ sps_status sps_resample(sps_ctx* ctx, const double* w, const double* u, int32_t 
   SPS_CUDA_TRY(dq.reserve(P * sizeof(unsigned long long)));
   resample_q_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
       pw, 1, N, static_cast<int64_t>(P), nullptr, dq.as<unsigned long long>()); ++ctx->launches;
-  resample_kernel<<<dim3(J, kResBlocks), kResThreads, 0, ctx->stream>>>(dq.as<unsigned long long>(), N, pu, 0, 0, pi,
-                                                                        df.as<int>()); ++ctx->launches;
-  SPS_CUDA_TRY(cudaGetLastError());
+  SPS_TRY(launch_resample(ctx, scheme, dq.as<unsigned long long>(), J, N, pu, 0, 0, pi, df.as<int>()));
   if (mem == SPS_MEM_HOST) {
     int bad = 0;
     SPS_CUDA_TRY(cudaMemcpyAsync(idx, di.ptr, P * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

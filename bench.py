@@ -242,7 +242,7 @@ def run_ours(args, world, rank, local):
             flush.zero_()
         st.cphase(st.get_t() + C_BLOCK)
         st.sphase()
-        st.mstep()
+        st.mstep(kernel=args.mkernel)
     torch.cuda.synchronize()
     counters(reset=1)
     lib.sps_set_timing(s.ctx, 1)
@@ -261,7 +261,7 @@ def run_ours(args, world, rank, local):
             a.record(stream)
             t_new, _, _ = st.cphase(st.get_t() + C_BLOCK)
             st.sphase()
-            st.mstep()
+            st.mstep(kernel=args.mkernel)
             b.record(stream)
             b.synchronize()
             ev_ms.append(a.elapsed_time(b))
@@ -317,7 +317,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": "c2 binary logit n=20000 k=30 (intercept, 19 AR(1) N(0,1), 10 Bernoulli(0.3)), "
                                "16 groups x 4096 particles, one SPS cycle per step (C phase 64 obs, S phase, M step)",
                    "global_batch": P * world, "seq_len": n, "parallelism": f"replicas{world}",
-                   "precision": args.precision, "l2": "flushed between steps (512 MB write)"},
+                   "precision": args.precision, "mkernel": args.mkernel,
+                   "l2": "flushed between steps (512 MB write)"},
         "wall_s": wall,
         "gpu_launches": launches,
         "clocks": clock,
@@ -387,6 +388,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split", choices=["split", "fp32"])
+    ap.add_argument("--mkernel", default="rw", choices=["rw", "mala"],
+                    help="M kernel of the timed step (MALA evaluates through the gradient kernel)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sps", action="store_true", help="skip the whole-simulator wall-time runs")
     ap.add_argument("--traffic", type=float, default=None,

@@ -340,6 +340,134 @@ grad_fp32_kernel(const double* __restrict__ theta, int64_t P, int k, int NC, con
   }
 }
 
+// Register-resident gradient for small models (k <= KMAX, NC = C - 1 fixed): each thread keeps
+// its particle's theta and its FP32 gradient sums over a 128-observation tile in registers; the
+// tile sums go to FP64 accumulators in shared memory once per tile (FP64 work per observation
+// D / 128). X rows are staged in shared memory padded with zeros to KMAX (broadcast float4).
+// Same outputs as grad_fp32_kernel: per chunk FP64 log-likelihood and gradient partials.
+constexpr int kGR = 128;   // particles per block
+constexpr int kGT = 128;   // observations per tile
+
+template <int KMAX, int NC>
+__global__ void __launch_bounds__(kGR)
+grad_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const float* __restrict__ X,
+                const int* __restrict__ y, int64_t t, int64_t chunk, double* __restrict__ llp,
+                double* __restrict__ gp) {
+  __shared__ __align__(16) float xs[kGT][KMAX];
+  __shared__ int ys[kGT];
+  extern __shared__ double g64[];   // [D][kGR]
+  const int D = k * NC;
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kGR;
+  const int64_t p = p0 + threadIdx.x;
+  const int64_t s_lo = static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t s_hi = (s_lo + chunk < t) ? s_lo + chunk : t;
+  float th[NC][KMAX];
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) th[c][i] = (p < P && i < k) ? f64_to_f32(theta[p * D + c * k + i]) : 0.f;
+  for (int d = 0; d < D; ++d) g64[d * kGR + threadIdx.x] = 0.0;
+  double acc = 0.0;
+  for (int64_t s0 = s_lo; s0 < s_hi; s0 += kGT) {
+    const int ns = static_cast<int>(s_hi - s0 < kGT ? s_hi - s0 : kGT);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kGT * KMAX; idx += blockDim.x) {
+      const int j = idx / KMAX, i = idx - j * KMAX;
+      xs[j][i] = (j < ns && i < k) ? X[(s0 + j) * k + i] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < ns; idx += blockDim.x) ys[idx] = y[s0 + idx];
+    __syncthreads();
+    float gt[NC][KMAX];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i) gt[c][i] = 0.f;
+    float tile = 0.f;
+    for (int j = 0; j < ns; ++j) {
+      float eta[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) eta[c] = 0.f;
+#pragma unroll
+      for (int i = 0; i < KMAX; i += 4) {
+        const float4 xv = *reinterpret_cast<const float4*>(&xs[j][i]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          eta[c] = fmaf(th[c][i], xv.x, eta[c]);
+          eta[c] = fmaf(th[c][i + 1], xv.y, eta[c]);
+          eta[c] = fmaf(th[c][i + 2], xv.z, eta[c]);
+          eta[c] = fmaf(th[c][i + 3], xv.w, eta[c]);
+        }
+      }
+      float m = 0.f;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) m = fmaxf(m, eta[c]);
+      float pr[NC];
+      float z = expf(-m);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        pr[c] = expf(eta[c] - m);
+        z += pr[c];
+      }
+      const float inv = 1.f / z;
+      const int yo = ys[j];
+      float obs = 0.f;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) obs = (yo == c + 1) ? eta[c] : obs;
+      tile += obs - (m + logf(z));
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float r = ((yo == c + 1) ? 1.f : 0.f) - pr[c] * inv;
+#pragma unroll
+        for (int i = 0; i < KMAX; i += 4) {
+          const float4 xv = *reinterpret_cast<const float4*>(&xs[j][i]);
+          gt[c][i] = fmaf(r, xv.x, gt[c][i]);
+          gt[c][i + 1] = fmaf(r, xv.y, gt[c][i + 1]);
+          gt[c][i + 2] = fmaf(r, xv.z, gt[c][i + 2]);
+          gt[c][i + 3] = fmaf(r, xv.w, gt[c][i + 3]);
+        }
+      }
+    }
+    acc += f32_to_f64(tile);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i)
+        if (i < k) g64[(c * k + i) * kGR + threadIdx.x] += f32_to_f64(gt[c][i]);
+  }
+  if (p < P) llp[static_cast<int64_t>(blockIdx.y) * P + p] = acc;
+  __syncthreads();
+  // gradient partials of the block's particles, written element by element (coalesced)
+  const int np = static_cast<int>(P - p0 < kGR ? P - p0 : kGR);
+  double* go = gp + (static_cast<int64_t>(blockIdx.y) * P + p0) * D;
+  for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
+    const int pp = q / D, d = q - pp * D;
+    go[q] = g64[d * kGR + pp];
+  }
+}
+
+bool launch_grad_reg(sps_ctx* ctx, dim3 grid, const double* theta, int64_t P, int64_t t, int64_t chunk,
+                     double* llp, double* gp) {
+  const int k = ctx->k, NC = ctx->NC;
+  const size_t smem = sizeof(double) * static_cast<size_t>(k) * NC * kGR;
+#define SPS_GRAD_CASE(KM, NCM)                                                                              \
+  if (NC == NCM && k <= KM) {                                                                               \
+    cudaFuncSetAttribute(grad_reg_kernel<KM, NCM>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                         static_cast<int>(smem));                                                            \
+    grad_reg_kernel<KM, NCM><<<grid, kGR, smem, ctx->stream>>>(theta, P, k, ctx->Xf.as<float>(),            \
+                                                               ctx->y.as<int>(), t, chunk, llp, gp);        \
+    ++ctx->launches;                                                                                        \
+    return true;                                                                                            \
+  }
+  SPS_GRAD_CASE(8, 1)
+  SPS_GRAD_CASE(32, 1)
+  SPS_GRAD_CASE(64, 1)
+  SPS_GRAD_CASE(8, 2)
+  SPS_GRAD_CASE(32, 2)
+  SPS_GRAD_CASE(8, 3)
+#undef SPS_GRAD_CASE
+  return false;
+}
+
 __global__ void grad_sum_kernel(const double* __restrict__ llp, const double* __restrict__ gp, int64_t P, int D,
                                 int slices, double* __restrict__ ll, double* __restrict__ grad) {
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -362,6 +490,30 @@ sps_status loglik_grad_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int6
                             double* d_grad) {
   const int D = ctx->D, k = ctx->k;
   if (ctx->NC > kMaxNC) return fail(ctx, SPS_ERR_UNSUPPORTED, "gradient: at most 16 outcomes");
+  {
+    // register-resident kernel when the model fits one of its instantiations
+    const int64_t ptiles = (P + kGR - 1) / kGR;
+    int64_t chunks = 1;
+    if (t > 0) {
+      const int64_t want = 4LL * ctx->num_sms;
+      const int64_t cap = std::max<int64_t>(1, (int64_t{1} << 26) / (P * (D + 1)));
+      chunks = std::max<int64_t>(1, std::min<int64_t>({(want + ptiles - 1) / ptiles, (t + kGT - 1) / kGT, cap}));
+    }
+    int64_t chunk = std::max<int64_t>(kGT, ((t + chunks - 1) / chunks + kGT - 1) / kGT * kGT);
+    chunks = std::max<int64_t>(1, (t + chunk - 1) / chunk);
+    SPS_CUDA_TRY(ctx->ll.partial.reserve(sizeof(double) * chunks * P));
+    SPS_CUDA_TRY(ctx->ll.aux.reserve(sizeof(double) * chunks * P * D));
+    const dim3 grid(static_cast<unsigned>(ptiles), static_cast<unsigned>(chunks));
+    if (launch_grad_reg(ctx, grid, d_theta, P, t, chunk, ctx->ll.partial.as<double>(), ctx->ll.aux.as<double>())) {
+      SPS_CUDA_TRY(cudaGetLastError());
+      const int64_t tot = P * (D + 1);
+      grad_sum_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, ctx->stream>>>(
+          ctx->ll.partial.as<double>(), ctx->ll.aux.as<double>(), P, D, t > 0 ? static_cast<int>(chunks) : 0, d_ll,
+          d_grad); ++ctx->launches;
+      SPS_CUDA_TRY(cudaGetLastError());
+      return SPS_OK;
+    }
+  }
   const size_t smem = sizeof(double) * D * kGP + sizeof(float) * (2 * static_cast<size_t>(D) * kGP + kTS * k) +
                       sizeof(int) * kTS;
   if (smem > 220 * 1024) return fail(ctx, SPS_ERR_UNSUPPORTED, "gradient: k*(C-1) too large");

@@ -119,3 +119,22 @@ def test_gprior_and_normalised_prior_match_oracle(cuda):
     m_o, c_o = OS.normalise_prior(mu, Sig)
     np.testing.assert_allclose(m, m_o, rtol=0, atol=0)
     np.testing.assert_allclose(c, c_o, rtol=0, atol=0)
+
+
+def test_autograd_function_backward_is_the_gradient_kernel(cuda):
+    torch = cuda
+    from oracle import logit as OL
+    from paper_1304_4333_b300.autograd import loglik
+    X, y = _small(n=600, k=6, C=3, seed=12)
+    s = _ctx(X, y, 3)
+    g = _gen(13)
+    th = torch.tensor(0.3 * g.standard_normal((90, 12)), device="cuda", requires_grad=True)
+    wts = torch.tensor(g.standard_normal(90), device="cuda")
+    ll = loglik(th, s, 550, "fp32")
+    (wts * ll).sum().backward()
+    _, G = s.loglik_grad(th.detach(), 550)
+    torch.testing.assert_close(th.grad, wts[:, None] * G, rtol=0, atol=0)
+    ll_o, G_o = OL.loglik_grad(X, y, th.detach().cpu().numpy(), 3, 550)
+    np.testing.assert_allclose(ll.detach().cpu().numpy(), ll_o, rtol=1e-6)
+    ref = wts.cpu().numpy()[:, None] * G_o
+    assert np.max(np.abs(th.grad.cpu().numpy() - ref)) / np.max(np.abs(ref)) < 1e-5

@@ -155,3 +155,23 @@ def test_cluster_pairs_match_single_ctas_bitwise(torch_cuda, C, k, exact, monkey
         np.testing.assert_array_equal(a, b)
         ref = oracle_loglik(X, y, theta, C, t)
         assert np.all(np.abs(a - ref) <= _tol(X, theta, C, t, ref, "split"))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+def test_c4_large_binary_sampled(torch_cuda, prec):
+    # the large workload: n = 1e6, k = 100 (three K blocks of operand rows), P = 65536
+    w = synthetic.make_c4()
+    theta = synthetic.particles_around(w.theta_true, w.P, 0.02, seed=3)
+    s = _sps(w.X, w.y, w.C)
+    got = s.loglik(theta, w.n, prec)
+    idx = np.random.Generator(np.random.PCG64(10)).choice(w.P, 16, replace=False)
+    idx = np.concatenate([idx, [0, w.P - 1]])
+    ref = oracle_loglik(w.X, w.y, theta[idx], w.C, w.n)
+    rtol = 1e-5 if prec == "split" else 1e-6
+    np.testing.assert_allclose(got[idx], ref, rtol=rtol)
+    # a ragged prefix
+    t = 777_777
+    got_t = s.loglik(theta[:300], t, prec)
+    ref_t = oracle_loglik(w.X, w.y, theta[[0, 299]], w.C, t)
+    np.testing.assert_allclose(got_t[[0, 299]], ref_t, rtol=rtol)

@@ -233,6 +233,18 @@ sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, d
  * errors as sps_loglik. */
 sps_status sps_loglik_noalloc(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll);
 
+/* Log-likelihoods of M nested models in one fused-kernel launch (split precision): model m uses
+ * the first k_models[m] covariates of the context's X (1 <= k_m <= k) with D_m = k_m (C-1)
+ * parameters, P_models[m] particles and the prefix t_models[m] (0 <= t_m <= n); its particles
+ * are evaluated as zero-padded rows of the context's operand layout, so the results equal
+ * sps_loglik on a context built from X[:, :k_m] (within the split tolerance).
+ *   theta: device FP64, the models' [P_m x D_m] class-major blocks concatenated in model order;
+ *   ll: device FP64 [sum P_m]; k_models, P_models, t_models: host [M], 1 <= M <= 1024.
+ * Work is enqueued on the context's stream. The paper runs one model at a time; batching the
+ * candidate models of a marginal-likelihood comparison into one launch fills the GPU. */
+sps_status sps_loglik_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, const int64_t* P_models,
+                              const int64_t* t_models, const double* theta, double* ll);
+
 /* Log-likelihood and its gradient d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s
  * (the derivative of Eq. 1; the paper prints no gradient).
  *   grad: [P x D] FP64 output, class-major like theta (mem). FP32 products and residuals,

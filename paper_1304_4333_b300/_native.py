@@ -82,6 +82,7 @@ SIGNATURES = {
                           C.POINTER(SpsResult)]),
     "sps_resample": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32]),
     "sps_set_prior": (C.c_int, [_P, C.POINTER(SpsPrior)]),
+    "sps_loglik_batched": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
     "sps_gprior": (C.c_int, [_P, C.c_double, _P, _P]),
     "sps_prior_normalize": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P]),
     "sps_philox": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,

@@ -198,6 +198,21 @@ class Sps:
         self._call("sps_loglik", C.c_void_p(theta_ptr), int(P), t, C.c_void_p(ll_ptr), PRECISIONS[precision],
                    N.MEM_HOST)
 
+    def loglik_batched(self, thetas, ks, ts):
+        """Log-likelihoods of nested models in one launch (sps_loglik_batched): thetas is a list of
+        CUDA float64 tensors [P_m, k_m (C-1)], ks the covariate counts, ts the prefixes. Returns a
+        list of CUDA tensors [P_m]."""
+        torch = _torch()
+        M = len(thetas)
+        flat = torch.cat([t.contiguous().to(torch.float64).reshape(-1) for t in thetas])
+        P = np.array([int(t.shape[0]) for t in thetas], dtype=np.int64)
+        km = np.array([int(k) for k in ks], dtype=np.int32)
+        tm = np.array([int(t) for t in ts], dtype=np.int64)
+        out = torch.empty(int(P.sum()), dtype=torch.float64, device=flat.device)
+        self._sync_stream()
+        self._call("sps_loglik_batched", M, _ptr(km), _ptr(P), _ptr(tm), _ptr(flat), _ptr(out))
+        return list(torch.split(out, P.tolist()))
+
     def loglik_grad(self, theta, t: Optional[int] = None):
         t = self.n if t is None else int(t)
         if _is_device(theta):

@@ -333,6 +333,17 @@ sps_status sps_get_dims(const sps_ctx* ctx, int64_t* n, int32_t* k, int32_t* C, 
   return SPS_OK;
 }
 
+sps_status sps_loglik_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, const int64_t* P_models,
+                              const int64_t* t_models, const double* theta, double* ll) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (M < 1 || M > 1024 || !k_models || !P_models || !t_models || !theta || !ll)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik_batched: bad arguments");
+  for (int m = 0; m < M; ++m)
+    if (k_models[m] < 1 || k_models[m] > ctx->k || P_models[m] < 1 || t_models[m] < 0 || t_models[m] > ctx->n)
+      return fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik_batched: bad model sizes");
+  return loglik_split_batched(ctx, M, k_models, P_models, t_models, theta, ll);
+}
+
 sps_status sps_set_prior(sps_ctx* ctx, const sps_prior* prior) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
   return apply_prior(ctx, prior);

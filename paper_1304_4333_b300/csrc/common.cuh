@@ -72,6 +72,9 @@ struct LoglikScratch {
   DevBuf partial;             // FP64 partial sums [slices x Ppad]
   DevBuf flag;                // int error/timeout flag
   DevBuf theta_in, ll_out, grad_out, aux;   // staging for host-memory calls
+  DevBuf batch_tab;           // int64 [M x 6] model table of a batched call
+  DevBuf batch_ptile_t;       // int2 [n_ptiles] prefix length and K-slice mask of each particle tile
+  DevBuf batch_lin;           // FP64 [M x NC x k] linear terms of the models
 };
 
 }  // namespace sps
@@ -164,6 +167,9 @@ sps_status make_map_bf16(sps_ctx* ctx, CUtensorMap* map, const void* base, uint6
 
 // Likelihood launchers (loglik_tc.cu, loglik_simt.cu). Device pointers, context stream.
 sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
+// Batched nested models (see sps_loglik_batched): one fused-kernel launch for all of them.
+sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
+                                const double* d_theta, double* d_ll);
 sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
 sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                            int precision);

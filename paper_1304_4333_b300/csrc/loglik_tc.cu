@@ -88,7 +88,21 @@ struct TcParams {
   double* partial;     // [n_chunks][nwg][ppad]
   int* flag;           // set to 1 on a timeout
   unsigned long long timeout_ns;
+  // batched models: per particle tile {prefix length, K-slice mask}, or null. Mask bits 0-15: the
+  // 16-wide slices of the Xh / Th / Tl blocks that hold any of the model's columns; bits 16-23:
+  // the number of Xl slices it needs (its continuous columns are a prefix of the Xl block).
+  const int2* ptile_info;
 };
+
+// Observation tiles [tile_lo, result) of a work item: its chunk cut at the prefix length of its
+// particle tile (an empty range when the chunk starts beyond it).
+template <int BN, bool BATCH>
+__device__ __forceinline__ int item_tile_hi(const TcParams& prm, int tile_lo, int ptile) {
+  if constexpr (BATCH)
+    return max(tile_lo, min(tile_lo + prm.chunk_tiles, (prm.ptile_info[ptile].x + BN - 1) / BN));
+  else
+    return min(tile_lo + prm.chunk_tiles, prm.n_tiles);
+}
 
 struct SmemLayout {
   uint32_t th_bytes;   // one theta buffer (all classes)
@@ -137,7 +151,9 @@ __device__ __forceinline__ uint64_t kslice_desc(uint32_t base, int rows, int e) 
          static_cast<uint64_t>(((e & 63) * 2) >> 4);
 }
 
-template <int NC, int BN, int CL>
+// BATCH: particle tiles of several nested models (per-tile prefix and K slices in ptile_info);
+// a separate instance so that the single-model issue loop stays minimal.
+template <int NC, int BN, int CL, bool BATCH>
 __global__ void __launch_bounds__(threads_for(NC), 1)
 loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                  const TcParams prm) {
@@ -220,7 +236,8 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int chunk = item / prm.n_pgroups;
         const int ptile = (item - chunk * prm.n_pgroups) * CL + rank;
         const int tile_lo = chunk * prm.chunk_tiles;
-        const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
+        const int tile_hi = item_tile_hi<BN, BATCH>(prm, tile_lo, ptile);
+        if (BATCH && tile_hi == tile_lo) continue;   // nothing of this item lies inside its prefix
         if (!ptx::mbar_wait_bounded(&th_empty[tb], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
         uint8_t* thb = smem + L.off_th + tb * L.th_bytes;
         ptx::mbar_arrive_expect_tx(&th_full[tb], L.th_bytes);
@@ -278,8 +295,14 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       bool issued_any = false;
       for (int item = cluster_id; ok && item < prm.n_items; item += n_clusters) {
         const int chunk = item / prm.n_pgroups;
+        const int ptile = (item - chunk * prm.n_pgroups) * CL + rank;
         const int tile_lo = chunk * prm.chunk_tiles;
-        const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
+        const int tile_hi = item_tile_hi<BN, BATCH>(prm, tile_lo, ptile);
+        if (BATCH && tile_hi == tile_lo) continue;
+        // K slices of this item's model (batched models)
+        const uint32_t kinfo = BATCH ? static_cast<uint32_t>(prm.ptile_info[ptile].y) : 0u;
+        const uint32_t hmask = kinfo & 0xFFFFu;
+        const int ksl_item = static_cast<int>(kinfo >> 16);
         if (!ptx::mbar_wait_bounded(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t thb = ptx::smem_u32(smem + L.off_th + tb * L.th_bytes);
@@ -294,12 +317,28 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           for (int c = 0; c < NC; ++c) {
             const uint32_t d = tmem_base + static_cast<uint32_t>((buf * NC + c) * BN);
             const uint32_t tc = thb + static_cast<uint32_t>(c * prm.kbt) * kTileA;
-            for (int i = 0; i < prm.ksh; ++i)   // Th_c Xh'
-              ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, 16 * i), idesc, i > 0);
-            for (int i = 0; i < prm.ksh; ++i)   // Tl_c Xh'
-              ptx::mma_bf16(d, kslice_desc(tc, kBM, prm.k16 + 16 * i), kslice_desc(xb, BN, 16 * i), idesc, 1);
-            for (int i = 0; i < prm.ksl; ++i)   // Th_c Xl' over the continuous columns
-              ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, prm.k16 + 16 * i), idesc, 1);
+            if constexpr (!BATCH) {
+              // one model: every K slice (the issuing thread's loop is kept minimal)
+              for (int i = 0; i < prm.ksh; ++i)   // Th_c Xh'
+                ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, 16 * i), idesc, i > 0);
+              for (int i = 0; i < prm.ksh; ++i)   // Tl_c Xh'
+                ptx::mma_bf16(d, kslice_desc(tc, kBM, prm.k16 + 16 * i), kslice_desc(xb, BN, 16 * i), idesc, 1);
+              for (int i = 0; i < prm.ksl; ++i)   // Th_c Xl' over the continuous columns
+                ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, prm.k16 + 16 * i), idesc, 1);
+            } else {
+              // batched models: only the slices holding the item's model's columns
+              uint32_t acc = 0;                   // the first MMA of a tile overwrites the accumulator
+              for (int i = 0; i < prm.ksh; ++i)
+                if ((hmask >> i) & 1u) {
+                  ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, 16 * i), idesc, acc);
+                  acc = 1;
+                }
+              for (int i = 0; i < prm.ksh; ++i)
+                if ((hmask >> i) & 1u)
+                  ptx::mma_bf16(d, kslice_desc(tc, kBM, prm.k16 + 16 * i), kslice_desc(xb, BN, 16 * i), idesc, 1);
+              for (int i = 0; i < ksl_item; ++i)
+                ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, prm.k16 + 16 * i), idesc, 1);
+            }
           }
           issued_any = true;
           if constexpr (CL > 1) ptx::mma_commit_multicast(&x_empty[st], kMask);
@@ -337,7 +376,9 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       const int chunk = item / prm.n_pgroups;
       const int ptile = (item - chunk * prm.n_pgroups) * CL + rank;
       const int tile_lo = chunk * prm.chunk_tiles;
-      const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
+      const int tile_hi = item_tile_hi<BN, BATCH>(prm, tile_lo, ptile);
+      int t_item = prm.t;
+      if constexpr (BATCH) t_item = prm.ptile_info[ptile].x;
       // FP32 sum of this item's tiles with Kahan compensation (converted to FP64 once per item)
       float ksum = 0.f, kcomp = 0.f;
       const int first = tile_lo + static_cast<int>((static_cast<uint32_t>(own) + STEP - acc_base % STEP) % STEP);
@@ -349,7 +390,7 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit));
         if (!ok) break;
         ptx::tc_fence_after();
-        const int valid = prm.t - tile * BN - col0;   // columns of this group inside [0, t)
+        const int valid = t_item - tile * BN - col0;   // columns of this group inside [0, t)
         const bool whole = valid >= COLS;
         const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN + col0);
         float tile_val;                               // this tile's non-linear sum in log2 units
@@ -502,6 +543,96 @@ loglik_finalize_kernel(const double* __restrict__ theta, int64_t P, int D,
   ll[p] = ((a0 + a1) + (a2 + a3)) - ((s0 + s1) + (s2 + s3));
 }
 
+// ---- batched models: M nested models, model m using the first k_m covariates, its particles in
+// its own block of operand rows (row_off_m, padded to the cluster's pair of tiles), zeros beyond
+// k_m. Model table rows (int64): [row_off, P, k, theta_off, particle_off, t].
+constexpr int kTab = 6;
+
+__device__ __forceinline__ int model_of_row(const int64_t* __restrict__ tab, int M, int64_t q) {
+  int m = 0;
+  while (m + 1 < M && tab[(m + 1) * kTab + 0] <= q) ++m;
+  return m;
+}
+__device__ __forceinline__ int model_of_particle(const int64_t* __restrict__ tab, int M, int64_t g) {
+  int m = 0;
+  while (m + 1 < M && tab[(m + 1) * kTab + 4] <= g) ++m;
+  return m;
+}
+
+__global__ void encode_theta_batched_kernel(const double* __restrict__ theta, const int64_t* __restrict__ tab,
+                                            int M, int NC, const int* __restrict__ perm, int k16, int kt,
+                                            int64_t PP, __nv_bfloat16* __restrict__ out) {
+  const int64_t r = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= NC * PP) return;
+  const int c = static_cast<int>(r / PP);
+  const int64_t q = r - c * PP;
+  const int m = model_of_row(tab, M, q);
+  const int64_t p = q - tab[m * kTab + 0];
+  const int64_t Pm = tab[m * kTab + 1];
+  const int km = static_cast<int>(tab[m * kTab + 2]);
+  const double* src = theta + tab[m * kTab + 3] + p * (static_cast<int64_t>(NC) * km) + c * km;
+  __nv_bfloat16* rowp = out + r * kt;
+  for (int j = lane; j < k16; j += 32) {
+    const int col = perm[j];
+    float v = 0.f;
+    if (p < Pm && col < km) v = f64_to_f32(src[col]) * 1.44269504f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    rowp[j] = h;
+    rowp[k16 + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+  for (int jj = 2 * k16 + lane; jj < kt; jj += 32) rowp[jj] = __float2bfloat16_rn(0.f);
+}
+
+// lin[m][c*k + i] = prefix[t_m / 128] + the tail rows [128 (t_m / 128), t_m), one warp per entry.
+__global__ void lin_tail_batched_kernel(const double* __restrict__ prefix, const double* __restrict__ X,
+                                        const int* __restrict__ y, int k, int NC, const int64_t* __restrict__ tab,
+                                        int M, double* __restrict__ lin) {
+  const int64_t w = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= static_cast<int64_t>(M) * NC * k) return;
+  const int m = static_cast<int>(w / (NC * k));
+  const int idx = static_cast<int>(w - static_cast<int64_t>(m) * NC * k);
+  const int c = idx / k, i = idx - c * k;
+  const int64_t t = tab[m * kTab + 5];
+  const int64_t tile = t / 128;
+  double a = 0.0;
+  for (int64_t s = tile * 128 + lane; s < t; s += 32) {
+    const int ys = y[s];
+    const double wgt = (NC == 1) ? (ys == 1 ? 0.5 : -0.5) : (ys == c + 1 ? 1.0 : 0.0);
+    a = fma(wgt, X[s * k + i], a);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) lin[w] = prefix[tile * NC * k + idx] + a;
+}
+
+__global__ void finalize_batched_kernel(const double* __restrict__ theta, const int64_t* __restrict__ tab, int M,
+                                        int NC, int k, int64_t Ptot, const double* __restrict__ lin,
+                                        const double* __restrict__ partial, int slices, int64_t PP,
+                                        double* __restrict__ ll) {
+  const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (g >= Ptot) return;
+  const int m = model_of_particle(tab, M, g);
+  const int64_t p = g - tab[m * kTab + 4];
+  const int km = static_cast<int>(tab[m * kTab + 2]);
+  const double* th = theta + tab[m * kTab + 3] + p * (static_cast<int64_t>(NC) * km);
+  const double* lm = lin + static_cast<int64_t>(m) * NC * k;
+  double a0 = 0.0, a1 = 0.0;
+  for (int c = 0; c < NC; ++c)
+    for (int i = 0; i < km; ++i) {
+      if (i & 1) a1 = fma(th[c * km + i], lm[c * k + i], a1);
+      else a0 = fma(th[c * km + i], lm[c * k + i], a0);
+    }
+  const double* q = partial + tab[m * kTab + 0] + p;
+  double s0 = 0.0, s1 = 0.0;
+  for (int j = 0; j < slices; ++j) {
+    if (j & 1) s1 += q[static_cast<size_t>(j) * PP];
+    else s0 += q[static_cast<size_t>(j) * PP];
+  }
+  ll[g] = (a0 + a1) - (s0 + s1);
+}
+
 sps_status launch_finalize(sps_ctx* ctx, const double* theta, int64_t P, const double* partial, int slices,
                            int ppad, double* ll) {
   loglik_finalize_kernel<<<static_cast<unsigned>((P + kFinThreads - 1) / kFinThreads), kFinThreads, 0,
@@ -552,10 +683,10 @@ cudaLaunchConfig_t launch_config(int grid, int NC, uint32_t smem_bytes, cudaStre
 }
 
 // Launch (launch = true) or query the co-resident clusters of one instance (launch = false).
-template <int NC, int BN, int CL>
+template <int NC, int BN, int CL, bool BATCH>
 sps_status run_tc(sps_ctx* ctx, const TcParams* prm, int grid, uint32_t smem_bytes, const CUtensorMap* mapT,
                   bool timed, int* max_clusters) {
-  auto kern = loglik_tc_kernel<NC, BN, CL>;
+  auto kern = loglik_tc_kernel<NC, BN, CL, BATCH>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem_bytes));
   if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
@@ -583,8 +714,11 @@ sps_status run_tc(sps_ctx* ctx, const TcParams* prm, int grid, uint32_t smem_byt
 template <int NC, int BN>
 sps_status run_cl(sps_ctx* ctx, int CL, const TcParams* prm, int grid, uint32_t smem_bytes, const CUtensorMap* mapT,
                   bool timed, int* max_clusters) {
-  return CL == 2 ? run_tc<NC, BN, 2>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters)
-                 : run_tc<NC, BN, 1>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  if (prm && prm->ptile_info)
+    return CL == 2 ? run_tc<NC, BN, 2, true>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters)
+                   : run_tc<NC, BN, 1, true>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  return CL == 2 ? run_tc<NC, BN, 2, false>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters)
+                 : run_tc<NC, BN, 1, false>(ctx, prm, grid, smem_bytes, mapT, timed, max_clusters);
 }
 
 sps_status run_any(sps_ctx* ctx, int CL, const TcParams* prm, int grid, uint32_t smem_bytes, const CUtensorMap* mapT,
@@ -714,6 +848,95 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
   if (prm.n_items > 0)
     SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));
   return launch_finalize(ctx, d_theta, P, prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad, d_ll);
+}
+
+sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
+                                const double* d_theta, double* d_ll) {
+  const int NC = ctx->NC;
+  if (NC > 3 || ctx->enc.bn == 0) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision: unsupported shape");
+  XEncoding& enc = ctx->enc;
+  LoglikScratch& S = ctx->ll;
+  const int64_t prow = static_cast<int64_t>(kBM) * enc.cl;
+  std::vector<int64_t> tab(static_cast<size_t>(M) * kTab);
+  int64_t PP = 0, Ptot = 0, thoff = 0, tmax = 0;
+  for (int m = 0; m < M; ++m) {
+    tab[m * kTab + 0] = PP;
+    tab[m * kTab + 1] = Pm[m];
+    tab[m * kTab + 2] = km[m];
+    tab[m * kTab + 3] = thoff;
+    tab[m * kTab + 4] = Ptot;
+    tab[m * kTab + 5] = tm[m];
+    PP += (Pm[m] + prow - 1) / prow * prow;
+    Ptot += Pm[m];
+    thoff += Pm[m] * NC * km[m];
+    tmax = std::max<int64_t>(tmax, tm[m]);
+  }
+  if (PP > (int64_t{1} << 28)) return fail(ctx, SPS_ERR_INVALID_ARG, "batched log-likelihood: too many particles");
+  // the work decomposition of one call over PP operand rows and the longest prefix; each
+  // particle tile then stops at its own model's prefix
+  TcParams prm;
+  uint32_t smem_bytes = 0;
+  if (!plan_call(ctx, PP, tmax, &prm, &smem_bytes))
+    return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
+  if (prm.ppad != PP) return fail(ctx, SPS_ERR_INVALID_ARG, "batched log-likelihood: internal padding mismatch");
+  // per particle tile: prefix length and the K slices of its model. Internal column j of the
+  // context's encoding holds original column perm[j]; a nested model's columns (original
+  // 0..k_m-1) are a prefix of the continuous block and a prefix of the exact block.
+  std::vector<int2> ptile_info(static_cast<size_t>(prm.n_ptiles));
+  for (int m = 0; m < M; ++m) {
+    uint32_t hmask = 0;
+    int kc_m = 0;
+    for (int j = 0; j < ctx->k; ++j)
+      if (enc.perm[j] < km[m]) {
+        hmask |= 1u << (j / 16);
+        if (j < enc.kc) ++kc_m;
+      }
+    const uint32_t info = hmask | (static_cast<uint32_t>((kc_m + 15) / 16) << 16);
+    const int64_t r0 = tab[m * kTab + 0] / kBM;
+    const int64_t r1 = r0 + (Pm[m] + prow - 1) / prow * prow / kBM;
+    for (int64_t r = r0; r < r1; ++r) ptile_info[r] = make_int2(static_cast<int>(tm[m]), static_cast<int>(info));
+  }
+  SPS_CUDA_TRY(S.batch_tab.reserve(sizeof(int64_t) * tab.size()));
+  SPS_CUDA_TRY(S.batch_ptile_t.reserve(sizeof(int2) * ptile_info.size()));
+  SPS_CUDA_TRY(S.batch_lin.reserve(sizeof(double) * M * NC * ctx->k));
+  SPS_CUDA_TRY(cudaMemcpyAsync(S.batch_tab.ptr, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(S.batch_ptile_t.ptr, ptile_info.data(), sizeof(int2) * ptile_info.size(),
+                               cudaMemcpyHostToDevice, ctx->stream));
+  if (S.ppad_cap < PP) {
+    const int64_t cap = std::max<int64_t>(PP, S.ppad_cap * 3 / 2 / kBM * kBM);
+    SPS_CUDA_TRY(S.thetaP.reserve(static_cast<size_t>(NC) * cap * enc.kt * sizeof(__nv_bfloat16)));
+    S.ppad_cap = cap;
+  }
+  SPS_TRY(make_map_bf16(ctx, &S.mapT, S.thetaP.ptr, static_cast<uint64_t>(NC) * PP, enc.kt, kBM));
+  const int64_t* dtab = S.batch_tab.as<int64_t>();
+  {
+    const int64_t rows = static_cast<int64_t>(NC) * PP;
+    encode_theta_batched_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
+        d_theta, dtab, M, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, PP, S.thetaP.as<__nv_bfloat16>());
+    ++ctx->launches;
+    const int64_t warps = static_cast<int64_t>(M) * NC * ctx->k;
+    lin_tail_batched_kernel<<<static_cast<unsigned>((warps + 3) / 4), 128, 0, ctx->stream>>>(
+        ctx->lin_prefix.as<double>(), ctx->Xd.as<double>(), ctx->y.as<int>(), ctx->k, NC, dtab, M,
+        S.batch_lin.as<double>());
+    ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+  }
+  const size_t slices = static_cast<size_t>(prm.n_chunks) * nwg_for(NC);
+  SPS_CUDA_TRY(S.partial.reserve(slices * PP * sizeof(double)));
+  SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
+  prm.partial = S.partial.as<double>();
+  prm.flag = S.flag.as<int>();
+  prm.ptile_info = S.batch_ptile_t.as<int2>();
+  SPS_CUDA_TRY(cudaMemsetAsync(prm.flag, 0, sizeof(int), ctx->stream));
+  if (prm.n_items > 0)
+    SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));
+  finalize_batched_kernel<<<static_cast<unsigned>((Ptot + 255) / 256), 256, 0, ctx->stream>>>(
+      d_theta, dtab, M, NC, ctx->k, Ptot, S.batch_lin.as<double>(), prm.partial,
+      prm.n_items > 0 ? static_cast<int>(slices) : 0, PP, d_ll);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
 }
 
 // ------------------------------------------------------------------------------------------

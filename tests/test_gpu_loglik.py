@@ -175,3 +175,38 @@ def test_c4_large_binary_sampled(torch_cuda, prec):
     got_t = s.loglik(theta[:300], t, prec)
     ref_t = oracle_loglik(w.X, w.y, theta[[0, 299]], w.C, t)
     np.testing.assert_allclose(got_t[[0, 299]], ref_t, rtol=rtol)
+
+
+@pytest.mark.parametrize("C", [2, 3])
+def test_batched_nested_models_match_oracle(torch_cuda, C):
+    # nested models (first k_m columns), ragged particle counts and prefixes, in one launch
+    torch = torch_cuda
+    n, kmax = 1000, 20
+    X, y = _mk(n, kmax, C, 31, 6)
+    s = _sps(X, y, C)
+    g = np.random.Generator(np.random.PCG64(32))
+    ks, Ps, ts = [3, 20, 11, 7], [300, 129, 1000, 7], [1000, 777, 1, 0]
+    thetas = [0.2 * g.standard_normal((P, k * (C - 1))) for k, P in zip(ks, Ps)]
+    got = s.loglik_batched([torch.from_numpy(t).cuda() for t in thetas], ks, ts)
+    torch.cuda.synchronize()
+    for k, t, th, gm in zip(ks, ts, thetas, got):
+        Xm = np.ascontiguousarray(X[:, :k])
+        ref = oracle_loglik(Xm, y, th, C, t)
+        tol = _tol(Xm, th, C, t, ref, "split")
+        assert np.all(np.abs(gm.cpu().numpy() - ref) <= tol), (k, t)
+
+
+@pytest.mark.slow
+def test_batched_c5_sampled(torch_cuda):
+    # the batched workload: 24 nested three-outcome models, k = 5..74, 16384 particles each
+    torch = torch_cuda
+    w = synthetic.make_c5()
+    s = _sps(w.X, w.y, w.C)
+    g = np.random.Generator(np.random.PCG64(33))
+    thetas = [0.1 * g.standard_normal((w.J * w.N, k * (w.C - 1))) for k in w.model_k]
+    got = s.loglik_batched([torch.from_numpy(t).cuda() for t in thetas], w.model_k, [w.n] * len(w.model_k))
+    for m in (0, 7, 23):
+        k = w.model_k[m]
+        idx = np.array([0, 5, w.J * w.N - 1])
+        ref = oracle_loglik(np.ascontiguousarray(w.X[:, :k]), w.y, thetas[m][idx], w.C, w.n)
+        np.testing.assert_allclose(got[m].cpu().numpy()[idx], ref, rtol=1e-5)

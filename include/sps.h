@@ -99,6 +99,11 @@ typedef struct sps_options {
   double mala_target_accept; /* 0.5: step-size target when mkernel == MALA (not in the paper) */
   uint64_t seed;           /* Philox key for sps_run's random numbers */
   int32_t resampling;      /* sps_resampling, default SPS_RESAMPLE_MULTINOMIAL */
+  int32_t graphs;          /* 1 (default): after its first step, an adaptive M phase of sps_run or
+                              sps_mphase runs as one captured CUDA graph (a conditional loop whose
+                              body is one M step and a device-side step-size and RNE rule), with one
+                              host synchronisation per phase; results are identical to graphs = 0,
+                              which issues and reads back every step from the host */
 } sps_options;
 
 typedef struct sps_ctx sps_ctx;
@@ -142,6 +147,7 @@ typedef struct sps_result {
                               the cycle containing s (Sec. 6 calls them a by-product of SPS);
                               over a cycle they sum to the log-ML increment */
   double* log_pred_nse;    /* [n] or NULL: their sd over groups / sqrt(J) */
+  int64_t graph_steps;     /* M steps that ran inside captured graphs (options.graphs) */
 } sps_result;
 
 /* ------------------------------------------------------------------ lifecycle */

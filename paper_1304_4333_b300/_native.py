@@ -29,7 +29,8 @@ class SpsOptions(C.Structure):
                 ("h_min", C.c_double), ("h_max", C.c_double), ("target_accept", C.c_double),
                 ("rne_cycle", C.c_double), ("rne_final", C.c_double), ("r_max", C.c_int32),
                 ("precision", C.c_int32), ("mkernel", C.c_int32), ("cphase_block", C.c_int32),
-                ("mala_target_accept", C.c_double), ("seed", C.c_uint64), ("resampling", C.c_int32)]
+                ("mala_target_accept", C.c_double), ("seed", C.c_uint64), ("resampling", C.c_int32),
+                ("graphs", C.c_int32)]
 
 
 class SpsSchedule(C.Structure):
@@ -43,7 +44,8 @@ class SpsResult(C.Structure):
                 ("rne", C.POINTER(C.c_double)), ("log_ml_group", C.POINTER(C.c_double)),
                 ("log_ml", C.c_double), ("log_ml_nse", C.c_double), ("log_ml_pooled", C.c_double),
                 ("n_cycles", C.c_int32), ("m_steps", C.c_int64), ("seconds", C.c_double),
-                ("log_pred", C.POINTER(C.c_double)), ("log_pred_nse", C.POINTER(C.c_double))]
+                ("log_pred", C.POINTER(C.c_double)), ("log_pred_nse", C.POINTER(C.c_double)),
+                ("graph_steps", C.c_int64)]
 
 
 class SpsMstepInfo(C.Structure):

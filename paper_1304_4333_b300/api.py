@@ -94,6 +94,7 @@ class RunResult:
     schedule: Optional["Schedule"] = None
     log_pred: Optional[np.ndarray] = None       # [n] log p(y_s | y_1:s-1), mean over groups
     log_pred_nse: Optional[np.ndarray] = None   # [n] sd over groups / sqrt(J)
+    graph_steps: int = 0                        # M steps run inside captured CUDA graphs
 
 
 @dataclass
@@ -350,7 +351,8 @@ class Sps:
                              rs[:S].copy() if rs is not None else np.zeros((0, self.D, self.D)),
                              rh[:S].copy(), ra[:S].copy())
         return RunResult(arrs["mean"], arrs["sd"], arrs["nse"], arrs["rne"], lmg, res.log_ml, res.log_ml_nse,
-                         res.log_ml_pooled, res.n_cycles, res.m_steps, res.seconds, sched, lp, lpn)
+                         res.log_ml_pooled, res.n_cycles, res.m_steps, res.seconds, sched, lp, lpn,
+                         res.graph_steps)
 
 
 class State:

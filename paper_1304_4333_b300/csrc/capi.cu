@@ -1,5 +1,6 @@
 // C ABI of the SPS library: context lifecycle, data encoding and the likelihood entry points.
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,8 +15,15 @@ DevBuf::~DevBuf() {
   if (ptr) cudaFree(ptr);
 }
 
+namespace {
+std::atomic<uint64_t> g_buffer_generation{0};
+}
+
+uint64_t buffer_generation() { return g_buffer_generation.load(std::memory_order_relaxed); }
+
 cudaError_t DevBuf::reserve(size_t nbytes) {
   if (nbytes <= bytes && ptr) return cudaSuccess;
+  g_buffer_generation.fetch_add(1, std::memory_order_relaxed);
   if (ptr) {
     cudaFree(ptr);
     ptr = nullptr;
@@ -257,7 +265,7 @@ sps_status ensure_lin(sps_ctx* ctx, int64_t t) {
 }
 
 void hot_begin(sps_ctx* ctx) {
-  if (!ctx->timing) return;
+  if (!ctx->timing || ctx->capturing) return;
   if (ctx->hot_used + 2 > ctx->hot_events.size()) {
     for (int q = 0; q < 2; ++q) {
       cudaEvent_t e;
@@ -269,7 +277,7 @@ void hot_begin(sps_ctx* ctx) {
 }
 
 void hot_end(sps_ctx* ctx) {
-  if (!ctx->timing || ctx->hot_used + 2 > ctx->hot_events.size()) return;
+  if (!ctx->timing || ctx->capturing || ctx->hot_used + 2 > ctx->hot_events.size()) return;
   cudaEventRecord(ctx->hot_events[ctx->hot_used + 1], ctx->stream);
   ctx->hot_used += 2;
 }
@@ -305,6 +313,7 @@ void sps_options_default(sps_options* o) {
   o->mala_target_accept = 0.5;
   o->seed = 0;
   o->resampling = SPS_RESAMPLE_MULTINOMIAL;
+  o->graphs = 1;
 }
 
 const char* sps_status_string(sps_status s) {
@@ -411,6 +420,7 @@ sps_status sps_set_stream(sps_ctx* ctx, void* stream) {
 void sps_destroy(sps_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -460,7 +470,7 @@ sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const 
   ctx->C = n_outcomes;
   ctx->NC = n_outcomes - 1;
   ctx->D = k * ctx->NC;
-  const int D = ctx->D, NC = ctx->NC;
+  const int NC = ctx->NC;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(SPS_ERR_CUDA);
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) return bail(SPS_ERR_CUDA);

@@ -77,6 +77,22 @@ struct LoglikScratch {
   DevBuf batch_lin;           // FP64 [M x NC x k] linear terms of the models
 };
 
+// Device-resident control block of a captured M phase: the step size h and the Philox step word
+// of the next M step, the steps taken so far, the stop flag and an error code (1: Cholesky
+// failure, 2: non-finite proposal log-likelihood).
+struct StepCtl {
+  double h;
+  unsigned long long step;
+  int r;
+  int r_max;
+  int stop;
+  int err;
+};
+
+// Incremented by every device-buffer (re)allocation: a captured graph whose generation differs
+// may point at freed memory and is captured again.
+uint64_t buffer_generation();
+
 }  // namespace sps
 
 struct sps_ctx {
@@ -113,6 +129,9 @@ struct sps_ctx {
   // fused log-likelihood kernel when timing is on
   int64_t launches = 0;
   bool timing = false;
+  bool capturing = false;                // stream capture in progress: no event records
+  cudaStream_t cap_stream = nullptr;     // private non-blocking stream for graph capture (the
+                                         // legacy default stream cannot be captured)
   std::vector<cudaEvent_t> hot_events;   // pairs (start, stop)
   size_t hot_used = 0;                   // events in use (2 per recorded launch)
   ~sps_ctx();
@@ -150,6 +169,26 @@ struct sps_state {
   sps::DevBuf zq;                 // FP32 [P x D] MALA: 1/2 L' g(theta) + z of the current proposal
   sps::DevBuf z2;                 // FP64 [P] MALA: |z|^2 of the current proposal
   std::vector<double> host_tmp;
+  // captured M phase: one M step and its control kernel inside a conditional WHILE node, valid
+  // while the key (prefix, kernel, precision, buffer generation and addresses) is unchanged
+  cudaGraphExec_t mgraph = nullptr;
+  struct MKey {
+    int64_t t = -1;
+    int kernel = -1, precision = -1, sig = 0;
+    uint64_t gen = 0;
+    const void* bufs[8] = {};
+    bool operator==(const MKey& o) const {
+      if (t != o.t || kernel != o.kernel || precision != o.precision || sig != o.sig || gen != o.gen) return false;
+      for (int i = 0; i < 8; ++i)
+        if (bufs[i] != o.bufs[i]) return false;
+      return true;
+    }
+  } mkey;
+  int64_t mgraph_launches = 0;    // kernels of one captured step (control kernel included)
+  sps::DevBuf ctl;                // StepCtl
+  sps::DevBuf steplog;            // FP64 [r_max x 3]: h, acceptance rate, min RNE of each step
+  sps::DevBuf sigmalog;           // FP64 [r_max x D x D]: Sigma of each step (recorded schedules)
+  int64_t graph_steps = 0;        // M steps run inside captured graphs
 };
 
 namespace sps {

@@ -643,8 +643,10 @@ cov_moments_kernel(const double* __restrict__ th, int64_t P, int D, int64_t per_
 
 // V = (S2 - S1 S1' / P) / (P - 1) from the block partials, one warp per lower-triangle entry
 // (lanes take every 32nd block, FP64); writes the full symmetric V and Sigma = scale V.
-__global__ void cov_final_kernel(const double* __restrict__ partial, int blocks, int D, int64_t P, double scale,
-                                 double* __restrict__ V, double* __restrict__ Sigma) {
+__global__ void cov_final_kernel(const double* __restrict__ partial, int blocks, int D, int64_t P, double scale_arg,
+                                 const double* __restrict__ scale_dev, double* __restrict__ V,
+                                 double* __restrict__ Sigma) {
+  const double scale = scale_dev ? *scale_dev : scale_arg;   // device-resident h in a captured M phase
   const int T = D * (D + 1) / 2, E = T + D;
   const int e = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -779,10 +781,12 @@ constexpr int kPropThreads = 64;   // particles per block
 // reads and writes); each thread updates its own row there. Skipped when the factorisation failed.
 __global__ void __launch_bounds__(kPropThreads)
 propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __restrict__ L32,
-               const double* __restrict__ z_given, uint64_t seed, uint64_t step, const double* __restrict__ mu,
+               const double* __restrict__ z_given, uint64_t seed, uint64_t step_arg,
+               const unsigned long long* __restrict__ step_dev, const double* __restrict__ mu,
                const double* __restrict__ prec, bool full, const int* __restrict__ flag,
                double* __restrict__ th_o, double* __restrict__ lp_o) {
   if (*flag) return;
+  const uint64_t step = step_dev ? *step_dev : step_arg;
   extern __shared__ double pd[];
   const int T = D * (D + 1) / 2;
   const int Dp = D | 1;
@@ -846,11 +850,12 @@ __global__ void __launch_bounds__(kAccThreads)
 accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restrict__ lp,
               const double* __restrict__ th_p, const double* __restrict__ ll_p,
               const double* __restrict__ lp_p, int64_t P, int D, const double* __restrict__ u_given,
-              uint64_t seed, uint64_t step, const int* __restrict__ flag,
-              unsigned long long* __restrict__ n_acc, int* __restrict__ nonfinite,
+              uint64_t seed, uint64_t step_arg, const unsigned long long* __restrict__ step_dev,
+              const int* __restrict__ flag, unsigned long long* __restrict__ n_acc, int* __restrict__ nonfinite,
               double* __restrict__ log_alpha_out, int* __restrict__ acc_out) {
   __shared__ unsigned char take[kAccThreads];
   if (*flag) return;
+  const uint64_t step = step_dev ? *step_dev : step_arg;
   const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kAccThreads;
   const int64_t p = p0 + threadIdx.x;
   bool acc = false;
@@ -905,11 +910,13 @@ __device__ __forceinline__ double prior_grad(const double* th, const double* mu,
 
 __global__ void __launch_bounds__(kMalaThreads)
 mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gll, int64_t P, int D,
-                    const float* __restrict__ L32, uint64_t seed, uint64_t step, const double* __restrict__ mu,
+                    const float* __restrict__ L32, uint64_t seed, uint64_t step_arg,
+                    const unsigned long long* __restrict__ step_dev, const double* __restrict__ mu,
                     const double* __restrict__ prec, bool full, const int* __restrict__ flag,
                     double* __restrict__ th_o, double* __restrict__ lp_o, float* __restrict__ zq_o,
                     double* __restrict__ z2_o) {
   if (*flag) return;
+  const uint64_t step = step_dev ? *step_dev : step_arg;
   extern __shared__ float ms[];
   const int T = D * (D + 1) / 2;
   float* Ls = ms;                                  // [T] packed lower triangle
@@ -963,9 +970,11 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
                    const double* __restrict__ lp_p, const double* __restrict__ g_p, const float* __restrict__ zq,
                    const double* __restrict__ z2, const float* __restrict__ L32, int64_t P, int D,
                    const double* __restrict__ mu, const double* __restrict__ prec, bool full, uint64_t seed,
-                   uint64_t step, const int* __restrict__ flag, unsigned long long* __restrict__ n_acc,
+                   uint64_t step_arg, const unsigned long long* __restrict__ step_dev,
+                   const int* __restrict__ flag, unsigned long long* __restrict__ n_acc,
                    int* __restrict__ nonfinite) {
   if (*flag) return;
+  const uint64_t step = step_dev ? *step_dev : step_arg;
   extern __shared__ float ms[];
   const int T = D * (D + 1) / 2;
   float* Ls = ms;
@@ -1114,6 +1123,89 @@ monitor_moments_kernel(const double* __restrict__ th, const double* __restrict__
   }
 }
 
+// Device side of the step-size rule and the stopping rule of an M phase (Algorithm 2 step
+// 2(c)ii-iii) for a captured M phase: the group sums of the monitoring functions reduced in the
+// order of the host path (reduce_parts, moments_from_sums, read_step, mstep_impl), every
+// operation rounded separately as there, so that both paths take identical decisions. Writes
+// h, the acceptance rate and the minimum RNE of the step to steplog[r], advances h and the
+// Philox step word and sets the loop condition (0 after the stopping rule, r_max steps or an
+// error); with sigma_log, also copies the step's Sigma (D x D) to sigma_log[r]. One block; sums:
+// J F 3 doubles of dynamic shared memory.
+constexpr int kCtlMaxF = 64;
+
+__global__ void __launch_bounds__(128)
+mstep_control_kernel(StepCtl* __restrict__ ctl, const unsigned long long* __restrict__ counters,
+                     const double* __restrict__ parts, int J, int F, int S, int N, int64_t P, double K,
+                     double target, double h_step, double h_min, double h_max, double* __restrict__ steplog,
+                     const double* __restrict__ sigma, int D, double* __restrict__ sigma_log,
+                     cudaGraphConditionalHandle cond) {
+  extern __shared__ double sums[];   // [J][F][3]
+  __shared__ double rne[kCtlMaxF];
+  const int r = ctl->r;   // read by every thread before thread 0 advances it
+  if (sigma_log)
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x)
+      sigma_log[static_cast<size_t>(r) * D * D + e] = sigma[e];
+  for (int q = threadIdx.x; q < J * F; q += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int z = 0; z < S; ++z) {
+      a = __dadd_rn(a, parts[(static_cast<size_t>(q) * S + z) * 3 + 0]);
+      b = __dadd_rn(b, parts[(static_cast<size_t>(q) * S + z) * 3 + 1]);
+    }
+    sums[q * 3 + 0] = a;
+    sums[q * 3 + 1] = b;
+  }
+  __syncthreads();
+  const double dN = static_cast<double>(N), dJ = static_cast<double>(J);
+  for (int f = threadIdx.x; f < F; f += blockDim.x) {
+    double gbar = 0.0, s2 = 0.0;
+    for (int j = 0; j < J; ++j) {
+      gbar = __dadd_rn(gbar, __ddiv_rn(sums[(j * F + f) * 3 + 0], dN));
+      s2 = __dadd_rn(s2, sums[(j * F + f) * 3 + 1]);
+    }
+    gbar = __ddiv_rn(gbar, dJ);
+    double vh = 0.0;
+    for (int j = 0; j < J; ++j) {
+      const double d = __dsub_rn(__ddiv_rn(sums[(j * F + f) * 3 + 0], dN), gbar);
+      vh = __dadd_rn(vh, __dmul_rn(d, d));
+    }
+    vh = __dmul_rn(vh, __ddiv_rn(dN, __dsub_rn(dJ, 1.0)));
+    const double v0 = __dsub_rn(__ddiv_rn(s2, __dmul_rn(dJ, dN)), __dmul_rn(gbar, gbar));
+    const double var = (0.0 < v0) ? v0 : 0.0;
+    rne[f] = vh > 0.0 ? __ddiv_rn(var, vh) : INFINITY;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int* flags = reinterpret_cast<const int*>(counters + 1);
+  const int err = flags[0] ? 1 : (flags[1] ? 2 : 0);
+  bool stop;
+  if (err) {
+    ctl->err = err;
+    stop = true;
+  } else {
+    double rmin = INFINITY;
+    for (int f = 0; f < F; ++f) rmin = (rne[f] < rmin) ? rne[f] : rmin;
+    const double alpha = __ddiv_rn(static_cast<double>(counters[0]), static_cast<double>(P));
+    const double h = ctl->h;
+    double hn;
+    if (alpha > target) {
+      const double a = __dadd_rn(h, h_step);
+      hn = (h_max < a) ? h_max : a;
+    } else {
+      const double a = __dsub_rn(h, h_step);
+      hn = (a < h_min) ? h_min : a;
+    }
+    steplog[3 * r + 0] = h;
+    steplog[3 * r + 1] = alpha;
+    steplog[3 * r + 2] = rmin;
+    ctl->h = hn;
+    ctl->step += 1;
+    ctl->r = r + 1;
+    stop = (rmin >= K) || (r + 1 >= ctl->r_max);
+  }
+  ctl->stop = stop ? 1 : 0;
+  cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ host helpers
@@ -1180,8 +1272,8 @@ static int cov_blocks(int64_t P) { return static_cast<int>(std::min<int64_t>(296
 
 // V = pooled covariance of theta [P x D] (divisor P - 1) into V and/or Sigma = scale V (device,
 // full symmetric); partial: cov_blocks(P) x (T + D) doubles of scratch.
-static sps_status launch_cov(sps_ctx* ctx, const double* theta, int64_t P, int D, double scale, double* partial,
-                             double* V, double* Sigma) {
+static sps_status launch_cov(sps_ctx* ctx, const double* theta, int64_t P, int D, double scale,
+                             const double* scale_dev, double* partial, double* V, double* Sigma) {
   const int T = D * (D + 1) / 2;
   const int blocks = cov_blocks(P);
   const int64_t per = (P + blocks - 1) / blocks;
@@ -1196,7 +1288,7 @@ static sps_status launch_cov(sps_ctx* ctx, const double* theta, int64_t P, int D
   else
     cov_moments_kernel<kCovMaxEnt><<<blocks, kCovThreads, smem, ctx->stream>>>(theta, P, D, per, partial);
   ++ctx->launches;
-  cov_final_kernel<<<static_cast<unsigned>((T + 7) / 8), 256, 0, ctx->stream>>>(partial, blocks, D, P, scale, V,
+  cov_final_kernel<<<static_cast<unsigned>((T + 7) / 8), 256, 0, ctx->stream>>>(partial, blocks, D, P, scale, scale_dev, V,
                                                                                  Sigma); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
@@ -1204,14 +1296,14 @@ static sps_status launch_cov(sps_ctx* ctx, const double* theta, int64_t P, int D
 
 // V (and Sigma = h V unless sigma_in) then its Cholesky factor into st->chol / scratch L32.
 static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_theta, double h,
-                                  const double* sigma_host, double* sigma_out, int* d_flag) {
+                                  const double* h_dev, const double* sigma_host, double* sigma_out, int* d_flag) {
   const int D = ctx->D;
   const int T = D * (D + 1) / 2;
   double* d_sigma = st->cov.as<double>();
   if (sigma_host) {
     SPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma_host, sizeof(double) * D * D, cudaMemcpyHostToDevice, ctx->stream));
   } else {
-    SPS_TRY(launch_cov(ctx, d_theta, st->P, D, h, st->scratch.as<double>(), nullptr, d_sigma));
+    SPS_TRY(launch_cov(ctx, d_theta, st->P, D, h, h_dev, st->scratch.as<double>(), nullptr, d_sigma));
   }
   if (sigma_out)
     SPS_CUDA_TRY(cudaMemcpyAsync(sigma_out, d_sigma, sizeof(double) * D * D, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1231,14 +1323,15 @@ static size_t propose_smem(int D) {
 }
 
 static sps_status launch_propose(sps_ctx* ctx, sps_state* st, const double* d_theta, int64_t P, const double* z,
-                                 uint64_t step, int* d_flag, double* th_o, double* lp_o) {
+                                 uint64_t step, const unsigned long long* step_dev, int* d_flag, double* th_o,
+                                 double* lp_o) {
   const int D = ctx->D;
   const size_t smem = propose_smem(D);
   SPS_CUDA_TRY(cudaFuncSetAttribute(propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
   propose_kernel<<<static_cast<unsigned>((P + kPropThreads - 1) / kPropThreads), kPropThreads, smem, ctx->stream>>>(
-      d_theta, P, D, L32, z, st->seed, step, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(),
+      d_theta, P, D, L32, z, st->seed, step, step_dev, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(),
       prior_full(ctx), d_flag, th_o, lp_o); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
@@ -1338,17 +1431,14 @@ sps_status read_step(sps_ctx* ctx, sps_state* st, Counters* c, double* rne_min) 
   return SPS_OK;
 }
 
-// One M step; recomputes the cached log-likelihood with the M-phase kernel first when the C
-// phase has updated it (so that both sides of the Metropolis ratio use one function).
-sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sigma, double* sigma_used,
-                      sps_mstep_info* info) {
+// Before an M step: the cached log-likelihood (and, for MALA, its gradient) recomputed with the
+// function the proposals are evaluated with, when the C phase or another kernel left it stale.
+sps_status mstep_prepare(sps_ctx* ctx, sps_state* st, int kernel) {
   if (kernel != SPS_MKERNEL_RW && kernel != SPS_MKERNEL_MALA)
     return fail(ctx, SPS_ERR_INVALID_ARG, "unknown M kernel");
   const int precision = ctx->opt.precision;
   const int D = ctx->D;
   const bool mala = (kernel == SPS_MKERNEL_MALA);
-  // the cached log-likelihood (and, for MALA, its gradient) must come from the function the
-  // proposals are evaluated with
   const int kind = mala ? 2 : (precision == SPS_PREC_FP32 ? 1 : 0);
   if (mala) {
     SPS_CUDA_TRY(st->grad.reserve(sizeof(double) * st->P * D));
@@ -1367,10 +1457,21 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
     st->ll_stale = false;
     st->ll_kind = kind;
   }
+  return SPS_OK;
+}
+
+// The work of one M step on the stream: counters cleared, Sigma = h V (or the given Sigma) and
+// its Cholesky factor, proposals with the prior log kernel, their log-likelihood (and gradient),
+// the Metropolis decisions, the monitoring sums. With ctl (a captured M phase) h and the Philox
+// step word are read on the device from ctl; otherwise they are h and step.
+sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* sigma, double* sigma_used, double h,
+                       uint64_t step, StepCtl* ctl) {
+  const int D = ctx->D;
+  const bool mala = (kernel == SPS_MKERNEL_MALA);
+  const unsigned long long* step_dev = ctl ? &ctl->step : nullptr;
   SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
-  const double h = st->h;
-  SPS_TRY(factor_proposal(ctx, st, st->theta.as<double>(), h, sigma, sigma_used, flag_ptr(st, 0)));
-  const uint64_t step = ++st->step_counter;
+  SPS_TRY(factor_proposal(ctx, st, st->theta.as<double>(), h, ctl ? &ctl->h : nullptr, sigma, sigma_used,
+                          flag_ptr(st, 0)));
   if (mala) {
     const int T = D * (D + 1) / 2;
     const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kMalaThreads);
@@ -1382,9 +1483,10 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
     const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
     const unsigned blocks = static_cast<unsigned>((st->P + kMalaThreads - 1) / kMalaThreads);
     mala_propose_kernel<<<blocks, kMalaThreads, smem_p, ctx->stream>>>(
-        st->theta.as<double>(), st->grad.as<double>(), st->P, D, L32, st->seed, step, ctx->d_prior_mean.as<double>(),
-        ctx->d_prior_prec.as<double>(), prior_full(ctx), flag_ptr(st, 0), st->theta_prop.as<double>(),
-        st->lp_prop.as<double>(), st->zq.as<float>(), st->z2.as<double>()); ++ctx->launches;
+        st->theta.as<double>(), st->grad.as<double>(), st->P, D, L32, st->seed, step, step_dev,
+        ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(), prior_full(ctx), flag_ptr(st, 0),
+        st->theta_prop.as<double>(), st->lp_prop.as<double>(), st->zq.as<float>(), st->z2.as<double>());
+    ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
     SPS_TRY(loglik_grad_fp32(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
                              st->grad_prop.as<double>()));
@@ -1392,21 +1494,33 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
         st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->grad.as<double>(),
         st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->grad_prop.as<double>(),
         st->zq.as<float>(), st->z2.as<double>(), L32, st->P, D, ctx->d_prior_mean.as<double>(),
-        ctx->d_prior_prec.as<double>(), prior_full(ctx), st->seed, step, flag_ptr(st, 0),
+        ctx->d_prior_prec.as<double>(), prior_full(ctx), st->seed, step, step_dev, flag_ptr(st, 0),
         st->counters.as<unsigned long long>(), flag_ptr(st, 1)); ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
   } else {
-    SPS_TRY(launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, flag_ptr(st, 0),
+    SPS_TRY(launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, step_dev, flag_ptr(st, 0),
                            st->theta_prop.as<double>(), st->lp_prop.as<double>()));
-    SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(), precision));
+    SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
+                            ctx->opt.precision));
     accept_kernel<<<static_cast<unsigned>((st->P + kAccThreads - 1) / kAccThreads), kAccThreads, 0, ctx->stream>>>(
         st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->theta_prop.as<double>(),
-        st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, flag_ptr(st, 0),
-        st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
+        st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, step_dev,
+        flag_ptr(st, 0), st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
-    st->grad_valid = false;
   }
   launch_monitoring(ctx, st);
+  return SPS_OK;
+}
+
+// One M step, issued and read back (Algorithm 2 step 2(c)): the acceptance rate drives the
+// step-size rule unless Sigma is given.
+sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sigma, double* sigma_used,
+                      sps_mstep_info* info) {
+  SPS_TRY(mstep_prepare(ctx, st, kernel));
+  const double h = st->h;
+  const uint64_t step = ++st->step_counter;
+  SPS_TRY(mstep_issue(ctx, st, kernel, sigma, sigma_used, h, step, nullptr));
+  if (kernel == SPS_MKERNEL_RW) st->grad_valid = false;
   Counters c;
   double rmin = 0.0;
   SPS_TRY(read_step(ctx, st, &c, &rmin));
@@ -1427,6 +1541,158 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
     info->rne_min = rmin;
     info->h_next = hn;
   }
+  return SPS_OK;
+}
+
+// The rest of an adaptive M phase, after its first (eager) step, as one graph launch: a
+// conditional WHILE node whose body is one M step (mstep_issue with h and the Philox step word
+// on the device) and mstep_control_kernel, captured when the key changes (each cycle's t, a swap
+// of the particle buffers, a reallocation) and replayed otherwise. The host synchronises once
+// per phase. Returns with *fallback set (and nothing run) when the graph cannot be built; then
+// the caller continues step by step.
+sps_status mphase_graph(sps_ctx* ctx, sps_state* st, int kernel, double K, int r_done, int* r_end,
+                        sps_schedule* rec, int64_t rec_step0, sps_mstep_info* info, bool* fallback) {
+  *fallback = false;
+  const sps_options& o = ctx->opt;
+  // a fallback leaves its reason in the context's last-error string (the call still succeeds)
+  auto give_up = [&](const char* what, cudaError_t e) {
+    ctx->last_error = std::string("M-phase graph not used: ") + what + (e != cudaSuccess ? std::string(": ") +
+                      cudaGetErrorString(e) : std::string());
+    cudaGetLastError();
+    *fallback = true;
+    return SPS_OK;
+  };
+  const int F = 1 + ctx->NC;
+  if (F > kCtlMaxF || o.r_max <= r_done) return give_up("shape", cudaSuccess);
+  SPS_CUDA_TRY(st->ctl.reserve(sizeof(StepCtl)));
+  SPS_CUDA_TRY(st->steplog.reserve(sizeof(double) * 3 * static_cast<size_t>(o.r_max)));
+  const bool want_sigma = rec && rec->sigma;
+  const size_t DD = static_cast<size_t>(ctx->D) * ctx->D;
+  if (want_sigma) SPS_CUDA_TRY(st->sigmalog.reserve(sizeof(double) * DD * o.r_max));
+  sps_state::MKey key;
+  key.t = st->t;
+  key.kernel = kernel;
+  key.precision = o.precision;
+  key.gen = buffer_generation();
+  key.sig = want_sigma ? 1 : 0;
+  const void* bufs[8] = {st->theta.ptr, st->theta_prop.ptr, st->ll.ptr, st->ll_prop.ptr,
+                         st->lp.ptr,    st->lp_prop.ptr,    st->grad.ptr, st->grad_prop.ptr};
+  for (int i = 0; i < 8; ++i) key.bufs[i] = bufs[i];
+  StepCtl* d_ctl = st->ctl.as<StepCtl>();
+  if (!st->mgraph || !(st->mkey == key)) {
+    if (st->mgraph) {
+      cudaGraphExecDestroy(st->mgraph);
+      st->mgraph = nullptr;
+    }
+    if (!ctx->cap_stream) {
+      const cudaError_t ec = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+      if (ec != cudaSuccess) {
+        ctx->cap_stream = nullptr;
+        return give_up("capture stream", ec);
+      }
+    }
+    cudaGraph_t g = nullptr;
+    SPS_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = cond;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    // the step is recorded on the private stream (nothing runs during capture); the graph is
+    // launched on the context's stream
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return give_up("conditional node", e);
+    }
+    const int64_t launches0 = ctx->launches;
+    const cudaStream_t user_stream = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    ctx->capturing = true;
+    sps_status is = mstep_issue(ctx, st, kernel, nullptr, nullptr, 0.0, 0, d_ctl);
+    if (is == SPS_OK) {
+      const double target = (kernel == SPS_MKERNEL_MALA) ? o.mala_target_accept : o.target_accept;
+      const size_t smem = sizeof(double) * 3 * static_cast<size_t>(st->J) * F;
+      if (smem > 48 * 1024)
+        is = SPS_ERR_UNSUPPORTED;
+      else {
+        mstep_control_kernel<<<1, 128, smem, ctx->stream>>>(d_ctl, st->counters.as<unsigned long long>(),
+                                                            st->scratch.as<double>(), st->J, F, kMomParts, st->N,
+                                                            st->P, K, target, o.h_step, o.h_min, o.h_max,
+                                                            st->steplog.as<double>(), st->cov.as<double>(), ctx->D,
+                                                            want_sigma ? st->sigmalog.as<double>() : nullptr, cond);
+        ++ctx->launches;
+        if (cudaGetLastError() != cudaSuccess) is = SPS_ERR_CUDA;
+      }
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(ctx->cap_stream, &captured);
+    ctx->capturing = false;
+    ctx->stream = user_stream;
+    const int64_t per_step = ctx->launches - launches0;
+    ctx->launches = launches0;
+    if (is != SPS_OK || e != cudaSuccess || buffer_generation() != key.gen) {
+      // nothing of the capture ran; continue step by step
+      cudaGraphDestroy(g);
+      const std::string why = is != SPS_OK ? "capture: " + ctx->last_error
+                              : e != cudaSuccess ? std::string("end capture") : std::string("reallocation");
+      return give_up(why.c_str(), e);
+    }
+    e = cudaGraphInstantiate(&st->mgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      st->mgraph = nullptr;
+      return give_up("instantiate", e);
+    }
+    st->mkey = key;
+    st->mgraph_launches = per_step;
+  }
+  StepCtl c{st->h, static_cast<unsigned long long>(st->step_counter + 1), r_done, o.r_max, 0, 0};
+  SPS_CUDA_TRY(cudaMemcpyAsync(d_ctl, &c, sizeof c, cudaMemcpyHostToDevice, ctx->stream));
+  SPS_CUDA_TRY(cudaGraphLaunch(st->mgraph, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(&c, d_ctl, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  const int ran = c.r - r_done + (c.err ? 1 : 0);
+  ctx->launches += static_cast<int64_t>(ran) * st->mgraph_launches;
+  st->graph_steps += ran;
+  st->step_counter = c.step - 1 + (c.err ? 1 : 0);
+  if (kernel == SPS_MKERNEL_RW) st->grad_valid = false;
+  if (c.err == 1) return fail(ctx, SPS_ERR_DEGENERATE, "proposal covariance h V is not positive definite");
+  if (c.err == 2) return fail(ctx, SPS_ERR_NONFINITE, "non-finite log-likelihood of a proposal");
+  std::vector<double> lg(3 * static_cast<size_t>(c.r - r_done));
+  if (!lg.empty()) {
+    SPS_CUDA_TRY(cudaMemcpy(lg.data(), st->steplog.as<double>() + 3 * static_cast<size_t>(r_done),
+                            sizeof(double) * lg.size(), cudaMemcpyDeviceToHost));
+  }
+  if (want_sigma && c.r > r_done && rec_step0 + r_done < rec->cap_steps) {
+    const int64_t n_copy = std::min<int64_t>(c.r - r_done, rec->cap_steps - (rec_step0 + r_done));
+    SPS_CUDA_TRY(cudaMemcpy(rec->sigma + (rec_step0 + r_done) * DD, st->sigmalog.as<double>() + r_done * DD,
+                            sizeof(double) * DD * n_copy, cudaMemcpyDeviceToHost));
+  }
+  for (int r = r_done; r < c.r; ++r) {
+    const double* q = lg.data() + 3 * static_cast<size_t>(r - r_done);
+    const int64_t rs = rec_step0 + r;
+    if (rec && rs < rec->cap_steps) {
+      if (rec->h) rec->h[rs] = q[0];
+      if (rec->accept) rec->accept[rs] = q[1];
+    }
+    if (info && r + 1 == c.r) {
+      info->h = q[0];
+      info->accept_rate = q[1];
+      info->rne_min = q[2];
+      info->h_next = c.h;
+    }
+  }
+  st->h = c.h;
+  *r_end = c.r;
   return SPS_OK;
 }
 
@@ -1558,6 +1824,7 @@ sps_status mphase_impl(sps_ctx* ctx, sps_state* st, int kernel, int fixed_steps,
   const int D = ctx->D;
   int r = 0;
   sps_mstep_info info{};
+  bool use_graph = ctx->opt.graphs && fixed_steps <= 0 && !sigmas;
   while (true) {
     const int64_t rs = rec_step0 + r;
     double* sig_out = nullptr;
@@ -1573,6 +1840,16 @@ sps_status mphase_impl(sps_ctx* ctx, sps_state* st, int kernel, int fixed_steps,
       if (r >= fixed_steps) break;
     } else if (info.rne_min >= K || r >= ctx->opt.r_max) {
       break;
+    }
+    if (use_graph) {
+      bool fallback = false;
+      int r_end = r;
+      SPS_TRY(mphase_graph(ctx, st, kernel, K, r, &r_end, rec, rec_step0, &info, &fallback));
+      if (!fallback) {
+        r = r_end;
+        break;
+      }
+      use_graph = false;
     }
   }
   if (steps) *steps = r;
@@ -1630,6 +1907,7 @@ sps_status sps_state_create(sps_ctx* ctx, int32_t J, int32_t N, uint64_t seed, s
 void sps_state_destroy(sps_state* st) {
   if (!st) return;
   if (st->ctx) cudaStreamSynchronize(st->ctx->stream);
+  if (st->mgraph) cudaGraphExecDestroy(st->mgraph);
   delete st;
 }
 
@@ -1794,6 +2072,7 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
   out->log_ml_pooled = mx + std::log(se / st->J);
   out->n_cycles = L;
   out->m_steps = total_steps;
+  out->graph_steps = st->graph_steps;
   if (want_lpl)
     for (int64_t q = 0; q < ctx->n; ++q) {
       const double* row = lpl.data() + q * groups;
@@ -1918,7 +2197,7 @@ sps_status sps_particle_cov(sps_ctx* ctx, const double* theta, int64_t P, double
   SPS_CUDA_TRY(dv.reserve(sizeof(double) * D * D));
   SPS_CUDA_TRY(dpart.reserve(sizeof(double) * (T + D) * blocks));
   double* pv = (mem == SPS_MEM_DEVICE) ? V : dv.as<double>();
-  SPS_TRY(launch_cov(ctx, pt, P, D, 1.0, dpart.as<double>(), pv, nullptr));
+  SPS_TRY(launch_cov(ctx, pt, P, D, 1.0, nullptr, dpart.as<double>(), pv, nullptr));
   if (mem == SPS_MEM_HOST)
     SPS_CUDA_TRY(cudaMemcpyAsync(V, pv, sizeof(double) * D * D, cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -1967,13 +2246,13 @@ sps_status sps_rw_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P,
   prior_lp_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
       tmp.theta.as<double>(), P, D, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(), prior_full(ctx),
       tmp.lp.as<double>()); ++ctx->launches;
-  SPS_TRY(factor_proposal(ctx, &tmp, tmp.theta.as<double>(), 1.0, sigma, nullptr, flag_ptr(&tmp, 0)));
-  SPS_TRY(launch_propose(ctx, &tmp, tmp.theta.as<double>(), P, pz, 0, flag_ptr(&tmp, 0), tmp.theta_prop.as<double>(),
-                         tmp.lp_prop.as<double>()));
+  SPS_TRY(factor_proposal(ctx, &tmp, tmp.theta.as<double>(), 1.0, nullptr, sigma, nullptr, flag_ptr(&tmp, 0)));
+  SPS_TRY(launch_propose(ctx, &tmp, tmp.theta.as<double>(), P, pz, 0, nullptr, flag_ptr(&tmp, 0),
+                         tmp.theta_prop.as<double>(), tmp.lp_prop.as<double>()));
   SPS_TRY(loglik_dispatch(ctx, tmp.theta_prop.as<double>(), P, t, tmp.ll_prop.as<double>(), precision));
   accept_kernel<<<static_cast<unsigned>((P + kAccThreads - 1) / kAccThreads), kAccThreads, 0, ctx->stream>>>(
       tmp.theta.as<double>(), tmp.ll.as<double>(), tmp.lp.as<double>(), tmp.theta_prop.as<double>(),
-      tmp.ll_prop.as<double>(), tmp.lp_prop.as<double>(), P, D, pu, 0, 0, flag_ptr(&tmp, 0),
+      tmp.ll_prop.as<double>(), tmp.lp_prop.as<double>(), P, D, pu, 0, 0, nullptr, flag_ptr(&tmp, 0),
       tmp.counters.as<unsigned long long>(), flag_ptr(&tmp, 1), pla, pacc); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   Counters c;

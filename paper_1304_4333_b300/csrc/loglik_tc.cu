@@ -88,9 +88,10 @@ struct TcParams {
   double* partial;     // [n_chunks][nwg][ppad]
   int* flag;           // set to 1 on a timeout
   unsigned long long timeout_ns;
-  // batched models: per particle tile {prefix length, K-slice mask}, or null. Mask bits 0-15: the
-  // 16-wide slices of the Xh / Th / Tl blocks that hold any of the model's columns; bits 16-23:
-  // the number of Xl slices it needs (its continuous columns are a prefix of the Xl block).
+  // batched models: per particle tile {prefix length, K slices}, or null. The K-slice word holds
+  // four 5-bit fields: the 16-wide slices of the Xh / Th / Tl blocks holding any of the model's
+  // columns are [0, ha) and [hb, hc) (bits 0-4, 5-9, 10-14), and the model needs the first hl
+  // slices of the Xl block (bits 15-19; its continuous columns are a prefix of that block).
   const int2* ptile_info;
 };
 
@@ -144,11 +145,12 @@ bool pick_stages(int NC, int BN, int kbx, int kbt, int* stages, int* th_bufs) {
   return false;
 }
 
-// Descriptor of the 16-element K slice starting at element `e` of an operand tile made of
-// 64-element K blocks of `rows` rows each.
-__device__ __forceinline__ uint64_t kslice_desc(uint32_t base, int rows, int e) {
-  return ptx::sdesc_sw128(base + static_cast<uint32_t>((e >> 6) * rows * 128)) +
-         static_cast<uint64_t>(((e & 63) * 2) >> 4);
+// Offset, in the 16-byte units of a descriptor's start address, of the 16-element K slice
+// starting at element `e` of an operand tile made of 64-element K blocks of `rows` rows each:
+// the descriptor of the slice is the tile's descriptor plus this offset (shared-memory addresses
+// stay below 2^18, so the start-address field does not overflow).
+__device__ __forceinline__ uint64_t kslice_off(int rows, int e) {
+  return static_cast<uint64_t>((e >> 6) * rows * 8 + ((e & 63) >> 3));
 }
 
 // BATCH: particle tiles of several nested models (per-tile prefix and K slices in ptile_info);
@@ -299,10 +301,11 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int tile_lo = chunk * prm.chunk_tiles;
         const int tile_hi = item_tile_hi<BN, BATCH>(prm, tile_lo, ptile);
         if (BATCH && tile_hi == tile_lo) continue;
-        // K slices of this item's model (batched models)
+        // K slices of this item's model (batched models): two ranges of Xh slices and a prefix
+        // of Xl slices, 5 bits each
         const uint32_t kinfo = BATCH ? static_cast<uint32_t>(prm.ptile_info[ptile].y) : 0u;
-        const uint32_t hmask = kinfo & 0xFFFFu;
-        const int ksl_item = static_cast<int>(kinfo >> 16);
+        const int ha = static_cast<int>(kinfo & 31u), hb = static_cast<int>((kinfo >> 5) & 31u);
+        const int hc = static_cast<int>((kinfo >> 10) & 31u), hl = static_cast<int>((kinfo >> 15) & 31u);
         if (!ptx::mbar_wait_bounded(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t thb = ptx::smem_u32(smem + L.off_th + tb * L.th_bytes);
@@ -312,32 +315,62 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           if (!ptx::mbar_wait_bounded(&acc_empty[buf], aph ^ 1u, abort_flag, limit)) { ok = false; break; }
           if (!ptx::mbar_wait_bounded(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
           ptx::tc_fence_after();
-          const uint32_t xb = ptx::smem_u32(smem + L.off_x + st * L.x_bytes);
+          const uint64_t dx = ptx::sdesc_sw128(ptx::smem_u32(smem + L.off_x + st * L.x_bytes));
+          // the NC classes accumulate into independent TMEM accumulators: issuing each K slice
+          // for all classes before the next keeps NC dependent MMA chains in flight (an MMA
+          // that accumulates into the result of the previous one waits for it)
+          uint32_t d[NC];
+          uint64_t dt[NC];
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const uint32_t d = tmem_base + static_cast<uint32_t>((buf * NC + c) * BN);
-            const uint32_t tc = thb + static_cast<uint32_t>(c * prm.kbt) * kTileA;
-            if constexpr (!BATCH) {
-              // one model: every K slice (the issuing thread's loop is kept minimal)
-              for (int i = 0; i < prm.ksh; ++i)   // Th_c Xh'
-                ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, 16 * i), idesc, i > 0);
-              for (int i = 0; i < prm.ksh; ++i)   // Tl_c Xh'
-                ptx::mma_bf16(d, kslice_desc(tc, kBM, prm.k16 + 16 * i), kslice_desc(xb, BN, 16 * i), idesc, 1);
-              for (int i = 0; i < prm.ksl; ++i)   // Th_c Xl' over the continuous columns
-                ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, prm.k16 + 16 * i), idesc, 1);
-            } else {
-              // batched models: only the slices holding the item's model's columns
-              uint32_t acc = 0;                   // the first MMA of a tile overwrites the accumulator
-              for (int i = 0; i < prm.ksh; ++i)
-                if ((hmask >> i) & 1u) {
-                  ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, 16 * i), idesc, acc);
-                  acc = 1;
-                }
-              for (int i = 0; i < prm.ksh; ++i)
-                if ((hmask >> i) & 1u)
-                  ptx::mma_bf16(d, kslice_desc(tc, kBM, prm.k16 + 16 * i), kslice_desc(xb, BN, 16 * i), idesc, 1);
-              for (int i = 0; i < ksl_item; ++i)
-                ptx::mma_bf16(d, kslice_desc(tc, kBM, 16 * i), kslice_desc(xb, BN, prm.k16 + 16 * i), idesc, 1);
+            d[c] = tmem_base + static_cast<uint32_t>((buf * NC + c) * BN);
+            dt[c] = ptx::sdesc_sw128(thb + static_cast<uint32_t>(c * prm.kbt) * kTileA);
+          }
+          if constexpr (!BATCH) {
+            for (int i = 0; i < prm.ksh; ++i) {   // Th_c Xh'
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, i > 0);
+            }
+            for (int i = 0; i < prm.ksh; ++i) {   // Tl_c Xh'
+              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(BN, 16 * i);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+            }
+            for (int i = 0; i < prm.ksl; ++i) {   // Th_c Xl' over the continuous columns
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, prm.k16 + 16 * i);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+            }
+          } else {
+            // batched models: the Xh / Th / Tl slices [0, ha) and [hb, hc) holding the item's
+            // model's columns and its hl slices of Xl; the first MMA of a tile overwrites the
+            // accumulator
+            for (int i = 0; i < ha; ++i) {
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, i > 0);
+            }
+            for (int i = hb; i < hc; ++i) {
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
+              const uint32_t acc = (ha > 0 || i > hb) ? 1u : 0u;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, acc);
+            }
+            for (int i = 0; i < ha; ++i) {
+              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(BN, 16 * i);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+            }
+            for (int i = hb; i < hc; ++i) {
+              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(BN, 16 * i);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+            }
+            for (int i = 0; i < hl; ++i) {
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, prm.k16 + 16 * i);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
             }
           }
           issued_any = true;
@@ -883,15 +916,35 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
   // context's encoding holds original column perm[j]; a nested model's columns (original
   // 0..k_m-1) are a prefix of the continuous block and a prefix of the exact block.
   std::vector<int2> ptile_info(static_cast<size_t>(prm.n_ptiles));
+  const int ksh = enc.k16 / 16;
+  if (ksh > 31) return fail(ctx, SPS_ERR_UNSUPPORTED, "batched log-likelihood: too many covariates");
   for (int m = 0; m < M; ++m) {
-    uint32_t hmask = 0;
+    // the slices holding any of the model's columns, written as [0, ha) and [hb, hc): with the
+    // continuous columns first, a nested model's columns are a prefix of the continuous block
+    // and a prefix of the exact block; any other set is widened to [0, ksh) (the theta rows
+    // are zero outside the model's columns, so extra slices only cost time)
+    std::vector<char> used(static_cast<size_t>(ksh), 0);
     int kc_m = 0;
     for (int j = 0; j < ctx->k; ++j)
       if (enc.perm[j] < km[m]) {
-        hmask |= 1u << (j / 16);
+        used[j / 16] = 1;
         if (j < enc.kc) ++kc_m;
       }
-    const uint32_t info = hmask | (static_cast<uint32_t>((kc_m + 15) / 16) << 16);
+    int ha = 0;
+    while (ha < ksh && used[ha]) ++ha;
+    int hb = ha;
+    while (hb < ksh && !used[hb]) ++hb;
+    int hc = hb;
+    while (hc < ksh && used[hc]) ++hc;
+    bool rest = false;
+    for (int i = hc; i < ksh; ++i) rest = rest || used[i];
+    if (rest) {
+      ha = ksh;
+      hb = hc = ksh;
+    }
+    const int hl = (kc_m + 15) / 16;
+    const uint32_t info = static_cast<uint32_t>(ha) | (static_cast<uint32_t>(hb) << 5) |
+                          (static_cast<uint32_t>(hc) << 10) | (static_cast<uint32_t>(hl) << 15);
     const int64_t r0 = tab[m * kTab + 0] / kBM;
     const int64_t r1 = r0 + (Pm[m] + prow - 1) / prow * prow / kBM;
     for (int64_t r = r0; r < r1; ++r) ptile_info[r] = make_int2(static_cast<int>(tm[m]), static_cast<int>(info));

@@ -251,6 +251,24 @@ sps_status sps_loglik_noalloc(sps_ctx* ctx, const double* theta, int64_t P, int6
 sps_status sps_loglik_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, const int64_t* P_models,
                               const int64_t* t_models, const double* theta, double* ll);
 
+/* Tile-shape autotuner of the fused split-precision kernel. Times every candidate launch shape
+ * on P particles at prefix t (1 <= t <= n) with CUDA events: observation rows per tile (the two
+ * widths the outcome count allows, where the pipeline fits shared memory), clusters of one or
+ * two CTAs sharing each X tile, and work items of 512 to 8192 observations. The fastest is kept
+ * in the context and used by every later split-precision call (results change only by the
+ * order of FP32/FP64 partial sums). Each candidate runs 1 untimed and 3 timed launches on zero
+ * particles; the call synchronises the context's stream.
+ *   out (optional): the chosen shape, its time per launch in ms and the candidates tried. */
+typedef struct sps_tune_result {
+  int32_t tile_rows;       /* observations per tile */
+  int32_t cluster;         /* CTAs per cluster */
+  int32_t chunk_obs;       /* observations per work item */
+  int32_t n_candidates;
+  double ms;               /* time per launch of the chosen shape */
+  double ms_default;       /* time per launch of the shape chosen at sps_init */
+} sps_tune_result;
+sps_status sps_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out);
+
 /* Log-likelihood and its gradient d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s
  * (the derivative of Eq. 1; the paper prints no gradient).
  *   grad: [P x D] FP64 output, class-major like theta (mem). FP32 products and residuals,

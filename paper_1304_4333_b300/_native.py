@@ -48,6 +48,11 @@ class SpsResult(C.Structure):
                 ("graph_steps", C.c_int64)]
 
 
+class SpsTuneResult(C.Structure):
+    _fields_ = [("tile_rows", C.c_int32), ("cluster", C.c_int32), ("chunk_obs", C.c_int32),
+                ("n_candidates", C.c_int32), ("ms", C.c_double), ("ms_default", C.c_double)]
+
+
 class SpsMstepInfo(C.Structure):
     _fields_ = [("h", C.c_double), ("accept_rate", C.c_double), ("rne_min", C.c_double), ("h_next", C.c_double)]
 
@@ -85,6 +90,7 @@ SIGNATURES = {
     "sps_resample": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32]),
     "sps_set_prior": (C.c_int, [_P, C.POINTER(SpsPrior)]),
     "sps_loglik_batched": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
+    "sps_autotune": (C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(SpsTuneResult)]),
     "sps_gprior": (C.c_int, [_P, C.c_double, _P, _P]),
     "sps_prior_normalize": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P]),
     "sps_philox": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,

@@ -199,6 +199,14 @@ class Sps:
         self._call("sps_loglik", C.c_void_p(theta_ptr), int(P), t, C.c_void_p(ll_ptr), PRECISIONS[precision],
                    N.MEM_HOST)
 
+    def autotune(self, P: int, t: Optional[int] = None) -> dict:
+        """Time the fused kernel's launch shapes on P particles at prefix t (default n) and keep
+        the fastest for later calls (sps_autotune)."""
+        r = N.SpsTuneResult()
+        self._call("sps_autotune", int(P), int(self.n if t is None else t), C.byref(r))
+        return {"tile_rows": r.tile_rows, "cluster": r.cluster, "chunk_obs": r.chunk_obs,
+                "n_candidates": r.n_candidates, "ms": r.ms, "ms_default": r.ms_default}
+
     def loglik_batched(self, thetas, ks, ts):
         """Log-likelihoods of nested models in one launch (sps_loglik_batched): thetas is a list of
         CUDA float64 tensors [P_m, k_m (C-1)], ks the covariate counts, ts the prefixes. Returns a

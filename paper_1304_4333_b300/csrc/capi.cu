@@ -353,6 +353,13 @@ sps_status sps_loglik_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, 
   return loglik_split_batched(ctx, M, k_models, P_models, t_models, theta, ll);
 }
 
+sps_status sps_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (P < 1 || P > (int64_t{1} << 28) || t < 1 || t > ctx->n)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_autotune: bad P or t");
+  return tc_autotune(ctx, P, t, out);
+}
+
 sps_status sps_set_prior(sps_ctx* ctx, const sps_prior* prior) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
   return apply_prior(ctx, prior);

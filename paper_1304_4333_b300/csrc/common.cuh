@@ -58,6 +58,7 @@ struct XEncoding {
   int cl = 1;                 // CTAs per cluster sharing each X tile (each loads bn / cl rows of
                               // it, multicast to all); the TMA box of X is {64, bn / cl}
   int max_clusters = 0;       // co-resident clusters of the fused kernel at this shape
+  int chunk_obs = 0;          // observations per work item chosen by the autotuner (0: heuristic)
   std::vector<int> perm;      // internal column j holds original column perm[j]
   DevBuf perm_dev;            // int [k]
   DevBuf Xp;                  // bf16 [n x kx]
@@ -218,6 +219,8 @@ int tc_tile_rows(int NC, int kx, int kt);
 // Cluster size of the fused kernel for the context's tile shape (sets enc.cl, enc.max_clusters):
 // 2 when clusters of two fit on the device, else 1; SPS_TC_CLUSTER=1 in the environment forces 1.
 sps_status tc_configure_cluster(sps_ctx* ctx);
+// Tile-shape autotuner (sps_autotune).
+sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out);
 // Start/stop event of one timed launch of the fused kernel (no-ops when timing is off).
 void hot_begin(sps_ctx* ctx);
 void hot_end(sps_ctx* ctx);

@@ -795,7 +795,8 @@ bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t
   // chunking: enough work items to balance the persistent grid, items long enough to amortise
   // the theta loads
   const int grid_max = (enc.cl > 1) ? enc.max_clusters : ctx->num_sms;   // concurrent work items
-  int chunk_tiles = std::max(1, std::min(prm->n_tiles, 4096 / BN));
+  const int chunk_obs = enc.chunk_obs > 0 ? enc.chunk_obs : 4096;   // autotuned, else 4096
+  int chunk_tiles = std::max(1, std::min(prm->n_tiles, chunk_obs / BN));
   const int64_t want_items = 8LL * grid_max;
   while (chunk_tiles > 2 &&
          static_cast<int64_t>(prm->n_pgroups) * ((prm->n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
@@ -827,6 +828,97 @@ int tc_tile_rows(int NC, int kx, int kt) {
   const int BN = cands[NC - 1][1];
   int st = 0, tb = 0;
   return pick_stages(NC, BN, kx / kKB, kt / kKB, &st, &tb) ? BN : 0;
+}
+
+// One launch shape of the fused kernel: tile rows, cluster size (with its co-resident
+// clusters) and work-item length, and the X tensor map for it.
+static sps_status tc_set_shape(sps_ctx* ctx, int bn, int cl, int max_clusters, int chunk_obs) {
+  XEncoding& enc = ctx->enc;
+  enc.bn = bn;
+  enc.cl = cl;
+  enc.max_clusters = max_clusters;
+  enc.chunk_obs = chunk_obs;
+  return make_map_bf16(ctx, &enc.mapX, enc.Xp.ptr, static_cast<uint64_t>(ctx->n), enc.kx,
+                       static_cast<uint32_t>(bn / cl));
+}
+
+sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out) {
+  XEncoding& enc = ctx->enc;
+  const int NC = ctx->NC;
+  if (NC > 3 || enc.bn == 0) return fail(ctx, SPS_ERR_UNSUPPORTED, "autotune: no tensor-core tile for this shape");
+  const int bn0 = enc.bn, cl0 = enc.cl, mc0 = enc.max_clusters, ch0 = enc.chunk_obs;
+  DevBuf th, ll;
+  SPS_CUDA_TRY(th.reserve(sizeof(double) * static_cast<size_t>(P) * ctx->D));
+  SPS_CUDA_TRY(ll.reserve(sizeof(double) * static_cast<size_t>(P)));
+  SPS_CUDA_TRY(cudaMemsetAsync(th.ptr, 0, sizeof(double) * static_cast<size_t>(P) * ctx->D, ctx->stream));
+  cudaEvent_t e0, e1;
+  SPS_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, SPS_ERR_CUDA, "autotune: event");
+  }
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  // time one shape: 1 untimed and 3 timed launches; +inf when it cannot run
+  auto time_shape = [&](int bn, int cl, int mc, int chunk) -> double {
+    if (tc_set_shape(ctx, bn, cl, mc, chunk) != SPS_OK) return INFINITY;
+    if (loglik_split(ctx, th.as<double>(), P, t, ll.as<double>()) != SPS_OK) return INFINITY;
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 3; ++r)
+      if (loglik_split(ctx, th.as<double>(), P, t, ll.as<double>()) != SPS_OK) return INFINITY;
+    cudaEventRecord(e1, ctx->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return INFINITY;
+    return ms / 3.0;
+  };
+  const double ms_default = time_shape(bn0, cl0, mc0, ch0);
+  double best = ms_default;
+  int bb = bn0, bc = cl0, bm = mc0, bk = ch0, tried = 1;
+  const int cands[3][2] = {{256, 128}, {128, 64}, {64, 32}};
+  const char* env = getenv("SPS_TC_CLUSTER");
+  const bool allow_cl2 = !(env && env[0] == '1' && env[1] == 0);
+  for (int q = 0; q < 2; ++q) {
+    const int bn = cands[NC - 1][q];
+    int stages = 0, th_bufs = 0;
+    if (!pick_stages(NC, bn, enc.kx / kKB, enc.kt / kKB, &stages, &th_bufs)) continue;
+    const uint32_t smem_bytes = smem_layout(NC, bn, enc.kx / kKB, enc.kt / kKB, stages, th_bufs).total + 1024;
+    for (int cl = 1; cl <= 2; ++cl) {
+      int mc = 0;
+      if (cl == 2) {
+        if (!allow_cl2) continue;
+        enc.bn = bn;
+        if (run_any(ctx, 2, nullptr, 0, smem_bytes, nullptr, false, &mc) != SPS_OK || mc < 1) continue;
+      }
+      for (int chunk = 512; chunk <= 8192; chunk *= 2) {
+        if (chunk < bn) continue;
+        const double ms = time_shape(bn, cl, mc, chunk);
+        ++tried;
+        if (ms < best) {
+          best = ms;
+          bb = bn;
+          bc = cl;
+          bm = mc;
+          bk = chunk;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->timing = timing;
+  cudaGetLastError();
+  ctx->last_error.clear();
+  SPS_TRY(tc_set_shape(ctx, bb, bc, bm, bk));
+  if (out) {
+    out->tile_rows = bb;
+    out->cluster = bc;
+    out->chunk_obs = bk > 0 ? bk : 4096;
+    out->n_candidates = tried;
+    out->ms = best;
+    out->ms_default = ms_default;
+  }
+  if (!std::isfinite(best)) return fail(ctx, SPS_ERR_CUDA, "autotune: no candidate ran");
+  return SPS_OK;
 }
 
 sps_status tc_configure_cluster(sps_ctx* ctx) {

@@ -210,3 +210,24 @@ def test_batched_c5_sampled(torch_cuda):
         idx = np.array([0, 5, w.J * w.N - 1])
         ref = oracle_loglik(np.ascontiguousarray(w.X[:, :k]), w.y, thetas[m][idx], w.C, w.n)
         np.testing.assert_allclose(got[m].cpu().numpy()[idx], ref, rtol=1e-5)
+
+
+def test_autotune_keeps_parity_and_is_no_slower(torch_cuda):
+    # the autotuner picks a launch shape by timing; results change only by summation order
+    from paper_1304_4333_b300 import Sps
+    g = np.random.Generator(np.random.PCG64(3))
+    X = g.standard_normal((3000, 12))
+    X[:, 0] = 1.0
+    X[:, 8:] = (X[:, 8:] > 0.3).astype(float)
+    y = g.integers(0, 3, 3000).astype(np.int32)
+    s = Sps(X, y, 3, prior_sd=5.0)
+    th = 0.2 * g.standard_normal((700, 24))
+    before = s.loglik(th, 2900)
+    r = s.autotune(700, 2900)
+    assert r["n_candidates"] >= 2
+    assert r["tile_rows"] in (128, 64) and r["cluster"] in (1, 2) and r["chunk_obs"] >= r["tile_rows"]
+    assert r["ms"] <= r["ms_default"] + 1e-9
+    after = s.loglik(th, 2900)
+    ref = oracle_loglik(X, y, th, 3, 2900)
+    assert np.all(np.abs(after - ref) <= _tol(X, th, 3, 2900, ref, "split"))
+    assert np.all(np.abs(before - ref) <= _tol(X, th, 3, 2900, ref, "split"))

@@ -316,6 +316,32 @@ class Sps:
         return th, l, la, acc.astype(bool)
 
     # ------------------------------------------------------------------ simulator
+    def run_batched(self, ks, J: int, N_: int) -> List[RunResult]:
+        """Adaptive SPS for nested models (sps_run_batched): model m uses the first ks[m]
+        covariates; the M phases of all models run in lockstep with one batched log-likelihood
+        launch per step. Returns one RunResult per model (no schedule)."""
+        ks = [int(v) for v in ks]
+        M = len(ks)
+        res = (N.SpsResult * M)()
+        keep = []
+        for m, km in enumerate(ks):
+            dim = km * (self.C - 1) + self.C - 1
+            arrs = {f: np.zeros(dim) for f in ("mean", "sd", "nse", "rne")}
+            lmg = np.zeros(J)
+            for f, a in arrs.items():
+                setattr(res[m], f, a.ctypes.data_as(C.POINTER(C.c_double)))
+            res[m].log_ml_group = lmg.ctypes.data_as(C.POINTER(C.c_double))
+            keep.append((arrs, lmg))
+        kk = np.ascontiguousarray(ks, dtype=np.int32)
+        self._call("sps_run_batched", M, kk.ctypes.data_as(C.c_void_p), J, N_, res)
+        out = []
+        for m in range(M):
+            arrs, lmg = keep[m]
+            r = res[m]
+            out.append(RunResult(arrs["mean"], arrs["sd"], arrs["nse"], arrs["rne"], lmg, r.log_ml, r.log_ml_nse,
+                                 r.log_ml_pooled, r.n_cycles, r.m_steps, r.seconds))
+        return out
+
     def state(self, J: int, N_: int, seed: int = 0) -> "State":
         return State(self, J, N_, seed)
 

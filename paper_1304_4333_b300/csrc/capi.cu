@@ -350,7 +350,16 @@ sps_status sps_loglik_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, 
   for (int m = 0; m < M; ++m)
     if (k_models[m] < 1 || k_models[m] > ctx->k || P_models[m] < 1 || t_models[m] < 0 || t_models[m] > ctx->n)
       return fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik_batched: bad model sizes");
-  return loglik_split_batched(ctx, M, k_models, P_models, t_models, theta, ll);
+  std::vector<const double*> th(M);
+  std::vector<double*> out(M);
+  int64_t thoff = 0, poff = 0;
+  for (int m = 0; m < M; ++m) {
+    th[m] = theta + thoff;
+    out[m] = ll + poff;
+    thoff += P_models[m] * ctx->NC * k_models[m];
+    poff += P_models[m];
+  }
+  return loglik_split_batched(ctx, M, k_models, P_models, t_models, th.data(), out.data());
 }
 
 sps_status sps_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out) {

@@ -207,9 +207,10 @@ sps_status make_map_bf16(sps_ctx* ctx, CUtensorMap* map, const void* base, uint6
 
 // Likelihood launchers (loglik_tc.cu, loglik_simt.cu). Device pointers, context stream.
 sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
-// Batched nested models (see sps_loglik_batched): one fused-kernel launch for all of them.
+// Batched nested models (see sps_loglik_batched): one fused-kernel launch for all of them; model
+// m's particles at device d_theta[m] ([P_m x k_m NC]), its results to d_ll[m] ([P_m]).
 sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
-                                const double* d_theta, double* d_ll);
+                                const double* const* d_theta, double* const* d_ll);
 sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
 sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                            int precision);

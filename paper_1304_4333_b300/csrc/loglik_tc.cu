@@ -578,8 +578,8 @@ loglik_finalize_kernel(const double* __restrict__ theta, int64_t P, int D,
 
 // ---- batched models: M nested models, model m using the first k_m covariates, its particles in
 // its own block of operand rows (row_off_m, padded to the cluster's pair of tiles), zeros beyond
-// k_m. Model table rows (int64): [row_off, P, k, theta_off, particle_off, t].
-constexpr int kTab = 6;
+// k_m. Model table rows (int64): [row_off, P, k, theta address, particle_off, t, ll address].
+constexpr int kTab = 7;
 
 __device__ __forceinline__ int model_of_row(const int64_t* __restrict__ tab, int M, int64_t q) {
   int m = 0;
@@ -592,7 +592,7 @@ __device__ __forceinline__ int model_of_particle(const int64_t* __restrict__ tab
   return m;
 }
 
-__global__ void encode_theta_batched_kernel(const double* __restrict__ theta, const int64_t* __restrict__ tab,
+__global__ void encode_theta_batched_kernel(const int64_t* __restrict__ tab,
                                             int M, int NC, const int* __restrict__ perm, int k16, int kt,
                                             int64_t PP, __nv_bfloat16* __restrict__ out) {
   const int64_t r = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
@@ -604,7 +604,7 @@ __global__ void encode_theta_batched_kernel(const double* __restrict__ theta, co
   const int64_t p = q - tab[m * kTab + 0];
   const int64_t Pm = tab[m * kTab + 1];
   const int km = static_cast<int>(tab[m * kTab + 2]);
-  const double* src = theta + tab[m * kTab + 3] + p * (static_cast<int64_t>(NC) * km) + c * km;
+  const double* src = reinterpret_cast<const double*>(tab[m * kTab + 3]) + p * (static_cast<int64_t>(NC) * km) + c * km;
   __nv_bfloat16* rowp = out + r * kt;
   for (int j = lane; j < k16; j += 32) {
     const int col = perm[j];
@@ -640,16 +640,15 @@ __global__ void lin_tail_batched_kernel(const double* __restrict__ prefix, const
   if (lane == 0) lin[w] = prefix[tile * NC * k + idx] + a;
 }
 
-__global__ void finalize_batched_kernel(const double* __restrict__ theta, const int64_t* __restrict__ tab, int M,
-                                        int NC, int k, int64_t Ptot, const double* __restrict__ lin,
-                                        const double* __restrict__ partial, int slices, int64_t PP,
-                                        double* __restrict__ ll) {
+__global__ void finalize_batched_kernel(const int64_t* __restrict__ tab, int M, int NC, int k, int64_t Ptot,
+                                        const double* __restrict__ lin, const double* __restrict__ partial,
+                                        int slices, int64_t PP) {
   const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (g >= Ptot) return;
   const int m = model_of_particle(tab, M, g);
   const int64_t p = g - tab[m * kTab + 4];
   const int km = static_cast<int>(tab[m * kTab + 2]);
-  const double* th = theta + tab[m * kTab + 3] + p * (static_cast<int64_t>(NC) * km);
+  const double* th = reinterpret_cast<const double*>(tab[m * kTab + 3]) + p * (static_cast<int64_t>(NC) * km);
   const double* lm = lin + static_cast<int64_t>(m) * NC * k;
   double a0 = 0.0, a1 = 0.0;
   for (int c = 0; c < NC; ++c)
@@ -663,7 +662,7 @@ __global__ void finalize_batched_kernel(const double* __restrict__ theta, const 
     if (j & 1) s1 += q[static_cast<size_t>(j) * PP];
     else s0 += q[static_cast<size_t>(j) * PP];
   }
-  ll[g] = (a0 + a1) - (s0 + s1);
+  reinterpret_cast<double*>(tab[m * kTab + 6])[p] = (a0 + a1) - (s0 + s1);
 }
 
 sps_status launch_finalize(sps_ctx* ctx, const double* theta, int64_t P, const double* partial, int slices,
@@ -976,24 +975,24 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
 }
 
 sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
-                                const double* d_theta, double* d_ll) {
+                                const double* const* d_theta, double* const* d_ll) {
   const int NC = ctx->NC;
   if (NC > 3 || ctx->enc.bn == 0) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision: unsupported shape");
   XEncoding& enc = ctx->enc;
   LoglikScratch& S = ctx->ll;
   const int64_t prow = static_cast<int64_t>(kBM) * enc.cl;
   std::vector<int64_t> tab(static_cast<size_t>(M) * kTab);
-  int64_t PP = 0, Ptot = 0, thoff = 0, tmax = 0;
+  int64_t PP = 0, Ptot = 0, tmax = 0;
   for (int m = 0; m < M; ++m) {
     tab[m * kTab + 0] = PP;
     tab[m * kTab + 1] = Pm[m];
     tab[m * kTab + 2] = km[m];
-    tab[m * kTab + 3] = thoff;
+    tab[m * kTab + 3] = static_cast<int64_t>(reinterpret_cast<uintptr_t>(d_theta[m]));
     tab[m * kTab + 4] = Ptot;
     tab[m * kTab + 5] = tm[m];
+    tab[m * kTab + 6] = static_cast<int64_t>(reinterpret_cast<uintptr_t>(d_ll[m]));
     PP += (Pm[m] + prow - 1) / prow * prow;
     Ptot += Pm[m];
-    thoff += Pm[m] * NC * km[m];
     tmax = std::max<int64_t>(tmax, tm[m]);
   }
   if (PP > (int64_t{1} << 28)) return fail(ctx, SPS_ERR_INVALID_ARG, "batched log-likelihood: too many particles");
@@ -1058,7 +1057,7 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
   {
     const int64_t rows = static_cast<int64_t>(NC) * PP;
     encode_theta_batched_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
-        d_theta, dtab, M, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, PP, S.thetaP.as<__nv_bfloat16>());
+        dtab, M, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, PP, S.thetaP.as<__nv_bfloat16>());
     ++ctx->launches;
     const int64_t warps = static_cast<int64_t>(M) * NC * ctx->k;
     lin_tail_batched_kernel<<<static_cast<unsigned>((warps + 3) / 4), 128, 0, ctx->stream>>>(
@@ -1077,8 +1076,8 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
   if (prm.n_items > 0)
     SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));
   finalize_batched_kernel<<<static_cast<unsigned>((Ptot + 255) / 256), 256, 0, ctx->stream>>>(
-      d_theta, dtab, M, NC, ctx->k, Ptot, S.batch_lin.as<double>(), prm.partial,
-      prm.n_items > 0 ? static_cast<int>(slices) : 0, PP, d_ll);
+      dtab, M, NC, ctx->k, Ptot, S.batch_lin.as<double>(), prm.partial,
+      prm.n_items > 0 ? static_cast<int>(slices) : 0, PP);
   ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;

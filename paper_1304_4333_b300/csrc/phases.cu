@@ -1464,15 +1464,45 @@ sps_status mstep_prepare(sps_ctx* ctx, sps_state* st, int kernel) {
 // its Cholesky factor, proposals with the prior log kernel, their log-likelihood (and gradient),
 // the Metropolis decisions, the monitoring sums. With ctl (a captured M phase) h and the Philox
 // step word are read on the device from ctl; otherwise they are h and step.
+// Random-walk step, first half: counters cleared, Sigma and its factor, proposals theta' with
+// their prior log kernel.
+sps_status rw_issue_propose(sps_ctx* ctx, sps_state* st, const double* sigma, double* sigma_used, double h,
+                            uint64_t step, StepCtl* ctl) {
+  SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
+  SPS_TRY(factor_proposal(ctx, st, st->theta.as<double>(), h, ctl ? &ctl->h : nullptr, sigma, sigma_used,
+                          flag_ptr(st, 0)));
+  return launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, ctl ? &ctl->step : nullptr,
+                        flag_ptr(st, 0), st->theta_prop.as<double>(), st->lp_prop.as<double>());
+}
+
+// Random-walk step, second half (after ll_prop holds the proposals' log-likelihoods): the
+// Metropolis decisions and the monitoring sums.
+sps_status rw_issue_accept(sps_ctx* ctx, sps_state* st, uint64_t step, StepCtl* ctl) {
+  accept_kernel<<<static_cast<unsigned>((st->P + kAccThreads - 1) / kAccThreads), kAccThreads, 0, ctx->stream>>>(
+      st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->theta_prop.as<double>(),
+      st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step,
+      ctl ? &ctl->step : nullptr, flag_ptr(st, 0), st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr,
+      nullptr); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  launch_monitoring(ctx, st);
+  return SPS_OK;
+}
+
 sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* sigma, double* sigma_used, double h,
                        uint64_t step, StepCtl* ctl) {
   const int D = ctx->D;
   const bool mala = (kernel == SPS_MKERNEL_MALA);
   const unsigned long long* step_dev = ctl ? &ctl->step : nullptr;
+  if (!mala) {
+    SPS_TRY(rw_issue_propose(ctx, st, sigma, sigma_used, h, step, ctl));
+    SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
+                            ctx->opt.precision));
+    return rw_issue_accept(ctx, st, step, ctl);
+  }
   SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
   SPS_TRY(factor_proposal(ctx, st, st->theta.as<double>(), h, ctl ? &ctl->h : nullptr, sigma, sigma_used,
                           flag_ptr(st, 0)));
-  if (mala) {
+  {
     const int T = D * (D + 1) / 2;
     const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kMalaThreads);
     const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kMalaThreads);
@@ -1497,20 +1527,12 @@ sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* si
         ctx->d_prior_prec.as<double>(), prior_full(ctx), st->seed, step, step_dev, flag_ptr(st, 0),
         st->counters.as<unsigned long long>(), flag_ptr(st, 1)); ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
-  } else {
-    SPS_TRY(launch_propose(ctx, st, st->theta.as<double>(), st->P, nullptr, step, step_dev, flag_ptr(st, 0),
-                           st->theta_prop.as<double>(), st->lp_prop.as<double>()));
-    SPS_TRY(loglik_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
-                            ctx->opt.precision));
-    accept_kernel<<<static_cast<unsigned>((st->P + kAccThreads - 1) / kAccThreads), kAccThreads, 0, ctx->stream>>>(
-        st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->theta_prop.as<double>(),
-        st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->P, ctx->D, nullptr, st->seed, step, step_dev,
-        flag_ptr(st, 0), st->counters.as<unsigned long long>(), flag_ptr(st, 1), nullptr, nullptr); ++ctx->launches;
-    SPS_CUDA_TRY(cudaGetLastError());
   }
   launch_monitoring(ctx, st);
   return SPS_OK;
 }
+
+sps_status mstep_finish(sps_ctx* ctx, sps_state* st, int kernel, double h, bool adapt, sps_mstep_info* info);
 
 // One M step, issued and read back (Algorithm 2 step 2(c)): the acceptance rate drives the
 // step-size rule unless Sigma is given.
@@ -1521,6 +1543,12 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
   const uint64_t step = ++st->step_counter;
   SPS_TRY(mstep_issue(ctx, st, kernel, sigma, sigma_used, h, step, nullptr));
   if (kernel == SPS_MKERNEL_RW) st->grad_valid = false;
+  return mstep_finish(ctx, st, kernel, h, sigma == nullptr, info);
+}
+
+// Read an issued M step back and apply the step-size rule (when adapt): errors of the step,
+// the acceptance rate and the minimum RNE of the monitoring set.
+sps_status mstep_finish(sps_ctx* ctx, sps_state* st, int kernel, double h, bool adapt, sps_mstep_info* info) {
   Counters c;
   double rmin = 0.0;
   SPS_TRY(read_step(ctx, st, &c, &rmin));
@@ -1530,7 +1558,7 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
   const double alpha = static_cast<double>(c.accepts) / static_cast<double>(st->P);
   const sps_options& o = ctx->opt;
   double hn = h;
-  if (!sigma) {
+  if (adapt) {
     const double target = (kernel == SPS_MKERNEL_MALA) ? o.mala_target_accept : o.target_accept;
     hn = (alpha > target) ? std::min(h + o.h_step, o.h_max) : std::max(h - o.h_step, o.h_min);
     st->h = hn;
@@ -1858,6 +1886,50 @@ sps_status mphase_impl(sps_ctx* ctx, sps_state* st, int kernel, int fixed_steps,
   return SPS_OK;
 }
 
+// Outputs of a finished run (Eqs. 3, 5-7, 10 and the log ML): moments of theta and of the
+// log-odds theta_c' xbar (Eq. 15) from the final particles, and the per-group log ML.
+sps_status finish_run(sps_ctx* ctx, sps_state* st, int32_t L, int64_t total_steps, sps_result* out) {
+  const int D = ctx->D;
+  // outputs: moments of theta and of the log-odds theta_c' xbar (Eq. 15), and the log ML
+  const int F = D + ctx->NC;
+  SPS_CUDA_TRY(st->scratch.reserve(sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64));
+  group_moments_kernel<<<dim3(st->J, F, 1), 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
+                                                          ctx->xbar.as<double>(), st->N, D, ctx->k, F, true, false,
+                                                          st->scratch.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> sums(static_cast<size_t>(st->J) * F * 3), lml(st->J);
+  SPS_CUDA_TRY(cudaMemcpyAsync(sums.data(), st->scratch.ptr, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(lml.data(), st->logml.ptr, sizeof(double) * st->J, cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  Moments m = moments_from_sums(sums, st->J, st->N, F);
+  for (int f = 0; f < F; ++f) {
+    out->mean[f] = m.mean[f];
+    out->sd[f] = m.sd[f];
+    out->nse[f] = m.nse[f];
+    out->rne[f] = m.rne[f];
+  }
+  double mean = 0.0, mx = -INFINITY;
+  for (int j = 0; j < st->J; ++j) {
+    out->log_ml_group[j] = lml[j];
+    mean += lml[j];
+    mx = std::max(mx, lml[j]);
+  }
+  mean /= st->J;
+  double var = 0.0, se = 0.0;
+  for (int j = 0; j < st->J; ++j) {
+    var += (lml[j] - mean) * (lml[j] - mean);
+    se += std::exp(lml[j] - mx);
+  }
+  out->log_ml = mean;
+  out->log_ml_nse = std::sqrt(var / (st->J - 1.0)) / std::sqrt(static_cast<double>(st->J));
+  out->log_ml_pooled = mx + std::log(se / st->J);
+  out->n_cycles = L;
+  out->m_steps = total_steps;
+  out->graph_steps = st->graph_steps;
+  return SPS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2036,43 +2108,7 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
     ++L;
   }
   if (record) record->n_cycles = L;
-  // outputs: moments of theta and of the log-odds theta_c' xbar (Eq. 15), and the log ML
-  const int F = D + ctx->NC;
-  SPS_CUDA_TRY(st->scratch.reserve(sizeof(double) * 3 * static_cast<size_t>(st->J) * F + 64));
-  group_moments_kernel<<<dim3(st->J, F, 1), 256, 0, ctx->stream>>>(st->theta.as<double>(), st->ll.as<double>(),
-                                                          ctx->xbar.as<double>(), st->N, D, ctx->k, F, true, false,
-                                                          st->scratch.as<double>()); ++ctx->launches;
-  SPS_CUDA_TRY(cudaGetLastError());
-  std::vector<double> sums(static_cast<size_t>(st->J) * F * 3), lml(st->J);
-  SPS_CUDA_TRY(cudaMemcpyAsync(sums.data(), st->scratch.ptr, sums.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                               ctx->stream));
-  SPS_CUDA_TRY(cudaMemcpyAsync(lml.data(), st->logml.ptr, sizeof(double) * st->J, cudaMemcpyDeviceToHost, ctx->stream));
-  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  Moments m = moments_from_sums(sums, st->J, st->N, F);
-  for (int f = 0; f < F; ++f) {
-    out->mean[f] = m.mean[f];
-    out->sd[f] = m.sd[f];
-    out->nse[f] = m.nse[f];
-    out->rne[f] = m.rne[f];
-  }
-  double mean = 0.0, mx = -INFINITY;
-  for (int j = 0; j < st->J; ++j) {
-    out->log_ml_group[j] = lml[j];
-    mean += lml[j];
-    mx = std::max(mx, lml[j]);
-  }
-  mean /= st->J;
-  double var = 0.0, se = 0.0;
-  for (int j = 0; j < st->J; ++j) {
-    var += (lml[j] - mean) * (lml[j] - mean);
-    se += std::exp(lml[j] - mx);
-  }
-  out->log_ml = mean;
-  out->log_ml_nse = std::sqrt(var / (st->J - 1.0)) / std::sqrt(static_cast<double>(st->J));
-  out->log_ml_pooled = mx + std::log(se / st->J);
-  out->n_cycles = L;
-  out->m_steps = total_steps;
-  out->graph_steps = st->graph_steps;
+  SPS_TRY(finish_run(ctx, st, L, total_steps, out));
   if (want_lpl)
     for (int64_t q = 0; q < ctx->n; ++q) {
       const double* row = lpl.data() + q * groups;
@@ -2085,6 +2121,175 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
       if (out->log_pred_nse) out->log_pred_nse[q] = std::sqrt(v / (groups - 1.0)) / std::sqrt(static_cast<double>(groups));
     }
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return SPS_OK;
+}
+
+sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, int32_t groups,
+                           int32_t particles_per_group, sps_result* out) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (M < 1 || M > 1024 || !k_models || !out) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_run_batched: bad arguments");
+  for (int m = 0; m < M; ++m) {
+    if (k_models[m] < 1 || k_models[m] > ctx->k)
+      return fail(ctx, SPS_ERR_INVALID_ARG, "sps_run_batched: model covariate count out of range");
+    const sps_result& o = out[m];
+    if (!o.mean || !o.sd || !o.nse || !o.rne || !o.log_ml_group)
+      return fail(ctx, SPS_ERR_INVALID_ARG, "sps_run_batched: result arrays missing");
+  }
+  if (ctx->opt.mkernel != SPS_MKERNEL_RW)
+    return fail(ctx, SPS_ERR_UNSUPPORTED, "sps_run_batched: the lockstep M phase uses the random-walk kernel");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = ctx->n;
+  const int k = ctx->k, NC = ctx->NC, D = ctx->D;
+  // the data on the host once, to build each model's context
+  std::vector<double> X(static_cast<size_t>(n) * k);
+  std::vector<int32_t> y(static_cast<size_t>(n));
+  SPS_CUDA_TRY(cudaMemcpyAsync(X.data(), ctx->Xd.ptr, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(y.data(), ctx->y.ptr, sizeof(int32_t) * y.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  struct Model {
+    sps_ctx* c = nullptr;
+    sps_state* st = nullptr;
+    int32_t L = 0;
+    int64_t steps = 0;
+  };
+  struct Models {
+    std::vector<Model> v;
+    ~Models() {
+      for (Model& m : v) {
+        sps_state_destroy(m.st);
+        sps_destroy(m.c);
+      }
+    }
+  } models;
+  models.v.resize(M);
+  // the sub-context's last error becomes the caller's
+  auto pass = [&](sps_ctx* c, sps_status st) {
+    ctx->last_error = std::string("model context: ") + c->last_error;
+    return st;
+  };
+  for (int m = 0; m < M; ++m) {
+    const int km = k_models[m], Dm = km * NC;
+    std::vector<double> Xm(static_cast<size_t>(n) * km);
+    for (int64_t s = 0; s < n; ++s)
+      for (int i = 0; i < km; ++i) Xm[s * km + i] = X[s * k + i];
+    // prior of the model's coordinates (theta_c, i < k_m): the marginal of the context's prior
+    std::vector<int> idx;
+    for (int c = 0; c < NC; ++c)
+      for (int i = 0; i < km; ++i) idx.push_back(c * k + i);
+    std::vector<double> mu(Dm), cov;
+    for (int a = 0; a < Dm; ++a) mu[a] = ctx->prior_mean[idx[a]];
+    sps_prior pr{};
+    if (ctx->prior_kind == SPS_PRIOR_FULL) {
+      cov.resize(static_cast<size_t>(Dm) * Dm);
+      for (int a = 0; a < Dm; ++a)
+        for (int b = 0; b < Dm; ++b) cov[a * Dm + b] = ctx->prior_cov[static_cast<size_t>(idx[a]) * D + idx[b]];
+      pr.kind = SPS_PRIOR_FULL;
+    } else {
+      cov.resize(Dm);
+      for (int a = 0; a < Dm; ++a) cov[a] = std::sqrt(ctx->prior_cov[static_cast<size_t>(idx[a]) * D + idx[a]]);
+      pr.kind = SPS_PRIOR_DIAG;
+    }
+    pr.mean = mu.data();
+    pr.cov_or_sd = cov.data();
+    sps_options o = ctx->opt;
+    o.graphs = 0;
+    const sps_status si = sps_init(&models.v[m].c, Xm.data(), n, km, y.data(), ctx->C, &pr, &o);
+    if (si != SPS_OK) {
+      if (models.v[m].c) return pass(models.v[m].c, si);
+      return fail(ctx, si, "sps_run_batched: model context");
+    }
+    sps_ctx* c = models.v[m].c;
+    c->stream = ctx->stream;
+    const uint64_t seed = ctx->opt.seed + 0x9E3779B97F4A7C15ull * static_cast<uint64_t>(m + 1);
+    const sps_status ss = sps_state_create(c, groups, particles_per_group, seed, &models.v[m].st);
+    if (ss != SPS_OK) return pass(c, ss);
+  }
+  const bool split = (ctx->opt.precision == SPS_PREC_SPLIT);
+  // log-likelihoods of the listed models' particles (theta or the proposals) at their own t:
+  // one batched fused-kernel launch on the context's encoding (split precision), else one
+  // FP32 launch per model
+  std::vector<int32_t> bk;
+  std::vector<int64_t> bP, bt;
+  std::vector<const double*> bth;
+  std::vector<double*> bll;
+  auto evaluate = [&](const std::vector<int>& list, bool proposals) -> sps_status {
+    if (list.empty()) return SPS_OK;
+    bk.clear(); bP.clear(); bt.clear(); bth.clear(); bll.clear();
+    for (int m : list) {
+      sps_state* st = models.v[m].st;
+      bk.push_back(k_models[m]);
+      bP.push_back(st->P);
+      bt.push_back(st->t);
+      bth.push_back(proposals ? st->theta_prop.as<double>() : st->theta.as<double>());
+      bll.push_back(proposals ? st->ll_prop.as<double>() : st->ll.as<double>());
+    }
+    if (split)
+      return loglik_split_batched(ctx, static_cast<int>(list.size()), bk.data(), bP.data(), bt.data(), bth.data(),
+                                  bll.data());
+    for (size_t q = 0; q < list.size(); ++q) {
+      sps_ctx* c = models.v[list[q]].c;
+      const sps_status e = loglik_fp32(c, bth[q], bP[q], bt[q], bll[q]);
+      if (e != SPS_OK) return pass(c, e);
+    }
+    return SPS_OK;
+  };
+  const sps_options& o = ctx->opt;
+  while (true) {
+    std::vector<int> active;
+    for (int m = 0; m < M; ++m)
+      if (models.v[m].st->t < n) active.push_back(m);
+    if (active.empty()) break;
+    // C and S phases per model (Algorithm 1 steps 2(a), 2(b))
+    for (int m : active) {
+      Model& md = models.v[m];
+      int64_t tn = 0;
+      sps_status e = cphase_impl(md.c, md.st, 0, &tn, nullptr, nullptr, nullptr);
+      if (e == SPS_OK) e = sphase_impl(md.c, md.st, nullptr, nullptr);
+      if (e != SPS_OK) return pass(md.c, e);
+      ++md.L;
+    }
+    // M phases in lockstep (Algorithm 2 step 2(c)): every step of the models still moving is
+    // one batched evaluation of their proposals; a model leaves when its RNE criterion or the
+    // step cap is met
+    SPS_TRY(evaluate(active, false));   // cached log-likelihoods with the proposals' function
+    for (int m : active) {
+      models.v[m].st->ll_stale = false;
+      models.v[m].st->ll_kind = split ? 0 : 1;
+    }
+    std::vector<int> run = active, r(M, 0);
+    std::vector<double> hs(M);
+    std::vector<uint64_t> steps(M);
+    while (!run.empty()) {
+      for (int m : run) {
+        Model& md = models.v[m];
+        hs[m] = md.st->h;
+        steps[m] = ++md.st->step_counter;
+        const sps_status e = rw_issue_propose(md.c, md.st, nullptr, nullptr, hs[m], steps[m], nullptr);
+        if (e != SPS_OK) return pass(md.c, e);
+      }
+      SPS_TRY(evaluate(run, true));
+      std::vector<int> next;
+      for (int m : run) {
+        Model& md = models.v[m];
+        sps_status e = rw_issue_accept(md.c, md.st, steps[m], nullptr);
+        sps_mstep_info info{};
+        if (e == SPS_OK) e = mstep_finish(md.c, md.st, SPS_MKERNEL_RW, hs[m], true, &info);
+        if (e != SPS_OK) return pass(md.c, e);
+        md.st->grad_valid = false;
+        ++r[m];
+        const double K = (md.st->t >= n) ? o.rne_final : o.rne_cycle;
+        if (!(info.rne_min >= K || r[m] >= o.r_max)) next.push_back(m);
+      }
+      run.swap(next);
+    }
+    for (int m : active) models.v[m].steps += r[m];
+  }
+  for (int m = 0; m < M; ++m) {
+    Model& md = models.v[m];
+    const sps_status e = finish_run(md.c, md.st, md.L, md.steps, &out[m]);
+    if (e != SPS_OK) return pass(md.c, e);
+    out[m].seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
   return SPS_OK;
 }
 

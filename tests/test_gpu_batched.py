@@ -1,0 +1,78 @@
+"""Batched model comparison (sps_run_batched): nested models of one data set run through the
+simulator together, their M phases in lockstep with one batched log-likelihood launch per step.
+Each model must behave as its own run of Algorithm 2: the log marginal likelihood and the
+posterior moments agree with separate runs on X[:, :k_m] within the Monte Carlo error, and the
+exact special case X = 0 gives log ML = -n log C for every model."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _nested_case(n=400, k=5, C=2, seed=4):
+    g = np.random.Generator(np.random.PCG64(seed))
+    X = g.standard_normal((n, k))
+    X[:, 0] = 1.0
+    X[:, 3:] = (X[:, 3:] > 0.2).astype(float)     # exact 0/1 columns after continuous ones
+    beta = np.zeros((k, C))
+    beta[:3, 1:] = 0.8 * g.standard_normal((3, C - 1))
+    eta = X @ beta
+    p = np.exp(eta - eta.max(axis=1, keepdims=True))
+    p /= p.sum(axis=1, keepdims=True)
+    y = np.array([g.choice(C, p=row) for row in p], dtype=np.int32)
+    return X, y
+
+
+def test_zero_covariates_every_model_exact(cuda):
+    from paper_1304_4333_b300 import Sps
+    n, C = 60, 3
+    X = np.zeros((n, 4))
+    y = np.random.Generator(np.random.PCG64(1)).integers(0, C, n).astype(np.int32)
+    s = Sps(X, y, C, prior_sd=5.0, seed=3)
+    rs = s.run_batched([1, 2, 4], 8, 256)
+    for r in rs:
+        assert r.n_cycles == 1
+        assert r.log_ml == pytest.approx(-n * math.log(C), abs=1e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("C,prec", [(2, "split"), (3, "split"), (2, "fp32")])
+def test_batched_agrees_with_separate_runs(cuda, C, prec):
+    from paper_1304_4333_b300 import Sps
+    X, y = _nested_case(C=C)
+    ks = [2, 3, 5]
+    s = Sps(X, y, C, prior_sd=5.0, seed=7, precision=prec)
+    rb = s.run_batched(ks, 16, 512)
+    s.close()
+    for km, r in zip(ks, rb):
+        s1 = Sps(np.ascontiguousarray(X[:, :km]), y, C, prior_sd=5.0, seed=100 + km, precision=prec)
+        r1 = s1.run(16, 512, record=False)
+        s1.close()
+        comb = math.hypot(r.log_ml_nse, r1.log_ml_nse)
+        assert abs(r.log_ml - r1.log_ml) < 4 * max(comb, 1e-3), (km, r.log_ml, r1.log_ml, comb)
+        D = km * (C - 1)
+        z = (r.mean[:D] - r1.mean[:D]) / np.hypot(r.nse[:D], r1.nse[:D])
+        assert np.all(np.abs(z) < 5), (km, z)
+        np.testing.assert_allclose(r.sd[:D], r1.sd[:D], rtol=0.2)
+        assert r.m_steps >= r.n_cycles >= 1
+
+
+def test_batched_rejects_bad_models(cuda):
+    from paper_1304_4333_b300 import Sps, SpsError
+    X, y = _nested_case()
+    s = Sps(X, y, 2, prior_sd=5.0)
+    with pytest.raises(SpsError):
+        s.run_batched([0, 2], 4, 64)
+    with pytest.raises(SpsError):
+        s.run_batched([6], 4, 64)
+    s.close()

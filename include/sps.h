@@ -342,18 +342,23 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
 
 /* Batched model comparison: the adaptive simulator (Algorithm 2, random-walk M kernel) for M
  * nested models of the context's data at once, model m using the first k_models[m] covariates
- * (1 <= k_m <= k) with J groups x N particles, the context's options, and as prior the marginal
- * of the context's prior on its coordinates (theta_c,i for i < k_m). Each model has its own
+ * (1 <= k_m <= k) with J groups x N particles and the context's options. Prior of model m: with
+ * g > 0 the paper's g-prior for its own covariates (Sec. 3.1, Eq. 18, as sps_gprior); else the
+ * marginal of the context's prior on its coordinates (theta_c,i for i < k_m). (A diffuse prior
+ * on many coordinates can leave fewer distinct particles than parameters after the first S
+ * phase; the step then fails with SPS_ERR_DEGENERATE, as the paper notes in Sec. 4.) Each model has its own
  * particles, C and S phases and step size (a context of its own, built from the context's data,
  * on the context's stream, with the Philox key options.seed + m-dependent offset). Their M
- * phases run in lockstep: every M step of the models still moving evaluates all their
- * proposals, each at its model's t, with one batched fused-kernel launch
- * (sps_loglik_batched; FP32 precision: one launch per model), and the cached log-likelihoods
- * after each S phase come from the same function. Marginal likelihoods for comparing the
+ * phases run in lockstep: in every M step the proposals of all models still moving are
+ * evaluated, each at its model's t, those of the models too small to fill the GPU alone (fewer
+ * than two waves of work items at their t) with one batched fused-kernel launch
+ * (sps_loglik_batched), the others with their own launches; the choice is fixed for each M
+ * phase and the cached log-likelihoods at its start come from the same function (FP32
+ * precision: one launch per model). Marginal likelihoods for comparing the
  * models (Sec. 2.3) are in out[m].log_ml.
  *   out: [M] caller-allocated results as for sps_run (log_pred ignored, graph_steps 0).
  * SPS_ERR_UNSUPPORTED for the MALA kernel; a model's error is returned with its message. */
-sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, int32_t groups,
+sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, double g, int32_t groups,
                            int32_t particles_per_group, sps_result* out);
 
 /* ------------------------------------------------------------------ building blocks */

@@ -91,7 +91,7 @@ SIGNATURES = {
     "sps_set_prior": (C.c_int, [_P, C.POINTER(SpsPrior)]),
     "sps_loglik_batched": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
     "sps_autotune": (C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(SpsTuneResult)]),
-    "sps_run_batched": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, C.POINTER(SpsResult)]),
+    "sps_run_batched": (C.c_int, [_P, C.c_int32, _P, C.c_double, C.c_int32, C.c_int32, C.POINTER(SpsResult)]),
     "sps_gprior": (C.c_int, [_P, C.c_double, _P, _P]),
     "sps_prior_normalize": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P]),
     "sps_philox": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,

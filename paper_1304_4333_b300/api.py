@@ -316,10 +316,11 @@ class Sps:
         return th, l, la, acc.astype(bool)
 
     # ------------------------------------------------------------------ simulator
-    def run_batched(self, ks, J: int, N_: int) -> List[RunResult]:
+    def run_batched(self, ks, J: int, N_: int, g: Optional[float] = None) -> List[RunResult]:
         """Adaptive SPS for nested models (sps_run_batched): model m uses the first ks[m]
-        covariates; the M phases of all models run in lockstep with one batched log-likelihood
-        launch per step. Returns one RunResult per model (no schedule)."""
+        covariates, with the paper's g-prior of its covariates when g is given (else the marginal
+        of the context's prior); the M phases of all models run in lockstep with one batched
+        log-likelihood launch per step. Returns one RunResult per model (no schedule)."""
         ks = [int(v) for v in ks]
         M = len(ks)
         res = (N.SpsResult * M)()
@@ -333,7 +334,7 @@ class Sps:
             res[m].log_ml_group = lmg.ctypes.data_as(C.POINTER(C.c_double))
             keep.append((arrs, lmg))
         kk = np.ascontiguousarray(ks, dtype=np.int32)
-        self._call("sps_run_batched", M, kk.ctypes.data_as(C.c_void_p), J, N_, res)
+        self._call("sps_run_batched", M, kk.ctypes.data_as(C.c_void_p), float(g or 0.0), J, N_, res)
         out = []
         for m in range(M):
             arrs, lmg = keep[m]

@@ -188,6 +188,8 @@ struct sps_state {
   int64_t mgraph_launches = 0;    // kernels of one captured step (control kernel included)
   sps::DevBuf ctl;                // StepCtl
   sps::DevBuf steplog;            // FP64 [r_max x 3]: h, acceptance rate, min RNE of each step
+  void* pinned = nullptr;         // page-locked host copy of an M step's counters and sums
+  size_t pinned_bytes = 0;
   sps::DevBuf sigmalog;           // FP64 [r_max x D x D]: Sigma of each step (recorded schedules)
   int64_t graph_steps = 0;        // M steps run inside captured graphs
 };
@@ -220,6 +222,9 @@ int tc_tile_rows(int NC, int kx, int kt);
 // Cluster size of the fused kernel for the context's tile shape (sets enc.cl, enc.max_clusters):
 // 2 when clusters of two fit on the device, else 1; SPS_TC_CLUSTER=1 in the environment forces 1.
 sps_status tc_configure_cluster(sps_ctx* ctx);
+// Waves of work items of one split-precision call of P particles at prefix t on the persistent
+// grid (work items / items run at once); 0 when the context has no tensor-core tile.
+double tc_waves(const sps_ctx* ctx, int64_t P, int64_t t);
 // Tile-shape autotuner (sps_autotune).
 sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out);
 // Start/stop event of one timed launch of the fused kernel (no-ops when timing is off).

@@ -814,6 +814,14 @@ bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t
 
 }  // namespace
 
+double tc_waves(const sps_ctx* ctx, int64_t P, int64_t t) {
+  TcParams prm;
+  uint32_t smem = 0;
+  if (ctx->enc.bn == 0 || !plan_call(ctx, P, t, &prm, &smem)) return 0.0;
+  const int conc = (ctx->enc.cl > 1) ? ctx->enc.max_clusters : ctx->num_sms;
+  return static_cast<double>(prm.n_items) / std::max(1, conc);
+}
+
 // Observation rows per tensor-core tile: the widest tile for the outcome count that keeps at
 // least three X stages in shared memory (0 when none fits).
 int tc_tile_rows(int NC, int kx, int kt) {

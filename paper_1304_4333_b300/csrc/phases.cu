@@ -1416,19 +1416,36 @@ void launch_monitoring(sps_ctx* ctx, sps_state* st) {
   ++ctx->launches;
 }
 
-sps_status read_step(sps_ctx* ctx, sps_state* st, Counters* c, double* rne_min) {
-  const int F = 1 + ctx->NC;
-  std::vector<double> parts(static_cast<size_t>(st->J) * F * kMomParts * 3);
+// An M step's counters and monitoring sums, copied to the state's page-locked host buffer
+// (enqueued; readback_result reads them after the stream has synchronised).
+sps_status readback_issue(sps_ctx* ctx, sps_state* st) {
+  const size_t n_parts = static_cast<size_t>(st->J) * (1 + ctx->NC) * kMomParts * 3;
+  const size_t bytes = sizeof(Counters) + n_parts * sizeof(double);
+  if (st->pinned_bytes < bytes) {
+    if (st->pinned) cudaFreeHost(st->pinned);
+    st->pinned = nullptr;
+    st->pinned_bytes = 0;
+    SPS_CUDA_TRY(cudaMallocHost(&st->pinned, bytes));
+    st->pinned_bytes = bytes;
+  }
   SPS_CUDA_TRY(cudaGetLastError());
-  SPS_CUDA_TRY(cudaMemcpyAsync(parts.data(), st->scratch.ptr, parts.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                               ctx->stream));
-  SPS_CUDA_TRY(cudaMemcpyAsync(c, st->counters.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
-  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  char* h = static_cast<char*>(st->pinned);
+  SPS_CUDA_TRY(cudaMemcpyAsync(h, st->counters.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(h + sizeof(Counters), st->scratch.ptr, n_parts * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  return SPS_OK;
+}
+
+void readback_result(sps_ctx* ctx, const sps_state* st, Counters* c, double* rne_min) {
+  const int F = 1 + ctx->NC;
+  const char* h = static_cast<const char*>(st->pinned);
+  std::memcpy(c, h, sizeof(Counters));
+  const double* p = reinterpret_cast<const double*>(h + sizeof(Counters));
+  const std::vector<double> parts(p, p + static_cast<size_t>(st->J) * F * kMomParts * 3);
   Moments m = moments_from_sums(reduce_parts(parts, st->J, F, kMomParts), st->J, st->N, F);
   double r = INFINITY;
   for (double v : m.rne) r = std::min(r, v);
   *rne_min = r;
-  return SPS_OK;
 }
 
 // Before an M step: the cached log-likelihood (and, for MALA, its gradient) recomputed with the
@@ -1533,6 +1550,7 @@ sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* si
 }
 
 sps_status mstep_finish(sps_ctx* ctx, sps_state* st, int kernel, double h, bool adapt, sps_mstep_info* info);
+sps_status mstep_rule(sps_ctx* ctx, sps_state* st, int kernel, double h, bool adapt, sps_mstep_info* info);
 
 // One M step, issued and read back (Algorithm 2 step 2(c)): the acceptance rate drives the
 // step-size rule unless Sigma is given.
@@ -1549,9 +1567,16 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
 // Read an issued M step back and apply the step-size rule (when adapt): errors of the step,
 // the acceptance rate and the minimum RNE of the monitoring set.
 sps_status mstep_finish(sps_ctx* ctx, sps_state* st, int kernel, double h, bool adapt, sps_mstep_info* info) {
+  SPS_TRY(readback_issue(ctx, st));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return mstep_rule(ctx, st, kernel, h, adapt, info);
+}
+
+// The step-size rule from a read-back step (after readback_issue and a synchronisation).
+sps_status mstep_rule(sps_ctx* ctx, sps_state* st, int kernel, double h, bool adapt, sps_mstep_info* info) {
   Counters c;
   double rmin = 0.0;
-  SPS_TRY(read_step(ctx, st, &c, &rmin));
+  readback_result(ctx, st, &c, &rmin);
   if (c.chol_bad)
     return fail(ctx, SPS_ERR_DEGENERATE, "proposal covariance h V is not positive definite");
   if (c.nonfinite) return fail(ctx, SPS_ERR_NONFINITE, "non-finite log-likelihood of a proposal");
@@ -1980,6 +2005,7 @@ void sps_state_destroy(sps_state* st) {
   if (!st) return;
   if (st->ctx) cudaStreamSynchronize(st->ctx->stream);
   if (st->mgraph) cudaGraphExecDestroy(st->mgraph);
+  if (st->pinned) cudaFreeHost(st->pinned);
   delete st;
 }
 
@@ -2124,7 +2150,7 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group, co
   return SPS_OK;
 }
 
-sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, int32_t groups,
+sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, double g, int32_t groups,
                            int32_t particles_per_group, sps_result* out) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
   if (M < 1 || M > 1024 || !k_models || !out) return fail(ctx, SPS_ERR_INVALID_ARG, "sps_run_batched: bad arguments");
@@ -2200,38 +2226,55 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, int
     }
     sps_ctx* c = models.v[m].c;
     c->stream = ctx->stream;
+    if (g > 0.0) {
+      // the paper's g-prior of this model's covariates
+      std::vector<double> gm(Dm), gc(static_cast<size_t>(Dm) * Dm);
+      sps_status e = sps_gprior(c, g, gm.data(), gc.data());
+      sps_prior pg{};
+      pg.kind = SPS_PRIOR_FULL;
+      pg.mean = gm.data();
+      pg.cov_or_sd = gc.data();
+      if (e == SPS_OK) e = sps_set_prior(c, &pg);
+      if (e != SPS_OK) return pass(c, e);
+    }
     const uint64_t seed = ctx->opt.seed + 0x9E3779B97F4A7C15ull * static_cast<uint64_t>(m + 1);
     const sps_status ss = sps_state_create(c, groups, particles_per_group, seed, &models.v[m].st);
     if (ss != SPS_OK) return pass(c, ss);
   }
   const bool split = (ctx->opt.precision == SPS_PREC_SPLIT);
-  // log-likelihoods of the listed models' particles (theta or the proposals) at their own t:
-  // one batched fused-kernel launch on the context's encoding (split precision), else one
-  // FP32 launch per model
+  // Which function evaluates a model's log-likelihoods in the current M phase (fixed for the
+  // phase, so that both sides of every Metropolis ratio use the same one): in split precision
+  // the batched fused-kernel launch on the context's encoding for the models that alone would
+  // fill fewer than kBatchWaves waves of the persistent grid (small t: batching fills the
+  // GPU), else the model's own launch with its own encoding (large t: each fills the GPU, and
+  // its own tile shape is faster); FP32 precision: the model's own FP32 launch.
+  constexpr double kBatchWaves = 2.0;
+  std::vector<char> in_batch(M, 0);
   std::vector<int32_t> bk;
   std::vector<int64_t> bP, bt;
   std::vector<const double*> bth;
   std::vector<double*> bll;
   auto evaluate = [&](const std::vector<int>& list, bool proposals) -> sps_status {
-    if (list.empty()) return SPS_OK;
     bk.clear(); bP.clear(); bt.clear(); bth.clear(); bll.clear();
     for (int m : list) {
       sps_state* st = models.v[m].st;
-      bk.push_back(k_models[m]);
-      bP.push_back(st->P);
-      bt.push_back(st->t);
-      bth.push_back(proposals ? st->theta_prop.as<double>() : st->theta.as<double>());
-      bll.push_back(proposals ? st->ll_prop.as<double>() : st->ll.as<double>());
+      const double* th = proposals ? st->theta_prop.as<double>() : st->theta.as<double>();
+      double* ll = proposals ? st->ll_prop.as<double>() : st->ll.as<double>();
+      if (in_batch[m]) {
+        bk.push_back(k_models[m]);
+        bP.push_back(st->P);
+        bt.push_back(st->t);
+        bth.push_back(th);
+        bll.push_back(ll);
+      } else {
+        sps_ctx* c = models.v[m].c;
+        const sps_status e = loglik_dispatch(c, th, st->P, st->t, ll, ctx->opt.precision);
+        if (e != SPS_OK) return pass(c, e);
+      }
     }
-    if (split)
-      return loglik_split_batched(ctx, static_cast<int>(list.size()), bk.data(), bP.data(), bt.data(), bth.data(),
-                                  bll.data());
-    for (size_t q = 0; q < list.size(); ++q) {
-      sps_ctx* c = models.v[list[q]].c;
-      const sps_status e = loglik_fp32(c, bth[q], bP[q], bt[q], bll[q]);
-      if (e != SPS_OK) return pass(c, e);
-    }
-    return SPS_OK;
+    if (bk.empty()) return SPS_OK;
+    return loglik_split_batched(ctx, static_cast<int>(bk.size()), bk.data(), bP.data(), bt.data(), bth.data(),
+                                bll.data());
   };
   const sps_options& o = ctx->opt;
   while (true) {
@@ -2251,6 +2294,10 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, int
     // M phases in lockstep (Algorithm 2 step 2(c)): every step of the models still moving is
     // one batched evaluation of their proposals; a model leaves when its RNE criterion or the
     // step cap is met
+    for (int m : active) {
+      sps_state* st = models.v[m].st;
+      in_batch[m] = split && tc_waves(models.v[m].c, st->P, st->t) < kBatchWaves;
+    }
     SPS_TRY(evaluate(active, false));   // cached log-likelihoods with the proposals' function
     for (int m : active) {
       models.v[m].st->ll_stale = false;
@@ -2268,12 +2315,19 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, int
         if (e != SPS_OK) return pass(md.c, e);
       }
       SPS_TRY(evaluate(run, true));
-      std::vector<int> next;
+      // every model's decisions and read-back enqueued, then one synchronisation
       for (int m : run) {
         Model& md = models.v[m];
         sps_status e = rw_issue_accept(md.c, md.st, steps[m], nullptr);
+        if (e == SPS_OK) e = readback_issue(md.c, md.st);
+        if (e != SPS_OK) return pass(md.c, e);
+      }
+      SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      std::vector<int> next;
+      for (int m : run) {
+        Model& md = models.v[m];
         sps_mstep_info info{};
-        if (e == SPS_OK) e = mstep_finish(md.c, md.st, SPS_MKERNEL_RW, hs[m], true, &info);
+        const sps_status e = mstep_rule(md.c, md.st, SPS_MKERNEL_RW, hs[m], true, &info);
         if (e != SPS_OK) return pass(md.c, e);
         md.st->grad_valid = false;
         ++r[m];

@@ -76,3 +76,21 @@ def test_batched_rejects_bad_models(cuda):
     with pytest.raises(SpsError):
         s.run_batched([6], 4, 64)
     s.close()
+
+
+def test_batched_gprior_matches_separate_gprior_runs(cuda):
+    # with g > 0 each model gets the g-prior of its own covariates, as sps_gprior + sps_set_prior
+    from paper_1304_4333_b300 import Sps
+    X, y = _nested_case(C=3, seed=8)
+    ks = [2, 4]
+    s = Sps(X, y, 3, prior_sd=5.0, seed=9)
+    rb = s.run_batched(ks, 16, 512, g=0.25)
+    s.close()
+    for km, r in zip(ks, rb):
+        s1 = Sps(np.ascontiguousarray(X[:, :km]), y, 3, prior_sd=5.0, seed=50 + km)
+        gm, gc = s1.gprior(0.25)
+        s1.set_prior(prior_mean=gm, prior_cov=gc)
+        r1 = s1.run(16, 512, record=False)
+        s1.close()
+        comb = math.hypot(r.log_ml_nse, r1.log_ml_nse)
+        assert abs(r.log_ml - r1.log_ml) < 4 * max(comb, 1e-3), (km, r.log_ml, r1.log_ml, comb)

@@ -226,7 +226,7 @@ def run_ours(args, world, rank, local):
     lib = s.lib
     lib.sps_set_stream(s.ctx, C.c_void_p(stream.cuda_stream))
     st = s.state(w.J, w.N, seed=100 + rank)
-    t0 = n - C_BLOCK * (warm + steps)
+    t0 = n - C_BLOCK * (warm + steps + (1 if args.ncu_step else 0))
     theta0 = synthetic.particles_around(w.theta_true, P, 0.05, seed=2)
     st.set(theta0, None, t0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -244,6 +244,18 @@ def run_ours(args, world, rank, local):
         st.sphase()
         st.mstep(kernel=args.mkernel)
     torch.cuda.synchronize()
+    if args.ncu_step:
+        # one more step inside a profiler range: `ncu --profile-from-start off` captures exactly
+        # the kernels of one step (C phase, S phase, M step)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        st.cphase(st.get_t() + C_BLOCK)
+        st.sphase()
+        st.mstep(kernel=args.mkernel)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     counters(reset=1)
     lib.sps_set_timing(s.ctx, 1)
     units = 0
@@ -392,6 +404,8 @@ def main():
                     help="M kernel of the timed step (MALA evaluates through the gradient kernel)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sps", action="store_true", help="skip the whole-simulator wall-time runs")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="run one extra step after warm-up inside a CUDA profiler range (for ncu --profile-from-start off)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     args = ap.parse_args()

@@ -382,51 +382,74 @@ grad_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const float*
     for (int c = 0; c < NC; ++c)
 #pragma unroll
       for (int i = 0; i < KMAX; ++i) gt[c][i] = 0.f;
-    float tile = 0.f;
+    // log-sum-exp arguments z_j = e^-m + sum_c e^(eta_c - m) (in [1, C]) multiplied over 8
+    // observations before one logarithm; m = max(0, eta_c)
+    float tile = 0.f, zprod = 1.f;
     for (int j = 0; j < ns; ++j) {
-      float eta[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) eta[c] = 0.f;
+      float xr[KMAX];
 #pragma unroll
       for (int i = 0; i < KMAX; i += 4) {
         const float4 xv = *reinterpret_cast<const float4*>(&xs[j][i]);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          eta[c] = fmaf(th[c][i], xv.x, eta[c]);
-          eta[c] = fmaf(th[c][i + 1], xv.y, eta[c]);
-          eta[c] = fmaf(th[c][i + 2], xv.z, eta[c]);
-          eta[c] = fmaf(th[c][i + 3], xv.w, eta[c]);
-        }
+        xr[i] = xv.x;
+        xr[i + 1] = xv.y;
+        xr[i + 2] = xv.z;
+        xr[i + 3] = xv.w;
       }
-      float m = 0.f;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) m = fmaxf(m, eta[c]);
-      float pr[NC];
-      float z = expf(-m);
+      float eta[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        pr[c] = expf(eta[c] - m);
-        z += pr[c];
-      }
-      const float inv = 1.f / z;
-      const int yo = ys[j];
-      float obs = 0.f;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) obs = (yo == c + 1) ? eta[c] : obs;
-      tile += obs - (m + logf(z));
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float r = ((yo == c + 1) ? 1.f : 0.f) - pr[c] * inv;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;   // four chains for the FMA latency
 #pragma unroll
         for (int i = 0; i < KMAX; i += 4) {
-          const float4 xv = *reinterpret_cast<const float4*>(&xs[j][i]);
-          gt[c][i] = fmaf(r, xv.x, gt[c][i]);
-          gt[c][i + 1] = fmaf(r, xv.y, gt[c][i + 1]);
-          gt[c][i + 2] = fmaf(r, xv.z, gt[c][i + 2]);
-          gt[c][i + 3] = fmaf(r, xv.w, gt[c][i + 3]);
+          a0 = fmaf(th[c][i], xr[i], a0);
+          a1 = fmaf(th[c][i + 1], xr[i + 1], a1);
+          a2 = fmaf(th[c][i + 2], xr[i + 2], a2);
+          a3 = fmaf(th[c][i + 3], xr[i + 3], a3);
+        }
+        eta[c] = (a0 + a1) + (a2 + a3);
+      }
+      const int yo = ys[j];
+      float r[NC];
+      float obs = 0.f, m;
+      if constexpr (NC == 1) {
+        // p = sigmoid(eta) from e = e^-|eta|; z = 1 + e, m = max(eta, 0)
+        const float e = __expf(-fabsf(eta[0]));
+        const float inv = __fdividef(1.f, 1.f + e);
+        const float pr = eta[0] >= 0.f ? inv : e * inv;
+        m = fmaxf(eta[0], 0.f);
+        zprod *= 1.f + e;
+        r[0] = ((yo == 1) ? 1.f : 0.f) - pr;
+        obs = (yo == 1) ? eta[0] : 0.f;
+      } else {
+        m = 0.f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) m = fmaxf(m, eta[c]);
+        float pr[NC];
+        float z = __expf(-m);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          pr[c] = __expf(eta[c] - m);
+          z += pr[c];
+        }
+        const float inv = __fdividef(1.f, z);
+        zprod *= z;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          r[c] = ((yo == c + 1) ? 1.f : 0.f) - pr[c] * inv;
+          obs = (yo == c + 1) ? eta[c] : obs;
         }
       }
+      tile += obs - m;
+      if ((j & 7) == 7) {
+        tile -= logf(zprod);
+        zprod = 1.f;
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < KMAX; ++i) gt[c][i] = fmaf(r[c], xr[i], gt[c][i]);
     }
+    tile -= logf(zprod);
     acc += f32_to_f64(tile);
 #pragma unroll
     for (int c = 0; c < NC; ++c)

@@ -685,6 +685,8 @@ __global__ void cov_final_kernel(const double* __restrict__ partial, int blocks,
 // one Newton reciprocal square root, the scaled column copied to a separate buffer, and the
 // trailing update spread over all threads by triangle entry (about two independent FMAs per
 // thread for D = 30). On failure (pivot not positive, or outside (1e-37, 1e37)) sets *flag.
+// (A one-warp register variant for D <= 32 ran at 58 us against 35 us at D = 30: masked lanes
+// still occupy the FP64 pipe, about 1.5 FMA per clock per SM on this GPU.)
 // Writes L in FP64 (full, zero upper part) and the packed lower triangle in FP32.
 __device__ __forceinline__ int tri(int i, int k) { return i * (i + 1) / 2 + k; }
 
@@ -774,12 +776,15 @@ __device__ __forceinline__ void unstage_rows(double* __restrict__ dst, int64_t p
   }
 }
 
-constexpr int kPropThreads = 64;   // particles per block
+constexpr int kPropPart = 64;   // particles per block
+constexpr int kPropSub = 4;     // threads per particle: the rows of L z are split among them
 
 // theta' = theta + L z (L packed lower triangle FP32; z FP32 normals from Philox, or given FP64),
 // plus the prior log kernel of theta'. The block's theta rows go through shared memory (coalesced
-// reads and writes); each thread updates its own row there. Skipped when the factorisation failed.
-__global__ void __launch_bounds__(kPropThreads)
+// reads and writes); the four threads of a particle update every fourth row of it (each row's
+// dot product in the order j = 0..i), then the first of them evaluates the prior log kernel of
+// the new row in the order of prior_log_kernel. Skipped when the factorisation failed.
+__global__ void __launch_bounds__(kPropPart * kPropSub)
 propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __restrict__ L32,
                const double* __restrict__ z_given, uint64_t seed, uint64_t step_arg,
                const unsigned long long* __restrict__ step_dev, const double* __restrict__ mu,
@@ -791,9 +796,9 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
   const int T = D * (D + 1) / 2;
   const int Dp = D | 1;
   double* rows = pd;                                                  // [64][Dp]
-  float* Ls = reinterpret_cast<float*>(rows + kPropThreads * Dp);     // [T]
+  float* Ls = reinterpret_cast<float*>(rows + kPropPart * Dp);        // [T]
   float* zs = Ls + ((T + 3) & ~3);                                    // [D][64]
-  float* mus = zs + D * kPropThreads;                                 // [D] f32(mu), [D] f32(prec)
+  float* mus = zs + D * kPropPart;                                    // [D] f32(mu), [D] f32(prec)
   float* prs = mus + D;
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
   if (!full)
@@ -801,47 +806,71 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
       mus[i] = f64_to_f32(mu[i]);
       prs[i] = f64_to_f32(prec[i]);
     }
-  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kPropThreads;
-  const int np = static_cast<int>(P - p0 < kPropThreads ? P - p0 : kPropThreads);
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kPropPart;
+  const int np = static_cast<int>(P - p0 < kPropPart ? P - p0 : kPropPart);
   stage_rows(th, p0, np, D, Dp, rows);
-  const int64_t p = p0 + threadIdx.x;
-  const bool live = p < P;
-  if (live) {
-    if (z_given) {
-      for (int d = 0; d < D; ++d) zs[d * kPropThreads + threadIdx.x] = static_cast<float>(z_given[p * D + d]);
-    } else {
-      const int per = (D + 3) / 4;
-      for (int q = 0; q < per; ++q) {
-        const uint4 r = draw(seed, static_cast<uint32_t>(p * per + q), kStreamPropose, step);
-        const float2 a = normals2(r.x, r.y), b = normals2(r.z, r.w);
-        const float v[4] = {a.x, a.y, b.x, b.y};
-        for (int u = 0; u < 4; ++u)
-          if (4 * q + u < D) zs[(4 * q + u) * kPropThreads + threadIdx.x] = v[u];
-      }
+  if (z_given) {
+    for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
+      const int pp = q / D, d = q - pp * D;
+      zs[d * kPropPart + pp] = static_cast<float>(z_given[(p0 + pp) * D + d]);
+    }
+  } else {
+    // draw (particle p, word q) as before: counter p * ceil(D / 4) + q
+    const int per = (D + 3) / 4;
+    for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
+      const int pp = q / per, qq = q - pp * per;
+      const uint4 r = draw(seed, static_cast<uint32_t>((p0 + pp) * per + qq), kStreamPropose, step);
+      const float2 a = normals2(r.x, r.y), b = normals2(r.z, r.w);
+      const float v[4] = {a.x, a.y, b.x, b.y};
+      for (int u = 0; u < 4; ++u)
+        if (4 * qq + u < D) zs[(4 * qq + u) * kPropPart + pp] = v[u];
     }
   }
   __syncthreads();
-  if (live) {
-    double* row = rows + threadIdx.x * Dp;
-    float a = 0.f;   // diagonal prior: the arithmetic of prior_log_kernel, on the new row
-    for (int i = 0; i < D; ++i) {
+  const int pp = threadIdx.x / kPropSub, sub = threadIdx.x - pp * kPropSub;
+  const bool live = pp < np;
+  double* row = rows + pp * Dp;
+  if (live)
+    for (int i = sub; i < D; i += kPropSub) {
       const float* Li = Ls + i * (i + 1) / 2;
       float dlt = 0.f;
-      for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], zs[j * kPropThreads + threadIdx.x], dlt);
-      const double v = row[i] + f32_to_f64(dlt);
-      row[i] = v;
-      if (!full) {
-        const float d = f64_to_f32(v) - mus[i];
+      for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], zs[j * kPropPart + pp], dlt);
+      row[i] = row[i] + f32_to_f64(dlt);
+    }
+  __syncwarp();   // a particle's four threads are consecutive lanes of one warp
+  if (live && sub == 0) {
+    double lp;
+    if (full) {
+      lp = prior_log_kernel(row, mu, prec, D, full);
+    } else {
+      float a = 0.f;   // diagonal prior: the arithmetic of prior_log_kernel
+      for (int i = 0; i < D; ++i) {
+        const float d = f64_to_f32(row[i]) - mus[i];
         a = fmaf(d * d, prs[i], a);
       }
+      lp = -0.5 * f32_to_f64(a);
     }
-    lp_o[p] = full ? prior_log_kernel(row, mu, prec, D, full) : -0.5 * f32_to_f64(a);
+    lp_o[p0 + pp] = lp;
   }
   __syncthreads();
   unstage_rows(th_o, p0, np, D, Dp, rows);
 }
 
 constexpr int kAccThreads = 256;
+
+// log u < la for u in [0, 1), decided as in FP64: la >= 0 always accepts; otherwise an FP32
+// logarithm (error below 1e-5 for u >= 1e-30) decides unless it lies within 1e-5 + 1e-6 |la| of
+// la, when the FP64 logarithm does.
+__device__ __forceinline__ bool log_u_below(double u, double la) {
+  if (la >= 0.0) return true;
+  if (u >= 1e-30) {
+    const double lf = static_cast<double>(logf(static_cast<float>(u)));
+    const double margin = 1e-5 + 1e-6 * fabs(la);
+    if (lf < la - margin) return true;
+    if (lf > la + margin) return false;
+  }
+  return log(u) < la;
+}
 
 // Metropolis accept (Algorithm 2 step 2(c)i): log alpha = ll' - ll + lp' - lp, accept when
 // log u < log alpha; the block then copies its accepted rows into the state element by element
@@ -870,7 +899,7 @@ accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restri
       const uint4 r = draw(seed, static_cast<uint32_t>(p), kStreamAccept, step);
       u = uniform53(r.x, r.y);
     }
-    acc = log(u) < la;
+    acc = log_u_below(u, la);
     if (acc) {
       ll[p] = lpp;
       lp[p] = lp_p[p];
@@ -1318,8 +1347,8 @@ static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_t
 
 static size_t propose_smem(int D) {
   const int T = D * (D + 1) / 2;
-  return sizeof(double) * kPropThreads * static_cast<size_t>(D | 1) +
-         sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kPropThreads + 2 * static_cast<size_t>(D));
+  return sizeof(double) * kPropPart * static_cast<size_t>(D | 1) +
+         sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kPropPart + 2 * static_cast<size_t>(D));
 }
 
 static sps_status launch_propose(sps_ctx* ctx, sps_state* st, const double* d_theta, int64_t P, const double* z,
@@ -1330,7 +1359,7 @@ static sps_status launch_propose(sps_ctx* ctx, sps_state* st, const double* d_th
   SPS_CUDA_TRY(cudaFuncSetAttribute(propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
-  propose_kernel<<<static_cast<unsigned>((P + kPropThreads - 1) / kPropThreads), kPropThreads, smem, ctx->stream>>>(
+  propose_kernel<<<static_cast<unsigned>((P + kPropPart - 1) / kPropPart), kPropPart * kPropSub, smem, ctx->stream>>>(
       d_theta, P, D, L32, z, st->seed, step, step_dev, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(),
       prior_full(ctx), d_flag, th_o, lp_o); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());

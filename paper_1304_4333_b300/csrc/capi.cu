@@ -601,14 +601,14 @@ extern "C" sps_status sps_loglik_grad(sps_ctx* ctx, const double* theta, int64_t
   if (!ctx) return SPS_ERR_INVALID_ARG;
   if (!theta || !ll || !grad || P < 1 || t < 0 || t > ctx->n || P > (1LL << 28))
     return fail(ctx, SPS_ERR_INVALID_ARG, "sps_loglik_grad: bad arguments");
-  if (mem == SPS_MEM_DEVICE) return loglik_grad_fp32(ctx, theta, P, t, ll, grad);
+  if (mem == SPS_MEM_DEVICE) return loglik_grad_dispatch(ctx, theta, P, t, ll, grad);
   LoglikScratch& S = ctx->ll;
   const size_t tb = static_cast<size_t>(P) * ctx->D * sizeof(double);
   SPS_CUDA_TRY(S.theta_in.reserve(tb));
   SPS_CUDA_TRY(S.ll_out.reserve(P * sizeof(double)));
   SPS_CUDA_TRY(S.grad_out.reserve(tb));
   SPS_CUDA_TRY(cudaMemcpyAsync(S.theta_in.ptr, theta, tb, cudaMemcpyHostToDevice, ctx->stream));
-  SPS_TRY(loglik_grad_fp32(ctx, S.theta_in.as<double>(), P, t, S.ll_out.as<double>(), S.grad_out.as<double>()));
+  SPS_TRY(loglik_grad_dispatch(ctx, S.theta_in.as<double>(), P, t, S.ll_out.as<double>(), S.grad_out.as<double>()));
   SPS_CUDA_TRY(cudaMemcpyAsync(ll, S.ll_out.ptr, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA_TRY(cudaMemcpyAsync(grad, S.grad_out.ptr, tb, cudaMemcpyDeviceToHost, ctx->stream));
   SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));

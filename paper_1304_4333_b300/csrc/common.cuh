@@ -61,6 +61,7 @@ struct XEncoding {
   int chunk_obs = 0;          // observations per work item chosen by the autotuner (0: heuristic)
   std::vector<int> perm;      // internal column j holds original column perm[j]
   DevBuf perm_dev;            // int [k]
+  DevBuf invperm_dev;         // int [k]: internal column of original column i (gradient kernel)
   DevBuf Xp;                  // bf16 [n x kx]
   CUtensorMap mapX;
 };
@@ -73,7 +74,10 @@ struct LoglikScratch {
   DevBuf partial;             // FP64 partial sums [slices x Ppad]
   DevBuf flag;                // int error/timeout flag
   DevBuf theta_in, ll_out, grad_out, aux;   // staging for host-memory calls
-  DevBuf batch_tab;           // int64 [M x 6] model table of a batched call
+  DevBuf batch_tab;           // int64 [M x 7] model table of a batched call
+  DevBuf gpartial;            // FP32 [n_chunks x Ppad x NC ng] gradient partial sums (tensor cores)
+  CUtensorMap mapXg;          // X tiles of the gradient kernel (box rows mapXg_rows)
+  int mapXg_rows = 0;
   DevBuf batch_ptile_t;       // int2 [n_ptiles] prefix length and K-slice mask of each particle tile
   DevBuf batch_lin;           // FP64 [M x NC x k] linear terms of the models
 };
@@ -235,6 +239,13 @@ void hot_end(sps_ctx* ctx);
 sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
                              int64_t s_hi, const float2* d_lw_in, float2* d_lw);
 // Log-likelihood and gradient (FP32 products, FP64 sums across 32-observation tiles).
+// Log-likelihood and gradient with the tensor cores (split precision; C - 1 <= 2 and covariate
+// widths whose gradient accumulators fit TMEM); SPS_ERR_UNSUPPORTED otherwise, nothing launched.
+sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll, double* d_grad);
+// The context's gradient function: tensor cores in split precision where supported, else the
+// FP32 SIMT kernel. Deterministic for a context and shape.
+sps_status loglik_grad_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
+                                double* d_grad);
 sps_status loglik_grad_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                             double* d_grad);
 

@@ -665,6 +665,488 @@ __global__ void finalize_batched_kernel(const int64_t* __restrict__ tab, int M, 
   reinterpret_cast<double*>(tab[m * kTab + 6])[p] = (a0 + a1) - (s0 + s1);
 }
 
+// ============================================================== log-likelihood and gradient
+// The gradient of Eq. 1, G_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s (the paper prints none), as
+// a second tensor-core contraction. Write q_{s,c} = p_{s,c} - 1/2 for C = 2 (the linear part of
+// the C = 2 log-likelihood uses y - 1/2) and q_{s,c} = p_{s,c} for C > 2; then G_c = lin_c(t) -
+// sum_s q_{s,c} x_s with lin the same prefix sums as the log-likelihood. Per tile of 128
+// particles x BN observations the forward MMAs give u = eta log2 e in TMEM (as in
+// loglik_tc_kernel); the epilogue forms the log-likelihood terms and q, writes q as BF16 hi + lo
+// tiles into shared memory (K-major, 128-byte swizzle: the A operand of the second MMA), and the
+// MMA thread accumulates D_c[particle, j] += sum_obs q x_j with the X tile already in shared
+// memory as the B operand read MN-major (N = the covariate columns [Xh | Xl], K = observations).
+// D stays in TMEM across the tiles of a work item (gch chains per class, by K slice) and is
+// written once per item as FP32 partials.
+constexpr int kGradWarps = 10;   // producer, MMA issuer, two epilogue groups of four warps
+constexpr int kGradThreads = 32 * kGradWarps;
+constexpr uint32_t kGradTmemOff = 256;   // gradient accumulators from this TMEM column
+
+struct GradParams {
+  int t, ppad, n_ptiles, n_tiles, chunk_tiles, n_chunks, n_items;
+  int kbx, kbt, k16, ksh, ksl, th_row_stride;
+  int stages, th_bufs, nq;   // X stages, theta buffers, q buffers
+  int ng;                    // gradient columns per class: k16 + kc16 ([Xh | Xl] of a row)
+  int gch;                   // accumulator chains per class (K slices alternate between them)
+  double* partial;           // [n_chunks][2][ppad] log-likelihood partial sums
+  float* gpartial;           // [n_chunks][ppad][NC ng] gradient partial sums
+  int* flag;
+  unsigned long long timeout_ns;
+};
+
+struct GradLayout {
+  uint32_t x_bytes, th_bytes, q_bytes;
+  uint32_t off_x, off_th, off_q, off_bar, total;
+};
+
+// X stages first, so that the operand reads of the second MMA stay inside the allocation
+__host__ __device__ inline GradLayout grad_layout(int NC, int BN, int kbx, int kbt, int stages, int th_bufs,
+                                                  int nq) {
+  GradLayout L;
+  L.x_bytes = static_cast<uint32_t>(kbx) * static_cast<uint32_t>(BN) * 128u;
+  L.th_bytes = static_cast<uint32_t>(NC * kbt) * kTileA;
+  L.q_bytes = static_cast<uint32_t>(NC * 2 * (BN / 64)) * kTileA;   // [class][hi, lo][K block]
+  L.off_x = 0;
+  L.off_th = L.off_x + stages * L.x_bytes;
+  L.off_q = L.off_th + th_bufs * L.th_bytes;
+  L.off_bar = L.off_q + nq * L.q_bytes;
+  // x_full[st], x_empty[st], th_full[2], th_empty[2], acc_full[2], acc_empty[2], q_full[2],
+  // q_empty[2], g_full, g_empty, drain; then tmem base and abort flag
+  L.total = L.off_bar + 8 * (2 * stages + 12 + 3) + 16;
+  return L;
+}
+
+// Descriptor of an MN-major operand tile written by TMA with 128-byte swizzle: 64-element rows
+// of 128 bytes along N, consecutive K rows 128 bytes apart in 1024-byte 8-row atoms (stride
+// byte offset), the next 64 N elements lbo bytes further (leading byte offset).
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(2u) << 61;
+  return d;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+               : "memory");
+}
+
+// bf16(a) in the low and bf16(b) in the high 16 bits (round to nearest even), one instruction
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+
+template <int NC, int BN>
+__global__ void __launch_bounds__(kGradThreads, 1)
+grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
+               const GradParams prm) {
+  static_assert(BN == 64 || BN == 128, "q tiles are whole 64-observation swizzle rows");
+  constexpr int NBUF = 2;
+  static_assert(NBUF * NC * BN <= static_cast<int>(kGradTmemOff), "forward accumulators below the gradient ones");
+  constexpr int NCH = BN / 32;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const GradLayout L = grad_layout(NC, BN, prm.kbx, prm.kbt, prm.stages, prm.th_bufs, prm.nq);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  uint64_t* x_full = bars;
+  uint64_t* x_empty = x_full + prm.stages;
+  uint64_t* th_full = x_empty + prm.stages;
+  uint64_t* th_empty = th_full + 2;
+  uint64_t* acc_full = th_empty + 2;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* q_full = acc_empty + 2;
+  uint64_t* q_empty = q_full + 2;
+  uint64_t* g_full = q_empty + 2;
+  uint64_t* g_empty = g_full + 1;
+  uint64_t* drain = g_empty + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < prm.stages; ++i) {
+      ptx::mbar_init(&x_full[i], 1);
+      ptx::mbar_init(&x_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&th_full[i], 1);
+      ptx::mbar_init(&th_empty[i], 1);
+      ptx::mbar_init(&acc_full[i], 1);
+      ptx::mbar_init(&acc_empty[i], 4);   // the four warps of the owning group
+      ptx::mbar_init(&q_full[i], 4);
+      ptx::mbar_init(&q_empty[i], 1);
+    }
+    ptx::mbar_init(g_full, 1);
+    ptx::mbar_init(g_empty, 4);            // the four warps of group 0
+    ptx::mbar_init(drain, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_holder, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  const uint64_t limit = prm.timeout_ns;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      ptx::prefetch_map(&mapX);
+      ptx::prefetch_map(&mapT);
+      int st = 0, tb = 0;
+      uint32_t xph = 0, tph = 0;
+      bool ok = true;
+      uint32_t issued_x = 0, issued_t = 0, par_x = 0, par_t = 0;
+      for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
+        const int chunk = item / prm.n_ptiles;
+        const int ptile = item - chunk * prm.n_ptiles;
+        const int tile_lo = chunk * prm.chunk_tiles;
+        const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
+        if (!ptx::mbar_wait_bounded(&th_empty[tb], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
+        uint8_t* thb = smem + L.off_th + tb * L.th_bytes;
+        ptx::mbar_arrive_expect_tx(&th_full[tb], L.th_bytes);
+        for (int c = 0; c < NC; ++c) {
+          const int row = c * prm.th_row_stride + ptile * kBM;
+          for (int kb = 0; kb < prm.kbt; ++kb)
+            ptx::tma_load_2d(thb + (c * prm.kbt + kb) * kTileA, &mapT, &th_full[tb], kb * kKB, row);
+        }
+        issued_t |= 1u << tb;
+        par_t = (par_t & ~(1u << tb)) | (tph << tb);
+        if (++tb == prm.th_bufs) { tb = 0; tph ^= 1u; }
+        for (int tile = tile_lo; tile < tile_hi; ++tile) {
+          if (!ptx::mbar_wait_bounded(&x_empty[st], xph ^ 1u, abort_flag, limit)) { ok = false; break; }
+          uint8_t* xb = smem + L.off_x + st * L.x_bytes;
+          ptx::mbar_arrive_expect_tx(&x_full[st], L.x_bytes);
+          for (int kb = 0; kb < prm.kbx; ++kb)
+            ptx::tma_load_2d(xb + kb * BN * 128, &mapX, &x_full[st], kb * kKB, tile * BN);
+          issued_x |= 1u << st;
+          par_x = (par_x & ~(1u << st)) | (xph << st);
+          if (++st == prm.stages) { st = 0; xph ^= 1u; }
+        }
+      }
+      volatile int no_abort = 0;
+      if (*abort_flag) {
+        for (int s = 0; s < prm.stages; ++s)
+          if (issued_x & (1u << s)) ptx::mbar_wait_bounded(&x_full[s], (par_x >> s) & 1u, &no_abort, limit);
+        for (int b = 0; b < 2; ++b)
+          if (issued_t & (1u << b)) ptx::mbar_wait_bounded(&th_full[b], (par_t >> b) & 1u, &no_abort, limit);
+      } else {
+        for (int s = 0; s < prm.stages; ++s)
+          if (issued_x & (1u << s)) ptx::mbar_wait_bounded(&x_empty[s], (par_x >> s) & 1u, abort_flag, limit);
+        for (int b = 0; b < 2; ++b)
+          if (issued_t & (1u << b)) ptx::mbar_wait_bounded(&th_empty[b], (par_t >> b) & 1u, abort_flag, limit);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc_f = ptx::idesc_bf16_f32(kBM, BN);
+      const uint32_t idesc_g = ptx::idesc_bf16_f32(kBM, prm.ng) | (1u << 16);   // B MN-major
+      const uint32_t lbo = static_cast<uint32_t>(BN) * 128u;
+      int st = 0, tb = 0;
+      uint32_t xph = 0, tph = 0, acc_count = 0, item_count = 0;
+      bool ok = true, issued_any = false;
+      for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
+        const int chunk = item / prm.n_ptiles;
+        const int tile_lo = chunk * prm.chunk_tiles;
+        const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
+        if (!ptx::mbar_wait_bounded(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t thb = ptx::smem_u32(smem + L.off_th + tb * L.th_bytes);
+        uint64_t dt[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) dt[c] = ptx::sdesc_sw128(thb + static_cast<uint32_t>(c * prm.kbt) * kTileA);
+        bool first_grad = true;
+        int pend_st = -1;
+        uint32_t pend_count = 0;
+        // the gradient MMAs of tile `count` (X stage `xs`), then release the stage and q buffer
+        auto gradient = [&](int xs, uint32_t count) -> bool {
+          const int qb = static_cast<int>(count % static_cast<uint32_t>(prm.nq));
+          const uint32_t qph = (count / static_cast<uint32_t>(prm.nq)) & 1u;
+          if (!ptx::mbar_wait_bounded(&q_full[qb], qph, abort_flag, limit)) return false;
+          if (first_grad && !ptx::mbar_wait_bounded(g_empty, (item_count & 1u) ^ 1u, abort_flag, limit))
+            return false;
+          ptx::tc_fence_after();
+          const uint32_t xs_addr = ptx::smem_u32(smem + L.off_x + xs * L.x_bytes);
+          const uint32_t qbase = ptx::smem_u32(smem + L.off_q + qb * L.q_bytes);
+          for (int s = 0; s < BN / 16; ++s) {
+            const int ch = s % prm.gch;
+            const uint64_t bx = sdesc_sw128_mn(xs_addr + static_cast<uint32_t>(s) * 2048u, lbo);
+            const uint64_t ka = kslice_off(kBM, 16 * s);
+            const uint32_t acc = (first_grad && s < prm.gch) ? 0u : 1u;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              const uint32_t dg = tmem_base + kGradTmemOff + static_cast<uint32_t>((c * prm.gch + ch) * prm.ng);
+              const uint64_t ah = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 0) * (BN / 64)) * kTileA);
+              const uint64_t al = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 1) * (BN / 64)) * kTileA);
+              ptx::mma_bf16(dg, ah + ka, bx, idesc_g, acc);
+              ptx::mma_bf16(dg, al + ka, bx, idesc_g, 1u);
+            }
+          }
+          first_grad = false;
+          ptx::mma_commit(&x_empty[xs]);
+          ptx::mma_commit(&q_empty[qb]);
+          return true;
+        };
+        for (int tile = tile_lo; tile < tile_hi; ++tile) {
+          const int buf = static_cast<int>(acc_count & 1u);
+          const uint32_t aph = (acc_count >> 1) & 1u;
+          if (!ptx::mbar_wait_bounded(&acc_empty[buf], aph ^ 1u, abort_flag, limit)) { ok = false; break; }
+          if (!ptx::mbar_wait_bounded(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint64_t dx = ptx::sdesc_sw128(ptx::smem_u32(smem + L.off_x + st * L.x_bytes));
+          uint32_t d[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) d[c] = tmem_base + static_cast<uint32_t>((buf * NC + c) * BN);
+          for (int i = 0; i < prm.ksh; ++i) {   // Th_c Xh'
+            const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc_f, i > 0);
+          }
+          for (int i = 0; i < prm.ksh; ++i) {   // Tl_c Xh'
+            const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(BN, 16 * i);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc_f, 1);
+          }
+          for (int i = 0; i < prm.ksl; ++i) {   // Th_c Xl'
+            const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, prm.k16 + 16 * i);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc_f, 1);
+          }
+          issued_any = true;
+          ptx::mma_commit(&acc_full[buf]);
+          // the previous tile's q is being (or has been) written: its gradient MMAs go next, so
+          // this tile's forward MMAs overlap that tile's epilogue
+          if (pend_st >= 0 && !gradient(pend_st, pend_count)) { ok = false; break; }
+          pend_st = st;
+          pend_count = acc_count;
+          ++acc_count;
+          if (++st == prm.stages) { st = 0; xph ^= 1u; }
+        }
+        if (ok && pend_st >= 0 && !gradient(pend_st, pend_count)) ok = false;
+        if (!ok) break;
+        ptx::mma_commit(g_full);
+        ptx::mma_commit(&th_empty[tb]);
+        ++item_count;
+        if (++tb == prm.th_bufs) { tb = 0; tph ^= 1u; }
+      }
+      if (*abort_flag && issued_any) {
+        ptx::mma_commit(drain);
+        volatile int no_abort = 0;
+        ptx::mbar_wait_bounded(drain, 0, &no_abort, limit);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int wg = (warp - 2) >> 2;                   // group: tiles with acc_count % 2 == wg
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;                 // particle within the tile
+    const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
+    constexpr float kLn2 = 0.6931471805599453f;
+    uint32_t acc_base = 0, item_count = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
+      const int chunk = item / prm.n_ptiles;
+      const int ptile = item - chunk * prm.n_ptiles;
+      const int tile_lo = chunk * prm.chunk_tiles;
+      const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
+      float ksum = 0.f, kcomp = 0.f;
+      const int first = tile_lo + static_cast<int>((static_cast<uint32_t>(wg) + 2u - (acc_base & 1u)) & 1u);
+      for (int tile = first; tile < tile_hi; tile += 2) {
+        const uint32_t acc_count = acc_base + static_cast<uint32_t>(tile - tile_lo);
+        const int buf = static_cast<int>(acc_count & 1u);
+        const uint32_t aph = (acc_count >> 1) & 1u;
+        const int qb = static_cast<int>(acc_count % static_cast<uint32_t>(prm.nq));
+        const uint32_t qph = (acc_count / static_cast<uint32_t>(prm.nq)) & 1u;
+        ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit) &&
+                                         ptx::mbar_wait_bounded(&q_empty[qb], qph ^ 1u, abort_flag, limit));
+        if (!ok) break;
+        ptx::tc_fence_after();
+        const int valid = prm.t - tile * BN;          // columns of this tile inside [0, t)
+        const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN);
+        const uint32_t qrow = ptx::smem_u32(smem + L.off_q + qb * L.q_bytes) + static_cast<uint32_t>(row) * 128u;
+        float la[4] = {0.f, 0.f, 0.f, 0.f};
+        float pr[4] = {1.f, 1.f, 1.f, 1.f};
+        int pexp = 0;
+#pragma unroll 1
+        for (int ch = 0; ch < NCH; ++ch) {
+          float v[NC][32];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
+          ptx::tmem_wait_ld();
+          if (ch == NCH - 1) {
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
+          }
+          // per column: the log-likelihood factor and q (overwrites v with q)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const bool in = (ch * 32 + j) < valid;
+            if constexpr (NC == 1) {
+              const float u = v[0][j];
+              const float a = fabsf(u);
+              const float e = ptx::ex2_approx(-a);
+              const float r = __fdividef(1.f, 1.f + e);
+              la[j & 3] += in ? a : 0.f;
+              pr[j & 3] *= in ? 1.f + e : 1.f;
+              v[0][j] = in ? ((u >= 0.f) ? r : e * r) - 0.5f : 0.f;
+            } else {
+              float m = 0.f;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) m = fmaxf(m, v[c][j]);
+              float ec[NC];
+              float sx = ptx::ex2_approx(-m);
+#pragma unroll
+              for (int c = 0; c < NC; ++c) {
+                ec[c] = ptx::ex2_approx(v[c][j] - m);
+                sx += ec[c];
+              }
+              const float r = __fdividef(1.f, sx);
+              la[j & 3] += in ? m : 0.f;
+              pr[j & 3] *= in ? sx : 1.f;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) v[c][j] = in ? ec[c] * r : 0.f;
+            }
+          }
+          if ((ch & 3) == 3) {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const int bits = __float_as_int(pr[qq]);
+              pexp += (bits >> 23) - 127;
+              pr[qq] = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
+            }
+          }
+          // q as BF16 hi + lo into the swizzled tile: 8 observations (16 bytes) per store
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int g8 = 0; g8 < 4; ++g8) {
+              const int col = ch * 32 + g8 * 8;        // observation within the tile
+              const uint32_t kb = static_cast<uint32_t>(col >> 6);
+              const uint32_t chunk16 = static_cast<uint32_t>((col & 63) >> 3) ^ static_cast<uint32_t>(row & 7);
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                // one packed conversion for the two high parts, one for the two low parts
+                const float q0 = v[c][g8 * 8 + 2 * h], q1 = v[c][g8 * 8 + 2 * h + 1];
+                hw[h] = pack_bf16x2(q0, q1);
+                const float h0 = __uint_as_float(hw[h] << 16), h1 = __uint_as_float(hw[h] & 0xFFFF0000u);
+                lw[h] = pack_bf16x2(q0 - h0, q1 - h1);
+              }
+              const uint32_t base_h = qrow + (static_cast<uint32_t>(c * 2 + 0) * (BN / 64) + kb) * kTileA + chunk16 * 16u;
+              const uint32_t base_l = qrow + (static_cast<uint32_t>(c * 2 + 1) * (BN / 64) + kb) * kTileA + chunk16 * 16u;
+              st_shared_v4(base_h, hw[0], hw[1], hw[2], hw[3]);
+              st_shared_v4(base_l, lw[0], lw[1], lw[2], lw[3]);
+            }
+        }
+        // q visible to the tensor cores, then the MMA thread may take it
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&q_full[qb]);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const int bits = __float_as_int(pr[qq]);
+          pexp += (bits >> 23) - 127;
+          pr[qq] = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
+        }
+        float tile_val;
+        if constexpr (NC == 1) {
+          // sum over terms of |u|/2 + log2(1 + 2^-|u|): the even part of softplus
+          const float lsum = (la[0] + la[1]) + (la[2] + la[3]);
+          tile_val = fmaf(0.5f, lsum, static_cast<float>(pexp) + ptx::lg2_approx((pr[0] * pr[1]) * (pr[2] * pr[3])));
+        } else {
+          const float lsum = (la[0] + la[1]) + (la[2] + la[3]);
+          tile_val = (lsum + static_cast<float>(pexp)) + ptx::lg2_approx((pr[0] * pr[1]) * (pr[2] * pr[3]));
+        }
+        const float y = kLn2 * tile_val - kcomp;
+        const float tsum = ksum + y;
+        kcomp = (tsum - ksum) - y;
+        ksum = tsum;
+      }
+      if (!ok) break;
+      acc_base += static_cast<uint32_t>(tile_hi - tile_lo);
+      prm.partial[(static_cast<size_t>(chunk) * 2 + wg) * prm.ppad + ptile * kBM + row] =
+          static_cast<double>(ksum) - static_cast<double>(kcomp);
+      if (wg == 0) {
+        // the item's gradient sums: TMEM -> FP32 partials, chains added
+        ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(g_full, item_count & 1u, abort_flag, limit));
+        if (!ok) break;
+        ptx::tc_fence_after();
+        float* gout = prm.gpartial + (static_cast<size_t>(chunk) * prm.ppad + ptile * kBM + row) *
+                                         static_cast<size_t>(NC * prm.ng);
+        for (int c = 0; c < NC; ++c)
+          for (int j0 = 0; j0 < prm.ng; j0 += 32) {
+            float g[32];
+            ptx::tmem_ld_32x32b_x32(tmem_base + lane_base + kGradTmemOff + static_cast<uint32_t>(c * prm.gch * prm.ng + j0), g);
+            ptx::tmem_wait_ld();
+            for (int ch = 1; ch < prm.gch; ++ch) {
+              float h[32];
+              ptx::tmem_ld_32x32b_x32(
+                  tmem_base + lane_base + kGradTmemOff + static_cast<uint32_t>((c * prm.gch + ch) * prm.ng + j0), h);
+              ptx::tmem_wait_ld();
+#pragma unroll
+              for (int q = 0; q < 32; ++q) g[q] += h[q];
+            }
+            const int nj = min(32, prm.ng - j0);
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (q < nj) gout[c * prm.ng + j0 + q] = g[q];
+          }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(g_empty);
+      }
+      ++item_count;
+    }
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(prm.flag, 1);
+  if (warp == 1) {
+    __syncwarp();
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, 512);
+  }
+}
+
+// grad[p][c k + i] = lin_c[i] - sum over chunks of D_c[internal column of i] (+ its low-part
+// column when i is continuous); FP64 in a fixed order. One thread per gradient entry.
+__global__ void grad_tc_finalize_kernel(const float* __restrict__ gpartial, int n_chunks, int64_t P, int ppad,
+                                        int NC, int k, int ng, int k16, int kc, const int* __restrict__ invperm,
+                                        const double* __restrict__ lin, double* __restrict__ grad) {
+  const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int D = NC * k;
+  if (e >= P * D) return;
+  const int64_t p = e / D;
+  const int ci = static_cast<int>(e - p * D);
+  const int c = ci / k, i = ci - c * k;
+  const int j = invperm[i];
+  double s = 0.0;
+  for (int q = 0; q < n_chunks; ++q) {
+    const float* g = gpartial + (static_cast<size_t>(q) * ppad + p) * static_cast<size_t>(NC * ng) + c * ng;
+    double v = static_cast<double>(g[j]);
+    if (j < kc) v += static_cast<double>(g[k16 + j]);
+    s += v;
+  }
+  grad[e] = lin[ci] - s;
+}
+
 sps_status launch_finalize(sps_ctx* ctx, const double* theta, int64_t P, const double* partial, int slices,
                            int ppad, double* ll) {
   loglik_finalize_kernel<<<static_cast<unsigned>((P + kFinThreads - 1) / kFinThreads), kFinThreads, 0,
@@ -980,6 +1462,138 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
   if (prm.n_items > 0)
     SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));
   return launch_finalize(ctx, d_theta, P, prm.partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad, d_ll);
+}
+
+// Shape of a gradient call, or false when the tensor-core form does not fit (C - 1 > 2, or the
+// gradient accumulators or the pipeline do not fit TMEM / shared memory).
+static bool grad_shape(const sps_ctx* ctx, int* BN, int* ng, int* gch, int* stages, int* th_bufs, int* nq,
+                       uint32_t* smem_bytes) {
+  const XEncoding& enc = ctx->enc;
+  const int NC = ctx->NC;
+  if (NC < 1 || NC > 2 || enc.bn == 0) return false;
+  *BN = (NC == 1) ? 128 : 64;
+  *ng = enc.k16 + enc.kc16;
+  if (*ng > 256) return false;
+  // 32-column TMEM reads of the last accumulator may run 16 columns past it
+  *gch = (static_cast<int>(kGradTmemOff) + NC * 2 * *ng + 16 <= 512) ? 2 : 1;
+  if (static_cast<int>(kGradTmemOff) + NC * *gch * *ng + 16 > 512) return false;
+  const int kbx = enc.kx / kKB, kbt = enc.kt / kKB;
+  for (int q = 2; q >= 1; --q)
+    for (int tb = 2; tb >= 1; --tb)
+      for (int st = 6; st >= 3; --st)
+        if (grad_layout(NC, *BN, kbx, kbt, st, tb, q).total + 1024 <= kSmemBudget + 1024) {
+          *stages = st;
+          *th_bufs = tb;
+          *nq = q;
+          *smem_bytes = grad_layout(NC, *BN, kbx, kbt, st, tb, q).total + 1024;
+          return true;
+        }
+  return false;
+}
+
+template <int NC, int BN>
+static sps_status run_grad(sps_ctx* ctx, const GradParams& prm, int grid, uint32_t smem_bytes) {
+  auto kern = grad_tc_kernel<NC, BN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
+  if (e == cudaSuccess) {
+    kern<<<grid, kGradThreads, smem_bytes, ctx->stream>>>(ctx->ll.mapXg, ctx->ll.mapT, prm);
+    ++ctx->launches;
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("grad_tc launch: ") + cudaGetErrorString(e));
+  return SPS_OK;
+}
+
+sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll, double* d_grad) {
+  const int NC = ctx->NC, k = ctx->k;
+  XEncoding& enc = ctx->enc;
+  LoglikScratch& S = ctx->ll;
+  int BN = 0, ng = 0, gch = 0, stages = 0, th_bufs = 0, nq = 0;
+  uint32_t smem_bytes = 0;
+  if (!grad_shape(ctx, &BN, &ng, &gch, &stages, &th_bufs, &nq, &smem_bytes))
+    return fail(ctx, SPS_ERR_UNSUPPORTED, "tensor-core gradient: unsupported shape");
+  if (t < 1) return fail(ctx, SPS_ERR_UNSUPPORTED, "tensor-core gradient: empty prefix");
+  GradParams prm{};
+  const int ppad = static_cast<int>((P + kBM - 1) / kBM * kBM);
+  prm.t = static_cast<int>(t);
+  prm.ppad = ppad;
+  prm.n_ptiles = ppad / kBM;
+  prm.n_tiles = static_cast<int>((t + BN - 1) / BN);
+  int chunk_tiles = std::max(1, std::min(prm.n_tiles, 4096 / BN));
+  while (chunk_tiles > 2 &&
+         static_cast<int64_t>(prm.n_ptiles) * ((prm.n_tiles + chunk_tiles - 1) / chunk_tiles) < 4LL * ctx->num_sms)
+    chunk_tiles /= 2;
+  prm.chunk_tiles = chunk_tiles;
+  prm.n_chunks = (prm.n_tiles + chunk_tiles - 1) / chunk_tiles;
+  prm.n_items = prm.n_ptiles * prm.n_chunks;
+  prm.kbx = enc.kx / kKB;
+  prm.kbt = enc.kt / kKB;
+  prm.k16 = enc.k16;
+  prm.ksh = enc.k16 / 16;
+  prm.ksl = enc.kc16 / 16;
+  prm.th_row_stride = ppad;
+  prm.stages = stages;
+  prm.th_bufs = th_bufs;
+  prm.nq = nq;
+  prm.ng = ng;
+  prm.gch = gch;
+  prm.timeout_ns = 2000000000ull;
+  // operands: theta rows as for the log-likelihood, X tiles of BN rows, inverse permutation
+  if (S.ppad_cap < ppad) {
+    const int64_t cap = std::max<int64_t>(ppad, S.ppad_cap * 3 / 2 / kBM * kBM);
+    SPS_CUDA_TRY(S.thetaP.reserve(static_cast<size_t>(NC) * cap * enc.kt * sizeof(__nv_bfloat16)));
+    S.ppad_cap = cap;
+  }
+  SPS_TRY(make_map_bf16(ctx, &S.mapT, S.thetaP.ptr, static_cast<uint64_t>(NC) * ppad, enc.kt, kBM));
+  if (S.mapXg_rows != BN) {
+    SPS_TRY(make_map_bf16(ctx, &S.mapXg, enc.Xp.ptr, static_cast<uint64_t>(ctx->n), enc.kx, static_cast<uint32_t>(BN)));
+    S.mapXg_rows = BN;
+  }
+  if (enc.invperm_dev.bytes < sizeof(int) * static_cast<size_t>(k)) {
+    std::vector<int> inv(k);
+    for (int j = 0; j < k; ++j) inv[enc.perm[j]] = j;
+    SPS_CUDA_TRY(enc.invperm_dev.reserve(sizeof(int) * k));
+    SPS_CUDA_TRY(cudaMemcpy(enc.invperm_dev.ptr, inv.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
+  }
+  {
+    const int64_t rows = static_cast<int64_t>(NC) * ppad;
+    encode_theta_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
+        d_theta, P, k, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, ppad, S.thetaP.as<__nv_bfloat16>());
+    ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+  }
+  SPS_TRY(ensure_lin(ctx, t));
+  SPS_CUDA_TRY(S.partial.reserve(sizeof(double) * static_cast<size_t>(prm.n_chunks) * 2 * ppad));
+  SPS_CUDA_TRY(S.gpartial.reserve(sizeof(float) * static_cast<size_t>(prm.n_chunks) * ppad * NC * ng));
+  SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
+  prm.partial = S.partial.as<double>();
+  prm.gpartial = S.gpartial.as<float>();
+  prm.flag = S.flag.as<int>();
+  SPS_CUDA_TRY(cudaMemsetAsync(prm.flag, 0, sizeof(int), ctx->stream));
+  const int grid = std::max(1, std::min(ctx->num_sms, prm.n_items));
+  hot_begin(ctx);
+  sps_status st;
+  if (NC == 1) st = run_grad<1, 128>(ctx, prm, grid, smem_bytes);
+  else st = run_grad<2, 64>(ctx, prm, grid, smem_bytes);
+  hot_end(ctx);
+  SPS_TRY(st);
+  SPS_TRY(launch_finalize(ctx, d_theta, P, prm.partial, prm.n_chunks * 2, ppad, d_ll));
+  const int64_t entries = P * ctx->D;
+  grad_tc_finalize_kernel<<<static_cast<unsigned>((entries + 255) / 256), 256, 0, ctx->stream>>>(
+      prm.gpartial, prm.n_chunks, P, ppad, NC, k, ng, enc.k16, enc.kc, enc.invperm_dev.as<int>(),
+      ctx->lin.as<double>(), d_grad);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
+sps_status loglik_grad_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
+                                double* d_grad) {
+  int BN, ng, gch, stages, tb, nq;
+  uint32_t smem;
+  if (ctx->opt.precision == SPS_PREC_SPLIT && t >= 1 && grad_shape(ctx, &BN, &ng, &gch, &stages, &tb, &nq, &smem))
+    return loglik_grad_tc(ctx, d_theta, P, t, d_ll, d_grad);
+  return loglik_grad_fp32(ctx, d_theta, P, t, d_ll, d_grad);
 }
 
 sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,

@@ -1492,7 +1492,7 @@ sps_status mstep_prepare(sps_ctx* ctx, sps_state* st, int kernel) {
     SPS_CUDA_TRY(st->zq.reserve(sizeof(float) * st->P * D));
     SPS_CUDA_TRY(st->z2.reserve(sizeof(double) * st->P));
     if (st->ll_stale || st->ll_kind != kind || !st->grad_valid) {
-      SPS_TRY(loglik_grad_fp32(ctx, st->theta.as<double>(), st->P, st->t, st->ll.as<double>(),
+      SPS_TRY(loglik_grad_dispatch(ctx, st->theta.as<double>(), st->P, st->t, st->ll.as<double>(),
                                st->grad.as<double>()));
       st->ll_stale = false;
       st->ll_kind = kind;
@@ -1564,7 +1564,7 @@ sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* si
         st->theta_prop.as<double>(), st->lp_prop.as<double>(), st->zq.as<float>(), st->z2.as<double>());
     ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
-    SPS_TRY(loglik_grad_fp32(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
+    SPS_TRY(loglik_grad_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
                              st->grad_prop.as<double>()));
     mala_accept_kernel<<<blocks, kMalaThreads, smem_a, ctx->stream>>>(
         st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->grad.as<double>(),

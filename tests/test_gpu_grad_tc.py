@@ -1,0 +1,83 @@
+"""The tensor-core gradient (split precision, C - 1 <= 2) against the FP64 oracle.
+
+Bound per gradient entry (c, i): the operands are BF16 hi + lo splits (theta, X: dropped lo x lo
+product, relative 2^-16 of each product; q: relative 2^-16) with FP32 accumulation within a work
+item. An error of delta in eta changes q by at most delta / 4, so
+  |G - G_oracle| <= 1e-5 |G_oracle| + 2^-13 sum_s (1 + |eta_s|) |x_si|
+(a factor 8 above the worst-case sum of these relative errors). The log-likelihood uses the
+bound of the split log-likelihood tests. Shapes span several tiles with a ragged last tile and
+a ragged particle tile."""
+import numpy as np
+import pytest
+
+from oracle import logit as OL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _data(n, k, C, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    X = g.standard_normal((n, k))
+    X[:, 0] = 1.0
+    X[:, k - k // 3:] = (X[:, k - k // 3:] > 0.4).astype(float)   # exact 0/1 columns
+    y = g.integers(0, C, n).astype(np.int32)
+    return X, y
+
+
+def _eta_bound(X, th, C, t):
+    k = X.shape[1]
+    Xt = X[:t]
+    out = np.zeros_like(th)
+    for c in range(C - 1):
+        eta = th[:, c * k:(c + 1) * k] @ Xt.T                        # [P, t]
+        out[:, c * k:(c + 1) * k] = (1.0 + np.abs(eta)) @ np.abs(Xt)  # [P, k]
+    return out
+
+
+@pytest.mark.parametrize("C,n,k,t", [(2, 1500, 30, 1500), (2, 1500, 30, 701), (2, 300, 7, 1),
+                                      (3, 1300, 12, 1300), (3, 1300, 12, 555), (3, 900, 74, 900)])
+def test_tensor_core_gradient_against_oracle(cuda, C, n, k, t):
+    from paper_1304_4333_b300 import Sps
+    X, y = _data(n, k, C, seed=n + k + C)
+    s = Sps(X, y, C, prior_sd=5.0, precision="split")
+    g = np.random.Generator(np.random.PCG64(7))
+    D = k * (C - 1)
+    th = (0.8 / np.sqrt(k)) * g.standard_normal((300, D))
+    ll, G = s.loglik_grad(th, t)
+    ll_o, G_o = OL.loglik_grad(X, y, th, C, t)
+    bound = 1e-5 * np.abs(G_o) + 2.0 ** -13 * _eta_bound(X, th, C, t)
+    assert np.all(np.abs(G - G_o) <= bound), np.max(np.abs(G - G_o) - bound)
+    ll_bound = 1e-5 * np.abs(ll_o) + 3 * 2.0 ** -16 * np.abs(th @ np.tile(np.abs(X[:t]).sum(0), C - 1))
+    assert np.all(np.abs(ll - ll_o) <= ll_bound + 1e-9)
+    # and against the FP32 SIMT form of the same gradient
+    s32 = Sps(X, y, C, prior_sd=5.0, precision="fp32")
+    _, G32 = s32.loglik_grad(th, t)
+    assert np.all(np.abs(G - G32) <= bound + 1e-5 * np.abs(G32))
+    s.close()
+    s32.close()
+
+
+def test_tensor_core_gradient_device_and_zero_theta(cuda):
+    # theta = 0: p = 1/C for every term, so G_c = sum_s (1[y_s = c] - 1/C) x_s exactly up to the
+    # BF16 split of X (exact for these columns) and FP32 accumulation
+    torch = cuda
+    from paper_1304_4333_b300 import Sps
+    X, y = _data(1000, 9, 3, seed=3)
+    X = np.round(X * 8) / 8            # exact in BF16
+    s = Sps(X, y, 3, prior_sd=5.0)
+    th = torch.zeros((200, 18), dtype=torch.float64, device="cuda")
+    ll, G = s.loglik_grad(th, 1000)
+    ref = np.zeros(18)
+    for c in (1, 2):
+        ref[(c - 1) * 9:c * 9] = ((y == c) - 1.0 / 3).astype(float) @ X
+    np.testing.assert_allclose(G.cpu().numpy(), np.tile(ref, (200, 1)), rtol=0, atol=2e-3)
+    np.testing.assert_allclose(ll.cpu().numpy(), -1000 * np.log(3.0), rtol=1e-6)
+    s.close()

@@ -106,8 +106,9 @@ def test_particle_covariance(cuda, C, k):
 
 @pytest.mark.parametrize("C", [2, 3])
 def test_gradient_against_oracle_and_finite_differences(cuda, C):
+    # the FP32 SIMT gradient kernel (precision fp32); the tensor-core form is in test_gpu_grad_tc.py
     X, y = _small(n=700, k=6, C=C, seed=5)
-    s = _ctx(X, y, C)
+    s = _ctx(X, y, C, precision="fp32")
     D = 6 * (C - 1)
     g = np.random.Generator(np.random.PCG64(6))
     th = 0.3 * g.standard_normal((130, D))

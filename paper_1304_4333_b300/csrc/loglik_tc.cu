@@ -677,7 +677,7 @@ __global__ void finalize_batched_kernel(const int64_t* __restrict__ tab, int M, 
 // memory as the B operand read MN-major (N = the covariate columns [Xh | Xl], K = observations).
 // D stays in TMEM across the tiles of a work item (gch chains per class, by K slice) and is
 // written once per item as FP32 partials.
-constexpr int kGradWarps = 10;   // producer, MMA issuer, two epilogue groups of four warps
+constexpr int kGradWarps = 18;   // producer, MMA issuer, four epilogue groups of four warps
 constexpr int kGradThreads = 32 * kGradWarps;
 constexpr uint32_t kGradTmemOff = 256;   // gradient accumulators from this TMEM column
 
@@ -687,7 +687,7 @@ struct GradParams {
   int stages, th_bufs, nq;   // X stages, theta buffers, q buffers
   int ng;                    // gradient columns per class: k16 + kc16 ([Xh | Xl] of a row)
   int gch;                   // accumulator chains per class (K slices alternate between them)
-  double* partial;           // [n_chunks][2][ppad] log-likelihood partial sums
+  double* partial;           // [n_chunks][4][ppad] log-likelihood partial sums
   float* gpartial;           // [n_chunks][ppad][NC ng] gradient partial sums
   int* flag;
   unsigned long long timeout_ns;
@@ -751,7 +751,9 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
   static_assert(BN == 64 || BN == 128, "q tiles are whole 64-observation swizzle rows");
   constexpr int NBUF = 2;
   static_assert(NBUF * NC * BN <= static_cast<int>(kGradTmemOff), "forward accumulators below the gradient ones");
-  constexpr int NCH = BN / 32;
+  // two groups per accumulator, each taking half of a tile's columns
+  constexpr int COLS = BN / 2;
+  constexpr int NCH = COLS / 32;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -782,8 +784,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
       ptx::mbar_init(&th_full[i], 1);
       ptx::mbar_init(&th_empty[i], 1);
       ptx::mbar_init(&acc_full[i], 1);
-      ptx::mbar_init(&acc_empty[i], 4);   // the four warps of the owning group
-      ptx::mbar_init(&q_full[i], 4);
+      ptx::mbar_init(&acc_empty[i], 8);   // the eight warps of the two owning groups
+      ptx::mbar_init(&q_full[i], 8);
       ptx::mbar_init(&q_empty[i], 1);
     }
     ptx::mbar_init(g_full, 1);
@@ -952,7 +954,9 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
     }
   } else {
     // ------------------------------------------------------------------ epilogue
-    const int wg = (warp - 2) >> 2;                   // group: tiles with acc_count % 2 == wg
+    const int wg = (warp - 2) >> 2;                   // group
+    const int own = wg >> 1;                          // its tiles: acc_count % 2 == own
+    const int col0 = (wg & 1) * COLS;                 // its half of each tile's columns
     const int quad = warp & 3;
     const int row = quad * 32 + lane;                 // particle within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
@@ -965,7 +969,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
       const int tile_lo = chunk * prm.chunk_tiles;
       const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
       float ksum = 0.f, kcomp = 0.f;
-      const int first = tile_lo + static_cast<int>((static_cast<uint32_t>(wg) + 2u - (acc_base & 1u)) & 1u);
+      const int first = tile_lo + static_cast<int>((static_cast<uint32_t>(own) + 2u - (acc_base & 1u)) & 1u);
       for (int tile = first; tile < tile_hi; tile += 2) {
         const uint32_t acc_count = acc_base + static_cast<uint32_t>(tile - tile_lo);
         const int buf = static_cast<int>(acc_count & 1u);
@@ -976,8 +980,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
                                          ptx::mbar_wait_bounded(&q_empty[qb], qph ^ 1u, abort_flag, limit));
         if (!ok) break;
         ptx::tc_fence_after();
-        const int valid = prm.t - tile * BN;          // columns of this tile inside [0, t)
-        const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN);
+        const int valid = prm.t - tile * BN - col0;   // columns of this group inside [0, t)
+        const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN + col0);
         const uint32_t qrow = ptx::smem_u32(smem + L.off_q + qb * L.q_bytes) + static_cast<uint32_t>(row) * 128u;
         float la[4] = {0.f, 0.f, 0.f, 0.f};
         float pr[4] = {1.f, 1.f, 1.f, 1.f};
@@ -1036,7 +1040,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
           for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int g8 = 0; g8 < 4; ++g8) {
-              const int col = ch * 32 + g8 * 8;        // observation within the tile
+              const int col = col0 + ch * 32 + g8 * 8;   // observation within the tile
               const uint32_t kb = static_cast<uint32_t>(col >> 6);
               const uint32_t chunk16 = static_cast<uint32_t>((col & 63) >> 3) ^ static_cast<uint32_t>(row & 7);
               uint32_t hw[4], lw[4];
@@ -1080,7 +1084,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
       }
       if (!ok) break;
       acc_base += static_cast<uint32_t>(tile_hi - tile_lo);
-      prm.partial[(static_cast<size_t>(chunk) * 2 + wg) * prm.ppad + ptile * kBM + row] =
+      prm.partial[(static_cast<size_t>(chunk) * 4 + wg) * prm.ppad + ptile * kBM + row] =
           static_cast<double>(ksum) - static_cast<double>(kcomp);
       if (wg == 0) {
         // the item's gradient sums: TMEM -> FP32 partials, chains added
@@ -1563,7 +1567,7 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
     SPS_CUDA_TRY(cudaGetLastError());
   }
   SPS_TRY(ensure_lin(ctx, t));
-  SPS_CUDA_TRY(S.partial.reserve(sizeof(double) * static_cast<size_t>(prm.n_chunks) * 2 * ppad));
+  SPS_CUDA_TRY(S.partial.reserve(sizeof(double) * static_cast<size_t>(prm.n_chunks) * 4 * ppad));
   SPS_CUDA_TRY(S.gpartial.reserve(sizeof(float) * static_cast<size_t>(prm.n_chunks) * ppad * NC * ng));
   SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
   prm.partial = S.partial.as<double>();
@@ -1577,7 +1581,7 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
   else st = run_grad<2, 64>(ctx, prm, grid, smem_bytes);
   hot_end(ctx);
   SPS_TRY(st);
-  SPS_TRY(launch_finalize(ctx, d_theta, P, prm.partial, prm.n_chunks * 2, ppad, d_ll));
+  SPS_TRY(launch_finalize(ctx, d_theta, P, prm.partial, prm.n_chunks * 4, ppad, d_ll));
   const int64_t entries = P * ctx->D;
   grad_tc_finalize_kernel<<<static_cast<unsigned>((entries + 255) / 256), 256, 0, ctx->stream>>>(
       prm.gpartial, prm.n_chunks, P, ppad, NC, k, ng, enc.k16, enc.kc, enc.invperm_dev.as<int>(),

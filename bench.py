@@ -376,19 +376,24 @@ def profiled_traffic():
 
 def sps_wall(w, rank):
     """Second half of the metric: wall time of the whole simulator (sps_run, Algorithm 2) on c2
-    with the split-BF16 path and with the plain FP32 path, the log-ML NSE each reaches at the
-    configured 16 x 4096 particles, and the projected wall time to NSE <= 0.05 (NSE scales as
-    particles^-1/2 and the time as particles, so time x (NSE / 0.05)^2; labelled as projected)."""
+    with the split-BF16 path (random-walk M kernel, and the MALA M kernel driven by the
+    tensor-core gradient) and with the plain FP32 random-walk path, the log-ML NSE each reaches
+    at the configured 16 x 4096 particles, and the projected wall time to NSE <= 0.05 (NSE
+    scales as particles^-1/2 and the time as particles, so time x (NSE / 0.05)^2; labelled as
+    projected)."""
     from paper_1304_4333_b300 import Sps
     out = {}
-    for prec in ("split", "fp32"):
-        s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=11 + rank, precision=prec)
+    for name, prec, mk in (("split", "split", "rw"), ("split_mala", "split", "mala"), ("fp32", "fp32", "rw")):
+        s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=11 + rank, precision=prec, mkernel=mk)
         r = s.run(w.J, w.N, record=False)
-        out[prec] = {"wall_s": r.seconds, "log_ml": r.log_ml, "log_ml_nse": r.log_ml_nse,
-                     "cycles": r.n_cycles, "m_steps": r.m_steps,
+        out[name] = {"wall_s": r.seconds, "log_ml": r.log_ml, "log_ml_nse": r.log_ml_nse,
+                     "cycles": r.n_cycles, "m_steps": r.m_steps, "mkernel": mk,
                      "projected_wall_s_to_nse_0.05": r.seconds * max(1.0, (r.log_ml_nse / 0.05) ** 2)}
         s.close()
     out["speedup_vs_fp32"] = out["fp32"]["wall_s"] / out["split"]["wall_s"]
+    out["speedup_mala_vs_fp32"] = out["fp32"]["wall_s"] / out["split_mala"]["wall_s"]
+    out["projected_speedup_mala_vs_fp32"] = (out["fp32"]["projected_wall_s_to_nse_0.05"]
+                                             / out["split_mala"]["projected_wall_s_to_nse_0.05"])
     out["particles"] = f"{w.J} groups x {w.N}"
     return out
 

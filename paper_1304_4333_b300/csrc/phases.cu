@@ -1646,6 +1646,15 @@ sps_status mphase_graph(sps_ctx* ctx, sps_state* st, int kernel, double K, int r
   };
   const int F = 1 + ctx->NC;
   if (F > kCtlMaxF || o.r_max <= r_done) return give_up("shape", cudaSuccess);
+  // the control kernel's group sums in dynamic shared memory (plus its static RNE array):
+  // settled before any capture, so that no launch inside a capture can be invalid
+  const size_t ctl_smem = sizeof(double) * 3 * static_cast<size_t>(st->J) * F;
+  if (ctl_smem + sizeof(double) * kCtlMaxF > 200 * 1024) return give_up("groups", cudaSuccess);
+  {
+    const cudaError_t ea = cudaFuncSetAttribute(mstep_control_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(ctl_smem));
+    if (ea != cudaSuccess) return give_up("control kernel shared memory", ea);
+  }
   SPS_CUDA_TRY(st->ctl.reserve(sizeof(StepCtl)));
   SPS_CUDA_TRY(st->steplog.reserve(sizeof(double) * 3 * static_cast<size_t>(o.r_max)));
   const bool want_sigma = rec && rec->sigma;
@@ -1702,11 +1711,8 @@ sps_status mphase_graph(sps_ctx* ctx, sps_state* st, int kernel, double K, int r
     sps_status is = mstep_issue(ctx, st, kernel, nullptr, nullptr, 0.0, 0, d_ctl);
     if (is == SPS_OK) {
       const double target = (kernel == SPS_MKERNEL_MALA) ? o.mala_target_accept : o.target_accept;
-      const size_t smem = sizeof(double) * 3 * static_cast<size_t>(st->J) * F;
-      if (smem > 48 * 1024)
-        is = SPS_ERR_UNSUPPORTED;
-      else {
-        mstep_control_kernel<<<1, 128, smem, ctx->stream>>>(d_ctl, st->counters.as<unsigned long long>(),
+      {
+        mstep_control_kernel<<<1, 128, ctl_smem, ctx->stream>>>(d_ctl, st->counters.as<unsigned long long>(),
                                                             st->scratch.as<double>(), st->J, F, kMomParts, st->N,
                                                             st->P, K, target, o.h_step, o.h_min, o.h_max,
                                                             st->steplog.as<double>(), st->cov.as<double>(), ctx->D,

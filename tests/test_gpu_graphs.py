@@ -102,3 +102,13 @@ def test_mphase_state_api_graph(cuda):
     np.testing.assert_array_equal(d1["theta"], d0["theta"])
     np.testing.assert_array_equal(d1["ll"], d0["ll"])
     assert d1["h"] == d0["h"]
+
+
+def test_graph_with_many_groups(cuda):
+    # J F 3 doubles of control-kernel sums above the default 48 KB of shared memory (J = 1100,
+    # F = 2): the limit is raised before the capture; results still equal the stepwise run
+    X, y = _logit_case(200, 3, 2, seed=13)
+    g = _run(X, y, 2, 1100, 4, 1, r_max=5)
+    e = _run(X, y, 2, 1100, 4, 0, r_max=5)
+    assert g.graph_steps > 0
+    _assert_identical(g, e)

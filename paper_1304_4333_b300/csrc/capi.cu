@@ -135,6 +135,12 @@ sps_status to_device(sps_ctx* ctx, DevBuf& buf, const void* host, size_t bytes) 
   return SPS_OK;
 }
 
+// FP32 copy (the library's FP64 -> FP32 conversion) of a full prior precision matrix.
+__global__ void prec_to_f32_kernel(const double* __restrict__ p, int64_t n, float* __restrict__ out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) out[i] = f64_to_f32(p[i]);
+}
+
 // Lower Cholesky factor of a symmetric positive definite matrix (host FP64, row-major).
 bool cholesky_host(const std::vector<double>& A, int D, std::vector<double>& L) {
   L.assign(static_cast<size_t>(D) * D, 0.0);
@@ -202,7 +208,19 @@ sps_status apply_prior(sps_ctx* ctx, const sps_prior* prior) {
     prec.resize(D);
     for (int i = 0; i < D; ++i) prec[i] = 1.0 / cov[i * D + i];
   }
-  SPS_TRY(to_device(ctx, ctx->d_prior_prec, prec.data(), prec.size() * sizeof(double)));
+  if (prior->kind == SPS_PRIOR_FULL) {
+    // FP64 precision matrix followed by its FP32 conversion (read by the prior log kernel)
+    const size_t dd = static_cast<size_t>(D) * D;
+    SPS_CUDA_TRY(ctx->d_prior_prec.reserve(dd * sizeof(double) + dd * sizeof(float)));
+    SPS_CUDA_TRY(cudaMemcpy(ctx->d_prior_prec.ptr, prec.data(), dd * sizeof(double), cudaMemcpyHostToDevice));
+    prec_to_f32_kernel<<<static_cast<unsigned>((dd + 255) / 256), 256>>>(
+        ctx->d_prior_prec.as<double>(), static_cast<int64_t>(dd),
+        reinterpret_cast<float*>(ctx->d_prior_prec.as<double>() + dd)); ++ctx->launches;
+    SPS_CUDA_TRY(cudaGetLastError());
+    SPS_CUDA_TRY(cudaDeviceSynchronize());
+  } else {
+    SPS_TRY(to_device(ctx, ctx->d_prior_prec, prec.data(), prec.size() * sizeof(double)));
+  }
   SPS_TRY(to_device(ctx, ctx->d_prior_mean, mean.data(), D * sizeof(double)));
   SPS_TRY(to_device(ctx, ctx->d_prior_chol, chol.data(), chol.size() * sizeof(double)));
   ctx->prior_kind = prior->kind;

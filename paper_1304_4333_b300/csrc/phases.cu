@@ -118,6 +118,8 @@ __device__ double block_max(double v, double* sh) {
 // FP32 element-wise (d = f32(theta) - f32(mu)) and FP32 sums: the same deterministic function
 // for every particle and proposal, so Metropolis ratios stay exact for it; its relative error
 // (about 1e-7) is far below the posterior's scale.
+constexpr int kMaxD = 155;   // covariance kernel: <= 48 moment entries per thread
+
 __device__ double prior_log_kernel(const double* th, const double* mu, const double* prec, int D, bool full) {
   float a = 0.f;
   if (!full) {
@@ -126,11 +128,16 @@ __device__ double prior_log_kernel(const double* th, const double* mu, const dou
       a = fmaf(d * d, f64_to_f32(prec[i]), a);
     }
   } else {
+    // full precision matrix: its FP32 copy follows the FP64 one; the centred coordinates are
+    // converted once (the values and the order of operations are those of the plain loops)
+    const float* p32 = reinterpret_cast<const float*>(prec + static_cast<size_t>(D) * D);
+    float d[kMaxD];
+    for (int j = 0; j < D; ++j) d[j] = f64_to_f32(th[j]) - f64_to_f32(mu[j]);
     for (int i = 0; i < D; ++i) {
-      const float di = f64_to_f32(th[i]) - f64_to_f32(mu[i]);
+      const float* pi = p32 + static_cast<size_t>(i) * D;
       float r = 0.f;
-      for (int j = 0; j < D; ++j) r = fmaf(f64_to_f32(prec[i * D + j]), f64_to_f32(th[j]) - f64_to_f32(mu[j]), r);
-      a = fmaf(di, r, a);
+      for (int j = 0; j < D; ++j) r = fmaf(pi[j], d[j], r);
+      a = fmaf(d[i], r, a);
     }
   }
   return -0.5 * f32_to_f64(a);
@@ -563,7 +570,6 @@ __global__ void gather_kernel(const double* __restrict__ th, const double* __res
 
 // ------------------------------------------------------------------------------ M phase
 
-constexpr int kMaxD = 155;   // covariance kernel: <= 48 moment entries per thread
 
 constexpr int kCovSub = 64;        // particles staged per shared-memory pass
 constexpr int kCovThreads = 256;
@@ -702,13 +708,11 @@ __device__ __forceinline__ double rsqrt_f64(double a) {
 
 constexpr int kCholThreads = 256;
 
-__global__ void __launch_bounds__(kCholThreads)
-cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
-                float* __restrict__ L32, int* __restrict__ flag) {
-  extern __shared__ double a[];   // packed lower triangle, row-major
-  __shared__ double col[kMaxD];   // scaled column j
-  __shared__ double rinv;
-  __shared__ int bad;
+// One block's factorisation; a: the packed lower triangle in shared memory, col: the scaled
+// column, rinv / bad: block-shared scalars.
+__device__ __forceinline__ void cholesky_block(const double* __restrict__ A, int D, double* __restrict__ L,
+                                               float* __restrict__ L32, int* __restrict__ flag, double* a,
+                                               double* col, double& rinv, int& bad) {
   const int T = D * (D + 1) / 2;
   for (int e = threadIdx.x; e < T; e += blockDim.x) {
     int i, k;
@@ -757,6 +761,37 @@ cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
   for (int e = threadIdx.x; e < T; e += blockDim.x) L32[e] = f64_to_f32(a[e]);
 }
 
+__global__ void __launch_bounds__(kCholThreads)
+cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
+                float* __restrict__ L32, int* __restrict__ flag) {
+  extern __shared__ double a[];   // packed lower triangle, row-major
+  __shared__ double col[kMaxD];   // scaled column j
+  __shared__ double rinv;
+  __shared__ int bad;
+  cholesky_block(A, D, L, L32, flag, a, col, rinv, bad);
+}
+
+// Several independent factorisations in one launch, one block each (the models of a batched
+// run): the same arithmetic as cholesky_kernel per matrix.
+struct CholJob {
+  const double* A;
+  double* L;
+  float* L32;
+  int* flag;
+  int D;
+  int pad;
+};
+
+__global__ void __launch_bounds__(kCholThreads)
+cholesky_batched_kernel(const CholJob* __restrict__ jobs) {
+  extern __shared__ double a[];
+  __shared__ double col[kMaxD];
+  __shared__ double rinv;
+  __shared__ int bad;
+  const CholJob job = jobs[blockIdx.x];
+  cholesky_block(job.A, job.D, job.L, job.L32, job.flag, a, col, rinv, bad);
+}
+
 // Particle rows [p0, p0 + np) of a [P x D] FP64 matrix to / from shared memory with row stride
 // Dp (odd, so that one row per lane reads without bank conflicts); global accesses coalesced.
 __device__ __forceinline__ void stage_rows(const double* __restrict__ src, int64_t p0, int np, int D, int Dp,
@@ -801,11 +836,10 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
   float* mus = zs + D * kPropPart;                                    // [D] f32(mu), [D] f32(prec)
   float* prs = mus + D;
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
-  if (!full)
-    for (int i = threadIdx.x; i < D; i += blockDim.x) {
-      mus[i] = f64_to_f32(mu[i]);
-      prs[i] = f64_to_f32(prec[i]);
-    }
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    mus[i] = f64_to_f32(mu[i]);
+    if (!full) prs[i] = f64_to_f32(prec[i]);
+  }
   const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kPropPart;
   const int np = static_cast<int>(P - p0 < kPropPart ? P - p0 : kPropPart);
   stage_rows(th, p0, np, D, Dp, rows);
@@ -838,10 +872,27 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
       row[i] = row[i] + f32_to_f64(dlt);
     }
   __syncwarp();   // a particle's four threads are consecutive lanes of one warp
+  if (full) {
+    // full prior: the particle's threads form r_i = sum_j P32_ij d_j for their rows (j in
+    // order) into the normals' slots, then its first thread sum_i d_i r_i in order i: the
+    // values and operation order of prior_log_kernel
+    if (live) {
+      const float* p32 = reinterpret_cast<const float*>(prec + static_cast<size_t>(D) * D);
+      for (int i = sub; i < D; i += kPropSub) {
+        const float* pi = p32 + static_cast<size_t>(i) * D;
+        float r = 0.f;
+        for (int j = 0; j < D; ++j) r = fmaf(pi[j], f64_to_f32(row[j]) - mus[j], r);
+        zs[i * kPropPart + pp] = r;
+      }
+    }
+    __syncwarp();
+  }
   if (live && sub == 0) {
     double lp;
     if (full) {
-      lp = prior_log_kernel(row, mu, prec, D, full);
+      float a = 0.f;
+      for (int i = 0; i < D; ++i) a = fmaf(f64_to_f32(row[i]) - mus[i], zs[i * kPropPart + pp], a);
+      lp = -0.5 * f32_to_f64(a);
     } else {
       float a = 0.f;   // diagonal prior: the arithmetic of prior_log_kernel
       for (int i = 0; i < D; ++i) {
@@ -1324,10 +1375,10 @@ static sps_status launch_cov(sps_ctx* ctx, const double* theta, int64_t P, int D
 }
 
 // V (and Sigma = h V unless sigma_in) then its Cholesky factor into st->chol / scratch L32.
-static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_theta, double h,
-                                  const double* h_dev, const double* sigma_host, double* sigma_out, int* d_flag) {
+// Sigma = h V (or the given Sigma) into st->cov; factor_proposal adds its Cholesky factor.
+static sps_status proposal_sigma(sps_ctx* ctx, sps_state* st, const double* d_theta, double h, const double* h_dev,
+                                 const double* sigma_host, double* sigma_out) {
   const int D = ctx->D;
-  const int T = D * (D + 1) / 2;
   double* d_sigma = st->cov.as<double>();
   if (sigma_host) {
     SPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma_host, sizeof(double) * D * D, cudaMemcpyHostToDevice, ctx->stream));
@@ -1336,6 +1387,28 @@ static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_t
   }
   if (sigma_out)
     SPS_CUDA_TRY(cudaMemcpyAsync(sigma_out, d_sigma, sizeof(double) * D * D, cudaMemcpyDeviceToHost, ctx->stream));
+  return SPS_OK;
+}
+
+// The Cholesky job of a state's Sigma (for one batched factorisation of several states).
+static CholJob chol_job(sps_ctx* ctx, sps_state* st, int* d_flag) {
+  const int D = ctx->D;
+  CholJob j;
+  j.A = st->cov.as<double>();
+  j.L = st->chol.as<double>();
+  j.L32 = reinterpret_cast<float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
+  j.flag = d_flag;
+  j.D = D;
+  j.pad = 0;
+  return j;
+}
+
+static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_theta, double h,
+                                  const double* h_dev, const double* sigma_host, double* sigma_out, int* d_flag) {
+  const int D = ctx->D;
+  const int T = D * (D + 1) / 2;
+  double* d_sigma = st->cov.as<double>();
+  SPS_TRY(proposal_sigma(ctx, st, d_theta, h, h_dev, sigma_host, sigma_out));
   float* L32 = reinterpret_cast<float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
   SPS_CUDA_TRY(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(sizeof(double) * T)));
@@ -2312,6 +2385,8 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
                                 bll.data());
   };
   const sps_options& o = ctx->opt;
+  DevBuf jobs_dev;
+  SPS_CUDA_TRY(jobs_dev.reserve(sizeof(CholJob) * static_cast<size_t>(M)));
   while (true) {
     std::vector<int> active;
     for (int m = 0; m < M; ++m)
@@ -2341,12 +2416,36 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
     std::vector<int> run = active, r(M, 0);
     std::vector<double> hs(M);
     std::vector<uint64_t> steps(M);
+    std::vector<CholJob> jobs;
+    jobs.reserve(M);
     while (!run.empty()) {
+      // every model's Sigma = h V, their Cholesky factors in one launch (one block each), then
+      // the proposals: the operations of rw_issue_propose, with the factorisations batched
+      jobs.clear();
+      size_t tmax = 1;
       for (int m : run) {
         Model& md = models.v[m];
         hs[m] = md.st->h;
         steps[m] = ++md.st->step_counter;
-        const sps_status e = rw_issue_propose(md.c, md.st, nullptr, nullptr, hs[m], steps[m], nullptr);
+        SPS_CUDA_TRY(cudaMemsetAsync(md.st->counters.ptr, 0, sizeof(Counters), ctx->stream));
+        const sps_status e = proposal_sigma(md.c, md.st, md.st->theta.as<double>(), hs[m], nullptr, nullptr, nullptr);
+        if (e != SPS_OK) return pass(md.c, e);
+        jobs.push_back(chol_job(md.c, md.st, flag_ptr(md.st, 0)));
+        const size_t Dm = static_cast<size_t>(md.c->D);
+        tmax = std::max(tmax, Dm * (Dm + 1) / 2);
+      }
+      SPS_CUDA_TRY(cudaMemcpyAsync(jobs_dev.ptr, jobs.data(), sizeof(CholJob) * jobs.size(), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+      SPS_CUDA_TRY(cudaFuncSetAttribute(cholesky_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(sizeof(double) * tmax)));
+      cholesky_batched_kernel<<<static_cast<unsigned>(jobs.size()), kCholThreads, sizeof(double) * tmax,
+                                ctx->stream>>>(jobs_dev.as<CholJob>()); ++ctx->launches;
+      SPS_CUDA_TRY(cudaGetLastError());
+      for (int m : run) {
+        Model& md = models.v[m];
+        const sps_status e = launch_propose(md.c, md.st, md.st->theta.as<double>(), md.st->P, nullptr, steps[m], nullptr,
+                                            flag_ptr(md.st, 0), md.st->theta_prop.as<double>(),
+                                            md.st->lp_prop.as<double>());
         if (e != SPS_OK) return pass(md.c, e);
       }
       SPS_TRY(evaluate(run, true));

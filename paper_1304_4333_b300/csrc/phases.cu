@@ -714,10 +714,20 @@ __device__ __forceinline__ void cholesky_block(const double* __restrict__ A, int
                                                float* __restrict__ L32, int* __restrict__ flag, double* a,
                                                double* col, double& rinv, int& bad) {
   const int T = D * (D + 1) / 2;
-  for (int e = threadIdx.x; e < T; e += blockDim.x) {
-    int i, k;
-    tri_ij(e, &i, &k);
-    a[e] = A[i * D + k];
+  // this thread's entries e = threadIdx.x + q blockDim.x of the packed triangle, as (i << 16) | k
+  // computed once (the trailing updates visit them every column)
+  constexpr int kQ = (kMaxD * (kMaxD + 1) / 2 + kCholThreads - 1) / kCholThreads;
+  int ik[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int e = threadIdx.x + q * kCholThreads;
+    ik[q] = 0;
+    if (e < T) {
+      int i, k;
+      tri_ij(e, &i, &k);
+      a[e] = A[i * D + k];
+      ik[q] = (i << 16) | k;
+    }
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
@@ -741,11 +751,12 @@ __device__ __forceinline__ void cholesky_block(const double* __restrict__ A, int
       col[i] = v;
     }
     __syncthreads();
-    // trailing update a[i][k] -= l_ij l_kj for j < k <= i, entries of the rows below j
-    const int e0 = tri(j + 1, 0);
-    for (int e = e0 + threadIdx.x; e < T; e += blockDim.x) {
-      int i, k;
-      tri_ij(e, &i, &k);
+    // trailing update a[i][k] -= l_ij l_kj for j < k <= i
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int e = threadIdx.x + q * kCholThreads;
+      if (e >= T) break;
+      const int i = ik[q] >> 16, k = ik[q] & 0xFFFF;
       if (k > j) a[e] = fma(-col[i], col[k], a[e]);
     }
     __syncthreads();
@@ -835,6 +846,7 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
   float* zs = Ls + ((T + 3) & ~3);                                    // [D][64]
   float* mus = zs + D * kPropPart;                                    // [D] f32(mu), [D] f32(prec)
   float* prs = mus + D;
+  float* ds = prs + D;                                                // [D][64] f32(theta') - f32(mu)
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
     mus[i] = f64_to_f32(mu[i]);
@@ -876,12 +888,15 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
     // full prior: the particle's threads form r_i = sum_j P32_ij d_j for their rows (j in
     // order) into the normals' slots, then its first thread sum_i d_i r_i in order i: the
     // values and operation order of prior_log_kernel
+    if (live)
+      for (int j = sub; j < D; j += kPropSub) ds[j * kPropPart + pp] = f64_to_f32(row[j]) - mus[j];
+    __syncwarp();
     if (live) {
       const float* p32 = reinterpret_cast<const float*>(prec + static_cast<size_t>(D) * D);
       for (int i = sub; i < D; i += kPropSub) {
         const float* pi = p32 + static_cast<size_t>(i) * D;
         float r = 0.f;
-        for (int j = 0; j < D; ++j) r = fmaf(pi[j], f64_to_f32(row[j]) - mus[j], r);
+        for (int j = 0; j < D; ++j) r = fmaf(pi[j], ds[j * kPropPart + pp], r);
         zs[i * kPropPart + pp] = r;
       }
     }
@@ -891,7 +906,7 @@ propose_kernel(const double* __restrict__ th, int64_t P, int D, const float* __r
     double lp;
     if (full) {
       float a = 0.f;
-      for (int i = 0; i < D; ++i) a = fmaf(f64_to_f32(row[i]) - mus[i], zs[i * kPropPart + pp], a);
+      for (int i = 0; i < D; ++i) a = fmaf(ds[i * kPropPart + pp], zs[i * kPropPart + pp], a);
       lp = -0.5 * f32_to_f64(a);
     } else {
       float a = 0.f;   // diagonal prior: the arithmetic of prior_log_kernel
@@ -1421,7 +1436,7 @@ static sps_status factor_proposal(sps_ctx* ctx, sps_state* st, const double* d_t
 static size_t propose_smem(int D) {
   const int T = D * (D + 1) / 2;
   return sizeof(double) * kPropPart * static_cast<size_t>(D | 1) +
-         sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kPropPart + 2 * static_cast<size_t>(D));
+         sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kPropPart + 2 * static_cast<size_t>(D));
 }
 
 static sps_status launch_propose(sps_ctx* ctx, sps_state* st, const double* d_theta, int64_t P, const double* z,

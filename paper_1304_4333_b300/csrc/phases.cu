@@ -1003,7 +1003,12 @@ __device__ __forceinline__ double prior_grad(const double* th, const double* mu,
   return -a;
 }
 
-__global__ void __launch_bounds__(kMalaThreads)
+// Four threads per particle (64 particles per block): each takes every fourth row of the
+// triangular products; the sums over a particle's coordinates (|z|^2, |w|^2), the prior log
+// kernel and the accept decision stay with its first thread, in the original order.
+constexpr int kMalaSub = 4;
+
+__global__ void __launch_bounds__(kMalaThreads * kMalaSub)
 mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gll, int64_t P, int D,
                     const float* __restrict__ L32, uint64_t seed, uint64_t step_arg,
                     const unsigned long long* __restrict__ step_dev, const double* __restrict__ mu,
@@ -1015,51 +1020,64 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
   extern __shared__ float ms[];
   const int T = D * (D + 1) / 2;
   float* Ls = ms;                                  // [T] packed lower triangle
-  float* vs = ms + ((T + 3) & ~3);                 // [D][64] gradient, then v
-  float* zs = vs + D * kMalaThreads;               // [D][64]
+  float* gs = ms + ((T + 3) & ~3);                 // [D][64] gradient of the log posterior
+  float* zs = gs + D * kMalaThreads;               // [D][64] normals
+  float* vs = zs + D * kMalaThreads;               // [D][64] v = (1/2) L' g + z
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
-  const int64_t p = blockIdx.x * static_cast<int64_t>(kMalaThreads) + threadIdx.x;
-  const bool live = p < P;
-  const int c = threadIdx.x;
-  double z2 = 0.0;
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kMalaThreads;
+  const int np = static_cast<int>(P - p0 < kMalaThreads ? P - p0 : kMalaThreads);
+  const int pp = threadIdx.x / kMalaSub, sub = threadIdx.x - pp * kMalaSub;
+  const int64_t p = p0 + pp;
+  const bool live = pp < np;
   if (live) {
     const double* t = th + p * D;
-    for (int i = 0; i < D; ++i)
-      vs[i * kMalaThreads + c] = static_cast<float>(gll[p * D + i] + prior_grad(t, mu, prec, D, full, i));
+    for (int i = sub; i < D; i += kMalaSub)
+      gs[i * kMalaThreads + pp] = static_cast<float>(gll[p * D + i] + prior_grad(t, mu, prec, D, full, i));
+  }
+  {
+    // draw (particle p, word q) as before: counter p * ceil(D / 4) + q
     const int per = (D + 3) / 4;
-    for (int q = 0; q < per; ++q) {
-      const uint4 r = draw(seed, static_cast<uint32_t>(p * per + q), kStreamPropose, step);
+    for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
+      const int qp = q / per, qq = q - qp * per;
+      const uint4 r = draw(seed, static_cast<uint32_t>((p0 + qp) * per + qq), kStreamPropose, step);
       const float2 a = normals2(r.x, r.y), b = normals2(r.z, r.w);
       const float v[4] = {a.x, a.y, b.x, b.y};
       for (int u = 0; u < 4; ++u)
-        if (4 * q + u < D) {
-          zs[(4 * q + u) * kMalaThreads + c] = v[u];
-          z2 += static_cast<double>(v[u]) * v[u];
-        }
+        if (4 * qq + u < D) zs[(4 * qq + u) * kMalaThreads + qp] = v[u];
     }
   }
   __syncthreads();
-  if (!live) return;
-  // v_j = (1/2) (L' g)_j + z_j, in place: (L' g)_j reads g_i for i >= j only
-  for (int j = 0; j < D; ++j) {
-    float a = 0.f;
-    for (int i = j; i < D; ++i) a = fmaf(Ls[i * (i + 1) / 2 + j], vs[i * kMalaThreads + c], a);
-    vs[j * kMalaThreads + c] = fmaf(0.5f, a, zs[j * kMalaThreads + c]);
-  }
-  const double* t = th + p * D;
+  if (live)
+    for (int j = sub; j < D; j += kMalaSub) {   // v_j = (1/2) (L' g)_j + z_j
+      float a = 0.f;
+      for (int i = j; i < D; ++i) a = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaThreads + pp], a);
+      vs[j * kMalaThreads + pp] = fmaf(0.5f, a, zs[j * kMalaThreads + pp]);
+    }
+  __syncwarp();
   double* o = th_o + p * D;
-  for (int i = 0; i < D; ++i) {
-    const float* Li = Ls + i * (i + 1) / 2;
-    float dlt = 0.f;
-    for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], vs[j * kMalaThreads + c], dlt);
-    o[i] = t[i] + static_cast<double>(dlt);
-    zq_o[p * D + i] = vs[i * kMalaThreads + c];
+  if (live) {
+    const double* t = th + p * D;
+    for (int i = sub; i < D; i += kMalaSub) {
+      const float* Li = Ls + i * (i + 1) / 2;
+      float dlt = 0.f;
+      for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], vs[j * kMalaThreads + pp], dlt);
+      o[i] = t[i] + static_cast<double>(dlt);
+      zq_o[p * D + i] = vs[i * kMalaThreads + pp];
+    }
   }
-  z2_o[p] = z2;
-  lp_o[p] = prior_log_kernel(o, mu, prec, D, full);
+  __syncwarp();   // the particle's new row is complete (global writes of its four lanes)
+  if (live && sub == 0) {
+    double z2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+      const float zd = zs[d * kMalaThreads + pp];
+      z2 += static_cast<double>(zd) * zd;
+    }
+    z2_o[p] = z2;
+    lp_o[p] = prior_log_kernel(o, mu, prec, D, full);
+  }
 }
 
-__global__ void __launch_bounds__(kMalaThreads)
+__global__ void __launch_bounds__(kMalaThreads * kMalaSub)
 mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restrict__ lp,
                    double* __restrict__ g, const double* __restrict__ th_p, const double* __restrict__ ll_p,
                    const double* __restrict__ lp_p, const double* __restrict__ g_p, const float* __restrict__ zq,
@@ -1073,24 +1091,32 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
   extern __shared__ float ms[];
   const int T = D * (D + 1) / 2;
   float* Ls = ms;
-  float* gs = ms + ((T + 3) & ~3);   // [D][64]
+  float* gs = ms + ((T + 3) & ~3);                                   // [D][64]
+  double* ws = reinterpret_cast<double*>(gs + ((D * kMalaThreads + 1) & ~1));   // [D][64]
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
-  const int64_t p = blockIdx.x * static_cast<int64_t>(kMalaThreads) + threadIdx.x;
-  const bool live = p < P;
-  const int c = threadIdx.x;
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kMalaThreads;
+  const int np = static_cast<int>(P - p0 < kMalaThreads ? P - p0 : kMalaThreads);
+  const int pp = threadIdx.x / kMalaSub, sub = threadIdx.x - pp * kMalaSub;
+  const int64_t p = p0 + pp;
+  const bool live = pp < np;
   if (live) {
     const double* tp = th_p + p * D;
-    for (int i = 0; i < D; ++i)
-      gs[i * kMalaThreads + c] = static_cast<float>(g_p[p * D + i] + prior_grad(tp, mu, prec, D, full, i));
+    for (int i = sub; i < D; i += kMalaSub)
+      gs[i * kMalaThreads + pp] = static_cast<float>(g_p[p * D + i] + prior_grad(tp, mu, prec, D, full, i));
   }
   __syncthreads();
+  if (live)
+    for (int j = sub; j < D; j += kMalaSub) {   // w_j = z_j + (1/2) (L' g')_j
+      float b = 0.f;
+      for (int i = j; i < D; ++i) b = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaThreads + pp], b);
+      ws[j * kMalaThreads + pp] = static_cast<double>(zq[p * D + j]) + 0.5 * static_cast<double>(b);
+    }
+  __syncwarp();
   bool acc = false;
-  if (live) {
+  if (live && sub == 0) {
     double w2 = 0.0;
     for (int j = 0; j < D; ++j) {
-      float b = 0.f;
-      for (int i = j; i < D; ++i) b = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaThreads + c], b);
-      const double w = static_cast<double>(zq[p * D + j]) + 0.5 * static_cast<double>(b);
+      const double w = ws[j * kMalaThreads + pp];
       w2 = fma(w, w, w2);
     }
     const double lpp = ll_p[p];
@@ -1099,15 +1125,18 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
     const uint4 r = draw(seed, static_cast<uint32_t>(p), kStreamAccept, step);
     acc = log(uniform53(r.x, r.y)) < la;
     if (acc) {
-      for (int d = 0; d < D; ++d) {
-        th[p * D + d] = th_p[p * D + d];
-        g[p * D + d] = g_p[p * D + d];
-      }
       ll[p] = lpp;
       lp[p] = lp_p[p];
     }
   }
-  const unsigned ballot = __ballot_sync(0xffffffffu, acc);
+  // the decision to the particle's four lanes, which copy its row and gradient
+  acc = __shfl_sync(0xffffffffu, acc ? 1 : 0, threadIdx.x & ~(kMalaSub - 1) & 31) != 0;
+  if (acc)
+    for (int d = sub; d < D; d += kMalaSub) {
+      th[p * D + d] = th_p[p * D + d];
+      g[p * D + d] = g_p[p * D + d];
+    }
+  const unsigned ballot = __ballot_sync(0xffffffffu, acc && sub == 0);
   if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, static_cast<unsigned long long>(__popc(ballot)));
 }
 
@@ -1638,15 +1667,16 @@ sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* si
                           flag_ptr(st, 0)));
   {
     const int T = D * (D + 1) / 2;
-    const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kMalaThreads);
-    const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + static_cast<size_t>(D) * kMalaThreads);
+    const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 3 * static_cast<size_t>(D) * kMalaThreads);
+    const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + ((static_cast<size_t>(D) * kMalaThreads + 1) & ~1)) +
+                          sizeof(double) * static_cast<size_t>(D) * kMalaThreads;
     SPS_CUDA_TRY(cudaFuncSetAttribute(mala_propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem_p)));
     SPS_CUDA_TRY(cudaFuncSetAttribute(mala_accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem_a)));
     const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
     const unsigned blocks = static_cast<unsigned>((st->P + kMalaThreads - 1) / kMalaThreads);
-    mala_propose_kernel<<<blocks, kMalaThreads, smem_p, ctx->stream>>>(
+    mala_propose_kernel<<<blocks, kMalaThreads * kMalaSub, smem_p, ctx->stream>>>(
         st->theta.as<double>(), st->grad.as<double>(), st->P, D, L32, st->seed, step, step_dev,
         ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(), prior_full(ctx), flag_ptr(st, 0),
         st->theta_prop.as<double>(), st->lp_prop.as<double>(), st->zq.as<float>(), st->z2.as<double>());
@@ -1654,7 +1684,7 @@ sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* si
     SPS_CUDA_TRY(cudaGetLastError());
     SPS_TRY(loglik_grad_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
                              st->grad_prop.as<double>()));
-    mala_accept_kernel<<<blocks, kMalaThreads, smem_a, ctx->stream>>>(
+    mala_accept_kernel<<<blocks, kMalaThreads * kMalaSub, smem_a, ctx->stream>>>(
         st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->grad.as<double>(),
         st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->grad_prop.as<double>(),
         st->zq.as<float>(), st->z2.as<double>(), L32, st->P, D, ctx->d_prior_mean.as<double>(),

@@ -728,6 +728,29 @@ __device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr, uint32_t lbo)
   return d;
 }
 
+// 32 lanes x 16 consecutive 32-bit columns from 16 registers: thread i writes lane (base + i).
+__device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] * B[smem desc]: A (128 rows x 16 bf16) from tensor memory, two bf16 per
+// 32-bit column, row i in lane i.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -744,10 +767,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return r;
 }
 
-template <int NC, int BN>
+// QT: q tiles in tensor memory (TMEM columns 384-511: hi then lo, two bf16 per column, one
+// buffer; the gradient MMAs read A from TMEM) instead of shared memory. C = 2 only.
+constexpr uint32_t kQtHi = 384, kQtLo = 448;
+
+template <int NC, int BN, bool QT>
 __global__ void __launch_bounds__(kGradThreads, 1)
 grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                const GradParams prm) {
+  static_assert(!QT || (NC == 1 && BN == 128), "q in TMEM: 64 columns each for hi and lo");
   static_assert(BN == 64 || BN == 128, "q tiles are whole 64-observation swizzle rows");
   constexpr int NBUF = 2;
   static_assert(NBUF * NC * BN <= static_cast<int>(kGradTmemOff), "forward accumulators below the gradient ones");
@@ -757,7 +785,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const GradLayout L = grad_layout(NC, BN, prm.kbx, prm.kbt, prm.stages, prm.th_bufs, prm.nq);
+  const GradLayout L = grad_layout(NC, BN, prm.kbx, prm.kbt, prm.stages, prm.th_bufs, QT ? 0 : prm.nq);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar);
   uint64_t* x_full = bars;
   uint64_t* x_empty = x_full + prm.stages;
@@ -893,10 +921,16 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
               const uint32_t dg = tmem_base + kGradTmemOff + static_cast<uint32_t>((c * prm.gch + ch) * prm.ng);
-              const uint64_t ah = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 0) * (BN / 64)) * kTileA);
-              const uint64_t al = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 1) * (BN / 64)) * kTileA);
-              ptx::mma_bf16(dg, ah + ka, bx, idesc_g, acc);
-              ptx::mma_bf16(dg, al + ka, bx, idesc_g, 1u);
+              if constexpr (QT) {
+                const uint32_t s8 = static_cast<uint32_t>(s) * 8u;   // 16 observations = 8 columns
+                mma_bf16_ts(dg, tmem_base + kQtHi + s8, bx, idesc_g, acc);
+                mma_bf16_ts(dg, tmem_base + kQtLo + s8, bx, idesc_g, 1u);
+              } else {
+                const uint64_t ah = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 0) * (BN / 64)) * kTileA);
+                const uint64_t al = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 1) * (BN / 64)) * kTileA);
+                ptx::mma_bf16(dg, ah + ka, bx, idesc_g, acc);
+                ptx::mma_bf16(dg, al + ka, bx, idesc_g, 1u);
+              }
             }
           }
           first_grad = false;
@@ -977,7 +1011,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
         const int qb = static_cast<int>(acc_count % static_cast<uint32_t>(prm.nq));
         const uint32_t qph = (acc_count / static_cast<uint32_t>(prm.nq)) & 1u;
         ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit) &&
-                                         ptx::mbar_wait_bounded(&q_empty[qb], qph ^ 1u, abort_flag, limit));
+                                         (QT || ptx::mbar_wait_bounded(&q_empty[qb], qph ^ 1u, abort_flag, limit)));
         if (!ok) break;
         ptx::tc_fence_after();
         const int valid = prm.t - tile * BN - col0;   // columns of this group inside [0, t)
@@ -1035,6 +1069,26 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
               pr[qq] = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);
             }
           }
+          if constexpr (QT) {
+            // q as BF16 hi + lo pairs into TMEM: observation pair (2w, 2w + 1) of the tile in
+            // column w of the hi and lo blocks; the previous tile's gradient MMAs must be done
+            uint32_t hw[16], lw[16];
+#pragma unroll
+            for (int h = 0; h < 16; ++h) {
+              const float q0 = v[0][2 * h], q1 = v[0][2 * h + 1];
+              hw[h] = pack_bf16x2(q0, q1);
+              const float h0 = __uint_as_float(hw[h] << 16), h1 = __uint_as_float(hw[h] & 0xFFFF0000u);
+              lw[h] = pack_bf16x2(q0 - h0, q1 - h1);
+            }
+            if (ch == 0) {
+              ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&q_empty[qb], qph ^ 1u, abort_flag, limit));
+              if (!ok) break;
+              ptx::tc_fence_after();
+            }
+            const uint32_t wcol = static_cast<uint32_t>((col0 + ch * 32) >> 1);
+            tmem_st_32x32b_x16(tmem_base + lane_base + kQtHi + wcol, hw);
+            tmem_st_32x32b_x16(tmem_base + lane_base + kQtLo + wcol, lw);
+          } else {
           // q as BF16 hi + lo into the swizzled tile: 8 observations (16 bytes) per store
 #pragma unroll
           for (int c = 0; c < NC; ++c)
@@ -1058,8 +1112,15 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
               st_shared_v4(base_l, lw[0], lw[1], lw[2], lw[3]);
             }
         }
+          }
+        if (!ok) break;
         // q visible to the tensor cores, then the MMA thread may take it
-        fence_proxy_async_smem();
+        if constexpr (QT) {
+          tmem_wait_st();
+          ptx::tc_fence_before();
+        } else {
+          fence_proxy_async_smem();
+        }
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&q_full[qb]);
 #pragma unroll
@@ -1471,33 +1532,42 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
 // Shape of a gradient call, or false when the tensor-core form does not fit (C - 1 > 2, or the
 // gradient accumulators or the pipeline do not fit TMEM / shared memory).
 static bool grad_shape(const sps_ctx* ctx, int* BN, int* ng, int* gch, int* stages, int* th_bufs, int* nq,
-                       uint32_t* smem_bytes) {
+                       uint32_t* smem_bytes, bool* qt) {
   const XEncoding& enc = ctx->enc;
   const int NC = ctx->NC;
   if (NC < 1 || NC > 2 || enc.bn == 0) return false;
   *BN = (NC == 1) ? 128 : 64;
   *ng = enc.k16 + enc.kc16;
   if (*ng > 256) return false;
-  // 32-column TMEM reads of the last accumulator may run 16 columns past it
-  *gch = (static_cast<int>(kGradTmemOff) + NC * 2 * *ng + 16 <= 512) ? 2 : 1;
-  if (static_cast<int>(kGradTmemOff) + NC * *gch * *ng + 16 > 512) return false;
+  const int off = static_cast<int>(kGradTmemOff);
+  // q in TMEM (C = 2) when the gradient accumulators end by column 384
+  *qt = (NC == 1) && off + *ng <= static_cast<int>(kQtHi);
+  if (*qt) {
+    *gch = (off + 2 * *ng <= static_cast<int>(kQtHi)) ? 2 : 1;
+  } else {
+    // 32-column TMEM reads of the last accumulator may run 16 columns past it
+    *gch = (off + NC * 2 * *ng + 16 <= 512) ? 2 : 1;
+    if (off + NC * *gch * *ng + 16 > 512) return false;
+  }
   const int kbx = enc.kx / kKB, kbt = enc.kt / kKB;
   for (int q = 2; q >= 1; --q)
     for (int tb = 2; tb >= 1; --tb)
-      for (int st = 6; st >= 3; --st)
-        if (grad_layout(NC, *BN, kbx, kbt, st, tb, q).total + 1024 <= kSmemBudget + 1024) {
+      for (int st = 6; st >= 3; --st) {
+        const int q_smem = *qt ? 0 : q;
+        if (grad_layout(NC, *BN, kbx, kbt, st, tb, q_smem).total + 1024 <= kSmemBudget + 1024) {
           *stages = st;
           *th_bufs = tb;
-          *nq = q;
-          *smem_bytes = grad_layout(NC, *BN, kbx, kbt, st, tb, q).total + 1024;
+          *nq = *qt ? 1 : q;
+          *smem_bytes = grad_layout(NC, *BN, kbx, kbt, st, tb, q_smem).total + 1024;
           return true;
         }
+      }
   return false;
 }
 
-template <int NC, int BN>
+template <int NC, int BN, bool QT>
 static sps_status run_grad(sps_ctx* ctx, const GradParams& prm, int grid, uint32_t smem_bytes) {
-  auto kern = grad_tc_kernel<NC, BN>;
+  auto kern = grad_tc_kernel<NC, BN, QT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
   if (e == cudaSuccess) {
     kern<<<grid, kGradThreads, smem_bytes, ctx->stream>>>(ctx->ll.mapXg, ctx->ll.mapT, prm);
@@ -1514,7 +1584,8 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
   LoglikScratch& S = ctx->ll;
   int BN = 0, ng = 0, gch = 0, stages = 0, th_bufs = 0, nq = 0;
   uint32_t smem_bytes = 0;
-  if (!grad_shape(ctx, &BN, &ng, &gch, &stages, &th_bufs, &nq, &smem_bytes))
+  bool qt = false;
+  if (!grad_shape(ctx, &BN, &ng, &gch, &stages, &th_bufs, &nq, &smem_bytes, &qt))
     return fail(ctx, SPS_ERR_UNSUPPORTED, "tensor-core gradient: unsupported shape");
   if (t < 1) return fail(ctx, SPS_ERR_UNSUPPORTED, "tensor-core gradient: empty prefix");
   GradParams prm{};
@@ -1577,8 +1648,9 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
   const int grid = std::max(1, std::min(ctx->num_sms, prm.n_items));
   hot_begin(ctx);
   sps_status st;
-  if (NC == 1) st = run_grad<1, 128>(ctx, prm, grid, smem_bytes);
-  else st = run_grad<2, 64>(ctx, prm, grid, smem_bytes);
+  if (NC == 1 && qt) st = run_grad<1, 128, true>(ctx, prm, grid, smem_bytes);
+  else if (NC == 1) st = run_grad<1, 128, false>(ctx, prm, grid, smem_bytes);
+  else st = run_grad<2, 64, false>(ctx, prm, grid, smem_bytes);
   hot_end(ctx);
   SPS_TRY(st);
   SPS_TRY(launch_finalize(ctx, d_theta, P, prm.partial, prm.n_chunks * 4, ppad, d_ll));
@@ -1595,7 +1667,8 @@ sps_status loglik_grad_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, 
                                 double* d_grad) {
   int BN, ng, gch, stages, tb, nq;
   uint32_t smem;
-  if (ctx->opt.precision == SPS_PREC_SPLIT && t >= 1 && grad_shape(ctx, &BN, &ng, &gch, &stages, &tb, &nq, &smem))
+  bool qt;
+  if (ctx->opt.precision == SPS_PREC_SPLIT && t >= 1 && grad_shape(ctx, &BN, &ng, &gch, &stages, &tb, &nq, &smem, &qt))
     return loglik_grad_tc(ctx, d_theta, P, t, d_ll, d_grad);
   return loglik_grad_fp32(ctx, d_theta, P, t, d_ll, d_grad);
 }

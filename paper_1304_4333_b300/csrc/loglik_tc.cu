@@ -1032,6 +1032,19 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
             if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
           }
           // per column: the log-likelihood factor and q (overwrites v with q)
+          if (NC == 1 && (ch * 32 + 32) <= valid) {
+            // whole chunk: no masks
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float u = v[0][j];
+              const float a = fabsf(u);
+              const float e = ptx::ex2_approx(-a);
+              const float r = __fdividef(1.f, 1.f + e);
+              la[j & 3] += a;
+              pr[j & 3] *= 1.f + e;
+              v[0][j] = ((u >= 0.f) ? r : e * r) - 0.5f;
+            }
+          } else
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const bool in = (ch * 32 + j) < valid;

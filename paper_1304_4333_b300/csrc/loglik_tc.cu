@@ -1042,7 +1042,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
               const float r = __fdividef(1.f, 1.f + e);
               la[j & 3] += a;
               pr[j & 3] *= 1.f + e;
-              v[0][j] = ((u >= 0.f) ? r : e * r) - 0.5f;
+              // sigmoid(eta) - 1/2 = sign(u) (1/2 - e / (1 + e))
+              v[0][j] = copysignf(fmaf(-e, r, 0.5f), u);
             }
           } else
 #pragma unroll

@@ -222,6 +222,9 @@ def run_ours(args, world, rank, local):
     P, n = w.P, w.n
     steps, warm = args.steps, args.warmup
     s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=1 + rank, precision=args.precision)
+    # the fused kernel's launch shape for this workload from the library's autotuner (setup,
+    # outside the timed region)
+    tuned = s.autotune(P, n) if args.precision == "split" else None
     stream = torch.cuda.Stream()
     lib = s.lib
     lib.sps_set_stream(s.ctx, C.c_void_p(stream.cuda_stream))
@@ -330,6 +333,8 @@ def run_ours(args, world, rank, local):
                                "16 groups x 4096 particles, one SPS cycle per step (C phase 64 obs, S phase, M step)",
                    "global_batch": P * world, "seq_len": n, "parallelism": f"replicas{world}",
                    "precision": args.precision, "mkernel": args.mkernel,
+                   "tile_shape": ({"rows": tuned["tile_rows"], "cluster": tuned["cluster"],
+                                   "chunk_obs": tuned["chunk_obs"], "source": "sps_autotune"} if tuned else None),
                    "l2": "flushed between steps (512 MB write)"},
         "wall_s": wall,
         "gpu_launches": launches,
@@ -339,7 +344,8 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Gop/s (ex2)",
                      "frac": achieved / sfu_peak, "traffic": traffic,
                      "traffic_source": traffic_src,
-                     "kernel": "loglik_tc_kernel<1,256>", "launches_timed": hot_launches,
+                     "kernel": f"loglik_tc_kernel<1,{tuned['tile_rows'] if tuned else 256}>",
+                     "launches_timed": hot_launches,
                      "avg_launch_ms": hot_avg_ms,
                      "bounds_ms_full_t": {"sfu": sfu_ms, "tensor_split": tensor_ms, "hbm": hbm_ms},
                      "peak_source": "148 SMs x 32 ex2/clk/SM x sm_max_mhz of MEASURED_PEAKS (ex2 rate from a probe)"},

@@ -1608,10 +1608,10 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
   prm.ppad = ppad;
   prm.n_ptiles = ppad / kBM;
   prm.n_tiles = static_cast<int>((t + BN - 1) / BN);
-  int chunk_tiles = std::max(1, std::min(prm.n_tiles, 4096 / BN));
-  while (chunk_tiles > 2 &&
-         static_cast<int64_t>(prm.n_ptiles) * ((prm.n_tiles + chunk_tiles - 1) / chunk_tiles) < 4LL * ctx->num_sms)
-    chunk_tiles /= 2;
+  // as few observation chunks as keep four work items per SM: fewer gradient partials to
+  // write and sum (each item writes its particles' gradient once)
+  const int64_t want_chunks = std::max<int64_t>(1, (4LL * ctx->num_sms + prm.n_ptiles - 1) / prm.n_ptiles);
+  int chunk_tiles = static_cast<int>(std::max<int64_t>(1, (prm.n_tiles + want_chunks - 1) / want_chunks));
   prm.chunk_tiles = chunk_tiles;
   prm.n_chunks = (prm.n_tiles + chunk_tiles - 1) / chunk_tiles;
   prm.n_items = prm.n_ptiles * prm.n_chunks;

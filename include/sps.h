@@ -272,11 +272,12 @@ sps_status sps_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out
 /* Log-likelihood and its gradient d ll / d theta_c = sum_{s<=t} (1[y_s = c] - p_{s,c}) x_s
  * (the derivative of Eq. 1; the paper prints no gradient).
  *   grad: [P x D] FP64 output, class-major like theta (mem).
- * With options.precision = SPS_PREC_SPLIT and C - 1 <= 2 (and gradient accumulators that fit
- * TMEM: (k16 + kc16) (C - 1) <= 240, k16 / kc16 the covariate counts rounded up to 16): tensor
- * cores, the forward products as in sps_loglik and sum_s q_s x_s as a second BF16 hi + lo MMA
- * (q = p - 1/2 for C = 2, p_c for C > 2) with FP32 accumulation per work item and FP64 across
- * items. Otherwise: FP32 SIMT products and residuals, FP64 sums across 128-observation tiles.
+ * With options.precision = SPS_PREC_SPLIT and C - 1 <= 3 (and gradient accumulators that fit
+ * TMEM: k16 + kc16 <= 256 for C = 2, (k16 + kc16) 2 <= 240 for C = 3, (k16 + kc16) 3 <= 400 for
+ * C = 4; k16 / kc16 the covariate counts rounded up to 16): tensor cores, the forward products
+ * as in sps_loglik and sum_s q_s x_s as a second BF16 hi + lo MMA (q = p - 1/2 for C = 2, p_c
+ * for C > 2) with FP32 accumulation per work item and FP64 across items. Otherwise: FP32 SIMT
+ * products and residuals, FP64 sums across 128-observation tiles.
  * One context always uses the same form for the same shape. */
 sps_status sps_loglik_grad(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
                            double* grad, int32_t mem);

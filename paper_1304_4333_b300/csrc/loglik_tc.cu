@@ -679,7 +679,13 @@ __global__ void finalize_batched_kernel(const int64_t* __restrict__ tab, int M, 
 // written once per item as FP32 partials.
 constexpr int kGradWarps = 18;   // producer, MMA issuer, four epilogue groups of four warps
 constexpr int kGradThreads = 32 * kGradWarps;
-constexpr uint32_t kGradTmemOff = 256;   // gradient accumulators from this TMEM column
+// Forward accumulators and the TMEM column where the gradient accumulators start, per shape:
+// two accumulators of NC x BN columns (C - 1 <= 2) or one (C - 1 = 3, 32-observation tiles).
+__host__ __device__ constexpr int grad_nbuf(int NC) { return NC == 3 ? 1 : 2; }
+__host__ __device__ constexpr int grad_bn(int NC) { return NC == 1 ? 128 : (NC == 2 ? 64 : 32); }
+__host__ __device__ constexpr uint32_t grad_goff(int NC) {
+  return static_cast<uint32_t>(grad_nbuf(NC) * NC * grad_bn(NC));
+}
 
 struct GradParams {
   int t, ppad, n_ptiles, n_tiles, chunk_tiles, n_chunks, n_items;
@@ -704,7 +710,7 @@ __host__ __device__ inline GradLayout grad_layout(int NC, int BN, int kbx, int k
   GradLayout L;
   L.x_bytes = static_cast<uint32_t>(kbx) * static_cast<uint32_t>(BN) * 128u;
   L.th_bytes = static_cast<uint32_t>(NC * kbt) * kTileA;
-  L.q_bytes = static_cast<uint32_t>(NC * 2 * (BN / 64)) * kTileA;   // [class][hi, lo][K block]
+  L.q_bytes = static_cast<uint32_t>(NC * 2 * ((BN + 63) / 64)) * kTileA;   // [class][hi, lo][K block]
   L.off_x = 0;
   L.off_th = L.off_x + stages * L.x_bytes;
   L.off_q = L.off_th + th_bufs * L.th_bytes;
@@ -776,12 +782,17 @@ __global__ void __launch_bounds__(kGradThreads, 1)
 grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                const GradParams prm) {
   static_assert(!QT || (NC == 1 && BN == 128), "q in TMEM: 64 columns each for hi and lo");
-  static_assert(BN == 64 || BN == 128, "q tiles are whole 64-observation swizzle rows");
-  constexpr int NBUF = 2;
-  static_assert(NBUF * NC * BN <= static_cast<int>(kGradTmemOff), "forward accumulators below the gradient ones");
-  // two groups per accumulator, each taking half of a tile's columns
-  constexpr int COLS = BN / 2;
+  static_assert(BN == grad_bn(NC), "tile rows of the shape");
+  constexpr int NBUF = grad_nbuf(NC);
+  constexpr uint32_t GOFF = grad_goff(NC);
+  constexpr int QKB = (BN + 63) / 64;             // 64-observation swizzle blocks of a q tile (a
+                                                  // 32-observation tile uses half of each row)
+  // with two accumulators two groups share each, half of a tile's columns each; with one, a
+  // single group takes whole tiles and the others idle
+  constexpr int GPW = (NBUF == 2) ? 2 : 1;        // working groups per accumulator
+  constexpr int COLS = BN / GPW;
   constexpr int NCH = COLS / 32;
+  static_assert(COLS % 32 == 0, "32-column TMEM loads");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -812,8 +823,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
       ptx::mbar_init(&th_full[i], 1);
       ptx::mbar_init(&th_empty[i], 1);
       ptx::mbar_init(&acc_full[i], 1);
-      ptx::mbar_init(&acc_empty[i], 8);   // the eight warps of the two owning groups
-      ptx::mbar_init(&q_full[i], 8);
+      ptx::mbar_init(&acc_empty[i], 4 * GPW);   // the warps of the owning groups
+      ptx::mbar_init(&q_full[i], 4 * GPW);
       ptx::mbar_init(&q_empty[i], 1);
     }
     ptx::mbar_init(g_full, 1);
@@ -920,14 +931,14 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
             const uint32_t acc = (first_grad && s < prm.gch) ? 0u : 1u;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-              const uint32_t dg = tmem_base + kGradTmemOff + static_cast<uint32_t>((c * prm.gch + ch) * prm.ng);
+              const uint32_t dg = tmem_base + GOFF + static_cast<uint32_t>((c * prm.gch + ch) * prm.ng);
               if constexpr (QT) {
                 const uint32_t s8 = static_cast<uint32_t>(s) * 8u;   // 16 observations = 8 columns
                 mma_bf16_ts(dg, tmem_base + kQtHi + s8, bx, idesc_g, acc);
                 mma_bf16_ts(dg, tmem_base + kQtLo + s8, bx, idesc_g, 1u);
               } else {
-                const uint64_t ah = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 0) * (BN / 64)) * kTileA);
-                const uint64_t al = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 1) * (BN / 64)) * kTileA);
+                const uint64_t ah = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 0) * QKB) * kTileA);
+                const uint64_t al = ptx::sdesc_sw128(qbase + static_cast<uint32_t>((c * 2 + 1) * QKB) * kTileA);
                 ptx::mma_bf16(dg, ah + ka, bx, idesc_g, acc);
                 ptx::mma_bf16(dg, al + ka, bx, idesc_g, 1u);
               }
@@ -939,8 +950,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
           return true;
         };
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
-          const int buf = static_cast<int>(acc_count & 1u);
-          const uint32_t aph = (acc_count >> 1) & 1u;
+          const int buf = static_cast<int>(acc_count % NBUF);
+          const uint32_t aph = (acc_count / NBUF) & 1u;
           if (!ptx::mbar_wait_bounded(&acc_empty[buf], aph ^ 1u, abort_flag, limit)) { ok = false; break; }
           if (!ptx::mbar_wait_bounded(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
           ptx::tc_fence_after();
@@ -989,8 +1000,9 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
   } else {
     // ------------------------------------------------------------------ epilogue
     const int wg = (warp - 2) >> 2;                   // group
-    const int own = wg >> 1;                          // its tiles: acc_count % 2 == own
-    const int col0 = (wg & 1) * COLS;                 // its half of each tile's columns
+    const bool working = wg < NBUF * GPW;             // idle groups only write zero partials
+    const int own = wg / GPW;                         // its tiles: acc_count % NBUF == own
+    const int col0 = (wg % GPW) * COLS;               // its share of each tile's columns
     const int quad = warp & 3;
     const int row = quad * 32 + lane;                 // particle within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
@@ -1003,11 +1015,12 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
       const int tile_lo = chunk * prm.chunk_tiles;
       const int tile_hi = min(tile_lo + prm.chunk_tiles, prm.n_tiles);
       float ksum = 0.f, kcomp = 0.f;
-      const int first = tile_lo + static_cast<int>((static_cast<uint32_t>(own) + 2u - (acc_base & 1u)) & 1u);
-      for (int tile = first; tile < tile_hi; tile += 2) {
+      const int first = working ? tile_lo + static_cast<int>((static_cast<uint32_t>(own) + NBUF - acc_base % NBUF) % NBUF)
+                                : tile_hi;
+      for (int tile = first; tile < tile_hi; tile += NBUF) {
         const uint32_t acc_count = acc_base + static_cast<uint32_t>(tile - tile_lo);
-        const int buf = static_cast<int>(acc_count & 1u);
-        const uint32_t aph = (acc_count >> 1) & 1u;
+        const int buf = static_cast<int>(acc_count % NBUF);
+        const uint32_t aph = (acc_count / NBUF) & 1u;
         const int qb = static_cast<int>(acc_count % static_cast<uint32_t>(prm.nq));
         const uint32_t qph = (acc_count / static_cast<uint32_t>(prm.nq)) & 1u;
         ok = __all_sync(0xffffffffu, ptx::mbar_wait_bounded(&acc_full[buf], aph, abort_flag, limit) &&
@@ -1120,8 +1133,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
                 const float h0 = __uint_as_float(hw[h] << 16), h1 = __uint_as_float(hw[h] & 0xFFFF0000u);
                 lw[h] = pack_bf16x2(q0 - h0, q1 - h1);
               }
-              const uint32_t base_h = qrow + (static_cast<uint32_t>(c * 2 + 0) * (BN / 64) + kb) * kTileA + chunk16 * 16u;
-              const uint32_t base_l = qrow + (static_cast<uint32_t>(c * 2 + 1) * (BN / 64) + kb) * kTileA + chunk16 * 16u;
+              const uint32_t base_h = qrow + (static_cast<uint32_t>(c * 2 + 0) * QKB + kb) * kTileA + chunk16 * 16u;
+              const uint32_t base_l = qrow + (static_cast<uint32_t>(c * 2 + 1) * QKB + kb) * kTileA + chunk16 * 16u;
               st_shared_v4(base_h, hw[0], hw[1], hw[2], hw[3]);
               st_shared_v4(base_l, lw[0], lw[1], lw[2], lw[3]);
             }
@@ -1171,12 +1184,12 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
         for (int c = 0; c < NC; ++c)
           for (int j0 = 0; j0 < prm.ng; j0 += 32) {
             float g[32];
-            ptx::tmem_ld_32x32b_x32(tmem_base + lane_base + kGradTmemOff + static_cast<uint32_t>(c * prm.gch * prm.ng + j0), g);
+            ptx::tmem_ld_32x32b_x32(tmem_base + lane_base + GOFF + static_cast<uint32_t>(c * prm.gch * prm.ng + j0), g);
             ptx::tmem_wait_ld();
             for (int ch = 1; ch < prm.gch; ++ch) {
               float h[32];
               ptx::tmem_ld_32x32b_x32(
-                  tmem_base + lane_base + kGradTmemOff + static_cast<uint32_t>((c * prm.gch + ch) * prm.ng + j0), h);
+                  tmem_base + lane_base + GOFF + static_cast<uint32_t>((c * prm.gch + ch) * prm.ng + j0), h);
               ptx::tmem_wait_ld();
 #pragma unroll
               for (int q = 0; q < 32; ++q) g[q] += h[q];
@@ -1549,11 +1562,11 @@ static bool grad_shape(const sps_ctx* ctx, int* BN, int* ng, int* gch, int* stag
                        uint32_t* smem_bytes, bool* qt) {
   const XEncoding& enc = ctx->enc;
   const int NC = ctx->NC;
-  if (NC < 1 || NC > 2 || enc.bn == 0) return false;
-  *BN = (NC == 1) ? 128 : 64;
+  if (NC < 1 || NC > 3 || enc.bn == 0) return false;
+  *BN = grad_bn(NC);
   *ng = enc.k16 + enc.kc16;
   if (*ng > 256) return false;
-  const int off = static_cast<int>(kGradTmemOff);
+  const int off = static_cast<int>(grad_goff(NC));
   // q in TMEM (C = 2) when the gradient accumulators end by column 384
   *qt = (NC == 1) && off + *ng <= static_cast<int>(kQtHi);
   if (*qt) {
@@ -1664,7 +1677,8 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
   sps_status st;
   if (NC == 1 && qt) st = run_grad<1, 128, true>(ctx, prm, grid, smem_bytes);
   else if (NC == 1) st = run_grad<1, 128, false>(ctx, prm, grid, smem_bytes);
-  else st = run_grad<2, 64, false>(ctx, prm, grid, smem_bytes);
+  else if (NC == 2) st = run_grad<2, 64, false>(ctx, prm, grid, smem_bytes);
+  else st = run_grad<3, 32, false>(ctx, prm, grid, smem_bytes);
   hot_end(ctx);
   SPS_TRY(st);
   SPS_TRY(launch_finalize(ctx, d_theta, P, prm.partial, prm.n_chunks * 4, ppad, d_ll));

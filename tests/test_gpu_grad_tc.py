@@ -1,4 +1,4 @@
-"""The tensor-core gradient (split precision, C - 1 <= 2) against the FP64 oracle.
+"""The tensor-core gradient (split precision, C - 1 <= 3) against the FP64 oracle.
 
 Bound per gradient entry (c, i): the operands are BF16 hi + lo splits (theta, X: dropped lo x lo
 product, relative 2^-16 of each product; q: relative 2^-16) with FP32 accumulation within a work
@@ -43,7 +43,8 @@ def _eta_bound(X, th, C, t):
 
 
 @pytest.mark.parametrize("C,n,k,t", [(2, 1500, 30, 1500), (2, 1500, 30, 701), (2, 300, 7, 1),
-                                      (3, 1300, 12, 1300), (3, 1300, 12, 555), (3, 900, 74, 900)])
+                                      (3, 1300, 12, 1300), (3, 1300, 12, 555), (3, 900, 74, 900),
+                                      (4, 1000, 50, 1000), (4, 700, 9, 333)])
 def test_tensor_core_gradient_against_oracle(cuda, C, n, k, t):
     from paper_1304_4333_b300 import Sps
     X, y = _data(n, k, C, seed=n + k + C)

@@ -677,8 +677,10 @@ __global__ void finalize_batched_kernel(const int64_t* __restrict__ tab, int M, 
 // memory as the B operand read MN-major (N = the covariate columns [Xh | Xl], K = observations).
 // D stays in TMEM across the tiles of a work item (gch chains per class, by K slice) and is
 // written once per item as FP32 partials.
-constexpr int kGradWarps = 18;   // producer, MMA issuer, four epilogue groups of four warps
-constexpr int kGradThreads = 32 * kGradWarps;
+// producer, MMA issuer and the epilogue groups of four warps: four groups with two forward
+// accumulators, one with one (C - 1 = 3; a smaller block leaves its warps more registers)
+__host__ __device__ constexpr int grad_groups(int NC) { return NC == 3 ? 1 : 4; }
+__host__ __device__ constexpr int grad_threads(int NC) { return 32 * (2 + 4 * grad_groups(NC)); }
 // Forward accumulators and the TMEM column where the gradient accumulators start, per shape:
 // two accumulators of NC x BN columns (C - 1 <= 2) or one (C - 1 = 3, 32-observation tiles).
 __host__ __device__ constexpr int grad_nbuf(int NC) { return NC == 3 ? 1 : 2; }
@@ -693,7 +695,7 @@ struct GradParams {
   int stages, th_bufs, nq;   // X stages, theta buffers, q buffers
   int ng;                    // gradient columns per class: k16 + kc16 ([Xh | Xl] of a row)
   int gch;                   // accumulator chains per class (K slices alternate between them)
-  double* partial;           // [n_chunks][4][ppad] log-likelihood partial sums
+  double* partial;           // [n_chunks][groups][ppad] log-likelihood partial sums
   float* gpartial;           // [n_chunks][ppad][NC ng] gradient partial sums
   int* flag;
   unsigned long long timeout_ns;
@@ -778,7 +780,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 constexpr uint32_t kQtHi = 384, kQtLo = 448;
 
 template <int NC, int BN, bool QT>
-__global__ void __launch_bounds__(kGradThreads, 1)
+__global__ void __launch_bounds__(grad_threads(NC), 1)
 grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                const GradParams prm) {
   static_assert(!QT || (NC == 1 && BN == 128), "q in TMEM: 64 columns each for hi and lo");
@@ -1172,7 +1174,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
       }
       if (!ok) break;
       acc_base += static_cast<uint32_t>(tile_hi - tile_lo);
-      prm.partial[(static_cast<size_t>(chunk) * 4 + wg) * prm.ppad + ptile * kBM + row] =
+      prm.partial[(static_cast<size_t>(chunk) * grad_groups(NC) + wg) * prm.ppad + ptile * kBM + row] =
           static_cast<double>(ksum) - static_cast<double>(kcomp);
       if (wg == 0) {
         // the item's gradient sums: TMEM -> FP32 partials, chains added
@@ -1597,7 +1599,7 @@ static sps_status run_grad(sps_ctx* ctx, const GradParams& prm, int grid, uint32
   auto kern = grad_tc_kernel<NC, BN, QT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
   if (e == cudaSuccess) {
-    kern<<<grid, kGradThreads, smem_bytes, ctx->stream>>>(ctx->ll.mapXg, ctx->ll.mapT, prm);
+    kern<<<grid, grad_threads(NC), smem_bytes, ctx->stream>>>(ctx->ll.mapXg, ctx->ll.mapT, prm);
     ++ctx->launches;
     e = cudaGetLastError();
   }
@@ -1665,7 +1667,7 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
     SPS_CUDA_TRY(cudaGetLastError());
   }
   SPS_TRY(ensure_lin(ctx, t));
-  SPS_CUDA_TRY(S.partial.reserve(sizeof(double) * static_cast<size_t>(prm.n_chunks) * 4 * ppad));
+  SPS_CUDA_TRY(S.partial.reserve(sizeof(double) * static_cast<size_t>(prm.n_chunks) * grad_groups(NC) * ppad));
   SPS_CUDA_TRY(S.gpartial.reserve(sizeof(float) * static_cast<size_t>(prm.n_chunks) * ppad * NC * ng));
   SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
   prm.partial = S.partial.as<double>();
@@ -1681,7 +1683,7 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
   else st = run_grad<3, 32, false>(ctx, prm, grid, smem_bytes);
   hot_end(ctx);
   SPS_TRY(st);
-  SPS_TRY(launch_finalize(ctx, d_theta, P, prm.partial, prm.n_chunks * 4, ppad, d_ll));
+  SPS_TRY(launch_finalize(ctx, d_theta, P, prm.partial, prm.n_chunks * grad_groups(NC), ppad, d_ll));
   const int64_t entries = P * ctx->D;
   grad_tc_finalize_kernel<<<static_cast<unsigned>((entries + 255) / 256), 256, 0, ctx->stream>>>(
       prm.gpartial, prm.n_chunks, P, ppad, NC, k, ng, enc.k16, enc.kc, enc.invperm_dev.as<int>(),

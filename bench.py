@@ -353,6 +353,11 @@ def run_ours(args, world, rank, local):
     }
     if not args.no_sps:
         line["sps"] = sps_wall(w, rank)
+    if args.sps_ladder:
+        forms = [tuple(f.split("_")) for f in args.sps_ladder.split(",")]
+        if any(f not in (("split", "rw"), ("split", "mala"), ("fp32", "rw"), ("fp32", "mala")) for f in forms):
+            raise SystemExit(f"--sps-ladder: unknown form in {args.sps_ladder!r}")
+        line.setdefault("sps", {})["ladder"] = sps_ladder(w, forms, args.sps_max_groups)
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_throughput(w)
     print(json.dumps(line), flush=True)
@@ -405,6 +410,41 @@ def sps_wall(w, rank):
     return out
 
 
+def sps_ladder(w, forms, max_groups: int, target: float = 0.05):
+    """The wall-time half of the metric as a measured protocol instead of a projection: for each
+    form (precision, M kernel), run seed 1 at the workload's groups x particles and double the
+    number of groups (particles per group stay at the workload's value, the resampling bound)
+    until its log-ML NSE is at most the target; then run seeds 2 and 3 at that rung and report
+    the median wall time of the three seeds with each seed's NSE. A form whose seed 1 misses the
+    target at max_groups reports its last rung with "reached": false."""
+    from paper_1304_4333_b300 import Sps
+    out = {}
+    for prec, mk in forms:
+        def one(J, seed):
+            s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=seed, precision=prec, mkernel=mk)
+            try:
+                r = s.run(J, w.N, record=False)
+            finally:
+                s.close()
+            return {"groups": J, "seed": seed, "wall_s": r.seconds, "log_ml": r.log_ml,
+                    "log_ml_nse": r.log_ml_nse, "m_steps": r.m_steps}
+        rungs, J = [], w.J
+        while True:
+            rungs.append(one(J, 1))
+            if rungs[-1]["log_ml_nse"] <= target or 2 * J > max_groups:
+                break
+            J *= 2
+        reached = rungs[-1]["log_ml_nse"] <= target
+        seeds = [rungs[-1]] + ([one(J, 2), one(J, 3)] if reached else [])
+        walls = sorted(x["wall_s"] for x in seeds)
+        out[f"{prec}_{mk}"] = {"reached": reached, "rung": f"{J} groups x {w.N}",
+                               "median_wall_s": walls[len(walls) // 2], "seeds": seeds,
+                               "ladder_seed1": [{k: x[k] for k in ("groups", "wall_s", "log_ml_nse")}
+                                                for x in rungs]}
+    out["target_log_ml_nse"] = target
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,6 +456,10 @@ def main():
                     help="M kernel of the timed step (MALA evaluates through the gradient kernel)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sps", action="store_true", help="skip the whole-simulator wall-time runs")
+    ap.add_argument("--sps-ladder", default="",
+                    help="comma list of forms (split_rw, split_mala, fp32_rw) run to log-ML NSE <= 0.05 "
+                         "by doubling the groups, three seeds at the rung reached (adds sps.ladder)")
+    ap.add_argument("--sps-max-groups", type=int, default=1024)
     ap.add_argument("--ncu-step", action="store_true",
                     help="run one extra step after warm-up inside a CUDA profiler range (for ncu --profile-from-start off)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -40,6 +40,7 @@ cudaError_t DevBuf::reserve(size_t nbytes) {
 
 sps_ctx::~sps_ctx() {
   for (cudaEvent_t e : hot_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : copy_events) cudaEventDestroy(e);
 }
 
 namespace sps {
@@ -455,6 +456,10 @@ void sps_destroy(sps_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
   delete ctx;
 }
 
@@ -589,6 +594,80 @@ static sps_status check_finite_ll(sps_ctx* ctx, const double* h_ll, int64_t P) {
   return SPS_OK;
 }
 
+// Split-precision log-likelihood of host-resident particles in slices: theta is copied slice by
+// slice on a second stream while the fused kernel runs on the slices already on the device, and
+// each slice's results are copied back as soon as they are final. At 65 536 particles and
+// k = 30 the host-to-device copy (15.7 MB) takes about twice as long as the kernel, so without
+// slices the two add up; with them the call takes about the copy plus one slice's kernel.
+// Results equal those of one call on all particles up to the order of the FP32/FP64 partial
+// sums (the observation chunking of a launch depends on its particle count).
+static constexpr int64_t kHostSlice = 16384;   // particles per slice at least
+static constexpr int kMaxHostSlices = 8;
+
+static sps_status loglik_host_sliced(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll) {
+  LoglikScratch& S = ctx->ll;
+  const int64_t D = ctx->D;
+  const int ns = static_cast<int>(std::min<int64_t>(kMaxHostSlices, P / kHostSlice));
+  const int64_t per = ((P + ns - 1) / ns + 255) / 256 * 256;   // whole 256-particle tile pairs
+  if (!ctx->copy_stream) {
+    const cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      ctx->copy_stream = nullptr;
+      return fail(ctx, SPS_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+  }
+  while (ctx->copy_events.size() < static_cast<size_t>(ns) + 1) {
+    cudaEvent_t e;
+    SPS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->copy_events.push_back(e);
+  }
+  SPS_CUDA_TRY(S.aux.reserve(kMaxHostSlices * sizeof(int)));
+  int* d_flags = S.aux.as<int>();
+  double* d_theta = S.theta_in.as<double>();
+  double* d_ll = S.ll_out.as<double>();
+  cudaEvent_t* ev = ctx->copy_events.data();
+  // the copies overwrite theta_in: they start after all earlier work on the context's stream
+  SPS_CUDA_TRY(cudaEventRecord(ev[ns], ctx->stream));
+  SPS_CUDA_TRY(cudaStreamWaitEvent(ctx->copy_stream, ev[ns], 0));
+  auto finish = [&](sps_status st) {
+    // no copy of the caller's buffer may still run when the call returns
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamSynchronize(ctx->stream);
+    return st;
+  };
+  int used = 0;
+  for (int i = 0; i < ns; ++i) {
+    const int64_t off = i * per, cnt = std::min(per, P - off);
+    if (cnt <= 0) break;
+    const cudaError_t e = cudaMemcpyAsync(d_theta + off * D, theta + off * D, cnt * D * sizeof(double),
+                                          cudaMemcpyHostToDevice, ctx->copy_stream);
+    if (e != cudaSuccess) return finish(fail(ctx, SPS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e)));
+    if (cudaEventRecord(ev[i], ctx->copy_stream) != cudaSuccess)
+      return finish(fail(ctx, SPS_ERR_CUDA, "cudaEventRecord"));
+    ++used;
+  }
+  for (int i = 0; i < used; ++i) {
+    const int64_t off = i * per, cnt = std::min(per, P - off);
+    if (cudaStreamWaitEvent(ctx->stream, ev[i], 0) != cudaSuccess)
+      return finish(fail(ctx, SPS_ERR_CUDA, "cudaStreamWaitEvent"));
+    const sps_status st = loglik_split(ctx, d_theta + off * D, cnt, t, d_ll + off);
+    if (st != SPS_OK) return finish(st);
+    // each launch clears the timeout flag: keep this slice's flag
+    cudaError_t e = cudaMemcpyAsync(d_flags + i, S.flag.ptr, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ll + off, d_ll + off, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return finish(fail(ctx, SPS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e)));
+  }
+  int flags[kMaxHostSlices] = {};
+  cudaError_t e = cudaMemcpyAsync(flags, d_flags, used * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  finish(SPS_OK);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, SPS_ERR_CUDA, std::string("sliced loglik: ") + cudaGetErrorString(e));
+  for (int i = 0; i < used; ++i)
+    if (flags[i]) return fail(ctx, SPS_ERR_TIMEOUT, "loglik kernel: bounded wait timed out");
+  return check_finite_ll(ctx, ll, P);
+}
+
 sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
                       int32_t precision, int32_t mem) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
@@ -600,6 +679,8 @@ sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, d
   const size_t tb = static_cast<size_t>(P) * ctx->D * sizeof(double);
   SPS_CUDA_TRY(S.theta_in.reserve(tb));
   SPS_CUDA_TRY(S.ll_out.reserve(P * sizeof(double)));
+  if (precision == SPS_PREC_SPLIT && P >= 2 * kHostSlice && !ctx->capturing)
+    return loglik_host_sliced(ctx, theta, P, t, ll);
   SPS_CUDA_TRY(cudaMemcpyAsync(S.theta_in.ptr, theta, tb, cudaMemcpyHostToDevice, ctx->stream));
   SPS_TRY(loglik_dispatch(ctx, S.theta_in.as<double>(), P, t, S.ll_out.as<double>(), precision));
   SPS_CUDA_TRY(cudaMemcpyAsync(ll, S.ll_out.ptr, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

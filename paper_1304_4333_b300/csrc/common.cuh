@@ -137,6 +137,8 @@ struct sps_ctx {
   bool capturing = false;                // stream capture in progress: no event records
   cudaStream_t cap_stream = nullptr;     // private non-blocking stream for graph capture (the
                                          // legacy default stream cannot be captured)
+  cudaStream_t copy_stream = nullptr;    // host-memory calls: theta slices are copied here
+  std::vector<cudaEvent_t> copy_events;  // one per slice, plus one ordering event
   std::vector<cudaEvent_t> hot_events;   // pairs (start, stop)
   size_t hot_used = 0;                   // events in use (2 per recorded launch)
   ~sps_ctx();

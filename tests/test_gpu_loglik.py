@@ -231,3 +231,21 @@ def test_autotune_keeps_parity_and_is_no_slower(torch_cuda):
     ref = oracle_loglik(X, y, th, 3, 2900)
     assert np.all(np.abs(after - ref) <= _tol(X, th, 3, 2900, ref, "split"))
     assert np.all(np.abs(before - ref) <= _tol(X, th, 3, 2900, ref, "split"))
+
+
+@pytest.mark.parametrize("P", [65_536, 50_003])
+def test_host_sliced_matches_device(torch_cuda, P):
+    # host-memory calls of at least 32 768 particles copy theta in slices that overlap the fused
+    # kernel; results agree with one device-memory call up to the order of partial sums
+    torch = torch_cuda
+    w = synthetic.make_c2()
+    theta = synthetic.particles_around(w.theta_true, P, 0.1, seed=3)
+    s = _sps(w.X, w.y, w.C)
+    for t in (w.n, 12_345):
+        host = s.loglik(theta, t, "split")
+        dev = s.loglik(torch.from_numpy(theta).cuda(), t, "split")
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(host, dev.cpu().numpy(), rtol=1e-7, atol=0)
+    idx = np.array([0, 16_383, 16_384, P // 2, P - 1])
+    ref = oracle_loglik(w.X, w.y, theta[idx], w.C, 12_345)
+    np.testing.assert_allclose(host[idx], ref, rtol=1e-5)

@@ -215,7 +215,10 @@ sps_status sps_counters(sps_ctx* ctx, int32_t reset, int64_t* launches, int64_t*
  * Sec. 2.1): ll[p] = sum_{s<=t} log P(Y_s = y_s | x_s, theta_p).
  *   theta: [P x D] FP64 class-major (mem); ll: [P] FP64 output (mem); 1 <= P; 0 <= t <= n.
  *   precision: sps_precision (the context's option is only the default of sps_run).
- * Deterministic: the same theta always gives the same bits. */
+ * Deterministic: the same theta always gives the same bits. With mem = SPS_MEM_HOST the call
+ * returns after the results are in ll; split-precision calls of at least 32 768 particles copy
+ * theta in up to eight particle slices on a second stream of the library, overlapping the copy
+ * with the kernel, and agree with a device-memory call up to the order of partial sums. */
 sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll,
                       int32_t precision, int32_t mem);
 

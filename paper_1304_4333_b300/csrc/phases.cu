@@ -1916,7 +1916,10 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
   int64_t block = std::max<int64_t>(1, std::min<int64_t>(ctx->opt.cphase_block > 0 ? ctx->opt.cphase_block : 64, max_rows));
   SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(float2) * max_rows * P));
   SPS_CUDA_TRY(st->lwstate.reserve(sizeof(float2) * P));
-  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * std::max<int64_t>(max_rows, st->J)));
+  // ESS of the rows of a block (the group log-mean-exp increments after the loop), plus one slot
+  // that keeps the ESS at the stop row of a known-target C phase
+  const int64_t ess_slot = std::max<int64_t>(max_rows, st->J);
+  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * (ess_slot + 1)));
   SPS_CUDA_TRY(st->gmax.reserve(sizeof(double) * st->J));
   if (lpl_out) SPS_CUDA_TRY(st->lpl_dev.reserve(sizeof(double) * max_rows * st->J));
   SPS_CUDA_TRY(cudaMemsetAsync(st->lwstate.ptr, 0, sizeof(float2) * P, ctx->stream));
@@ -1926,8 +1929,11 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
   std::vector<double> lme_rows, lme_prev(st->J, 0.0);   // log mean of the weights before s
   int64_t found = -1;
   double ess_found = 0.0;
+  // With a target and no log predictive likelihoods the stop row is known: blocks end at the
+  // target, no ESS is read back inside the loop and the call synchronises at most once, at the end.
+  const bool known = (t_target > 0) && !lpl_out;
   while (s < n) {
-    const int64_t b = std::min<int64_t>(block, n - s);
+    const int64_t b = known ? std::min<int64_t>(block, t_target - s) : std::min<int64_t>(block, n - s);
     SPS_TRY(cphase_increments(ctx, st->theta.as<double>(), P, s, s + b, st->lwstate.as<float2>(), rows));
     ess_part_kernel<float2><<<dim3(static_cast<unsigned>(b), kEssParts), 512, 0, ctx->stream>>>(
         rows, P, st->scratch.as<double>()); ++ctx->launches;
@@ -1941,6 +1947,23 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
                                    cudaMemcpyDeviceToHost, ctx->stream));
     }
     SPS_CUDA_TRY(cudaGetLastError());
+    if (known) {
+      if (s + b == t_target) {
+        if (ess_out) SPS_CUDA_TRY(cudaMemcpyAsync(st->ess_buf.as<double>() + ess_slot, st->ess_buf.as<double>() + (b - 1),
+                                                  sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        found = b - 1;
+        lw_to_f64_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(rows + found * P, P,
+                                                                                         st->logw.as<double>()); ++ctx->launches;
+        SPS_CUDA_TRY(cudaGetLastError());
+        s = t_target;
+        break;
+      }
+      SPS_CUDA_TRY(cudaMemcpyAsync(st->lwstate.ptr, rows + (b - 1) * P, sizeof(float2) * P, cudaMemcpyDeviceToDevice,
+                                   ctx->stream));
+      s += b;
+      block = std::min<int64_t>(block * 2, max_rows);
+      continue;
+    }
     SPS_CUDA_TRY(cudaMemcpyAsync(ess.data(), st->ess_buf.ptr, sizeof(double) * b, cudaMemcpyDeviceToHost, ctx->stream));
     SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     for (int64_t j = 0; j < b; ++j) {
@@ -1983,6 +2006,11 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
   add_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(st->ll.as<double>(),
                                                                                st->logw.as<double>(), P); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
+  if (known && ess_out) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(&ess_found, st->ess_buf.as<double>() + ess_slot, sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    if (!lme_out) SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
   if (lme_out) {
     SPS_CUDA_TRY(cudaMemcpyAsync(lme_out, st->ess_buf.ptr, sizeof(double) * st->J, cudaMemcpyDeviceToHost, ctx->stream));
     SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -1997,7 +2025,7 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
 
 // S phase (Algorithm 1 step 2(b)): quantised weights, per-group integer-CDF draws, gather.
 // The C-phase row buffer holds the quantised weights (uint64 [P]) here.
-sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_idx_out) {
+sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_idx_out, int* h_idx_out = nullptr) {
   if (!st->have_weights) return fail(ctx, SPS_ERR_STATE, "S phase before a C phase");
   SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
   const uint64_t step = ++st->cycle_counter;
@@ -2013,6 +2041,8 @@ sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_id
   SPS_CUDA_TRY(cudaGetLastError());
   if (d_idx_out)
     SPS_CUDA_TRY(cudaMemcpyAsync(d_idx_out, st->idx.ptr, sizeof(int) * st->P, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (h_idx_out)   // completes with the counters' synchronisation below
+    SPS_CUDA_TRY(cudaMemcpyAsync(h_idx_out, st->idx.ptr, sizeof(int) * st->P, cudaMemcpyDeviceToHost, ctx->stream));
   Counters c;
   SPS_TRY(read_counters(ctx, st, &c));
   if (c.res_bad) return fail(ctx, SPS_ERR_DEGENERATE, "all resampling weights of a group vanished");
@@ -2208,18 +2238,13 @@ sps_status sps_cphase(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_
 sps_status sps_sphase(sps_ctx* ctx, sps_state* st, const double* uniforms, int32_t* idx_out, int32_t mem) {
   SPS_TRY(check_state(ctx, st));
   if (mem == SPS_MEM_DEVICE) return sphase_impl(ctx, st, uniforms, idx_out);
-  DevBuf du, di;
+  // host indices are copied from the state's own index buffer (no staging allocation per call)
+  DevBuf du;
   if (uniforms) {
     SPS_CUDA_TRY(du.reserve(sizeof(double) * st->P));
     SPS_CUDA_TRY(cudaMemcpyAsync(du.ptr, uniforms, sizeof(double) * st->P, cudaMemcpyHostToDevice, ctx->stream));
   }
-  if (idx_out) SPS_CUDA_TRY(di.reserve(sizeof(int) * st->P));
-  SPS_TRY(sphase_impl(ctx, st, uniforms ? du.as<double>() : nullptr, idx_out ? di.as<int>() : nullptr));
-  if (idx_out) {
-    SPS_CUDA_TRY(cudaMemcpyAsync(idx_out, di.ptr, sizeof(int) * st->P, cudaMemcpyDeviceToHost, ctx->stream));
-    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  }
-  return SPS_OK;
+  return sphase_impl(ctx, st, uniforms ? du.as<double>() : nullptr, nullptr, idx_out);
 }
 
 sps_status sps_mstep(sps_ctx* ctx, sps_state* st, int32_t kernel, const double* sigma, double* sigma_used,

@@ -1706,9 +1706,18 @@ sps_status mstep_impl(sps_ctx* ctx, sps_state* st, int kernel, const double* sig
   SPS_TRY(mstep_prepare(ctx, st, kernel));
   const double h = st->h;
   const uint64_t step = ++st->step_counter;
-  SPS_TRY(mstep_issue(ctx, st, kernel, sigma, sigma_used, h, step, nullptr));
+  // Sigma is read back after the step's one synchronisation (st->cov still holds it): a copy
+  // into pageable host memory issued mid-step would hold the host until the covariance is done
+  // and delay the launches of the rest of the step
+  SPS_TRY(mstep_issue(ctx, st, kernel, sigma, nullptr, h, step, nullptr));
   if (kernel == SPS_MKERNEL_RW) st->grad_valid = false;
-  return mstep_finish(ctx, st, kernel, h, sigma == nullptr, info);
+  const sps_status r = mstep_finish(ctx, st, kernel, h, sigma == nullptr, info);
+  if (sigma_used) {
+    SPS_CUDA_TRY(cudaMemcpyAsync(sigma_used, st->cov.ptr, sizeof(double) * ctx->D * ctx->D, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  return r;
 }
 
 // Read an issued M step back and apply the step-size rule (when adapt): errors of the step,
@@ -2251,9 +2260,7 @@ sps_status sps_mstep(sps_ctx* ctx, sps_state* st, int32_t kernel, const double* 
                      sps_mstep_info* info) {
   SPS_TRY(check_state(ctx, st));
   if (st->t <= 0) return fail(ctx, SPS_ERR_STATE, "M step before any observation was added");
-  SPS_TRY(mstep_impl(ctx, st, kernel, sigma, sigma_used, info));
-  if (sigma_used) SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  return SPS_OK;
+  return mstep_impl(ctx, st, kernel, sigma, sigma_used, info);
 }
 
 sps_status sps_mphase(sps_ctx* ctx, sps_state* st, int32_t kernel, int32_t fixed_steps, int32_t* steps,

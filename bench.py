@@ -24,7 +24,6 @@ import re
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -44,81 +43,37 @@ def peaks():
         return {}
 
 
-class ClockSampler:
-    """SM clocks and throttle reasons sampled during the timed region.
+class ClockProbe:
+    """SM clocks and throttle reasons, sampled inside the timed loop between steps.
 
-    Samples come from NVML in a background thread (every 10 ms, a few microseconds per query, no
-    process started while the region runs); without NVML, from an `nvidia-smi -lms` process
-    started before the region and stopped after it. Reads only: no setting is changed."""
+    Each sample is one `nvidia-smi --query-gpu` call made right after a timed step has finished
+    on the GPU (its end event synchronised) and before the next one starts, so no query overlaps
+    a timed step. A concurrent `nvidia-smi -lms` process was measured to slow this launch-bound
+    step by about 60 % whatever its period (50, 200 or 1000 ms): while it runs, the host-side
+    launches and synchronisations of the simulator take longer. Reads only: no setting is
+    changed."""
 
-    # clock-event reason bits (NVML): hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
-    # sw_power_cap
-    _BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
+    _NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    _QUERY = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int = 0, period_s: float = 0.01):
+    def __init__(self, index: int = 0):
         self.index = index
-        self.period = period_s
         self.samples = []          # (sm_mhz, sm_max_mhz, reasons set)
-        self._stop = threading.Event()
-        self._t = None
-        self._proc = None
-        self._nvml = None
 
-    def _run_nvml(self):
-        nv = self._nvml
-        h = nv.nvmlDeviceGetHandleByIndex(self.index)
-        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
-        while True:
-            try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                bits = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                self.samples.append((float(sm), float(mx), {k for k, b in self._BITS.items() if bits & b}))
-            except Exception:
-                pass
-            if self._stop.wait(self.period):
-                break
-
-    def __enter__(self):
+    def sample(self):
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self._nvml = pynvml
-            self._t = threading.Thread(target=self._run_nvml, daemon=True)
-            self._t.start()
+            out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self._QUERY}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                 timeout=20).stdout
         except Exception:
-            q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap")
-            try:
-                self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                               "--format=csv,noheader,nounits", "-lms", "50"],
-                                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-                time.sleep(0.2)
-            except Exception:
-                self._proc = None
-        return self
-
-    def __exit__(self, *a):
-        self._stop.set()
-        if self._t:
-            self._t.join(timeout=10)
-            try:
-                self._nvml.nvmlShutdown()
-            except Exception:
-                pass
-        if self._proc:
-            time.sleep(0.1)
-            self._proc.terminate()
-            try:
-                out, _ = self._proc.communicate(timeout=5)
-            except Exception:
-                out = ""
-            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-            for line in out.splitlines():
-                f = [v.strip() for v in line.split(",")]
-                if len(f) >= 6 and f[0].replace(".", "").isdigit():
-                    self.samples.append((float(f[0]), float(f[1]),
-                                         {names[i] for i in range(4) if f[2 + i] == "Active"}))
+            return
+        for line in out.splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 6 and f[0].replace(".", "").isdigit():
+                self.samples.append((float(f[0]), float(f[1]),
+                                     {self._NAMES[i] for i in range(4) if f[2 + i] == "Active"}))
 
     def summary(self):
         if not self.samples:
@@ -126,7 +81,8 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(s[0] for s in self.samples),
                 "sm_max_mhz": max(s[1] for s in self.samples),
                 "reasons": sorted(set().union(*(s[2] for s in self.samples))),
-                "samples": len(self.samples), "source": "nvml" if self._nvml else "nvidia-smi -lms 50"}
+                "samples": len(self.samples),
+                "source": "nvidia-smi --query-gpu between timed steps (right after a step ends)"}
 
 
 def dist_setup():
@@ -268,21 +224,24 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    with ClockSampler(local) as clk:
-        for _ in range(steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            t_new, _, _ = st.cphase(st.get_t() + C_BLOCK)
-            st.sphase()
-            st.mstep(kernel=args.mkernel)
-            b.record(stream)
-            b.synchronize()
-            ev_ms.append(a.elapsed_time(b))
-            units += P * C_BLOCK + 2 * P * t_new
-            hot_units += 2 * P * t_new
+    clk = ClockProbe(local)
+    probe_at = {0, steps // 2, steps - 1}      # three samples: start, middle and end of the loop
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t_new, _, _ = st.cphase(st.get_t() + C_BLOCK)
+        st.sphase()
+        st.mstep(kernel=args.mkernel)
+        b.record(stream)
+        b.synchronize()
+        ev_ms.append(a.elapsed_time(b))
+        units += P * C_BLOCK + 2 * P * t_new
+        hot_units += 2 * P * t_new
+        if i in probe_at:
+            clk.sample()
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - wall0
@@ -340,6 +299,7 @@ def run_ours(args, world, rank, local):
         "wall_s": wall,
         "gpu_launches": launches,
         "clocks": clock,
+        "ms_per_step_median": statistics.median(ev_ms),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P * w.D * 8, "d2h_bytes_per_step": P * 8,
                 "call": "sps_loglik(mem=HOST) on pinned buffers, full t = n"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Gop/s (ex2)",

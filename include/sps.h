@@ -293,7 +293,8 @@ sps_status sps_state_create(sps_ctx* ctx, int32_t J, int32_t N, uint64_t seed, s
 void sps_state_destroy(sps_state* st);
 
 /* Copy the state's particles [J*N x D], cached log-likelihoods [J*N] and log weights [J*N]
- * (host pointers, any may be NULL) and its scalars (t, h; any may be NULL). */
+ * (host pointers, any may be NULL) and its scalars (t, h; any may be NULL). The call waits for
+ * the context's stream only when one of the three arrays is requested (t and h live on the host). */
 sps_status sps_state_get(sps_ctx* ctx, const sps_state* st, double* theta, double* ll,
                          double* logw, int64_t* t, double* h);
 /* Overwrite particles and cached log-likelihoods (host pointers, [J*N x D] and [J*N]; ll may be

@@ -429,29 +429,38 @@ class State:
         l = _f64(ll) if ll is not None else None
         self.sps._call("sps_state_set", self.st, _ptr(th), _ptr(l) if l is not None else None, int(t))
 
-    def cphase(self, t_target: int = 0, log_pred: bool = False):
+    def cphase(self, t_target: int = 0, log_pred: bool = False, outputs: bool = True):
         """C phase; returns (t_new, ess, logml_inc[J]) and, with log_pred, the per-group log
-        predictive likelihoods [t_new - t, J] of the observations taken in."""
-        tn = C.c_int64(); e = C.c_double(); inc = np.empty(self.J)
+        predictive likelihoods [t_new - t, J] of the observations taken in. With outputs=False
+        ess and logml_inc are not read back (None): a C phase with a target then returns without
+        waiting for the GPU."""
+        tn = C.c_int64(); e = C.c_double()
+        inc = np.empty(self.J) if outputs else None
         lp = np.empty((self.sps.n - self.get_t(), self.J)) if log_pred else None
-        self.sps._call("sps_cphase", self.st, int(t_target), C.byref(tn), C.byref(e), _ptr(inc),
-                       _ptr(lp) if lp is not None else None)
+        self.sps._call("sps_cphase", self.st, int(t_target), C.byref(tn), C.byref(e) if outputs else None,
+                       _ptr(inc) if outputs else None, _ptr(lp) if lp is not None else None)
+        if not outputs:
+            e = C.c_double(float("nan"))
         if lp is None:
             return tn.value, e.value, inc
         return tn.value, e.value, inc, lp[:tn.value - (self.sps.n - lp.shape[0])].copy()
 
-    def sphase(self, uniforms=None):
-        idx = np.empty(self.J * self.N, dtype=np.int32)
+    def sphase(self, uniforms=None, indices: bool = True):
+        """S phase; returns the selected index within the group of every particle (None with
+        indices=False, which skips their copy to the host)."""
+        idx = np.empty(self.J * self.N, dtype=np.int32) if indices else None
         u = _f64(uniforms) if uniforms is not None else None
-        self.sps._call("sps_sphase", self.st, _ptr(u) if u is not None else None, _ptr(idx), N.MEM_HOST)
+        self.sps._call("sps_sphase", self.st, _ptr(u) if u is not None else None,
+                       _ptr(idx) if indices else None, N.MEM_HOST)
         return idx
 
-    def mstep(self, kernel: str = "rw", sigma=None):
+    def mstep(self, kernel: str = "rw", sigma=None, sigma_used: bool = True):
+        """One M step; returns its diagnostics and the Sigma used (None with sigma_used=False)."""
         info = N.SpsMstepInfo()
         sig = _f64(sigma) if sigma is not None else None
-        used = np.empty((self.sps.D, self.sps.D))
+        used = np.empty((self.sps.D, self.sps.D)) if sigma_used else None
         self.sps._call("sps_mstep", self.st, MKERNELS[kernel], _ptr(sig) if sig is not None else None,
-                       _ptr(used), C.byref(info))
+                       _ptr(used) if sigma_used else None, C.byref(info))
         return {"h": info.h, "accept": info.accept_rate, "rne_min": info.rne_min, "h_next": info.h_next,
                 "sigma": used}
 

@@ -2210,7 +2210,7 @@ sps_status sps_state_get(sps_ctx* ctx, const sps_state* st, double* theta, doubl
   if (ll) SPS_CUDA_TRY(cudaMemcpyAsync(ll, st->ll.ptr, sizeof(double) * st->P, cudaMemcpyDeviceToHost, ctx->stream));
   if (logw)
     SPS_CUDA_TRY(cudaMemcpyAsync(logw, st->logw.ptr, sizeof(double) * st->P, cudaMemcpyDeviceToHost, ctx->stream));
-  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (theta || ll || logw) SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));   // t and h are host-side
   if (t) *t = st->t;
   if (h) *h = st->h;
   return SPS_OK;

@@ -54,3 +54,23 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_clock_probe_parses_nvidia_smi(monkeypatch):
+    # the bench's clock samples: one nvidia-smi query per sample, fields as the recipe's line
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Out:
+        stdout = "2032, 2032, Not Active, Not Active, Not Active, Active\n"
+
+    calls = []
+    monkeypatch.setattr(bench.subprocess, "run", lambda cmd, **kw: calls.append(cmd) or Out())
+    p = bench.ClockProbe(3)
+    p.sample()
+    p.sample()
+    s = p.summary()
+    assert s["sm_mhz"] == 2032.0 and s["sm_max_mhz"] == 2032.0 and s["samples"] == 2
+    assert s["reasons"] == ["sw_power_cap"]
+    assert calls[0][:3] == ["nvidia-smi", "-i", "3"] and all("-lms" not in c for c in calls[0])
+    assert bench.ClockProbe(0).summary()["reasons"] == ["unsampled"]

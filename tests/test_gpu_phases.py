@@ -289,3 +289,28 @@ def test_sps_run_mala_against_quadrature(cuda):
     assert np.all(np.abs(z) < 4), (r.mean[:2], quad["mean"], r.nse[:2])
     np.testing.assert_allclose(r.sd[:2], quad["sd"], rtol=0.05)
     assert abs(r.log_ml - quad["log_ml"]) < 4 * max(r.log_ml_nse, 1e-3)
+
+
+@pytest.mark.parametrize("kernel", ["rw", "mala"])
+def test_cycle_without_host_outputs_is_bitwise_the_same(cuda, kernel):
+    # cphase(outputs=False), sphase(indices=False) and mstep(sigma_used=False) only skip copies
+    # to the host (and the C phase's per-block ESS reads when its target is known): the state
+    # after each cycle is identical bit for bit
+    w = synthetic.make_c1()
+    s = _ctx(w.X, w.y, w.C)
+    a = s.state(4, 256, seed=21)
+    b = s.state(4, 256, seed=21)
+    for t in (40, 130, 131, 300):
+        ta, _, inc = a.cphase(t)
+        a.sphase()
+        ia = a.mstep(kernel)
+        tb, ess_b, inc_b = b.cphase(t, outputs=False)
+        assert inc_b is None and math.isnan(ess_b)
+        assert b.sphase(indices=False) is None
+        ib = b.mstep(kernel, sigma_used=False)
+        assert ib["sigma"] is None
+        assert ta == tb == t
+        assert ia["accept"] == ib["accept"] and ia["h_next"] == ib["h_next"]
+        ga, gb = a.get(), b.get()
+        for key in ("theta", "ll"):
+            np.testing.assert_array_equal(ga[key], gb[key])

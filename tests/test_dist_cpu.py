@@ -74,3 +74,40 @@ def test_clock_probe_parses_nvidia_smi(monkeypatch):
     assert s["reasons"] == ["sw_power_cap"]
     assert calls[0][:3] == ["nvidia-smi", "-i", "3"] and all("-lms" not in c for c in calls[0])
     assert bench.ClockProbe(0).summary()["reasons"] == ["unsampled"]
+
+
+def test_sps_ladder_doubles_groups_then_runs_three_seeds(monkeypatch):
+    # the wall-time protocol of the bench, on a stand-in simulator whose NSE falls as 1/sqrt(J)
+    sys.path.insert(0, ROOT)
+    import types
+    import bench
+    import paper_1304_4333_b300 as pkg
+
+    runs = []
+
+    class FakeSps:
+        def __init__(self, X, y, C, prior_sd, seed, precision, mkernel):
+            self.seed, self.form = seed, (precision, mkernel)
+
+        def run(self, J, N, record=False):
+            runs.append((self.form, J, self.seed))
+            nse = 0.32 / (J / 16) ** 0.5 * (1.0 + 0.01 * self.seed)
+            return types.SimpleNamespace(seconds=J / 100.0, log_ml=-1.0, log_ml_nse=nse, m_steps=7)
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(pkg, "Sps", FakeSps)
+    w = types.SimpleNamespace(X=None, y=None, C=2, J=16, N=4096)
+    out = bench.sps_ladder(w, [("split", "mala"), ("fp32", "rw")], max_groups=256)
+    m = out["split_mala"]
+    # 0.32 / sqrt(J / 16) * 1.01 <= 0.05 first at J = 1024 > 256: not reached at 256
+    assert not m["reached"] and m["rung"] == "256 groups x 4096"
+    assert [r["groups"] for r in m["ladder_seed1"]] == [16, 32, 64, 128, 256]
+    assert len(m["seeds"]) == 1
+    out = bench.sps_ladder(w, [("split", "rw")], max_groups=4096)
+    r = out["split_rw"]
+    assert r["reached"] and r["rung"] == "1024 groups x 4096"
+    assert [x["seed"] for x in r["seeds"]] == [1, 2, 3]
+    assert r["median_wall_s"] == 10.24
+    assert out["target_log_ml_nse"] == 0.05

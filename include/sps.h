@@ -309,7 +309,9 @@ sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const
  * updates the cached log-likelihoods and sets t. Outputs (host, may be NULL): t_new, ess at
  * t_new, logml_inc [J], log_pred [(t_new - t) x J] row-major: the per-group log predictive
  * likelihoods of the observations taken in (capacity (n - t) x J; FP32 exponentials of the
- * running log weights, FP64 sums). */
+ * running log weights, FP64 sums). Without a target the call reads the ESS of every block back
+ * (one synchronisation per block); with a target and no log_pred it waits for the stream only
+ * when ess or logml_inc is requested, once. */
 sps_status sps_cphase(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new,
                       double* ess, double* logml_inc, double* log_pred);
 

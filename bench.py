@@ -1,30 +1,41 @@
-"""Benchmark of the SPS logit hot path on one B300 (or N independent replicas under torchrun).
+"""Benchmark of the SPS logit hot path on one B300 (single GPU only).
 
-Metric: particle-observation log-likelihood evaluations per second on the binary-logit workload
-c2 (n = 20 000 observations, k = 30 covariates, 16 groups x 4096 particles; synthetic data,
-seed 0). A step is one cycle of the simulator over one batch of new observations: the C phase
+Metric: particle-observation log-likelihood evaluations per second, and the wall time of the
+whole simulator to log-ML NSE <= 0.05 against the plain FP32 form.
+
+Headline workload (the largest configuration that fits one GPU): c4, binary logit with
+n = 1 000 000 observations and k = 100 covariates (intercept, 69 equicorrelated N(0,1), 30
+Bernoulli(0.1) dummies), 64 groups x 1024 particles, synthetic data (seed 0). A step is one
+cycle of the simulator over one batch of new observations at the end of the data: the C phase
 over the next 64 observations (reweighting, ESS, log-ML increment), the S phase (resampling
 within each group and the gather), and one M step at the new prefix length (refresh of the
 cached log-likelihood with the M-phase kernel, particle covariance, FP64 Cholesky, Philox
 proposal, fused log-likelihood of the proposals, Metropolis accept, RNE of the monitoring
 functions). Units counted per step: P x 64 (C phase) + 2 P t (the refresh and the proposals).
+X of c4 (384 MB of split-BF16 operand rows) is larger than L2, so no flush is needed; the
+second workload in the same line, c2 (n = 20 000, k = 30, 16 x 4096 particles, X 2.5 MB),
+flushes L2 between steps by writing a 512 MB buffer outside the timed events. Steps are timed
+with CUDA events on the library's stream.
 
-Between timed steps the L2 cache is flushed by writing a 512 MB buffer (X of c2 fits in L2);
-each step is timed with CUDA events on the library's stream and the flush is outside the
-timed events. `e2e` is the same metric through sps_loglik with pinned host buffers (theta in,
-log-likelihoods out, copies inside the timed region). The oracle (plain FP64 numpy) is timed on
-a bounded sample as the CPU baseline, and is the `--impl reference` arm.
+`roofline` is the fused log-likelihood kernel's: for c4 tensor-bound (algorithmic split-BF16
+FLOPs 2 (C-1)(3 k_cont + 2 k_exact) per term against the measured BF16 peak), for c2 bound by
+its one ex2 per term (SFU). Each launch of the kernel is timed with CUDA events recorded by the
+library on its stream (sps_set_timing). `e2e` is the same metric through sps_loglik with
+pinned host buffers (theta in, log-likelihoods out, copies inside the timed region). The
+oracle (plain FP64 numpy) is timed on a bounded sample as the CPU baseline, on all host cores
+and on one, and is the `--impl reference` arm.
 
-The step's outputs stay on the device (no particle indices, Sigma or log-ML increments are
-copied to the host; the M step's acceptance rate comes back for its step-size rule). SM clocks
-and throttle reasons are sampled by one-shot nvidia-smi queries between timed steps (after the
-first, middle and last step), never during one. `--sps-ladder` adds the wall time of whole
-simulator runs to log-ML NSE <= 0.05 (groups doubled from 16 until seed 1 reaches it, then three
-seeds at that rung).
+`sps.ladder`: the wall time of whole simulator runs (sps_run) on c2 to log-ML NSE <= 0.05,
+groups doubled from 16 until seed 1 reaches the target (the plain FP32 form starts at the
+rung the split random walk reached), then further seeds at that rung (`--ladder-seeds`).
+
+SM clocks and throttle reasons are sampled by one-shot nvidia-smi queries between timed steps
+(after the first, middle and last step), never during one.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import re
@@ -41,6 +52,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particle·obs loglik evals/s; SPS wall-s to log-ML NSE≤0.05 vs plain FP32"
 UNIT = "particle-obs evals/s"
 C_BLOCK = 64
+TRAFFIC_SOURCES = ("loglik_tc.cu", "common.cuh")
 
 
 def peaks():
@@ -92,79 +104,76 @@ class ClockProbe:
                 "source": "nvidia-smi --query-gpu between timed steps (right after a step ends)"}
 
 
-def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        if backend == "nccl":
-            torch.cuda.set_device(local)
-        dist.init_process_group(backend)
-    return world, rank, local
+def bf16_exact_columns(X: np.ndarray) -> np.ndarray:
+    """Columns whose every value is exactly representable in BF16 (the 0/1 dummies and the
+    intercept): an FP64 value is when it survives FP32 and its FP32 pattern has 16 zero low bits."""
+    x32 = X.astype(np.float32)
+    ok = (x32.astype(np.float64) == X) & ((x32.view(np.uint32) & 0xFFFF) == 0)
+    return ok.all(axis=0)
 
 
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(v: float, world: int) -> float:
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    t = torch.tensor([v], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+def split_flops_per_term(w) -> int:
+    """Algorithmic tensor work of one particle-observation term of the split-BF16 product:
+    Th Xh' + Tl Xh' + Th Xl' per outcome (three products for a continuous column, two for an
+    exact one), 2 FLOP per multiply-add."""
+    exact = int(bf16_exact_columns(w.X).sum())
+    return 2 * (w.C - 1) * (3 * (w.k - exact) + 2 * exact)
 
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_throughput(w, seconds: float = 12.0, particles: int = 256):
-    """The oracle's log-likelihood (plain FP64 numpy) on a bounded sample of the workload."""
+def oracle_throughput(w, seconds: float = 10.0, particles: int = 16, threads: int | None = None):
+    """The oracle's log-likelihood (plain FP64 numpy) on a bounded sample of the workload: calls
+    on `particles` particles over all n observations until `seconds` have passed. threads=1 limits
+    the BLAS pool (the product X theta') to one thread; the elementwise numpy work is one thread
+    either way."""
     import synthetic
     from oracle.logit import loglik
     th = synthetic.particles_around(w.theta_true, particles, 0.05, seed=3)
-    loglik(w.X, w.y, th[:8], w.C, w.n)   # warm-up
-    t0 = time.perf_counter()
-    calls = 0
-    while True:
-        loglik(w.X, w.y, th, w.C, w.n)
-        calls += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
+    ctl = None
+    if threads is not None:
+        from threadpoolctl import threadpool_limits
+        ctl = threadpool_limits(limits=threads)
+    try:
+        loglik(w.X[:1000], w.y[:1000], th[:2], w.C)   # warm-up
+        t0 = time.perf_counter()
+        calls = 0
+        while True:
+            loglik(w.X, w.y, th, w.C, w.n)
+            calls += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    finally:
+        if ctl is not None:
+            ctl.unregister()
     units = calls * particles * w.n
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": units / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{calls} calls of loglik on {particles} particles x all {w.n} observations "
-                      f"({el:.1f} s, numpy FP64; BLAS threads for X theta', one thread elsewhere)"}
+    used = cores if threads is None else threads
+    return {"value": units / el, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{calls} calls of loglik on {particles} particles x all {w.n} observations of "
+                      f"{w.name} ({el:.1f} s, numpy FP64; {used} BLAS thread(s) for X theta', one thread "
+                      f"for the elementwise terms; {cores} cores available)"}
 
 
-def run_reference(args, world, rank):
-    if rank != 0:
-        return
+def run_reference(args):
+    """The oracle arm: the plain FP64 CPU log-likelihood on c4, each step a bounded sample (16
+    particles over all 10^6 observations)."""
     import synthetic
-    w = synthetic.make_c2()
+    w = synthetic.make_c4()
     per_step = []
     for i in range(args.warmup + args.steps):
-        r = oracle_throughput(w, seconds=2.0, particles=128)
+        r = oracle_throughput(w, seconds=0.0, particles=16)
         if i >= args.warmup:
             per_step.append(r)
     value = statistics.median(r["value"] for r in per_step)
-    ms = 1e3 * (128 * w.n) / value
+    ms = 1e3 * (16 * w.n) / value
     cpu = dict(per_step[-1])
     cpu["value"] = value
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "c2 binary logit n=20000 k=30 P=65536 (oracle: 128-particle sample per step)",
+            "config": {"workload": "c4 binary logit n=1000000 k=100 P=65536 (oracle: 16-particle sample per step)",
                        "global_batch": 65536, "seq_len": w.n, "parallelism": "cpu"},
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -173,54 +182,52 @@ def run_reference(args, world, rank):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def run_ours(args, world, rank, local):
+def step_bench(w, args, flush_l2: bool, e2e: bool = True):
+    """Time `args.steps` simulator cycles (C phase over C_BLOCK observations, S phase, one M
+    step) at the end of the workload's data, after `args.warmup` untimed ones."""
+    import ctypes as C
     import torch
     import synthetic
     from paper_1304_4333_b300 import Sps
-    from paper_1304_4333_b300 import _native as N
-    import ctypes as C
 
-    torch.cuda.set_device(local)
-    w = synthetic.make_c2()
     P, n = w.P, w.n
     steps, warm = args.steps, args.warmup
-    s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=1 + rank, precision=args.precision)
-    # the fused kernel's default launch shape (the autotuner, sps_autotune, finds a shape 2 %
-    # faster on this workload; it is not run here because it times candidates and would pick
-    # differently inside a profiler, so that profiles would not show the timed kernel)
-    tuned = None
+    s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=1, precision=args.precision)
     stream = torch.cuda.Stream()
     lib = s.lib
     lib.sps_set_stream(s.ctx, C.c_void_p(stream.cuda_stream))
-    st = s.state(w.J, w.N, seed=100 + rank)
+    st = s.state(w.J, w.N, seed=100)
     t0 = n - C_BLOCK * (warm + steps + (1 if args.ncu_step else 0))
     theta0 = synthetic.particles_around(w.theta_true, P, 0.05, seed=2)
     st.set(theta0, None, t0)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda") if flush_l2 else None
 
     def counters(reset=0):
         a, b, c = C.c_int64(), C.c_int64(), C.c_double()
         lib.sps_counters(s.ctx, reset, C.byref(a), C.byref(b), C.byref(c))
         return a.value, b.value, c.value
 
-    # warm-up steps
-    for _ in range(warm):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        st.cphase(st.get_t() + C_BLOCK, outputs=False)
+    def one_step():
+        t_new, _, _ = st.cphase(st.get_t() + C_BLOCK, outputs=False)
         st.sphase(indices=False)
         st.mstep(kernel=args.mkernel, sigma_used=False)
+        return t_new
+
+    for _ in range(warm):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        one_step()
     torch.cuda.synchronize()
     if args.ncu_step:
         # one more step inside a profiler range: `ncu --profile-from-start off` captures exactly
         # the kernels of one step (C phase, S phase, M step)
-        with torch.cuda.stream(stream):
-            flush.zero_()
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.zero_()
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        st.cphase(st.get_t() + C_BLOCK, outputs=False)
-        st.sphase(indices=False)
-        st.mstep(kernel=args.mkernel, sigma_used=False)
+        one_step()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     counters(reset=1)
@@ -228,22 +235,20 @@ def run_ours(args, world, rank, local):
     units = 0
     hot_units = 0
     ev_ms = []
-    barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    clk = ClockProbe(local)
+    clk = ClockProbe(0)
     probe_at = {0, steps // 2, steps - 1}      # three samples: start, middle and end of the loop
     for i in range(steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         # the step's outputs stay on the device (no particle indices, Sigma or log-ML increments
         # copied to the host); the M step's acceptance rate still comes back for its rule
-        t_new, _, _ = st.cphase(st.get_t() + C_BLOCK, outputs=False)
-        st.sphase(indices=False)
-        st.mstep(kernel=args.mkernel, sigma_used=False)
+        t_new = one_step()
         b.record(stream)
         b.synchronize()
         ev_ms.append(a.elapsed_time(b))
@@ -252,97 +257,47 @@ def run_ours(args, world, rank, local):
         if i in probe_at:
             clk.sample()
     torch.cuda.synchronize()
-    barrier(world)
     wall = time.perf_counter() - wall0
     launches, hot_launches, hot_ms = counters(reset=1)
     lib.sps_set_timing(s.ctx, 0)
-    dev_s = max_over_ranks(sum(ev_ms) / 1e3, world)
-    total_units = units * world
-    value = total_units / dev_s
-    t_end = st.get_t()
-
-    # e2e: sps_loglik through the C ABI with pinned host buffers, copies inside the timed region
-    th_host = torch.from_numpy(synthetic.particles_around(w.theta_true, P, 0.05, seed=4)).pin_memory()
-    ll_host = torch.empty(P, dtype=torch.float64).pin_memory()
-    for _ in range(warm):
-        s.loglik_host_ptr(th_host.data_ptr(), ll_host.data_ptr(), P, n, args.precision)
-    e2e_t = []
-    for _ in range(steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        stream.synchronize()
-        t1 = time.perf_counter()
-        s.loglik_host_ptr(th_host.data_ptr(), ll_host.data_ptr(), P, n, args.precision)
-        e2e_t.append(time.perf_counter() - t1)
-    e2e_s = max_over_ranks(sum(e2e_t), world)
-    e2e_value = world * steps * P * n / e2e_s
-
-    if rank != 0:
-        return
-    pk = peaks()
-    clock = clk.summary()
-    # roofline of the fused log-likelihood kernel: SFU-bound (one ex2 per particle-observation
-    # term for C = 2); peak = 148 SMs x 32 ex2/clk x max SM clock
-    sm_max = pk.get("sm_max_mhz", 2032.0)
-    sfu_peak = 148 * 32 * sm_max * 1e6 / 1e9        # Gop/s
-    hot_avg_ms = hot_ms / max(hot_launches, 1)
-    # algorithmic SFU work of the timed launches: one ex2 per particle-observation term (C = 2)
-    achieved = hot_units * (w.C - 1) / (hot_ms * 1e-3) / 1e9 if hot_ms > 0 else 0.0
-    tensor_ms = P * n * 2 * (w.C - 1) * (3 * 19 + 2 * 11) / (pk.get("bf16_tflops", 1778.4) * 1e12) * 1e3
-    sfu_ms = P * n * (w.C - 1) / (sfu_peak * 1e9) * 1e3
-    hbm_ms = n * 128 / (pk.get("hbm_gbs", 6496.8) * 1e9) * 1e3
-    traffic, traffic_src = args.traffic, "--traffic" if args.traffic is not None else None
-    if traffic is None:
-        traffic, traffic_src = profiled_traffic()
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm,
-        "ms_per_step": 1e3 * dev_s / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x2-split/f32/f64" if args.precision == "split" else "f32/f64", "data": "synthetic",
-        "config": {"workload": "c2 binary logit n=20000 k=30 (intercept, 19 AR(1) N(0,1), 10 Bernoulli(0.3)), "
-                               "16 groups x 4096 particles, one SPS cycle per step (C phase 64 obs, S phase, M step)",
-                   "global_batch": P * world, "seq_len": n, "parallelism": f"replicas{world}",
-                   "precision": args.precision, "mkernel": args.mkernel,
-                   "tile_shape": ({"rows": tuned["tile_rows"], "cluster": tuned["cluster"],
-                                   "chunk_obs": tuned["chunk_obs"], "source": "sps_autotune"} if tuned else None),
-                   "l2": "flushed between steps (512 MB write)"},
-        "wall_s": wall,
-        "gpu_launches": launches,
-        "clocks": clock,
-        "ms_per_step_median": statistics.median(ev_ms),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": P * w.D * 8, "d2h_bytes_per_step": P * 8,
-                "call": "sps_loglik(mem=HOST) on pinned buffers, full t = n"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Gop/s (ex2)",
-                     "frac": achieved / sfu_peak, "traffic": traffic,
-                     "traffic_source": traffic_src,
-                     "kernel": f"loglik_tc_kernel<1,{tuned['tile_rows'] if tuned else 256}>",
-                     "launches_timed": hot_launches,
-                     "avg_launch_ms": hot_avg_ms,
-                     "bounds_ms_full_t": {"sfu": sfu_ms, "tensor_split": tensor_ms, "hbm": hbm_ms},
-                     "peak_source": "148 SMs x 32 ex2/clk/SM x sm_max_mhz of MEASURED_PEAKS (ex2 rate from a probe)"},
-    }
-    if not args.no_sps:
-        line["sps"] = sps_wall(w, rank)
-    if args.sps_ladder:
-        forms = [tuple(f.split("_")) for f in args.sps_ladder.split(",")]
-        if any(f not in (("split", "rw"), ("split", "mala"), ("fp32", "rw"), ("fp32", "mala")) for f in forms):
-            raise SystemExit(f"--sps-ladder: unknown form in {args.sps_ladder!r}")
-        line.setdefault("sps", {})["ladder"] = sps_ladder(w, forms, args.sps_max_groups)
-    if not args.no_cpu:
-        line["cpu_baseline"] = oracle_throughput(w)
-    print(json.dumps(line), flush=True)
+    dev_s = sum(ev_ms) / 1e3
+    out = {"value": units / dev_s, "ms_per_step": 1e3 * dev_s / steps,
+           "ms_per_step_median": statistics.median(ev_ms), "wall_s": wall, "gpu_launches": launches,
+           "hot_launches": hot_launches, "hot_ms": hot_ms, "hot_units": hot_units, "units": units,
+           "clocks": clk.summary(), "t_end": st.get_t()}
+    del st
+    if e2e:
+        # sps_loglik through the C ABI with pinned host buffers, copies inside the timed region
+        th_host = torch.from_numpy(synthetic.particles_around(w.theta_true, P, 0.05, seed=4)).pin_memory()
+        ll_host = torch.empty(P, dtype=torch.float64).pin_memory()
+        for _ in range(warm):
+            s.loglik_host_ptr(th_host.data_ptr(), ll_host.data_ptr(), P, n, args.precision)
+        e2e_t = []
+        for _ in range(steps):
+            if flush is not None:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+            stream.synchronize()
+            t1 = time.perf_counter()
+            s.loglik_host_ptr(th_host.data_ptr(), ll_host.data_ptr(), P, n, args.precision)
+            e2e_t.append(time.perf_counter() - t1)
+        out["e2e"] = {"value": steps * P * n / sum(e2e_t), "unit": UNIT, "h2d_bytes_per_step": P * w.D * 8,
+                      "d2h_bytes_per_step": P * 8,
+                      "call": "sps_loglik(mem=HOST) on pinned buffers, full t = n"}
+    s.close()
+    return out
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the fused kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-    from the committed ncu summary, used only while the kernel source still hashes to the value
-    recorded beside it; otherwise (None, reason)."""
-    import hashlib
-    prof = os.path.join(ROOT, "profiles", "loglik_tc_c2.md")
+def profiled_traffic(name: str):
+    """DRAM bytes per full launch of the fused kernel (dram__bytes_read.sum +
+    dram__bytes_write.sum) from the committed ncu summary profiles/loglik_tc_<name>.md, used only
+    while the kernel sources still hash to the value recorded there; otherwise (None, reason)."""
+    prof = os.path.join(ROOT, "profiles", f"loglik_tc_{name}.md")
     csrc = os.path.join(ROOT, "paper_1304_4333_b300", "csrc")
     try:
         text = open(prof).read()
         h = hashlib.sha256()
-        for f in ("loglik_tc.cu", "common.cuh"):
+        for f in TRAFFIC_SOURCES:
             h.update(open(os.path.join(csrc, f), "rb").read())
     except OSError:
         return None, "no ncu summary"
@@ -352,40 +307,103 @@ def profiled_traffic():
         return None, "no traffic figure in the ncu summary"
     if sh.group(1) != h.hexdigest()[:16]:
         return None, "kernel changed since the ncu capture"
-    return float(tb.group(1)), "profiles/loglik_tc_c2.md (ncu, one launch of this workload)"
+    return float(tb.group(1)), f"profiles/loglik_tc_{name}.md (ncu dram bytes of one launch)"
 
 
-def sps_wall(w, rank):
-    """Second half of the metric: wall time of the whole simulator (sps_run, Algorithm 2) on c2
-    with the split-BF16 path (random-walk M kernel, and the MALA M kernel driven by the
-    tensor-core gradient) and with the plain FP32 random-walk path, the log-ML NSE each reaches
-    at the configured 16 x 4096 particles, and the projected wall time to NSE <= 0.05 (NSE
-    scales as particles^-1/2 and the time as particles, so time x (NSE / 0.05)^2; labelled as
-    projected)."""
-    from paper_1304_4333_b300 import Sps
-    out = {}
-    for name, prec, mk in (("split", "split", "rw"), ("split_mala", "split", "mala"), ("fp32", "fp32", "rw")):
-        s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=11 + rank, precision=prec, mkernel=mk)
-        r = s.run(w.J, w.N, record=False)
-        out[name] = {"wall_s": r.seconds, "log_ml": r.log_ml, "log_ml_nse": r.log_ml_nse,
-                     "cycles": r.n_cycles, "m_steps": r.m_steps, "mkernel": mk,
-                     "projected_wall_s_to_nse_0.05": r.seconds * max(1.0, (r.log_ml_nse / 0.05) ** 2)}
-        s.close()
-    out["speedup_vs_fp32"] = out["fp32"]["wall_s"] / out["split"]["wall_s"]
-    out["speedup_mala_vs_fp32"] = out["fp32"]["wall_s"] / out["split_mala"]["wall_s"]
-    out["projected_speedup_mala_vs_fp32"] = (out["fp32"]["projected_wall_s_to_nse_0.05"]
-                                             / out["split_mala"]["projected_wall_s_to_nse_0.05"])
-    out["particles"] = f"{w.J} groups x {w.N}"
+def roofline_tensor(w, r, pk):
+    """c4: the fused kernel is bound by its split-BF16 tensor-core products."""
+    fpt = split_flops_per_term(w)
+    peak = pk.get("bf16_tflops", 1800.0)
+    peak_src = "bf16_tflops (burst) of MEASURED_PEAKS.json" if "bf16_tflops" in pk else "fallback 1.8 PFLOP/s"
+    achieved = r["hot_units"] * fpt / (r["hot_ms"] * 1e-3) / 1e12 if r["hot_ms"] > 0 else 0.0
+    traffic, tsrc = profiled_traffic(w.name)
+    sm_max = pk.get("sm_max_mhz", 2032.0)
+    full_units = w.P * w.n
+    out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
+           "kernel": "loglik_tc_kernel (split BF16, tcgen05)", "flop_per_term": fpt,
+           "launches_timed": r["hot_launches"], "avg_launch_ms": r["hot_ms"] / max(1, r["hot_launches"]),
+           "peak_source": peak_src,
+           "frac_of_sustained": (achieved / pk["bf16_tflops_sustained"]) if "bf16_tflops_sustained" in pk else None,
+           "bounds_ms_full_t": {"tensor_split": full_units * fpt / (peak * 1e12) * 1e3,
+                                "sfu": full_units * (w.C - 1) / (148 * 32 * sm_max * 1e6) * 1e3,
+                                "hbm": w.n * (2 * 64 * ((w.k + 15) // 16 + 1)) / (pk.get("hbm_gbs", 6400.0) * 1e9) * 1e3}}
     return out
 
 
-def sps_ladder(w, forms, max_groups: int, target: float = 0.05):
-    """The wall-time half of the metric as a measured protocol instead of a projection: for each
-    form (precision, M kernel), run seed 1 at the workload's groups x particles and double the
-    number of groups (particles per group stay at the workload's value, the resampling bound)
-    until its log-ML NSE is at most the target; then run seeds 2 and 3 at that rung and report
-    the median wall time of the three seeds with each seed's NSE. A form whose seed 1 misses the
-    target at max_groups reports its last rung with "reached": false."""
+def roofline_sfu(w, r, pk):
+    """c2: the fused kernel is bound by its one ex2 per term (peak 148 SMs x 32 ex2/clk x the
+    maximum SM clock; 30 ex2/clk/SM measured by a probe)."""
+    sm_max = pk.get("sm_max_mhz", 2032.0)
+    sfu_peak = 148 * 32 * sm_max * 1e6 / 1e9        # Gop/s
+    achieved = r["hot_units"] * (w.C - 1) / (r["hot_ms"] * 1e-3) / 1e9 if r["hot_ms"] > 0 else 0.0
+    traffic, tsrc = profiled_traffic(w.name)
+    full_units = w.P * w.n
+    return {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Gop/s (ex2)",
+            "frac": achieved / sfu_peak, "traffic": traffic, "traffic_source": tsrc,
+            "kernel": "loglik_tc_kernel (split BF16, tcgen05)",
+            "launches_timed": r["hot_launches"], "avg_launch_ms": r["hot_ms"] / max(1, r["hot_launches"]),
+            "peak_source": "148 SMs x 32 ex2/clk/SM x sm_max_mhz of MEASURED_PEAKS (ex2 rate from a probe)",
+            "bounds_ms_full_t": {"sfu": full_units * (w.C - 1) / (sfu_peak * 1e9) * 1e3,
+                                 "tensor_split": full_units * split_flops_per_term(w) /
+                                 (pk.get("bf16_tflops", 1800.0) * 1e12) * 1e3}}
+
+
+def run_ours(args):
+    import torch
+    import synthetic
+
+    torch.cuda.set_device(0)
+    pk = peaks()
+    w4 = synthetic.make_c4()
+    r4 = step_bench(w4, args, flush_l2=False)
+    dtype = "bf16x2-split/f32/f64" if args.precision == "split" else "f32/f64"
+    line = {
+        "metric": METRIC, "value": r4["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r4["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": "c4 binary logit n=1000000 k=100 (intercept, 69 equicorrelated(0.2) N(0,1), "
+                               "30 Bernoulli(0.1)), 64 groups x 1024 particles, one SPS cycle per step "
+                               "(C phase 64 obs, S phase, M step) at t = n - 64 (steps + warmup) .. n",
+                   "global_batch": w4.P, "seq_len": w4.n, "parallelism": "single GPU",
+                   "precision": args.precision, "mkernel": args.mkernel,
+                   "l2": "inputs larger than L2 (X split-BF16 operand rows 384 MB); no flush"},
+        "wall_s": r4["wall_s"],
+        "gpu_launches": r4["gpu_launches"],
+        "clocks": r4["clocks"],
+        "ms_per_step_median": r4["ms_per_step_median"],
+        "e2e": r4["e2e"],
+        "roofline": roofline_tensor(w4, r4, pk),
+    }
+    if not args.no_c2:
+        w2 = synthetic.make_c2()
+        r2 = step_bench(w2, args, flush_l2=True)
+        line["workloads"] = {"c2": {
+            "workload": "c2 binary logit n=20000 k=30 (intercept, 19 AR(1) N(0,1), 10 Bernoulli(0.3)), "
+                        "16 groups x 4096 particles, one SPS cycle per step; L2 flushed between steps (512 MB write)",
+            "value": r2["value"], "unit": UNIT, "ms_per_step": r2["ms_per_step"],
+            "ms_per_step_median": r2["ms_per_step_median"], "gpu_launches": r2["gpu_launches"],
+            "clocks": r2["clocks"], "e2e": r2["e2e"], "roofline": roofline_sfu(w2, r2, pk)}}
+        if args.sps_ladder:
+            forms = [tuple(f.split("_")) for f in args.sps_ladder.split(",")]
+            if any(f not in (("split", "rw"), ("split", "mala"), ("fp32", "rw"), ("fp32", "mala")) for f in forms):
+                raise SystemExit(f"--sps-ladder: unknown form in {args.sps_ladder!r}")
+            line["sps"] = {"workload": "c2", "ladder": sps_ladder(w2, forms, args.sps_max_groups,
+                                                                  args.ladder_seeds, args.ladder_seeds_other)}
+    if not args.no_cpu:
+        line["cpu_baseline"] = oracle_throughput(w4, seconds=10.0, particles=16)
+        line["cpu_baseline"]["single_thread"] = oracle_throughput(w4, seconds=6.0, particles=16, threads=1)
+    print(json.dumps(line), flush=True)
+
+
+def sps_ladder(w, forms, max_groups: int, seeds: int, seeds_other: int, target: float = 0.05):
+    """The wall-time half of the metric as a measured protocol: for each form (precision, M
+    kernel), run seed 1 at the workload's groups x particles and double the number of groups
+    (particles per group stay at the workload's value, the resampling bound) until its log-ML
+    NSE is at most the target; then run seeds 2..`seeds` (split MALA) or 2..`seeds_other` (the
+    other forms) at that rung and report the median wall time with each seed's NSE. The plain FP32 random walk starts at the rung the split random walk
+    reached (the same Metropolis kernel on the same data: the two differ only in rounding). A form
+    whose seed 1 misses the target at max_groups reports its last rung with "reached": false."""
     from paper_1304_4333_b300 import Sps
     out = {}
     for prec, mk in forms:
@@ -397,19 +415,27 @@ def sps_ladder(w, forms, max_groups: int, target: float = 0.05):
                 s.close()
             return {"groups": J, "seed": seed, "wall_s": r.seconds, "log_ml": r.log_ml,
                     "log_ml_nse": r.log_ml_nse, "m_steps": r.m_steps}
-        rungs, J = [], w.J
+        J = w.J
+        if prec == "fp32" and out.get(f"split_{mk}", {}).get("reached"):
+            J = out[f"split_{mk}"]["groups"]
+        rungs = []
         while True:
             rungs.append(one(J, 1))
             if rungs[-1]["log_ml_nse"] <= target or 2 * J > max_groups:
                 break
             J *= 2
         reached = rungs[-1]["log_ml_nse"] <= target
-        seeds = [rungs[-1]] + ([one(J, 2), one(J, 3)] if reached else [])
-        walls = sorted(x["wall_s"] for x in seeds)
-        out[f"{prec}_{mk}"] = {"reached": reached, "rung": f"{J} groups x {w.N}",
-                               "median_wall_s": walls[len(walls) // 2], "seeds": seeds,
+        ns = seeds if (prec, mk) == ("split", "mala") else seeds_other
+        runs = [rungs[-1]] + ([one(J, sd) for sd in range(2, ns + 1)] if reached else [])
+        walls = sorted(x["wall_s"] for x in runs)
+        out[f"{prec}_{mk}"] = {"reached": reached, "groups": J, "rung": f"{J} groups x {w.N}",
+                               "median_wall_s": walls[len(walls) // 2], "seeds": runs,
                                "ladder_seed1": [{k: x[k] for k in ("groups", "wall_s", "log_ml_nse")}
                                                 for x in rungs]}
+    if "fp32_rw" in out:
+        for name in ("split_rw", "split_mala"):
+            if name in out and out[name]["reached"] and out["fp32_rw"]["reached"]:
+                out[f"speedup_{name}_vs_fp32_rw"] = out["fp32_rw"]["median_wall_s"] / out[name]["median_wall_s"]
     out["target_log_ml_nse"] = target
     return out
 
@@ -424,24 +450,26 @@ def main():
     ap.add_argument("--mkernel", default="rw", choices=["rw", "mala"],
                     help="M kernel of the timed step (MALA evaluates through the gradient kernel)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-sps", action="store_true", help="skip the whole-simulator wall-time runs")
-    ap.add_argument("--sps-ladder", default="",
-                    help="comma list of forms (split_rw, split_mala, fp32_rw) run to log-ML NSE <= 0.05 "
-                         "by doubling the groups, three seeds at the rung reached (adds sps.ladder)")
+    ap.add_argument("--no-c2", action="store_true", help="skip the c2 workload and the ladder")
+    ap.add_argument("--sps-ladder", default="split_mala,split_rw,fp32_rw",
+                    help="comma list of forms (split_rw, split_mala, fp32_rw) run on c2 to log-ML NSE <= 0.05 "
+                         "by doubling the groups ('' to skip)")
+    ap.add_argument("--ladder-seeds", type=int, default=3, help="seeds of the split MALA form at the rung reached")
+    ap.add_argument("--ladder-seeds-other", type=int, default=1,
+                    help="seeds of the other forms at the rung reached (each run of the plain FP32 form at "
+                         "512 groups takes about 170 s)")
     ap.add_argument("--sps-max-groups", type=int, default=1024)
     ap.add_argument("--ncu-step", action="store_true",
                     help="run one extra step after warm-up inside a CUDA profiler range (for ncu --profile-from-start off)")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per launch of the fused kernel from an ncu capture")
     args = ap.parse_args()
-    world, rank, local = dist_setup()
+    if args.gpus != 1:
+        print(json.dumps({"metric": METRIC, "impl": args.impl, "n_gpus": args.gpus,
+                          "unavailable": "single-GPU build: the simulator runs on one GPU"}), flush=True)
+        return
     if args.impl == "reference":
-        run_reference(args, world, rank)
+        run_reference(args)
     else:
-        run_ours(args, world, rank, local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        run_ours(args)
 
 
 if __name__ == "__main__":

@@ -32,7 +32,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .logit import log_prob_terms, loglik
+from .logit import log_prob_terms, loglik, loglik_grad
 
 
 class DegenerateError(RuntimeError):
@@ -360,6 +360,50 @@ def rw_step(X, y, C, t: int, theta, ll, prior: GaussianPrior, Sigma: np.ndarray,
     theta = np.where(acc[:, None], prop, theta)
     ll = np.where(acc, ll_prop, ll)
     return theta, ll, acc
+
+
+def mala_step(X, y, C, t: int, theta, ll, prior: GaussianPrior, Sigma: np.ndarray,
+              z: np.ndarray, u: np.ndarray):
+    """One Metropolis-adjusted Langevin step with given randomness (not in the paper: an exact
+    Metropolis-Hastings kernel for the same posterior given y_{1:t}, Eq. 13, used beside the
+    random walk of Algorithm 2 step 2(c)i).
+
+    With g(theta) the gradient of the log posterior (log-likelihood plus log prior) and L the
+    lower Cholesky factor of Sigma, the proposal density is q(theta' | theta) =
+    N(theta'; theta + Sigma g(theta) / 2, Sigma), drawn as theta' = theta + Sigma g(theta) / 2 + L z.
+    The acceptance ratio is the Metropolis-Hastings ratio of the posterior kernel and the two
+    proposal densities (their normalising constants are equal and cancel):
+        log alpha = ell(theta') + log p(theta') + log q(theta | theta')
+                  - ell(theta)  - log p(theta)  - log q(theta' | theta),
+    accept when log u < log alpha. Returns (theta, ll, accepted mask, log alpha).
+    """
+    try:
+        L = np.linalg.cholesky(Sigma)
+    except np.linalg.LinAlgError as exc:
+        raise DegenerateError(str(exc)) from exc
+    Sinv = np.linalg.inv(Sigma)
+    theta = np.atleast_2d(np.asarray(theta, dtype=np.float64))
+
+    def grad_log_post(th):
+        _, gl = loglik_grad(X, y, th, C, t)
+        return gl - (th - prior.mean[None, :]) @ prior.prec.T
+
+    def log_q(to, frm, g_frm):
+        # log N(to; frm + Sigma g(frm) / 2, Sigma) up to the shared constant
+        r = to - frm - 0.5 * g_frm @ Sigma.T
+        return -0.5 * np.einsum("pi,ij,pj->p", r, Sinv, r)
+
+    g = grad_log_post(theta)
+    prop = theta + 0.5 * g @ Sigma.T + z @ L.T
+    ll_prop = loglik(X, y, prop, C, t)
+    g_prop = grad_log_post(prop)
+    log_alpha = (ll_prop + prior.log_kernel(prop) + log_q(theta, prop, g_prop)
+                 - ll - prior.log_kernel(theta) - log_q(prop, theta, g))
+    with np.errstate(divide="ignore"):
+        acc = np.log(u) < log_alpha
+    theta = np.where(acc[:, None], prop, theta)
+    ll = np.where(acc, ll_prop, ll)
+    return theta, ll, acc, log_alpha
 
 
 def next_h(h: float, alpha: float, opt: SpsOptions) -> float:

@@ -209,6 +209,15 @@ sps_status sps_set_timing(sps_ctx* ctx, int32_t on);
 sps_status sps_counters(sps_ctx* ctx, int32_t reset, int64_t* launches, int64_t* hot_launches,
                         double* hot_ms);
 
+/* Diagnostics of the failure path (the paper has no counterpart). Every wait of the fused
+ * split-precision log-likelihood kernel on its pipeline barriers is bounded by a wall-clock
+ * limit, after which the kernel stops its CTAs cleanly and the call reports SPS_ERR_TIMEOUT.
+ * timeout_ns sets that limit for later launches on ctx (0 restores the default, 2 s);
+ * stall_producer != 0 makes the kernel's TMA producer issue no copy at all, so that every
+ * consumer wait runs out after timeout_ns and the call returns SPS_ERR_TIMEOUT with nothing left
+ * in flight; 0 restores normal operation. The context stays usable. */
+sps_status sps_set_debug(sps_ctx* ctx, int32_t stall_producer, uint64_t timeout_ns);
+
 /* ------------------------------------------------------------------ the likelihood hot path */
 
 /* Log-likelihood of every particle over the first t observations (Eq. 1, product form of
@@ -230,16 +239,21 @@ sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, d
  * one 32 MiB device array that every GPU loading the library holds until the process exits;
  * the call allocates nothing.
  *   theta: [P x D] device FP64; ll: [P] device FP64 output; work is enqueued on the context's
- *   stream (the call returns before it completes). Same results as sps_loglik(SPS_PREC_SPLIT).
+ *   stream (the call returns before it completes). Same results as sps_loglik(SPS_PREC_SPLIT),
+ *   bit for bit (the same kernels and summation order).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  * the context's device current; make that first call before any stream capture. All calls share
  * the array: calls whose GPU work overlaps race and must be serialised by the caller.
- * Limit: the call needs 4 (C-1) P' k64 bytes of operand rows (P' = P rounded up to 256, k64 = k
- * rounded up to 64) plus 8 W P' c bytes of partial sums (W = 4 for C = 2, 2 for C > 2; c = the
- * call's observation chunks, at most ceil(t / 64)) and must fit in 32 MiB: the binary workload
- * with 65 536 particles, k = 30 and n = 20 000 (c = 5) needs about 26 MiB. Larger calls return
- * SPS_ERR_INVALID_ARG, with the required size in sps_last_error, and launch nothing; other
- * errors as sps_loglik. */
+ * Limit: with k16 = k rounded up to 16, kt = 2 k16 rounded up to 64, P' = P rounded up to the
+ * particles of one work item (128, or 256 when the context's kernel runs on CTA pairs) and c the
+ * call's observation chunks (at most ceil(t / 64)), the call needs 2 kt (C-1) P' bytes of operand
+ * rows plus 8 W c P' bytes of partial sums (W = 4 for C = 2, 2 for C > 2) plus 256 bytes, each
+ * part rounded up to 256 bytes, within 32 MiB: the binary workload with 65 536 particles,
+ * k = 30 and n = 20 000 needs about 18 MiB. Larger calls return SPS_ERR_INVALID_ARG, with the
+ * required size in sps_last_error, and launch nothing.
+ * Timeouts: when the fused kernel gives up on a bounded wait (see sps_set_debug) this call cannot
+ * report it in its status, which is returned before the kernel runs; every ll[p] is then set to
+ * NaN instead. Other errors as sps_loglik. */
 sps_status sps_loglik_noalloc(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, double* ll);
 
 /* Log-likelihoods of M nested models in one fused-kernel launch (split precision): model m uses
@@ -411,6 +425,22 @@ sps_status sps_rw_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P,
                              const double* sigma, const double* z, const double* u,
                              int32_t precision, double* log_alpha, int32_t* accepted,
                              int32_t mem);
+
+/* One MALA step with given randomness, for step-level parity (the MALA M kernel is not in the
+ * paper; it is an exact Metropolis-Hastings kernel for the posterior given y_1:t, Eq. 13, beside
+ * the random walk of Algorithm 2 step 2(c)i). With L the lower Cholesky factor of sigma (host
+ * [D x D]) and g the gradient of the log posterior (log-likelihood and log prior) at theta:
+ * theta' = theta + sigma g(theta) / 2 + L z; log alpha = ll(theta') - ll(theta) + log p(theta')
+ * - log p(theta) + log q(theta | theta') - log q(theta' | theta), q(. | a) = N(a + sigma g(a) / 2,
+ * sigma); accept when log u < log alpha. The log-likelihood and gradient at theta and theta' come
+ * from the function of sps_loglik_grad; the drift and the proposal ratio are formed with FP32
+ * products of L and g (as in the simulator's MALA steps).
+ *   theta [P x D] is updated in place; ll [P] receives the log-likelihood of the returned
+ *   particles (mem); z [P x D], u [P] (mem); log_alpha [P], accepted [P] (int32) outputs (mem, may
+ *   be NULL). 1 <= t <= n. SPS_ERR_DEGENERATE when sigma is not positive definite. */
+sps_status sps_mala_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P, int64_t t,
+                               const double* sigma, const double* z, const double* u,
+                               double* log_alpha, int32_t* accepted, int32_t mem);
 
 #ifdef __cplusplus
 }

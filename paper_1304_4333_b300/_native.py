@@ -99,6 +99,8 @@ SIGNATURES = {
     "sps_ess": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P, C.c_int32]),
     "sps_particle_cov": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int32]),
     "sps_rw_step_given": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int64, _P, _P, _P, C.c_int32, _P, _P, C.c_int32]),
+    "sps_set_debug": (C.c_int, [_P, C.c_int32, C.c_uint64]),
+    "sps_mala_step_given": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, C.c_int32]),
 }
 
 _lib = None

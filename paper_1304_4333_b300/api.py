@@ -315,6 +315,20 @@ class Sps:
                    PRECISIONS[precision], _ptr(la), _ptr(acc), N.MEM_HOST)
         return th, l, la, acc.astype(bool)
 
+    def mala_step_given(self, theta, t: int, sigma, z, u):
+        """One MALA step with given normals z [P, D] and uniforms u [P] (sps_mala_step_given):
+        returns (theta, ll, log alpha, accepted)."""
+        th = _f64(theta).reshape(-1, self.D).copy()
+        l = np.empty(th.shape[0])
+        sig = _f64(sigma).reshape(self.D, self.D)
+        z = _f64(z).reshape(th.shape)
+        u = _f64(u)
+        la = np.empty(th.shape[0])
+        acc = np.empty(th.shape[0], dtype=np.int32)
+        self._call("sps_mala_step_given", _ptr(th), _ptr(l), th.shape[0], int(t), _ptr(sig), _ptr(z), _ptr(u),
+                   _ptr(la), _ptr(acc), N.MEM_HOST)
+        return th, l, la, acc.astype(bool)
+
     # ------------------------------------------------------------------ simulator
     def run_batched(self, ks, J: int, N_: int, g: Optional[float] = None) -> List[RunResult]:
         """Adaptive SPS for nested models (sps_run_batched): model m uses the first ks[m]

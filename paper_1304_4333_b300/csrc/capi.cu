@@ -469,6 +469,13 @@ sps_status sps_set_timing(sps_ctx* ctx, int32_t on) {
   return SPS_OK;
 }
 
+sps_status sps_set_debug(sps_ctx* ctx, int32_t stall_producer, uint64_t timeout_ns) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  ctx->debug_stall = stall_producer != 0;
+  ctx->debug_timeout_ns = timeout_ns;
+  return SPS_OK;
+}
+
 sps_status sps_counters(sps_ctx* ctx, int32_t reset, int64_t* launches, int64_t* hot_launches, double* hot_ms) {
   if (!ctx) return SPS_ERR_INVALID_ARG;
   SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -548,7 +555,7 @@ sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const 
     enc.kc16 = (enc.kc + 15) / 16 * 16;
     enc.kx = (enc.k16 + enc.kc16 + 63) / 64 * 64;
     enc.kt = (2 * enc.k16 + 63) / 64 * 64;
-    enc.bn = (NC <= 3) ? tc_tile_rows(NC, enc.kx, enc.kt) : 0;
+    enc.bn = (NC <= 3) ? tc_tile_rows(NC, enc.kx, enc.kt, 1) : 0;
     if ((st = to_device(ctx, enc.perm_dev, enc.perm.data(), k * sizeof(int))) != SPS_OK) return bail(st);
     if (enc.Xp.reserve(static_cast<size_t>(n) * enc.kx * 2) != cudaSuccess ||
         ctx->Xf.reserve(static_cast<size_t>(n) * k * 4) != cudaSuccess)

@@ -55,8 +55,8 @@ struct XEncoding {
   int k16 = 0, kc16 = 0;      // k and kc rounded up to 16 (MMA K step)
   int kx = 0, kt = 0;         // row widths of the X and theta operands (multiples of 64)
   int bn = 0;                 // observation rows per tile; 0: no tile fits
-  int cl = 1;                 // CTAs per cluster sharing each X tile (each loads bn / cl rows of
-                              // it, multicast to all); the TMA box of X is {64, bn / cl}
+  int cl = 1;                 // 1: one CTA per work item; 2: a CTA pair issuing 256-row MMAs,
+                              // each CTA holding bn / 2 rows of every X tile (TMA box {64, bn / cl})
   int max_clusters = 0;       // co-resident clusters of the fused kernel at this shape
   int chunk_obs = 0;          // observations per work item chosen by the autotuner (0: heuristic)
   std::vector<int> perm;      // internal column j holds original column perm[j]
@@ -134,6 +134,10 @@ struct sps_ctx {
   // fused log-likelihood kernel when timing is on
   int64_t launches = 0;
   bool timing = false;
+  // diagnostics (sps_set_debug): wall limit of the fused kernel's bounded waits (0: 2 s) and a
+  // switch that makes its TMA producer issue no copy, so that the waits run out
+  uint64_t debug_timeout_ns = 0;
+  int debug_stall = 0;
   bool capturing = false;                // stream capture in progress: no event records
   cudaStream_t cap_stream = nullptr;     // private non-blocking stream for graph capture (the
                                          // legacy default stream cannot be captured)
@@ -224,7 +228,7 @@ sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64
                            int precision);
 sps_status ensure_lin(sps_ctx* ctx, int64_t t);
 // Observation rows per tensor-core tile for NC = C - 1 outcomes and operand widths kx, kt.
-int tc_tile_rows(int NC, int kx, int kt);
+int tc_tile_rows(int NC, int kx, int kt, int CL);
 // Cluster size of the fused kernel for the context's tile shape (sets enc.cl, enc.max_clusters):
 // 2 when clusters of two fit on the device, else 1; SPS_TC_CLUSTER=1 in the environment forces 1.
 sps_status tc_configure_cluster(sps_ctx* ctx);
@@ -331,6 +335,20 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity
   return ok;
 }
 
+// As mbar_try_wait with acquire semantics at cluster scope: for phases completed by arrives
+// from the other CTA of a pair.
+__device__ __forceinline__ uint32_t mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -345,6 +363,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (globaltimer() - t0 > limit_ns) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded_cluster(uint64_t* bar, uint32_t parity,
+                                                          volatile int* abort, uint64_t limit_ns) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
     if (*abort) return false;
     if (globaltimer() - t0 > limit_ns) {
       *abort = 1;
@@ -436,6 +468,56 @@ __device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t cta
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
       " [%0], %1;" ::"r"(smem_u32(bar)), "h"(cta_mask)
       : "memory");
+}
+
+// ---- CTA pairs (cta_group::2): one MMA of 256 rows over the two CTAs of a cluster ----
+
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// D[tmem of both CTAs] (+)= A * B^T over the CTA pair: rows 0-127 of A (and of D) in the even
+// CTA, 128-255 in the odd one; each CTA holds half of B's rows. Issued by the even CTA only; the
+// descriptors' shared-memory addresses are read at the same offsets in both CTAs.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive once on the mbarrier at the offset of `bar` in every CTA of `cta_mask` when all pair
+// MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)), "h"(cta_mask)
+      : "memory");
+}
+
+// Address in the shared::cluster window of the variable at the offset of `p` in CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+// Arrive (release at cluster scope) on an mbarrier of another CTA of the cluster.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
 }
 
 // 32 lanes x 32 consecutive 32-bit columns: thread i of the warp gets lane (base + i).

@@ -23,9 +23,9 @@
 // (the Tl Xl' product, relative size 2^-16, is dropped).
 //
 // Kernel structure (one CTA per SM, persistent over work items):
-//   warp 0      TMA producer: theta tiles (double-buffered) and X tiles (stage ring),
-//               cp.async.bulk.tensor with mbarrier transaction counts;
-//   warp 1      allocates TMEM, then one thread issues tcgen05.mma into two TMEM accumulators;
+//   warp 0      TMA producer: theta tiles (double-buffered when they fit) and X tiles (stage
+//               ring), cp.async.bulk.tensor with mbarrier transaction counts;
+//   warp 1      allocates TMEM, then one thread issues tcgen05.mma into the TMEM accumulators;
 //   warps 2..   epilogue groups of four warps; warp w reads TMEM lane quadrant w % 4, so a
 //               group covers the 128 lanes (lane = particle). C = 2: four groups, two per
 //               accumulator, each taking half of its columns; C > 2: two groups, each owning
@@ -33,16 +33,21 @@
 //               thread reduces its own particle's row: FP32 within a tile, FP32 with Kahan
 //               compensation across the tiles of a work item, FP64 across work items.
 // Work item = (observation chunk, group of CL particle tiles), chunk-major so that concurrent
-// CTAs read the same X chunk through L2. With CL = 2 the two CTAs of a cluster take the two
-// particle tiles of an item and share its X tiles: each loads half of the rows of every X tile
-// and multicasts them to both, and each CTA's MMA completion releases the stage in both, so a
-// stage is refilled only when both have consumed it. This halves the X traffic out of L2.
+// CTAs read the same X chunk through L2. With CL = 2 the two CTAs of a cluster form a tensor-core
+// pair: the even CTA issues cta_group::2 MMAs of 256 particles (each CTA's 128 particles in its
+// own shared and tensor memory) x BN observations, each CTA loading and holding only BN / 2 rows
+// of every X tile. Per observation processed, a CTA then receives half the X bytes of a single
+// CTA, and the pipeline holds twice the MMA time per stage. The odd CTA's MMA warp relays each of
+// its landed X stages and theta buffers to the even CTA (remote mbarrier arrive), so that every
+// TMA copy completes on a barrier of its own CTA; the MMA completions arrive on both CTAs'
+// barriers, and both CTAs' epilogue warps release accumulators on the even CTA's barrier.
 // Partial sums go to a [chunk][group][particle] FP64 buffer that the finalize kernel sums in a
 // fixed order: the result is deterministic.
 //
 // Every mbarrier wait is bounded (wall-clock limit); on a timeout the CTA raises a flag, drains
 // its own copies and MMAs with bounded waits, frees TMEM and returns (a stalled peer makes the
-// other CTA of its cluster time out as well; both meet at the final cluster barrier). Warps
+// other CTA of its pair time out as well; both meet at the cluster barriers before and after the
+// pair's TMEM is freed). Warps
 // reconverge before every .sync.aligned tcgen05 instruction, and the producer waits for every
 // stage it filled to be released before the CTA exits, so no asynchronous arrive is still in
 // flight at exit.
@@ -88,6 +93,7 @@ struct TcParams {
   double* partial;     // [n_chunks][nwg][ppad]
   int* flag;           // set to 1 on a timeout
   unsigned long long timeout_ns;
+  int stall;           // diagnostics: non-zero makes the TMA producer issue no copy
   // batched models: per particle tile {prefix length, K slices}, or null. The K-slice word holds
   // four 5-bit fields: the 16-wide slices of the Xh / Th / Tl blocks holding any of the model's
   // columns are [0, ha) and [hb, hc) (bits 0-4, 5-9, 10-14), and the model needs the first hl
@@ -107,21 +113,23 @@ __device__ __forceinline__ int item_tile_hi(const TcParams& prm, int tile_lo, in
 
 struct SmemLayout {
   uint32_t th_bytes;   // one theta buffer (all classes)
-  uint32_t x_bytes;    // one X stage
+  uint32_t x_bytes;    // one X stage (this CTA's rows of a tile)
   uint32_t off_th, off_x, off_bar;
   uint32_t total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int NC, int BN, int kbx, int kbt, int stages, int th_bufs) {
+// CL = 2: a CTA pair; each CTA holds BN / 2 rows of every X tile.
+__host__ __device__ inline SmemLayout smem_layout(int NC, int BN, int CL, int kbx, int kbt, int stages,
+                                                  int th_bufs) {
   SmemLayout L;
   L.th_bytes = static_cast<uint32_t>(NC * kbt) * kTileA;
-  L.x_bytes = static_cast<uint32_t>(kbx) * static_cast<uint32_t>(BN) * 128u;
+  L.x_bytes = static_cast<uint32_t>(kbx) * static_cast<uint32_t>(BN / CL) * 128u;
   L.off_th = 0;
   L.off_x = L.off_th + th_bufs * L.th_bytes;
   L.off_bar = L.off_x + stages * L.x_bytes;
-  // barriers: x_full[st], x_empty[st], th_full[2], th_empty[2], acc_full[2], acc_empty[2],
-  // drain; then tmem base (u32) and abort flag (int)
-  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * nbuf_for(NC, BN) + 1) + 16;
+  // barriers: x_full[st], x_empty[st], x_peer[st], th_full[2], th_empty[2], th_peer[2],
+  // acc_full[NBUF], acc_empty[NBUF], drain; then tmem base (u32) and abort flag (int)
+  L.total = L.off_bar + 8 * (3 * stages + 6 + 2 * nbuf_for(NC, BN) + 1) + 16;
   return L;
 }
 
@@ -131,11 +139,11 @@ constexpr uint32_t kSmemBudget = 227 * 1024 - 1024;
 // next particle tile) if at least 4 X stages still fit, else single-buffered theta with as many
 // stages as fit (c3: 8 stages single-buffered 8.5 ms, 2 stages double-buffered 16.0 ms); false
 // when fewer than 2 stages fit.
-bool pick_stages(int NC, int BN, int kbx, int kbt, int* stages, int* th_bufs) {
+bool pick_stages(int NC, int BN, int CL, int kbx, int kbt, int* stages, int* th_bufs) {
   for (int tb = 2; tb >= 1; --tb) {
     int st = 0;
     for (int s = 8; s >= 2; --s)
-      if (smem_layout(NC, BN, kbx, kbt, s, tb).total <= kSmemBudget) { st = s; break; }
+      if (smem_layout(NC, BN, CL, kbx, kbt, s, tb).total <= kSmemBudget) { st = s; break; }
     if (st >= 4 || (tb == 1 && st >= 2)) {
       *stages = st;
       *th_bufs = tb;
@@ -153,15 +161,22 @@ __device__ __forceinline__ uint64_t kslice_off(int rows, int e) {
   return static_cast<uint64_t>((e >> 6) * rows * 8 + ((e & 63) >> 3));
 }
 
-// BATCH: particle tiles of several nested models (per-tile prefix and K slices in ptile_info);
-// a separate instance so that the single-model issue loop stays minimal.
+// BATCH: particle tiles of several nested models; a separate instance so that the single-model
+// issue loop stays minimal.
+// CL = 1: one CTA per work item (cta_group::1 MMAs of 128 particles x BN observations).
+// CL = 2: a CTA pair per work item. The even CTA issues cta_group::2 MMAs of 256 particles
+// (128 in each CTA's shared memory and tensor memory) x BN observations, each CTA holding BN / 2
+// rows of every X tile; each CTA's TMA copies complete on its own barriers, and the odd CTA's
+// MMA warp relays each completed stage and theta buffer to the even CTA with a remote arrive.
+// The MMA completions arrive on both CTAs' barriers (commit multicast), and both CTAs' epilogue
+// warps release an accumulator on the even CTA's barrier.
 template <int NC, int BN, int CL, bool BATCH>
 __global__ void __launch_bounds__(threads_for(NC), 1)
 loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                  const TcParams prm) {
-  static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
-  constexpr int HR = BN / CL;                     // X rows of a tile loaded by this CTA
-  constexpr uint16_t kMask = (1u << CL) - 1u;     // every CTA of the cluster
+  static_assert(CL == 1 || CL == 2, "one CTA or a CTA pair");
+  constexpr int HR = BN / CL;                     // X rows of a tile held by this CTA
+  constexpr uint16_t kPair = 3u;                  // both CTAs of the pair
   constexpr int NBUF = nbuf_for(NC, BN);
   constexpr int NWG = nwg_for(NC);
   static_assert(NWG % NBUF == 0 || NBUF % NWG == 0, "groups and accumulators");
@@ -175,13 +190,15 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   // 1024-byte alignment for the 128B-swizzle atoms
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const SmemLayout L = smem_layout(NC, BN, prm.kbx, prm.kbt, prm.stages, prm.th_bufs);
+  const SmemLayout L = smem_layout(NC, BN, CL, prm.kbx, prm.kbt, prm.stages, prm.th_bufs);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar);
   uint64_t* x_full = bars;
   uint64_t* x_empty = x_full + prm.stages;
-  uint64_t* th_full = x_empty + prm.stages;
+  uint64_t* x_peer = x_empty + prm.stages;         // even CTA: the odd CTA's stage landed
+  uint64_t* th_full = x_peer + prm.stages;
   uint64_t* th_empty = th_full + 2;
-  uint64_t* acc_full = th_empty + 2;
+  uint64_t* th_peer = th_empty + 2;                // even CTA: the odd CTA's theta landed
+  uint64_t* acc_full = th_peer + 2;
   uint64_t* acc_empty = acc_full + NBUF;
   uint64_t* drain = acc_empty + NBUF;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
@@ -196,27 +213,34 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   if (threadIdx.x == 0) {
     for (int i = 0; i < prm.stages; ++i) {
       ptx::mbar_init(&x_full[i], 1);
-      ptx::mbar_init(&x_empty[i], CL);   // released by the MMA of every CTA of the cluster
+      ptx::mbar_init(&x_empty[i], 1);
+      ptx::mbar_init(&x_peer[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&th_full[i], 1);
       ptx::mbar_init(&th_empty[i], 1);
+      ptx::mbar_init(&th_peer[i], 1);
     }
     for (int i = 0; i < NBUF; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
-      ptx::mbar_init(&acc_empty[i], 4 * GPB);   // one arrive per warp of the owning groups
+      ptx::mbar_init(&acc_empty[i], 4 * GPB * CL);   // one arrive per warp of the owning groups
     }
     ptx::mbar_init(drain, 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(tmem_holder, kTmemCols);
-    ptx::tmem_relinquish();
+    if constexpr (CL > 1) {
+      ptx::tmem_alloc_pair(tmem_holder, kTmemCols);
+      ptx::tmem_relinquish_pair();
+    } else {
+      ptx::tmem_alloc(tmem_holder, kTmemCols);
+      ptx::tmem_relinquish();
+    }
   }
   ptx::tc_fence_before();
   __syncthreads();
-  // the peer's copies and arrives target this CTA's barriers: both must be initialised first
+  // the peer's arrives and MMA completions target this CTA's barriers: both must be initialised
   if constexpr (CL > 1) ptx::cluster_sync();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
@@ -231,7 +255,7 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       uint32_t xph = 0;
       int tb = 0;
       uint32_t tph = 0;
-      bool ok = true;
+      bool ok = (prm.stall == 0);   // diagnostics: a stalled producer issues no copy at all
       // bit s: stage / theta buffer s was filled; parity of its last fill
       uint32_t issued_x = 0, issued_t = 0, par_x = 0, par_t = 0;
       for (int item = cluster_id; ok && item < prm.n_items; item += n_clusters) {
@@ -254,15 +278,10 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
           if (!ptx::mbar_wait_bounded(&x_empty[st], xph ^ 1u, abort_flag, limit)) { ok = false; break; }
           uint8_t* xb = smem + L.off_x + st * L.x_bytes;
-          ptx::mbar_arrive_expect_tx(&x_full[st], L.x_bytes);   // the whole tile, both halves
+          ptx::mbar_arrive_expect_tx(&x_full[st], L.x_bytes);   // this CTA's rows of the tile
           const int obs = tile * BN + rank * HR;
-          for (int kb = 0; kb < prm.kbx; ++kb) {
-            uint8_t* dst = xb + kb * BN * 128 + rank * HR * 128;
-            if constexpr (CL > 1)
-              ptx::tma_load_2d_multicast(dst, &mapX, &x_full[st], kb * kKB, obs, kMask);
-            else
-              ptx::tma_load_2d(dst, &mapX, &x_full[st], kb * kKB, obs);
-          }
+          for (int kb = 0; kb < prm.kbx; ++kb)
+            ptx::tma_load_2d(xb + kb * HR * 128, &mapX, &x_full[st], kb * kKB, obs);
           issued_x |= 1u << st;
           par_x = (par_x & ~(1u << st)) | (xph << st);
           if (++st == prm.stages) { st = 0; xph ^= 1u; }
@@ -284,10 +303,36 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           if (issued_t & (1u << b)) ptx::mbar_wait_bounded(&th_empty[b], (par_t >> b) & 1u, abort_flag, limit);
       }
     }
+  } else if (warp == 1 && CL > 1 && rank != 0) {
+    // ------------------------------------------------------------------ relay (odd CTA of a pair)
+    // each landed theta buffer and X stage of this CTA is announced on the even CTA's th_peer /
+    // x_peer barrier, in the order the MMA thread consumes them
+    if (lane == 0) {
+      const uint32_t r_th_peer = ptx::cluster_addr(th_peer, 0);
+      const uint32_t r_x_peer = ptx::cluster_addr(x_peer, 0);
+      int st = 0, tb = 0;
+      uint32_t xph = 0, tph = 0;
+      bool ok = true;
+      for (int item = cluster_id; ok && item < prm.n_items; item += n_clusters) {
+        const int chunk = item / prm.n_pgroups;
+        const int ptile = (item - chunk * prm.n_pgroups) * CL + rank;
+        const int tile_lo = chunk * prm.chunk_tiles;
+        const int tile_hi = item_tile_hi<BN, BATCH>(prm, tile_lo, ptile);
+        if (BATCH && tile_hi == tile_lo) continue;
+        if (!ptx::mbar_wait_bounded_cluster(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
+        ptx::mbar_arrive_remote(r_th_peer + 8u * static_cast<uint32_t>(tb));
+        if (++tb == prm.th_bufs) { tb = 0; tph ^= 1u; }
+        for (int tile = tile_lo; tile < tile_hi; ++tile) {
+          if (!ptx::mbar_wait_bounded_cluster(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
+          ptx::mbar_arrive_remote(r_x_peer + 8u * static_cast<uint32_t>(st));
+          if (++st == prm.stages) { st = 0; xph ^= 1u; }
+        }
+      }
+    }
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = ptx::idesc_bf16_f32(kBM, BN);
+      const uint32_t idesc = ptx::idesc_bf16_f32(kBM * CL, BN);
       int st = 0;
       uint32_t xph = 0;
       int tb = 0;
@@ -307,18 +352,21 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int ha = static_cast<int>(kinfo & 31u), hb = static_cast<int>((kinfo >> 5) & 31u);
         const int hc = static_cast<int>((kinfo >> 10) & 31u), hl = static_cast<int>((kinfo >> 15) & 31u);
         if (!ptx::mbar_wait_bounded(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
+        if constexpr (CL > 1)
+          if (!ptx::mbar_wait_bounded_cluster(&th_peer[tb], tph, abort_flag, limit)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t thb = ptx::smem_u32(smem + L.off_th + tb * L.th_bytes);
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
           const int buf = acc_count % NBUF;
           const uint32_t aph = (acc_count / NBUF) & 1u;
-          if (!ptx::mbar_wait_bounded(&acc_empty[buf], aph ^ 1u, abort_flag, limit)) { ok = false; break; }
+          if (!ptx::mbar_wait_bounded_cluster(&acc_empty[buf], aph ^ 1u, abort_flag, limit)) { ok = false; break; }
           if (!ptx::mbar_wait_bounded(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
+          if constexpr (CL > 1)
+            if (!ptx::mbar_wait_bounded_cluster(&x_peer[st], xph, abort_flag, limit)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint64_t dx = ptx::sdesc_sw128(ptx::smem_u32(smem + L.off_x + st * L.x_bytes));
           // the NC classes accumulate into independent TMEM accumulators: issuing each K slice
-          // for all classes before the next keeps NC dependent MMA chains in flight (an MMA
-          // that accumulates into the result of the previous one waits for it)
+          // for all classes before the next keeps NC dependent MMA chains in flight
           uint32_t d[NC];
           uint64_t dt[NC];
 #pragma unroll
@@ -326,65 +374,75 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             d[c] = tmem_base + static_cast<uint32_t>((buf * NC + c) * BN);
             dt[c] = ptx::sdesc_sw128(thb + static_cast<uint32_t>(c * prm.kbt) * kTileA);
           }
+          auto mma = [&](int c, uint64_t ka, uint64_t kb, uint32_t acc) {
+            if constexpr (CL > 1) ptx::mma_bf16_pair(d[c], dt[c] + ka, dx + kb, idesc, acc);
+            else ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, acc);
+          };
           if constexpr (!BATCH) {
             for (int i = 0; i < prm.ksh; ++i) {   // Th_c Xh'
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, i > 0);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, i > 0);
             }
             for (int i = 0; i < prm.ksh; ++i) {   // Tl_c Xh'
-              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(BN, 16 * i);
+              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(HR, 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
             }
             for (int i = 0; i < prm.ksl; ++i) {   // Th_c Xl' over the continuous columns
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, prm.k16 + 16 * i);
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, prm.k16 + 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
             }
           } else {
             // batched models: the Xh / Th / Tl slices [0, ha) and [hb, hc) holding the item's
             // model's columns and its hl slices of Xl; the first MMA of a tile overwrites the
             // accumulator
             for (int i = 0; i < ha; ++i) {
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, i > 0);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, i > 0);
             }
             for (int i = hb; i < hc; ++i) {
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, 16 * i);
               const uint32_t acc = (ha > 0 || i > hb) ? 1u : 0u;
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, acc);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, acc);
             }
             for (int i = 0; i < ha; ++i) {
-              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(BN, 16 * i);
+              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(HR, 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
             }
             for (int i = hb; i < hc; ++i) {
-              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(BN, 16 * i);
+              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(HR, 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
             }
             for (int i = 0; i < hl; ++i) {
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, prm.k16 + 16 * i);
+              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, prm.k16 + 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, 1);
+              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
             }
           }
           issued_any = true;
-          if constexpr (CL > 1) ptx::mma_commit_multicast(&x_empty[st], kMask);
-          else ptx::mma_commit(&x_empty[st]);
-          ptx::mma_commit(&acc_full[buf]);
+          if constexpr (CL > 1) {
+            ptx::mma_commit_pair(&x_empty[st], kPair);
+            ptx::mma_commit_pair(&acc_full[buf], kPair);
+          } else {
+            ptx::mma_commit(&x_empty[st]);
+            ptx::mma_commit(&acc_full[buf]);
+          }
           ++acc_count;
           if (++st == prm.stages) { st = 0; xph ^= 1u; }
         }
-        ptx::mma_commit(&th_empty[tb]);
+        if constexpr (CL > 1) ptx::mma_commit_pair(&th_empty[tb], kPair);
+        else ptx::mma_commit(&th_empty[tb]);
         if (++tb == prm.th_bufs) { tb = 0; tph ^= 1u; }
       }
       if (*abort_flag && issued_any) {
-        ptx::mma_commit(drain);
+        if constexpr (CL > 1) ptx::mma_commit_pair(drain, 1u);
+        else ptx::mma_commit(drain);
         volatile int no_abort = 0;
         ptx::mbar_wait_bounded(drain, 0, &no_abort, limit);
       }
@@ -401,6 +459,8 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     const int quad = warp & 3;
     const int row = quad * 32 + lane;                 // particle within the tile
     const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
+    // the accumulator release goes to the MMA-issuing CTA (this CTA when alone)
+    const uint32_t r_acc_empty = (CL > 1) ? ptx::cluster_addr(acc_empty, 0) : 0u;
     constexpr float kLn2 = 0.6931471805599453f;
     constexpr int NCH = COLS / 32;                    // 32-column chunks per group and tile
     uint32_t acc_base = 0;                            // accumulator uses before this item
@@ -426,6 +486,15 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int valid = t_item - tile * BN - col0;   // columns of this group inside [0, t)
         const bool whole = valid >= COLS;
         const uint32_t tbase = tmem_base + lane_base + static_cast<uint32_t>(buf * NC * BN + col0);
+        auto release = [&]() {
+          // this group's columns are in registers: release its share of the accumulator
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            if constexpr (CL > 1) ptx::mbar_arrive_remote(r_acc_empty + 8u * static_cast<uint32_t>(buf));
+            else ptx::mbar_arrive(&acc_empty[buf]);
+          }
+        };
         float tile_val;                               // this tile's non-linear sum in log2 units
         if constexpr (NC == 1) {
           // four chains as two packed pairs (one FP32x2 add and one FP32x2 FMA per two terms):
@@ -437,12 +506,7 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             float v[32];
             ptx::tmem_ld_32x32b_x32(tbase + ch * 32, v);
             ptx::tmem_wait_ld();
-            if (ch == NCH - 1) {
-              // this group's columns are in registers: release its share of the accumulator
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
-            }
+            if (ch == NCH - 1) release();
             if (whole) {
 #pragma unroll
               for (int j = 0; j < 32; j += 4) {
@@ -494,11 +558,7 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 #pragma unroll
             for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
             ptx::tmem_wait_ld();
-            if (ch == NCH - 1) {
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
-            }
+            if (ch == NCH - 1) release();
             const int j0 = ch * 32;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
@@ -534,12 +594,16 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   ptx::tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicExch(prm.flag, 1);
+  // a pair's MMAs write both CTAs' tensor memory and read both CTAs' shared memory: neither CTA
+  // frees its tensor memory before the even CTA's MMA thread has seen them all complete
+  if constexpr (CL > 1) ptx::cluster_sync();
   if (warp == 1) {
     __syncwarp();   // lane 0 ran the MMA role alone: reconverge before the aligned dealloc
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem_base, kTmemCols);
+    if constexpr (CL > 1) ptx::tmem_dealloc_pair(tmem_base, kTmemCols);
+    else ptx::tmem_dealloc(tmem_base, kTmemCols);
   }
-  // no CTA leaves while its peer may still arrive on its barriers or write its shared memory
+  // no CTA leaves while its peer may still arrive on its barriers or read its shared memory
   if constexpr (CL > 1) ptx::cluster_sync();
 }
 
@@ -550,9 +614,14 @@ constexpr int kFinThreads = 256;
 __global__ void __launch_bounds__(kFinThreads)
 loglik_finalize_kernel(const double* __restrict__ theta, int64_t P, int D,
                        const double* __restrict__ lin, const double* __restrict__ partial,
-                       int slices, int ppad, double* __restrict__ ll) {
+                       int slices, int ppad, double* __restrict__ ll, const int* __restrict__ poison) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= P) return;
+  if (poison && *poison) {
+    // the fused kernel gave up on a bounded wait: its partial sums are incomplete
+    ll[p] = __longlong_as_double(0x7FF8000000000000LL);
+    return;
+  }
   const double* th = theta + p * D;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int i = 0;
@@ -1242,9 +1311,10 @@ __global__ void grad_tc_finalize_kernel(const float* __restrict__ gpartial, int 
 }
 
 sps_status launch_finalize(sps_ctx* ctx, const double* theta, int64_t P, const double* partial, int slices,
-                           int ppad, double* ll) {
+                           int ppad, double* ll, const int* poison = nullptr) {
   loglik_finalize_kernel<<<static_cast<unsigned>((P + kFinThreads - 1) / kFinThreads), kFinThreads, 0,
-                           ctx->stream>>>(theta, P, ctx->D, ctx->lin.as<double>(), partial, slices, ppad, ll);
+                           ctx->stream>>>(theta, P, ctx->D, ctx->lin.as<double>(), partial, slices, ppad, ll,
+                                          poison);
   ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
@@ -1380,11 +1450,12 @@ bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t
   prm->n_chunks = std::max(1, (prm->n_tiles + chunk_tiles - 1) / chunk_tiles);
   prm->n_items = prm->n_tiles > 0 ? prm->n_pgroups * prm->n_chunks : 0;
   int stages = 0, th_bufs = 0;
-  if (!pick_stages(NC, BN, prm->kbx, prm->kbt, &stages, &th_bufs)) return false;
+  if (!pick_stages(NC, BN, enc.cl, prm->kbx, prm->kbt, &stages, &th_bufs)) return false;
   prm->stages = stages;
   prm->th_bufs = th_bufs;
-  prm->timeout_ns = 2000000000ull;
-  *smem_bytes = smem_layout(NC, BN, prm->kbx, prm->kbt, stages, th_bufs).total + 1024;
+  prm->timeout_ns = ctx->debug_timeout_ns ? ctx->debug_timeout_ns : 2000000000ull;
+  prm->stall = ctx->debug_stall;
+  *smem_bytes = smem_layout(NC, BN, enc.cl, prm->kbx, prm->kbt, stages, th_bufs).total + 1024;
   return true;
 }
 
@@ -1398,19 +1469,20 @@ double tc_waves(const sps_ctx* ctx, int64_t P, int64_t t) {
   return static_cast<double>(prm.n_items) / std::max(1, conc);
 }
 
-// Observation rows per tensor-core tile: the widest tile for the outcome count that keeps at
-// least three X stages in shared memory (0 when none fits).
-int tc_tile_rows(int NC, int kx, int kt) {
+// Observation rows per tensor-core tile for one CTA (CL = 1) or a CTA pair (CL = 2, each CTA
+// holding half of every X tile): the widest tile for the outcome count that keeps at least
+// three X stages in shared memory (0 when none fits).
+int tc_tile_rows(int NC, int kx, int kt, int CL) {
   const int cands[3][2] = {{256, 128}, {128, 64}, {64, 32}};
   if (NC < 1 || NC > 3) return 0;
   for (int q = 0; q < 2; ++q) {
     const int BN = cands[NC - 1][q];
     int st = 0, tb = 0;
-    if (pick_stages(NC, BN, kx / kKB, kt / kKB, &st, &tb) && st >= 3) return BN;
+    if (pick_stages(NC, BN, CL, kx / kKB, kt / kKB, &st, &tb) && st >= 3) return BN;
   }
   const int BN = cands[NC - 1][1];
   int st = 0, tb = 0;
-  return pick_stages(NC, BN, kx / kKB, kt / kKB, &st, &tb) ? BN : 0;
+  return pick_stages(NC, BN, CL, kx / kKB, kt / kKB, &st, &tb) ? BN : 0;
 }
 
 // One launch shape of the fused kernel: tile rows, cluster size (with its co-resident
@@ -1462,10 +1534,10 @@ sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out)
   const bool allow_cl2 = !(env && env[0] == '1' && env[1] == 0);
   for (int q = 0; q < 2; ++q) {
     const int bn = cands[NC - 1][q];
-    int stages = 0, th_bufs = 0;
-    if (!pick_stages(NC, bn, enc.kx / kKB, enc.kt / kKB, &stages, &th_bufs)) continue;
-    const uint32_t smem_bytes = smem_layout(NC, bn, enc.kx / kKB, enc.kt / kKB, stages, th_bufs).total + 1024;
     for (int cl = 1; cl <= 2; ++cl) {
+      int stages = 0, th_bufs = 0;
+      if (!pick_stages(NC, bn, cl, enc.kx / kKB, enc.kt / kKB, &stages, &th_bufs)) continue;
+      const uint32_t smem_bytes = smem_layout(NC, bn, cl, enc.kx / kKB, enc.kt / kKB, stages, th_bufs).total + 1024;
       int mc = 0;
       if (cl == 2) {
         if (!allow_cl2) continue;
@@ -1506,17 +1578,35 @@ sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out)
 
 sps_status tc_configure_cluster(sps_ctx* ctx) {
   XEncoding& enc = ctx->enc;
+  const int NC = ctx->NC;
   enc.cl = 1;
   enc.max_clusters = 0;
+  enc.bn = (NC <= 3) ? tc_tile_rows(NC, enc.kx, enc.kt, 1) : 0;
   if (enc.bn == 0) return SPS_OK;
   const char* env = getenv("SPS_TC_CLUSTER");
   if (env && env[0] == '1' && env[1] == 0) return SPS_OK;
+  // CTA pairs where a tile's MMAs take longer than its epilogue (tensor-bound shapes: the pair
+  // halves the X bytes each CTA receives per MMA clock and doubles the MMA time a stage covers),
+  // and where two CTAs of the pair's shape can be co-scheduled. An epilogue-bound shape stays on
+  // single CTAs: there the pair's cross-CTA accumulator release only lengthens the turnaround
+  // (binary logit k = 30: 0.32 ms per launch in pairs against 0.24 ms).
+  const int bn1 = enc.bn, bn2 = tc_tile_rows(NC, enc.kx, enc.kt, 2);
+  {
+    const double slices = 2.0 * (enc.k16 / 16) + enc.kc16 / 16;   // K = 16 MMAs per class and tile
+    const double mma_clk = slices * NC * std::max(54.0, bn1 / 2.0);    // M = 128 MMA issue cost
+    const double epi_clk = 128.0 * bn1 * (NC == 1 ? 1 : NC + 1) / 30.0; // ex2 per tile at 30 / clk
+    if (mma_clk <= epi_clk) return SPS_OK;
+  }
   int stages = 0, th_bufs = 0;
-  if (!pick_stages(ctx->NC, enc.bn, enc.kx / kKB, enc.kt / kKB, &stages, &th_bufs)) return SPS_OK;
-  const uint32_t smem_bytes = smem_layout(ctx->NC, enc.bn, enc.kx / kKB, enc.kt / kKB, stages, th_bufs).total + 1024;
+  if (bn2 == 0 || !pick_stages(NC, bn2, 2, enc.kx / kKB, enc.kt / kKB, &stages, &th_bufs)) return SPS_OK;
+  const uint32_t smem_bytes = smem_layout(NC, bn2, 2, enc.kx / kKB, enc.kt / kKB, stages, th_bufs).total + 1024;
   int n = 0;
-  SPS_TRY(run_any(ctx, 2, nullptr, 0, smem_bytes, nullptr, false, &n));
+  enc.bn = bn2;
+  const sps_status s = run_any(ctx, 2, nullptr, 0, smem_bytes, nullptr, false, &n);
+  enc.bn = bn1;
+  SPS_TRY(s);
   if (n >= 1) {
+    enc.bn = bn2;
     enc.cl = 2;
     enc.max_clusters = n;
   }
@@ -1901,7 +1991,10 @@ sps_status loglik_split_static(sps_ctx* ctx, const double* d_theta, int64_t P, i
   SPS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));   // the flag must start at zero
   if (prm.n_items > 0)
     SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &mapT, false, nullptr));
-  return launch_finalize(ctx, d_theta, P, partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad, d_ll);
+  // a timeout leaves NaN in every ll (this call returns before the kernel runs, so the flag cannot
+  // be read back here)
+  return launch_finalize(ctx, d_theta, P, partial, prm.n_items > 0 ? static_cast<int>(slices) : 0, ppad, d_ll,
+                         flag);
 }
 
 }  // namespace sps

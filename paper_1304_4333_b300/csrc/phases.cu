@@ -1014,7 +1014,7 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
                     const unsigned long long* __restrict__ step_dev, const double* __restrict__ mu,
                     const double* __restrict__ prec, bool full, const int* __restrict__ flag,
                     double* __restrict__ th_o, double* __restrict__ lp_o, float* __restrict__ zq_o,
-                    double* __restrict__ z2_o) {
+                    double* __restrict__ z2_o, const double* __restrict__ z_given) {
   if (*flag) return;
   const uint64_t step = step_dev ? *step_dev : step_arg;
   extern __shared__ float ms[];
@@ -1034,7 +1034,13 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
     for (int i = sub; i < D; i += kMalaSub)
       gs[i * kMalaThreads + pp] = static_cast<float>(gll[p * D + i] + prior_grad(t, mu, prec, D, full, i));
   }
-  {
+  if (z_given) {
+    // given normals (step-level parity), rounded to FP32 like the drawn ones
+    for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
+      const int qp = q / D, d = q - qp * D;
+      zs[d * kMalaThreads + qp] = static_cast<float>(z_given[(p0 + qp) * D + d]);
+    }
+  } else {
     // draw (particle p, word q) as before: counter p * ceil(D / 4) + q
     const int per = (D + 3) / 4;
     for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
@@ -1085,7 +1091,8 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
                    const double* __restrict__ mu, const double* __restrict__ prec, bool full, uint64_t seed,
                    uint64_t step_arg, const unsigned long long* __restrict__ step_dev,
                    const int* __restrict__ flag, unsigned long long* __restrict__ n_acc,
-                   int* __restrict__ nonfinite) {
+                   int* __restrict__ nonfinite, const double* __restrict__ u_given,
+                   double* __restrict__ la_out, int* __restrict__ acc_out) {
   if (*flag) return;
   const uint64_t step = step_dev ? *step_dev : step_arg;
   extern __shared__ float ms[];
@@ -1122,8 +1129,16 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
     const double lpp = ll_p[p];
     if (!isfinite(lpp)) atomicOr(nonfinite, 1);
     const double la = (lpp - ll[p]) + (lp_p[p] - lp[p]) - 0.5 * w2 + 0.5 * z2[p];
-    const uint4 r = draw(seed, static_cast<uint32_t>(p), kStreamAccept, step);
-    acc = log(uniform53(r.x, r.y)) < la;
+    double u;
+    if (u_given) {
+      u = u_given[p];
+    } else {
+      const uint4 r = draw(seed, static_cast<uint32_t>(p), kStreamAccept, step);
+      u = uniform53(r.x, r.y);
+    }
+    acc = log(u) < la;
+    if (la_out) la_out[p] = la;
+    if (acc_out) acc_out[p] = acc ? 1 : 0;
     if (acc) {
       ll[p] = lpp;
       lp[p] = lp_p[p];
@@ -1651,9 +1666,44 @@ sps_status rw_issue_accept(sps_ctx* ctx, sps_state* st, uint64_t step, StepCtl* 
   return SPS_OK;
 }
 
+// MALA proposal, the proposals' log-likelihood and gradient, and the Metropolis-Hastings
+// decisions, after factor_proposal has left the FP32 factor of Sigma in st->chol. z_given /
+// u_given replace the Philox normals / uniforms; la_out / acc_out receive log alpha and the
+// decisions (all optional).
+static sps_status mala_issue(sps_ctx* ctx, sps_state* st, uint64_t step, const unsigned long long* step_dev,
+                             const double* z_given, const double* u_given, double* la_out, int* acc_out) {
+  const int D = ctx->D;
+  const int T = D * (D + 1) / 2;
+  const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 3 * static_cast<size_t>(D) * kMalaThreads);
+  const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + ((static_cast<size_t>(D) * kMalaThreads + 1) & ~1)) +
+                        sizeof(double) * static_cast<size_t>(D) * kMalaThreads;
+  SPS_CUDA_TRY(cudaFuncSetAttribute(mala_propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem_p)));
+  SPS_CUDA_TRY(cudaFuncSetAttribute(mala_accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem_a)));
+  const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
+  const unsigned blocks = static_cast<unsigned>((st->P + kMalaThreads - 1) / kMalaThreads);
+  mala_propose_kernel<<<blocks, kMalaThreads * kMalaSub, smem_p, ctx->stream>>>(
+      st->theta.as<double>(), st->grad.as<double>(), st->P, D, L32, st->seed, step, step_dev,
+      ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(), prior_full(ctx), flag_ptr(st, 0),
+      st->theta_prop.as<double>(), st->lp_prop.as<double>(), st->zq.as<float>(), st->z2.as<double>(), z_given);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  SPS_TRY(loglik_grad_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
+                               st->grad_prop.as<double>()));
+  mala_accept_kernel<<<blocks, kMalaThreads * kMalaSub, smem_a, ctx->stream>>>(
+      st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->grad.as<double>(),
+      st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->grad_prop.as<double>(),
+      st->zq.as<float>(), st->z2.as<double>(), L32, st->P, D, ctx->d_prior_mean.as<double>(),
+      ctx->d_prior_prec.as<double>(), prior_full(ctx), st->seed, step, step_dev, flag_ptr(st, 0),
+      st->counters.as<unsigned long long>(), flag_ptr(st, 1), u_given, la_out, acc_out);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
 sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* sigma, double* sigma_used, double h,
                        uint64_t step, StepCtl* ctl) {
-  const int D = ctx->D;
   const bool mala = (kernel == SPS_MKERNEL_MALA);
   const unsigned long long* step_dev = ctl ? &ctl->step : nullptr;
   if (!mala) {
@@ -1665,33 +1715,7 @@ sps_status mstep_issue(sps_ctx* ctx, sps_state* st, int kernel, const double* si
   SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
   SPS_TRY(factor_proposal(ctx, st, st->theta.as<double>(), h, ctl ? &ctl->h : nullptr, sigma, sigma_used,
                           flag_ptr(st, 0)));
-  {
-    const int T = D * (D + 1) / 2;
-    const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 3 * static_cast<size_t>(D) * kMalaThreads);
-    const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + ((static_cast<size_t>(D) * kMalaThreads + 1) & ~1)) +
-                          sizeof(double) * static_cast<size_t>(D) * kMalaThreads;
-    SPS_CUDA_TRY(cudaFuncSetAttribute(mala_propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem_p)));
-    SPS_CUDA_TRY(cudaFuncSetAttribute(mala_accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem_a)));
-    const float* L32 = reinterpret_cast<const float*>(st->chol.as<double>() + static_cast<size_t>(D) * D);
-    const unsigned blocks = static_cast<unsigned>((st->P + kMalaThreads - 1) / kMalaThreads);
-    mala_propose_kernel<<<blocks, kMalaThreads * kMalaSub, smem_p, ctx->stream>>>(
-        st->theta.as<double>(), st->grad.as<double>(), st->P, D, L32, st->seed, step, step_dev,
-        ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(), prior_full(ctx), flag_ptr(st, 0),
-        st->theta_prop.as<double>(), st->lp_prop.as<double>(), st->zq.as<float>(), st->z2.as<double>());
-    ++ctx->launches;
-    SPS_CUDA_TRY(cudaGetLastError());
-    SPS_TRY(loglik_grad_dispatch(ctx, st->theta_prop.as<double>(), st->P, st->t, st->ll_prop.as<double>(),
-                             st->grad_prop.as<double>()));
-    mala_accept_kernel<<<blocks, kMalaThreads * kMalaSub, smem_a, ctx->stream>>>(
-        st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->grad.as<double>(),
-        st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>(), st->grad_prop.as<double>(),
-        st->zq.as<float>(), st->z2.as<double>(), L32, st->P, D, ctx->d_prior_mean.as<double>(),
-        ctx->d_prior_prec.as<double>(), prior_full(ctx), st->seed, step, step_dev, flag_ptr(st, 0),
-        st->counters.as<unsigned long long>(), flag_ptr(st, 1)); ++ctx->launches;
-    SPS_CUDA_TRY(cudaGetLastError());
-  }
+  SPS_TRY(mala_issue(ctx, st, step, step_dev, nullptr, nullptr, nullptr, nullptr));
   launch_monitoring(ctx, st);
   return SPS_OK;
 }
@@ -2725,6 +2749,70 @@ sps_status sps_rw_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P,
       tmp.ll_prop.as<double>(), tmp.lp_prop.as<double>(), P, D, pu, 0, 0, nullptr, flag_ptr(&tmp, 0),
       tmp.counters.as<unsigned long long>(), flag_ptr(&tmp, 1), pla, pacc); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
+  Counters c;
+  SPS_TRY(read_counters(ctx, &tmp, &c));
+  if (c.chol_bad) return fail(ctx, SPS_ERR_DEGENERATE, "sigma is not positive definite");
+  const cudaMemcpyKind k = (mem == SPS_MEM_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  SPS_CUDA_TRY(cudaMemcpyAsync(theta, tmp.theta.ptr, pd, k, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(ll, tmp.ll.ptr, sizeof(double) * P, k, ctx->stream));
+  if (mem == SPS_MEM_HOST) {
+    if (log_alpha) SPS_CUDA_TRY(cudaMemcpyAsync(log_alpha, pla, sizeof(double) * P, k, ctx->stream));
+    if (accepted) SPS_CUDA_TRY(cudaMemcpyAsync(accepted, pacc, sizeof(int) * P, k, ctx->stream));
+  }
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (c.nonfinite) return fail(ctx, SPS_ERR_NONFINITE, "non-finite log-likelihood of a proposal");
+  return SPS_OK;
+}
+
+sps_status sps_mala_step_given(sps_ctx* ctx, double* theta, double* ll, int64_t P, int64_t t, const double* sigma,
+                               const double* z, const double* u, double* log_alpha, int32_t* accepted,
+                               int32_t mem) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  if (!theta || !ll || !sigma || !z || !u || P < 1 || t < 1 || t > ctx->n)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_mala_step_given: bad arguments");
+  const int D = ctx->D;
+  if (D > kMaxD) return fail(ctx, SPS_ERR_UNSUPPORTED, "at most 155 parameters");
+  // a temporary state holds the buffers; its particles are the caller's
+  sps_state tmp;
+  tmp.ctx = ctx;
+  tmp.J = 1;
+  tmp.N = 2;
+  tmp.P = P;
+  tmp.t = t;
+  SPS_TRY(state_buffers(ctx, &tmp));
+  const size_t pd = sizeof(double) * P * D;
+  SPS_CUDA_TRY(tmp.grad.reserve(pd));
+  SPS_CUDA_TRY(tmp.grad_prop.reserve(pd));
+  SPS_CUDA_TRY(tmp.zq.reserve(sizeof(float) * P * D));
+  SPS_CUDA_TRY(tmp.z2.reserve(sizeof(double) * P));
+  DevBuf dz, du, dla, dacc;
+  const double* pz = z;
+  const double* pu = u;
+  double* pla = log_alpha;
+  int* pacc = accepted;
+  const cudaMemcpyKind kin = (mem == SPS_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  SPS_CUDA_TRY(cudaMemcpyAsync(tmp.theta.ptr, theta, pd, kin, ctx->stream));
+  if (mem == SPS_MEM_HOST) {
+    SPS_CUDA_TRY(dz.reserve(pd));
+    SPS_CUDA_TRY(du.reserve(sizeof(double) * P));
+    SPS_CUDA_TRY(dla.reserve(sizeof(double) * P));
+    SPS_CUDA_TRY(dacc.reserve(sizeof(int) * P));
+    SPS_CUDA_TRY(cudaMemcpyAsync(dz.ptr, z, pd, cudaMemcpyHostToDevice, ctx->stream));
+    SPS_CUDA_TRY(cudaMemcpyAsync(du.ptr, u, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream));
+    pz = dz.as<double>();
+    pu = du.as<double>();
+    pla = dla.as<double>();
+    pacc = dacc.as<int>();
+  }
+  SPS_CUDA_TRY(cudaMemsetAsync(tmp.counters.ptr, 0, sizeof(Counters), ctx->stream));
+  prior_lp_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
+      tmp.theta.as<double>(), P, D, ctx->d_prior_mean.as<double>(), ctx->d_prior_prec.as<double>(), prior_full(ctx),
+      tmp.lp.as<double>()); ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  // the log-likelihood and its gradient at theta, from the function that evaluates the proposals
+  SPS_TRY(loglik_grad_dispatch(ctx, tmp.theta.as<double>(), P, t, tmp.ll.as<double>(), tmp.grad.as<double>()));
+  SPS_TRY(factor_proposal(ctx, &tmp, tmp.theta.as<double>(), 1.0, nullptr, sigma, nullptr, flag_ptr(&tmp, 0)));
+  SPS_TRY(mala_issue(ctx, &tmp, 0, nullptr, pz, pu, pla, pacc));
   Counters c;
   SPS_TRY(read_counters(ctx, &tmp, &c));
   if (c.chol_bad) return fail(ctx, SPS_ERR_DEGENERATE, "sigma is not positive definite");

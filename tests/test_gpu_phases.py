@@ -260,6 +260,32 @@ def test_two_pass_replay(cuda):
     assert abs(p1.log_ml - p2.log_ml) < 5 * max(math.hypot(p1.log_ml_nse, p2.log_ml_nse), 1e-3)
 
 
+def test_two_pass_replay_against_oracle_replay(cuda):
+    # Algorithm 3: the oracle replays the schedule recorded by the library's adaptive pass (its t_l,
+    # R_l and Sigma_lr, with its own random numbers); both replays follow the schedule exactly
+    # and their log marginal likelihoods agree within 4x the combined NSE
+    X, y, quad = _quad_case()
+    s = _ctx(X, y, 2, seed=41)
+    p1 = s.run(8, 512)
+    sch = p1.schedule
+    cycles, r0 = [], 0
+    for tl, Rl in zip(sch.t, sch.R):
+        cycles.append(OS.CycleRecord(t=int(tl), R=int(Rl), sigmas=[sch.sigma[r0 + r] for r in range(int(Rl))]))
+        r0 += int(Rl)
+    prior = OS.GaussianPrior.isotropic(2, 5.0)
+    o = OS.sps_run(X, y, 2, prior, 8, 512, np.random.Generator(np.random.PCG64(42)), schedule=cycles)
+    assert [c.t for c in o.cycles] == list(sch.t)
+    assert [c.R for c in o.cycles] == list(sch.R)
+    s2 = _ctx(X, y, 2, seed=43)
+    p2 = s2.run(8, 512, schedule=sch)
+    np.testing.assert_array_equal(p2.schedule.t, sch.t)
+    comb = math.hypot(p2.log_ml_nse, o.log_ml_nse)
+    assert abs(p2.log_ml - o.log_ml) < 4 * comb, (p2.log_ml, o.log_ml, comb)
+    z = (p2.mean[:2] - o.moments.mean[:2]) / np.hypot(p2.nse[:2], o.moments.nse[:2])
+    assert np.all(np.abs(z) < 4)
+    assert abs(o.log_ml - quad["log_ml"]) < 4 * max(o.log_ml_nse, 1e-3)
+
+
 def test_mala_leaves_the_prior_invariant_when_x_is_zero(cuda):
     # X = 0: the likelihood is constant, the posterior is the N(0, 25 I) prior and the MALA drift
     # comes from the prior alone. An exact MH kernel keeps prior draws distributed as the prior;

@@ -168,9 +168,11 @@ sps_status sps_prior_normalize(int32_t k, int32_t n_outcomes, const double* mu, 
  *   n >= 1, 1 <= k <= 256, 2 <= n_outcomes <= 4 for the tensor-core path (the FP32 path
  *   accepts up to 16 outcomes). prior: Gaussian on the D = k*(n_outcomes-1) free coefficients.
  *   opt may be NULL (defaults). Copies and encodes X and y to the current CUDA device.
- *   The fused split-precision kernel runs in clusters of two CTAs that share X tiles when the
- *   device can co-schedule them; the environment variable SPS_TC_CLUSTER=1, read here, keeps it
- *   to single CTAs (same results, for comparison).
+ *   For binary logits whose tiles are bound by their tensor-core products (many covariates) the
+ *   fused split-precision kernel runs on CTA pairs (tcgen05 MMAs of 256 particles over two CTAs,
+ *   each holding half of every X tile) when the device can co-schedule them, else on single
+ *   CTAs; the environment variable SPS_TC_CLUSTER, read here, overrides the choice: "1" single
+ *   CTAs, "2" CTA pairs wherever they can be co-scheduled (same results either way).
  * Errors: SPS_ERR_INVALID_ARG for bad sizes, y out of range, non-finite X or a prior covariance
  * that is not positive definite; SPS_ERR_OOM; SPS_ERR_CUDA. *out is NULL on failure. */
 sps_status sps_init(sps_ctx** out, const double* X, int64_t n, int32_t k, const int32_t* y,
@@ -270,8 +272,9 @@ sps_status sps_loglik_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, 
 
 /* Tile-shape autotuner of the fused split-precision kernel. Times every candidate launch shape
  * on P particles at prefix t (1 <= t <= n) with CUDA events: observation rows per tile (the two
- * widths the outcome count allows, where the pipeline fits shared memory), clusters of one or
- * two CTAs sharing each X tile, and work items of 512 to 8192 observations. The fastest is kept
+ * widths the outcome count allows, where the pipeline fits shared memory), single CTAs or CTA
+ * pairs (256-particle MMAs over two CTAs, each holding half of every X tile), and work items of
+ * 512 to 16384 observations. The fastest is kept
  * in the context and used by every later split-precision call (results change only by the
  * order of FP32/FP64 partial sums). Each candidate runs 1 untimed and 3 timed launches on zero
  * particles; the call synchronises the context's stream.

@@ -1440,7 +1440,10 @@ bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t
   // chunking: enough work items to balance the persistent grid, items long enough to amortise
   // the theta loads
   const int grid_max = (enc.cl > 1) ? enc.max_clusters : ctx->num_sms;   // concurrent work items
-  const int chunk_obs = enc.chunk_obs > 0 ? enc.chunk_obs : 4096;   // autotuned, else 4096
+  // autotuned, else 16384: each work item writes its particles' partial sums once (at 10^6
+  // observations and 65 536 particles, 4096-observation items wrote 514 MB of partial sums per
+  // launch, more than the 384 MB of X) and reloads its theta tile once
+  const int chunk_obs = enc.chunk_obs > 0 ? enc.chunk_obs : 16384;
   int chunk_tiles = std::max(1, std::min(prm->n_tiles, chunk_obs / BN));
   const int64_t want_items = 8LL * grid_max;
   while (chunk_tiles > 2 &&
@@ -1544,7 +1547,7 @@ sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out)
         enc.bn = bn;
         if (run_any(ctx, 2, nullptr, 0, smem_bytes, nullptr, false, &mc) != SPS_OK || mc < 1) continue;
       }
-      for (int chunk = 512; chunk <= 8192; chunk *= 2) {
+      for (int chunk = 512; chunk <= 16384; chunk *= 2) {
         if (chunk < bn) continue;
         const double ms = time_shape(bn, cl, mc, chunk);
         ++tried;
@@ -1585,6 +1588,7 @@ sps_status tc_configure_cluster(sps_ctx* ctx) {
   if (enc.bn == 0) return SPS_OK;
   const char* env = getenv("SPS_TC_CLUSTER");
   if (env && env[0] == '1' && env[1] == 0) return SPS_OK;
+  const bool force_pairs = env && env[0] == '2' && env[1] == 0;
   // CTA pairs where a tile's MMAs take longer than its epilogue (tensor-bound shapes: the pair
   // halves the X bytes each CTA receives per MMA clock and doubles the MMA time a stage covers),
   // and where two CTAs of the pair's shape can be co-scheduled. An epilogue-bound shape stays on
@@ -1595,7 +1599,9 @@ sps_status tc_configure_cluster(sps_ctx* ctx) {
     const double slices = 2.0 * (enc.k16 / 16) + enc.kc16 / 16;   // K = 16 MMAs per class and tile
     const double mma_clk = slices * NC * std::max(54.0, bn1 / 2.0);    // M = 128 MMA issue cost
     const double epi_clk = 128.0 * bn1 * (NC == 1 ? 1 : NC + 1) / 30.0; // ex2 per tile at 30 / clk
-    if (mma_clk <= epi_clk) return SPS_OK;
+    // C > 2: the two-group epilogue is latency-bound whatever the MMA does (four outcomes,
+    // k = 50: 6.65 ms per launch in pairs against 6.42 ms on single CTAs)
+    if (!force_pairs && (NC > 1 || mma_clk <= epi_clk)) return SPS_OK;
   }
   int stages = 0, th_bufs = 0;
   if (bn2 == 0 || !pick_stages(NC, bn2, 2, enc.kx / kKB, enc.kt / kKB, &stages, &th_bufs)) return SPS_OK;

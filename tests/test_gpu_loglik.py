@@ -162,12 +162,14 @@ def test_c3_multinomial_sampled(torch_cuda, prec):
     np.testing.assert_allclose(got[idx], ref, rtol=rtol)
 
 
-@pytest.mark.parametrize("C,k,exact", [(2, 30, 10), (3, 12, 4), (4, 50, 10)])
+@pytest.mark.parametrize("C,k,exact", [(2, 30, 10), (2, 100, 31), (3, 12, 4), (4, 50, 10)])
 def test_cluster_pairs_match_single_ctas_bitwise(torch_cuda, C, k, exact, monkeypatch):
-    # the fused kernel's CTA pairs share X tiles by multicast; each tile's arithmetic and the
-    # order of the partial sums are those of single CTAs, so the results are identical
+    # CTA pairs (forced with SPS_TC_CLUSTER=2) issue 256-particle MMAs over two CTAs, each CTA
+    # holding half of every X tile; each particle's products, the tile arithmetic and the order
+    # of the partial sums are those of single CTAs, so the results are identical
     X, y = _mk(1000, k, C, 20 + k, exact)
     g = np.random.Generator(np.random.PCG64(5))
+    monkeypatch.setenv("SPS_TC_CLUSTER", "2")
     s_pair = _sps(X, y, C)
     monkeypatch.setenv("SPS_TC_CLUSTER", "1")
     s_single = _sps(X, y, C)
@@ -201,12 +203,14 @@ def test_c4_large_binary_sampled(torch_cuda, prec):
     np.testing.assert_allclose(got_t[[0, 299]], ref_t, rtol=rtol)
 
 
-@pytest.mark.parametrize("C", [2, 3])
-def test_batched_nested_models_match_oracle(torch_cuda, C):
-    # nested models (first k_m columns), ragged particle counts and prefixes, in one launch
+@pytest.mark.parametrize("C,pairs", [(2, False), (3, False), (2, True), (3, True)])
+def test_batched_nested_models_match_oracle(torch_cuda, C, pairs, monkeypatch):
+    # nested models (first k_m columns), ragged particle counts and prefixes, in one launch, on
+    # single CTAs and on CTA pairs
     torch = torch_cuda
     n, kmax = 1000, 20
     X, y = _mk(n, kmax, C, 31, 6)
+    monkeypatch.setenv("SPS_TC_CLUSTER", "2" if pairs else "1")
     s = _sps(X, y, C)
     g = np.random.Generator(np.random.PCG64(32))
     ks, Ps, ts = [3, 20, 11, 7], [300, 129, 1000, 7], [1000, 777, 1, 0]

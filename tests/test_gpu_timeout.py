@@ -4,8 +4,7 @@ sps_set_debug stops the kernel's TMA producer before it issues any copy, so noth
 flight; every consumer wait (MMA thread, epilogue warps, and the relay of a CTA pair) then gives
 up after the short limit, the CTAs drain, free their tensor memory and return, and the call
 reports SPS_ERR_TIMEOUT. The next call on the same context must succeed and match the oracle.
-Both launch forms are covered: CTA pairs (the default where two CTAs can be co-scheduled) and
-single CTAs (SPS_TC_CLUSTER=1).
+Both launch forms are covered: CTA pairs (SPS_TC_CLUSTER=2) and single CTAs (SPS_TC_CLUSTER=1).
 """
 import numpy as np
 import pytest
@@ -23,12 +22,11 @@ def cuda():
     return torch
 
 
-@pytest.mark.parametrize("C,single", [(2, False), (2, True), (3, False)])
-def test_stalled_producer_times_out_and_context_recovers(cuda, monkeypatch, C, single):
+@pytest.mark.parametrize("C,mode", [(2, "2"), (2, "1"), (3, "2"), (3, "1")])
+def test_stalled_producer_times_out_and_context_recovers(cuda, monkeypatch, C, mode):
     from paper_1304_4333_b300 import Sps
     from paper_1304_4333_b300._native import SpsError
-    if single:
-        monkeypatch.setenv("SPS_TC_CLUSTER", "1")
+    monkeypatch.setenv("SPS_TC_CLUSTER", mode)
     g = np.random.Generator(np.random.PCG64(9 + C))
     n, k = 1200, 10
     X = g.standard_normal((n, k))

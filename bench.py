@@ -447,6 +447,34 @@ def sps_ladder(w, forms, max_groups: int, seeds: int, seeds_other: int, target: 
     return out
 
 
+def run_loglik_only(args):
+    """Profiling entry: `--calls` calls of the fused split-precision log-likelihood on the named
+    workload at t = n with `--particles` particles around the true coefficients (device memory),
+    after one untimed call; prints the per-launch kernel time from the library's CUDA events."""
+    import ctypes as C
+    import torch
+    import synthetic
+    from paper_1304_4333_b300 import Sps
+    torch.cuda.set_device(0)
+    w = synthetic.make_workload(args.loglik_only)
+    P = args.particles or w.P
+    th = torch.from_numpy(synthetic.particles_around(w.theta_true, P, 0.05, seed=2)).cuda()
+    s = Sps(w.X, w.y, w.C, prior_sd=5.0)
+    s.loglik(th, w.n, "split")
+    torch.cuda.synchronize()
+    s.lib.sps_set_timing(s.ctx, 1)
+    s.lib.sps_counters(s.ctx, 1, None, None, None)
+    for _ in range(args.calls):
+        s.loglik(th, w.n, "split")
+    torch.cuda.synchronize()
+    a, b, c = C.c_int64(), C.c_int64(), C.c_double()
+    s.lib.sps_counters(s.ctx, 1, C.byref(a), C.byref(b), C.byref(c))
+    ms = c.value / max(b.value, 1)
+    print(json.dumps({"workload": w.name, "particles": P, "t": w.n, "launches": b.value, "ms_per_launch": ms,
+                      "terms_per_s": P * w.n / (ms * 1e-3)}), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,7 +496,14 @@ def main():
     ap.add_argument("--sps-max-groups", type=int, default=1024)
     ap.add_argument("--ncu-step", action="store_true",
                     help="run one extra step after warm-up inside a CUDA profiler range (for ncu --profile-from-start off)")
+    ap.add_argument("--loglik-only", default="", choices=["", "c1", "c2", "c3", "c4", "c5"],
+                    help="profiling entry: only time the fused log-likelihood on this workload")
+    ap.add_argument("--particles", type=int, default=0, help="with --loglik-only: particles (0 = the workload's)")
+    ap.add_argument("--calls", type=int, default=2, help="with --loglik-only: timed calls")
     args = ap.parse_args()
+    if args.loglik_only:
+        run_loglik_only(args)
+        return
     if args.gpus != 1:
         print(json.dumps({"metric": METRIC, "impl": args.impl, "n_gpus": args.gpus,
                           "unavailable": "single-GPU build: the simulator runs on one GPU"}), flush=True)

@@ -249,7 +249,7 @@ sps_status sps_loglik(sps_ctx* ctx, const double* theta, int64_t P, int64_t t, d
  * Limit: with k16 = k rounded up to 16, kt = 2 k16 rounded up to 64, P' = P rounded up to the
  * particles of one work item (128, or 256 when the context's kernel runs on CTA pairs) and c the
  * call's observation chunks (at most ceil(t / 64)), the call needs 2 kt (C-1) P' bytes of operand
- * rows plus 8 W c P' bytes of partial sums (W = 4 for C = 2, 2 for C > 2) plus 256 bytes, each
+ * rows plus 32 c P' bytes of partial sums plus 256 bytes, each
  * part rounded up to 256 bytes, within 32 MiB: the binary workload with 65 536 particles,
  * k = 30 and n = 20 000 needs about 18 MiB. Larger calls return SPS_ERR_INVALID_ARG, with the
  * required size in sps_last_error, and launch nothing.
@@ -369,8 +369,8 @@ sps_status sps_mphase(sps_ctx* ctx, sps_state* st, int32_t kernel, int32_t fixed
 sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
                    const sps_schedule* schedule, sps_schedule* record, sps_result* out);
 
-/* Batched model comparison: the adaptive simulator (Algorithm 2, random-walk M kernel) for M
- * nested models of the context's data at once, model m using the first k_models[m] covariates
+/* Batched model comparison: the adaptive simulator (Algorithm 2, with the context's M kernel,
+ * random walk or MALA) for M nested models of the context's data at once, model m using the first k_models[m] covariates
  * (1 <= k_m <= k) with J groups x N particles and the context's options. Prior of model m: with
  * g > 0 the paper's g-prior for its own covariates (Sec. 3.1, Eq. 18, as sps_gprior); else the
  * marginal of the context's prior on its coordinates (theta_c,i for i < k_m). (A diffuse prior
@@ -383,10 +383,11 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
  * than two waves of work items at their t) with one batched fused-kernel launch
  * (sps_loglik_batched), the others with their own launches; the choice is fixed for each M
  * phase and the cached log-likelihoods at its start come from the same function (FP32
- * precision: one launch per model). Marginal likelihoods for comparing the
- * models (Sec. 2.3) are in out[m].log_ml.
+ * precision: one launch per model; MALA: each model's own gradient launch, which also gives the
+ * log-likelihoods). Marginal likelihoods for comparing the models (Sec. 2.3) are in
+ * out[m].log_ml.
  *   out: [M] caller-allocated results as for sps_run (log_pred ignored, graph_steps 0).
- * SPS_ERR_UNSUPPORTED for the MALA kernel; a model's error is returned with its message. */
+ * A model's error is returned with its message. */
 sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, double g, int32_t groups,
                            int32_t particles_per_group, sps_result* out);
 

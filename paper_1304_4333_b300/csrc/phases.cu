@@ -2370,8 +2370,7 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
     if (!o.mean || !o.sd || !o.nse || !o.rne || !o.log_ml_group)
       return fail(ctx, SPS_ERR_INVALID_ARG, "sps_run_batched: result arrays missing");
   }
-  if (ctx->opt.mkernel != SPS_MKERNEL_RW)
-    return fail(ctx, SPS_ERR_UNSUPPORTED, "sps_run_batched: the lockstep M phase uses the random-walk kernel");
+  const bool mala = (ctx->opt.mkernel == SPS_MKERNEL_MALA);
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t n = ctx->n;
   const int k = ctx->k, NC = ctx->NC, D = ctx->D;
@@ -2505,14 +2504,23 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
     // M phases in lockstep (Algorithm 2 step 2(c)): every step of the models still moving is
     // one batched evaluation of their proposals; a model leaves when its RNE criterion or the
     // step cap is met
-    for (int m : active) {
-      sps_state* st = models.v[m].st;
-      in_batch[m] = split && tc_waves(models.v[m].c, st->P, st->t) < kBatchWaves;
-    }
-    SPS_TRY(evaluate(active, false));   // cached log-likelihoods with the proposals' function
-    for (int m : active) {
-      models.v[m].st->ll_stale = false;
-      models.v[m].st->ll_kind = split ? 0 : 1;
+    if (mala) {
+      // MALA: each model's log-likelihood and gradient come from its own gradient launch (the
+      // cached values at the start of the phase included)
+      for (int m : active) {
+        const sps_status e = mstep_prepare(models.v[m].c, models.v[m].st, SPS_MKERNEL_MALA);
+        if (e != SPS_OK) return pass(models.v[m].c, e);
+      }
+    } else {
+      for (int m : active) {
+        sps_state* st = models.v[m].st;
+        in_batch[m] = split && tc_waves(models.v[m].c, st->P, st->t) < kBatchWaves;
+      }
+      SPS_TRY(evaluate(active, false));   // cached log-likelihoods with the proposals' function
+      for (int m : active) {
+        models.v[m].st->ll_stale = false;
+        models.v[m].st->ll_kind = split ? 0 : 1;
+      }
     }
     std::vector<int> run = active, r(M, 0);
     std::vector<double> hs(M);
@@ -2542,29 +2550,42 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
       cholesky_batched_kernel<<<static_cast<unsigned>(jobs.size()), kCholThreads, sizeof(double) * tmax,
                                 ctx->stream>>>(jobs_dev.as<CholJob>()); ++ctx->launches;
       SPS_CUDA_TRY(cudaGetLastError());
-      for (int m : run) {
-        Model& md = models.v[m];
-        const sps_status e = launch_propose(md.c, md.st, md.st->theta.as<double>(), md.st->P, nullptr, steps[m], nullptr,
-                                            flag_ptr(md.st, 0), md.st->theta_prop.as<double>(),
-                                            md.st->lp_prop.as<double>());
-        if (e != SPS_OK) return pass(md.c, e);
-      }
-      SPS_TRY(evaluate(run, true));
-      // every model's decisions and read-back enqueued, then one synchronisation
-      for (int m : run) {
-        Model& md = models.v[m];
-        sps_status e = rw_issue_accept(md.c, md.st, steps[m], nullptr);
-        if (e == SPS_OK) e = readback_issue(md.c, md.st);
-        if (e != SPS_OK) return pass(md.c, e);
+      if (mala) {
+        // proposals with the drift, their log-likelihoods and gradients, the decisions
+        for (int m : run) {
+          Model& md = models.v[m];
+          sps_status e = mala_issue(md.c, md.st, steps[m], nullptr, nullptr, nullptr, nullptr, nullptr);
+          if (e == SPS_OK) {
+            launch_monitoring(md.c, md.st);
+            e = readback_issue(md.c, md.st);
+          }
+          if (e != SPS_OK) return pass(md.c, e);
+        }
+      } else {
+        for (int m : run) {
+          Model& md = models.v[m];
+          const sps_status e = launch_propose(md.c, md.st, md.st->theta.as<double>(), md.st->P, nullptr, steps[m],
+                                              nullptr, flag_ptr(md.st, 0), md.st->theta_prop.as<double>(),
+                                              md.st->lp_prop.as<double>());
+          if (e != SPS_OK) return pass(md.c, e);
+        }
+        SPS_TRY(evaluate(run, true));
+        // every model's decisions and read-back enqueued, then one synchronisation
+        for (int m : run) {
+          Model& md = models.v[m];
+          sps_status e = rw_issue_accept(md.c, md.st, steps[m], nullptr);
+          if (e == SPS_OK) e = readback_issue(md.c, md.st);
+          if (e != SPS_OK) return pass(md.c, e);
+        }
       }
       SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
       std::vector<int> next;
       for (int m : run) {
         Model& md = models.v[m];
         sps_mstep_info info{};
-        const sps_status e = mstep_rule(md.c, md.st, SPS_MKERNEL_RW, hs[m], true, &info);
+        const sps_status e = mstep_rule(md.c, md.st, ctx->opt.mkernel, hs[m], true, &info);
         if (e != SPS_OK) return pass(md.c, e);
-        md.st->grad_valid = false;
+        if (!mala) md.st->grad_valid = false;
         ++r[m];
         const double K = (md.st->t >= n) ? o.rne_final : o.rne_cycle;
         if (!(info.rne_min >= K || r[m] >= o.r_max)) next.push_back(m);

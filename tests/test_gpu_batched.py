@@ -94,3 +94,40 @@ def test_batched_gprior_matches_separate_gprior_runs(cuda):
         s1.close()
         comb = math.hypot(r.log_ml_nse, r1.log_ml_nse)
         assert abs(r.log_ml - r1.log_ml) < 4 * max(comb, 1e-3), (km, r.log_ml, r1.log_ml, comb)
+
+
+def test_batched_mala_agrees_with_separate_runs(cuda):
+    # MALA M phases in lockstep (each model's gradient from its own launch): the same posterior and
+    # marginal likelihood as separate MALA runs within the Monte Carlo error
+    from paper_1304_4333_b300 import Sps
+    X, y = _nested_case(C=2, seed=12)
+    ks = [2, 3, 5]
+    s = Sps(X, y, 2, prior_sd=5.0, seed=13, mkernel="mala")
+    rb = s.run_batched(ks, 16, 512)
+    s.close()
+    for km, r in zip(ks, rb):
+        s1 = Sps(np.ascontiguousarray(X[:, :km]), y, 2, prior_sd=5.0, seed=60 + km, mkernel="mala")
+        r1 = s1.run(16, 512, record=False)
+        s1.close()
+        comb = math.hypot(r.log_ml_nse, r1.log_ml_nse)
+        assert abs(r.log_ml - r1.log_ml) < 4 * max(comb, 1e-3), (km, r.log_ml, r1.log_ml, comb)
+        z = (r.mean[:km] - r1.mean[:km]) / np.hypot(r.nse[:km], r1.nse[:km])
+        assert np.all(np.abs(z) < 5), (km, z)
+
+
+def test_batched_small_nested_case_against_oracle(cuda):
+    # per-model log marginal likelihoods of a batched run against the FP64 oracle simulator run on
+    # each model's own columns (independent random numbers): within 4x the combined NSE
+    from oracle import smc as OS
+    from paper_1304_4333_b300 import Sps
+    X, y = _nested_case(n=200, k=4, C=2, seed=21)
+    ks = [1, 2, 4]
+    s = Sps(X, y, 2, prior_sd=5.0, seed=22)
+    rb = s.run_batched(ks, 8, 256)
+    s.close()
+    for km, r in zip(ks, rb):
+        prior = OS.GaussianPrior.isotropic(km, 5.0)
+        o = OS.sps_run(np.ascontiguousarray(X[:, :km]), y, 2, prior, 8, 256,
+                       np.random.Generator(np.random.PCG64(23 + km)))
+        comb = math.hypot(r.log_ml_nse, o.log_ml_nse)
+        assert abs(r.log_ml - o.log_ml) < 4 * max(comb, 1e-3), (km, r.log_ml, o.log_ml, comb)

@@ -260,9 +260,11 @@ sps_status sps_loglik_noalloc(sps_ctx* ctx, const double* theta, int64_t P, int6
 
 /* Log-likelihoods of M nested models in one fused-kernel launch (split precision): model m uses
  * the first k_models[m] covariates of the context's X (1 <= k_m <= k) with D_m = k_m (C-1)
- * parameters, P_models[m] particles and the prefix t_models[m] (0 <= t_m <= n); its particles
- * are evaluated as zero-padded rows of the context's operand layout, so the results equal
- * sps_loglik on a context built from X[:, :k_m] (within the split tolerance).
+ * parameters, P_models[m] particles and the prefix t_models[m] (0 <= t_m <= n). Each model's
+ * tiles use the model's own encoding of X[:, :k_m] (its continuous columns first; built on the
+ * device at the first call with that k_m and kept by the context, n x 64 or more BF16 values
+ * per model), so they load the X bytes and issue the MMAs of the model's own launch, and the
+ * results equal sps_loglik on a context built from X[:, :k_m] (within the split tolerance).
  *   theta: device FP64, the models' [P_m x D_m] class-major blocks concatenated in model order;
  *   ll: device FP64 [sum P_m]; k_models, P_models, t_models: host [M], 1 <= M <= 1024.
  * Work is enqueued on the context's stream. The paper runs one model at a time; batching the
@@ -370,22 +372,20 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
                    const sps_schedule* schedule, sps_schedule* record, sps_result* out);
 
 /* Batched model comparison: the adaptive simulator (Algorithm 2, with the context's M kernel,
- * random walk or MALA) for M nested models of the context's data at once, model m using the first k_models[m] covariates
- * (1 <= k_m <= k) with J groups x N particles and the context's options. Prior of model m: with
- * g > 0 the paper's g-prior for its own covariates (Sec. 3.1, Eq. 18, as sps_gprior); else the
- * marginal of the context's prior on its coordinates (theta_c,i for i < k_m). (A diffuse prior
- * on many coordinates can leave fewer distinct particles than parameters after the first S
- * phase; the step then fails with SPS_ERR_DEGENERATE, as the paper notes in Sec. 4.) Each model has its own
- * particles, C and S phases and step size (a context of its own, built from the context's data,
- * on the context's stream, with the Philox key options.seed + m-dependent offset). Their M
- * phases run in lockstep: in every M step the proposals of all models still moving are
- * evaluated, each at its model's t, those of the models too small to fill the GPU alone (fewer
- * than two waves of work items at their t) with one batched fused-kernel launch
- * (sps_loglik_batched), the others with their own launches; the choice is fixed for each M
- * phase and the cached log-likelihoods at its start come from the same function (FP32
- * precision: one launch per model; MALA: each model's own gradient launch, which also gives the
- * log-likelihoods). Marginal likelihoods for comparing the models (Sec. 2.3) are in
- * out[m].log_ml.
+ * random walk or MALA) for M nested models of the context's data at once, model m using the
+ * first k_models[m] covariates (1 <= k_m <= k) with J groups x N particles and the context's
+ * options. Prior of model m: with g > 0 the paper's g-prior for its own covariates (Sec. 3.1,
+ * Eq. 18, as sps_gprior); else the marginal of the context's prior on its coordinates
+ * (theta_c,i for i < k_m). (A diffuse prior on many coordinates can leave fewer distinct
+ * particles than parameters after the first S phase; the step then fails with
+ * SPS_ERR_DEGENERATE, as the paper notes in Sec. 4.) Each model has its own particles, C and S
+ * phases and step size (a context of its own, built from the context's data, on the context's
+ * stream, with the Philox key options.seed + m-dependent offset). Their M phases run in
+ * lockstep: in every M step the proposals of all models still moving are evaluated, each at its
+ * model's t, with one batched fused-kernel launch (sps_loglik_batched, in which each model's
+ * tiles use the model's own encoding of its covariates); FP32 precision: one launch per model;
+ * MALA: each model's own gradient launch, which also gives the log-likelihoods. Marginal
+ * likelihoods for comparing the models (Sec. 2.3) are in out[m].log_ml.
  *   out: [M] caller-allocated results as for sps_run (log_pred ignored, graph_steps 0).
  * A model's error is returned with its message. */
 sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, double g, int32_t groups,

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -66,6 +68,25 @@ struct XEncoding {
   CUtensorMap mapX;
 };
 
+// Encoding of the first k_m covariates for batched calls of nested models: the same layout as
+// XEncoding for X[:, :k_m] (continuous columns of the model first), so that a model's tiles in a
+// batched launch issue exactly the MMAs, and load exactly the X bytes, of its own launch.
+struct ModelEncoding {
+  int k = 0, kc = 0, k16 = 0, kc16 = 0, kx = 0;
+  DevBuf perm_dev;            // int [k]: internal column j holds original column perm[j]
+  DevBuf Xp;                  // bf16 [n x kx]
+};
+
+// Per model of a batched launch (device table, one entry per model of the call): its X tiles'
+// tensor map and the K blocks and MMA slices of its rows.
+struct BatchModel {
+  CUtensorMap mapX;
+  int kbx;                    // K blocks of an X row
+  int k16;                    // element offset of the theta low parts
+  int ksh;                    // 16-wide K slices over Xh (and Th, Tl)
+  int ksl;                    // over Xl
+};
+
 // Per-call scratch of the likelihood kernels.
 struct LoglikScratch {
   DevBuf thetaP;              // bf16 [NC * Ppad x kt] operand rows (class-major row blocks)
@@ -80,6 +101,7 @@ struct LoglikScratch {
   int mapXg_rows = 0;
   DevBuf batch_ptile_t;       // int2 [n_ptiles] prefix length and K-slice mask of each particle tile
   DevBuf batch_lin;           // FP64 [M x NC x k] linear terms of the models
+  DevBuf batch_models;        // BatchModel [M]
 };
 
 // Device-resident control block of a captured M phase: the step size h and the Philox step word
@@ -129,6 +151,7 @@ struct sps_ctx {
   sps::DevBuf d_prior_chol;   // FP64 [D x D] lower Cholesky factor of cov
 
   sps::LoglikScratch ll;
+  std::map<int, std::unique_ptr<sps::ModelEncoding>> model_enc;   // by k_m, built on first use
 
   // instrumentation: kernels launched on this context; CUDA events around each launch of the
   // fused log-likelihood kernel when timing is on

@@ -96,11 +96,10 @@ struct TcParams {
   int* flag;           // set to 1 on a timeout
   unsigned long long timeout_ns;
   int stall;           // diagnostics: non-zero makes the TMA producer issue no copy
-  // batched models: per particle tile {prefix length, K slices}, or null. The K-slice word holds
-  // four 5-bit fields: the 16-wide slices of the Xh / Th / Tl blocks holding any of the model's
-  // columns are [0, ha) and [hb, hc) (bits 0-4, 5-9, 10-14), and the model needs the first hl
-  // slices of the Xl block (bits 15-19; its continuous columns are a prefix of that block).
+  // batched models: per particle tile {prefix length, model slot}, or null; per model slot its X
+  // tensor map (the model's own encoding of its first k_m covariates), K blocks and MMA slices
   const int2* ptile_info;
+  const BatchModel* bmodels;
 };
 
 // Observation tiles [tile_lo, result) of a work item: its chunk cut at the prefix length of its
@@ -266,6 +265,14 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int tile_lo = chunk * prm.chunk_tiles;
         const int tile_hi = item_tile_hi<BN, BATCH>(prm, tile_lo, ptile);
         if (BATCH && tile_hi == tile_lo) continue;   // nothing of this item lies inside its prefix
+        // the X tiles of this item: the launch's map, or (batched models) the item's model's own
+        const CUtensorMap* mx = &mapX;
+        int kbx = prm.kbx;
+        if constexpr (BATCH) {
+          const BatchModel* bm = prm.bmodels + prm.ptile_info[ptile].y;
+          mx = &bm->mapX;
+          kbx = bm->kbx;
+        }
         if (!ptx::mbar_wait_bounded(&th_empty[tb], tph ^ 1u, abort_flag, limit)) { ok = false; break; }
         uint8_t* thb = smem + L.off_th + tb * L.th_bytes;
         ptx::mbar_arrive_expect_tx(&th_full[tb], L.th_bytes);
@@ -277,13 +284,14 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         issued_t |= 1u << tb;
         par_t = (par_t & ~(1u << tb)) | (tph << tb);
         if (++tb == prm.th_bufs) { tb = 0; tph ^= 1u; }
+        const uint32_t x_bytes = static_cast<uint32_t>(kbx) * HR * 128u;   // this CTA's rows of a tile
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
           if (!ptx::mbar_wait_bounded(&x_empty[st], xph ^ 1u, abort_flag, limit)) { ok = false; break; }
           uint8_t* xb = smem + L.off_x + st * L.x_bytes;
-          ptx::mbar_arrive_expect_tx(&x_full[st], L.x_bytes);   // this CTA's rows of the tile
+          ptx::mbar_arrive_expect_tx(&x_full[st], x_bytes);
           const int obs = tile * BN + rank * HR;
-          for (int kb = 0; kb < prm.kbx; ++kb)
-            ptx::tma_load_2d(xb + kb * HR * 128, &mapX, &x_full[st], kb * kKB, obs);
+          for (int kb = 0; kb < kbx; ++kb)
+            ptx::tma_load_2d(xb + kb * HR * 128, mx, &x_full[st], kb * kKB, obs);
           issued_x |= 1u << st;
           par_x = (par_x & ~(1u << st)) | (xph << st);
           if (++st == prm.stages) { st = 0; xph ^= 1u; }
@@ -348,11 +356,15 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int tile_lo = chunk * prm.chunk_tiles;
         const int tile_hi = item_tile_hi<BN, BATCH>(prm, tile_lo, ptile);
         if (BATCH && tile_hi == tile_lo) continue;
-        // K slices of this item's model (batched models): two ranges of Xh slices and a prefix
-        // of Xl slices, 5 bits each
-        const uint32_t kinfo = BATCH ? static_cast<uint32_t>(prm.ptile_info[ptile].y) : 0u;
-        const int ha = static_cast<int>(kinfo & 31u), hb = static_cast<int>((kinfo >> 5) & 31u);
-        const int hc = static_cast<int>((kinfo >> 10) & 31u), hl = static_cast<int>((kinfo >> 15) & 31u);
+        // the MMA slices of this item's rows: the launch's, or (batched models) those of the
+        // item's model's own encoding
+        int ksh = prm.ksh, ksl = prm.ksl, k16 = prm.k16;
+        if constexpr (BATCH) {
+          const BatchModel* bm = prm.bmodels + prm.ptile_info[ptile].y;
+          ksh = bm->ksh;
+          ksl = bm->ksl;
+          k16 = bm->k16;
+        }
         if (!ptx::mbar_wait_bounded(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
         if constexpr (CL > 1)
           if (!ptx::mbar_wait_bounded_cluster(&th_peer[tb], tph, abort_flag, limit)) { ok = false; break; }
@@ -380,52 +392,20 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             if constexpr (CL > 1) ptx::mma_bf16_pair(d[c], dt[c] + ka, dx + kb, idesc, acc);
             else ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc, acc);
           };
-          if constexpr (!BATCH) {
-            for (int i = 0; i < prm.ksh; ++i) {   // Th_c Xh'
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, 16 * i);
+          for (int i = 0; i < ksh; ++i) {   // Th_c Xh'
+            const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, i > 0);
-            }
-            for (int i = 0; i < prm.ksh; ++i) {   // Tl_c Xh'
-              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(HR, 16 * i);
+            for (int c = 0; c < NC; ++c) mma(c, ka, kb, i > 0);
+          }
+          for (int i = 0; i < ksh; ++i) {   // Tl_c Xh'
+            const uint64_t ka = kslice_off(kBM, k16 + 16 * i), kb = kslice_off(HR, 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
-            }
-            for (int i = 0; i < prm.ksl; ++i) {   // Th_c Xl' over the continuous columns
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, prm.k16 + 16 * i);
+            for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
+          }
+          for (int i = 0; i < ksl; ++i) {   // Th_c Xl' over the continuous columns
+            const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, k16 + 16 * i);
 #pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
-            }
-          } else {
-            // batched models: the Xh / Th / Tl slices [0, ha) and [hb, hc) holding the item's
-            // model's columns and its hl slices of Xl; the first MMA of a tile overwrites the
-            // accumulator
-            for (int i = 0; i < ha; ++i) {
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, 16 * i);
-#pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, i > 0);
-            }
-            for (int i = hb; i < hc; ++i) {
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, 16 * i);
-              const uint32_t acc = (ha > 0 || i > hb) ? 1u : 0u;
-#pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, acc);
-            }
-            for (int i = 0; i < ha; ++i) {
-              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(HR, 16 * i);
-#pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
-            }
-            for (int i = hb; i < hc; ++i) {
-              const uint64_t ka = kslice_off(kBM, prm.k16 + 16 * i), kb = kslice_off(HR, 16 * i);
-#pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
-            }
-            for (int i = 0; i < hl; ++i) {
-              const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(HR, prm.k16 + 16 * i);
-#pragma unroll
-              for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
-            }
+            for (int c = 0; c < NC; ++c) mma(c, ka, kb, 1);
           }
           issued_any = true;
           if constexpr (CL > 1) {
@@ -664,9 +644,11 @@ loglik_finalize_kernel(const double* __restrict__ theta, int64_t P, int D,
 }
 
 // ---- batched models: M nested models, model m using the first k_m covariates, its particles in
-// its own block of operand rows (row_off_m, padded to the cluster's pair of tiles), zeros beyond
-// k_m. Model table rows (int64): [row_off, P, k, theta address, particle_off, t, ll address].
-constexpr int kTab = 7;
+// its own block of operand rows (row_off_m, padded to the CTAs of a work item) laid out as the
+// model's own encoding (its continuous columns first, low parts at k16_m), zeros beyond.
+// Model table rows (int64): [row_off, P, k, theta address, particle_off, t, ll address, address
+// of the model's column permutation, k16_m].
+constexpr int kTab = 9;
 
 __device__ __forceinline__ int model_of_row(const int64_t* __restrict__ tab, int M, int64_t q) {
   int m = 0;
@@ -679,8 +661,7 @@ __device__ __forceinline__ int model_of_particle(const int64_t* __restrict__ tab
   return m;
 }
 
-__global__ void encode_theta_batched_kernel(const int64_t* __restrict__ tab,
-                                            int M, int NC, const int* __restrict__ perm, int k16, int kt,
+__global__ void encode_theta_batched_kernel(const int64_t* __restrict__ tab, int M, int NC, int kt,
                                             int64_t PP, __nv_bfloat16* __restrict__ out) {
   const int64_t r = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -692,16 +673,36 @@ __global__ void encode_theta_batched_kernel(const int64_t* __restrict__ tab,
   const int64_t Pm = tab[m * kTab + 1];
   const int km = static_cast<int>(tab[m * kTab + 2]);
   const double* src = reinterpret_cast<const double*>(tab[m * kTab + 3]) + p * (static_cast<int64_t>(NC) * km) + c * km;
+  const int* perm = reinterpret_cast<const int*>(tab[m * kTab + 7]);
+  const int k16 = static_cast<int>(tab[m * kTab + 8]);
   __nv_bfloat16* rowp = out + r * kt;
   for (int j = lane; j < k16; j += 32) {
-    const int col = perm[j];
     float v = 0.f;
-    if (p < Pm && col < km) v = f64_to_f32(src[col]) * 1.44269504f;
+    if (p < Pm && j < km) v = f64_to_f32(src[perm[j]]) * 1.44269504f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     rowp[j] = h;
     rowp[k16 + j] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
   for (int jj = 2 * k16 + lane; jj < kt; jj += 32) rowp[jj] = __float2bfloat16_rn(0.f);
+}
+
+// A model's own operand rows of X[:, :km] (row stride k of the context's FP64 X): [Xh | Xl | 0]
+// over its internal columns (its continuous columns first), as the context's encoding of X.
+__global__ void encode_x_model_kernel(const double* __restrict__ X, int64_t n, int k, int km,
+                                      const int* __restrict__ perm, int k16, int kc, int kx,
+                                      __nv_bfloat16* __restrict__ Xp) {
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (idx >= n * kx) return;
+  const int64_t s = idx / kx;
+  const int e = static_cast<int>(idx - s * kx);
+  double v = 0.0;
+  if (e < k16) {
+    if (e < km) v = static_cast<double>(__bfloat162float(__double2bfloat16(X[s * k + perm[e]])));
+  } else if (e - k16 < kc) {
+    const double x = X[s * k + perm[e - k16]];
+    v = x - static_cast<double>(__bfloat162float(__double2bfloat16(x)));
+  }
+  Xp[idx] = __double2bfloat16(v);
 }
 
 // lin[m][c*k + i] = prefix[t_m / 128] + the tail rows [128 (t_m / 128), t_m), one warp per entry.
@@ -1817,6 +1818,40 @@ sps_status loglik_grad_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, 
   return loglik_grad_fp32(ctx, d_theta, P, t, d_ll, d_grad);
 }
 
+// The encoding of X[:, :km] for batched calls: the model's continuous columns (in original order,
+// as the context found them) first, then its exact ones; built once per k_m and kept.
+static sps_status model_encoding(sps_ctx* ctx, int km, ModelEncoding** out) {
+  auto it = ctx->model_enc.find(km);
+  if (it != ctx->model_enc.end()) {
+    *out = it->second.get();
+    return SPS_OK;
+  }
+  const XEncoding& enc = ctx->enc;
+  std::unique_ptr<ModelEncoding> me(new ModelEncoding());
+  std::vector<int> perm;
+  for (int j = 0; j < enc.kc; ++j)
+    if (enc.perm[j] < km) perm.push_back(enc.perm[j]);
+  me->kc = static_cast<int>(perm.size());
+  for (int j = enc.kc; j < ctx->k; ++j)
+    if (enc.perm[j] < km) perm.push_back(enc.perm[j]);
+  me->k = km;
+  me->k16 = (km + 15) / 16 * 16;
+  me->kc16 = (me->kc + 15) / 16 * 16;
+  me->kx = (me->k16 + me->kc16 + 63) / 64 * 64;
+  SPS_CUDA_TRY(me->perm_dev.reserve(sizeof(int) * km));
+  SPS_CUDA_TRY(cudaMemcpy(me->perm_dev.ptr, perm.data(), sizeof(int) * km, cudaMemcpyHostToDevice));
+  SPS_CUDA_TRY(me->Xp.reserve(static_cast<size_t>(ctx->n) * me->kx * sizeof(__nv_bfloat16)));
+  const int64_t tot = ctx->n * me->kx;
+  encode_x_model_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, ctx->stream>>>(
+      ctx->Xd.as<double>(), ctx->n, ctx->k, km, me->perm_dev.as<int>(), me->k16, me->kc, me->kx,
+      me->Xp.as<__nv_bfloat16>());
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  *out = me.get();
+  ctx->model_enc[km] = std::move(me);
+  return SPS_OK;
+}
+
 sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
                                 const double* const* d_theta, double* const* d_ll) {
   const int NC = ctx->NC;
@@ -1846,43 +1881,31 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
   if (!plan_call(ctx, PP, tmax, &prm, &smem_bytes))
     return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
   if (prm.ppad != PP) return fail(ctx, SPS_ERR_INVALID_ARG, "batched log-likelihood: internal padding mismatch");
-  // per particle tile: prefix length and the K slices of its model. Internal column j of the
-  // context's encoding holds original column perm[j]; a nested model's columns (original
-  // 0..k_m-1) are a prefix of the continuous block and a prefix of the exact block.
-  std::vector<int2> ptile_info(static_cast<size_t>(prm.n_ptiles));
-  const int ksh = enc.k16 / 16;
-  if (ksh > 31) return fail(ctx, SPS_ERR_UNSUPPORTED, "batched log-likelihood: too many covariates");
+  // each model's own encoding of its first k_m covariates (built on first use and kept): its tiles
+  // load only its own X bytes and issue only its own MMA slices
+  std::vector<BatchModel> bms(static_cast<size_t>(M));
   for (int m = 0; m < M; ++m) {
-    // the slices holding any of the model's columns, written as [0, ha) and [hb, hc): with the
-    // continuous columns first, a nested model's columns are a prefix of the continuous block
-    // and a prefix of the exact block; any other set is widened to [0, ksh) (the theta rows
-    // are zero outside the model's columns, so extra slices only cost time)
-    std::vector<char> used(static_cast<size_t>(ksh), 0);
-    int kc_m = 0;
-    for (int j = 0; j < ctx->k; ++j)
-      if (enc.perm[j] < km[m]) {
-        used[j / 16] = 1;
-        if (j < enc.kc) ++kc_m;
-      }
-    int ha = 0;
-    while (ha < ksh && used[ha]) ++ha;
-    int hb = ha;
-    while (hb < ksh && !used[hb]) ++hb;
-    int hc = hb;
-    while (hc < ksh && used[hc]) ++hc;
-    bool rest = false;
-    for (int i = hc; i < ksh; ++i) rest = rest || used[i];
-    if (rest) {
-      ha = ksh;
-      hb = hc = ksh;
-    }
-    const int hl = (kc_m + 15) / 16;
-    const uint32_t info = static_cast<uint32_t>(ha) | (static_cast<uint32_t>(hb) << 5) |
-                          (static_cast<uint32_t>(hc) << 10) | (static_cast<uint32_t>(hl) << 15);
+    ModelEncoding* me = nullptr;
+    SPS_TRY(model_encoding(ctx, km[m], &me));
+    SPS_TRY(make_map_bf16(ctx, &bms[m].mapX, me->Xp.ptr, static_cast<uint64_t>(ctx->n), me->kx,
+                          static_cast<uint32_t>(enc.bn / enc.cl)));
+    bms[m].kbx = me->kx / kKB;
+    bms[m].k16 = me->k16;
+    bms[m].ksh = me->k16 / 16;
+    bms[m].ksl = me->kc16 / 16;
+    tab[m * kTab + 7] = static_cast<int64_t>(reinterpret_cast<uintptr_t>(me->perm_dev.ptr));
+    tab[m * kTab + 8] = me->k16;
+  }
+  // per particle tile: its model's prefix length and slot
+  std::vector<int2> ptile_info(static_cast<size_t>(prm.n_ptiles));
+  for (int m = 0; m < M; ++m) {
     const int64_t r0 = tab[m * kTab + 0] / kBM;
     const int64_t r1 = r0 + (Pm[m] + prow - 1) / prow * prow / kBM;
-    for (int64_t r = r0; r < r1; ++r) ptile_info[r] = make_int2(static_cast<int>(tm[m]), static_cast<int>(info));
+    for (int64_t r = r0; r < r1; ++r) ptile_info[r] = make_int2(static_cast<int>(tm[m]), m);
   }
+  SPS_CUDA_TRY(S.batch_models.reserve(sizeof(BatchModel) * bms.size()));
+  SPS_CUDA_TRY(cudaMemcpyAsync(S.batch_models.ptr, bms.data(), sizeof(BatchModel) * bms.size(),
+                               cudaMemcpyHostToDevice, ctx->stream));
   SPS_CUDA_TRY(S.batch_tab.reserve(sizeof(int64_t) * tab.size()));
   SPS_CUDA_TRY(S.batch_ptile_t.reserve(sizeof(int2) * ptile_info.size()));
   SPS_CUDA_TRY(S.batch_lin.reserve(sizeof(double) * M * NC * ctx->k));
@@ -1900,7 +1923,7 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
   {
     const int64_t rows = static_cast<int64_t>(NC) * PP;
     encode_theta_batched_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
-        dtab, M, NC, enc.perm_dev.as<int>(), enc.k16, enc.kt, PP, S.thetaP.as<__nv_bfloat16>());
+        dtab, M, NC, enc.kt, PP, S.thetaP.as<__nv_bfloat16>());
     ++ctx->launches;
     const int64_t warps = static_cast<int64_t>(M) * NC * ctx->k;
     lin_tail_batched_kernel<<<static_cast<unsigned>((warps + 3) / 4), 128, 0, ctx->stream>>>(
@@ -1915,6 +1938,7 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
   prm.partial = S.partial.as<double>();
   prm.flag = S.flag.as<int>();
   prm.ptile_info = S.batch_ptile_t.as<int2>();
+  prm.bmodels = S.batch_models.as<BatchModel>();
   SPS_CUDA_TRY(cudaMemsetAsync(prm.flag, 0, sizeof(int), ctx->stream));
   if (prm.n_items > 0)
     SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));

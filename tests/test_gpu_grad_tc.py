@@ -7,7 +7,7 @@ item. An error of delta in eta changes q by at most delta / 4, so
 (a factor 8 above the worst-case sum of these relative errors). The log-likelihood uses the
 bound of the split log-likelihood tests. Shapes span several tiles with a ragged last tile and
 a ragged particle tile. The bound is a guarantee, far above the achieved error; the gradient is
-also held to north-star's 1e-4 relative (norm-wise) against central finite differences of the
+also held to 1e-4 relative (norm-wise) against central finite differences of the
 FP64 oracle log-likelihood."""
 import numpy as np
 import pytest

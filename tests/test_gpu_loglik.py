@@ -57,7 +57,7 @@ def _tol(X, theta, C, t, ref, prec):
 
 
 def _strict(got, ref, t, prec="split"):
-    """The spec relative bar (1e-5 split, 1e-6 FP32) for prefixes of a whole tile or more,
+    """The per-particle relative bar (1e-5 split, 1e-6 FP32) for prefixes of a whole tile or more,
     where it holds with margin (the bound of _tol is a worst case for the short prefixes)."""
     if t < 128:
         return 0.0
@@ -100,7 +100,7 @@ def test_parity_ragged_sizes(torch_cuda, C, k, exact, prec):
         assert np.all(np.abs(got - ref) <= tol), (t, np.max(np.abs(got - ref) - tol))
         rel = np.max(np.abs(got - ref) / np.abs(ref))
         if t >= 128:
-            # a whole tile or more: the spec relative bar itself
+            # a whole tile or more: the relative bar itself
             assert rel <= rtol, (t, rel)
             worst = max(worst, rel)
     print(f"C={C} k={k} {prec}: max relative error over t >= 128: {worst:.2e}")

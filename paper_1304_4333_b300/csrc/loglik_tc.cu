@@ -37,10 +37,15 @@
 // pair: the even CTA issues cta_group::2 MMAs of 256 particles (each CTA's 128 particles in its
 // own shared and tensor memory) x BN observations, each CTA loading and holding only BN / 2 rows
 // of every X tile. Per observation processed, a CTA then receives half the X bytes of a single
-// CTA, and the pipeline holds twice the MMA time per stage. The odd CTA's MMA warp relays each of
-// its landed X stages and theta buffers to the even CTA (remote mbarrier arrive), so that every
-// TMA copy completes on a barrier of its own CTA; the MMA completions arrive on both CTAs'
-// barriers, and both CTAs' epilogue warps release accumulators on the even CTA's barrier.
+// CTA, and the pipeline holds twice the MMA time per stage. Every TMA copy completes on a barrier
+// of its own CTA; the odd CTA's MMA warp relays each of its landed X stages and theta buffers to
+// the even CTA as the second arrive on the even CTA's full barrier of the same index, so that the
+// MMA thread waits once per stage (each wait of the MMA-issuing thread is a shared-memory access
+// that queues behind the MMAs' own operand reads and stalls the tensor pipe). The MMA completions
+// arrive on both CTAs' barriers, and both CTAs' epilogue warps release accumulators on the even
+// CTA's barrier. (On a timeout the even CTA's producer drains its copies through those two-arrive
+// barriers: if the relay stopped first, that wait runs to its limit, far beyond any copy's
+// latency, before the CTA leaves.)
 // Partial sums go to a [chunk][group][particle] FP64 buffer that the finalize kernel sums in a
 // fixed order: the result is deterministic.
 //
@@ -128,9 +133,9 @@ __host__ __device__ inline SmemLayout smem_layout(int NC, int BN, int CL, int kb
   L.off_th = 0;
   L.off_x = L.off_th + th_bufs * L.th_bytes;
   L.off_bar = L.off_x + stages * L.x_bytes;
-  // barriers: x_full[st], x_empty[st], x_peer[st], th_full[2], th_empty[2], th_peer[2],
-  // acc_full[NBUF], acc_empty[NBUF], drain; then tmem base (u32) and abort flag (int)
-  L.total = L.off_bar + 8 * (3 * stages + 6 + 2 * nbuf_for(NC, BN) + 1) + 16;
+  // barriers: x_full[st], x_empty[st], th_full[2], th_empty[2], acc_full[NBUF], acc_empty[NBUF],
+  // drain; then tmem base (u32) and abort flag (int)
+  L.total = L.off_bar + 8 * (2 * stages + 4 + 2 * nbuf_for(NC, BN) + 1) + 16;
   return L;
 }
 
@@ -168,7 +173,9 @@ __device__ __forceinline__ uint64_t kslice_off(int rows, int e) {
 // CL = 2: a CTA pair per work item. The even CTA issues cta_group::2 MMAs of 256 particles
 // (128 in each CTA's shared memory and tensor memory) x BN observations, each CTA holding BN / 2
 // rows of every X tile; each CTA's TMA copies complete on its own barriers, and the odd CTA's
-// MMA warp relays each completed stage and theta buffer to the even CTA with a remote arrive.
+// MMA warp relays each completed stage and theta buffer to the even CTA with a remote arrive on
+// the even CTA's full barrier of that stage (which counts two arrives), so that the MMA thread
+// waits once per stage.
 // The MMA completions arrive on both CTAs' barriers (commit multicast), and both CTAs' epilogue
 // warps release an accumulator on the even CTA's barrier.
 template <int NC, int BN, int CL, bool BATCH>
@@ -193,13 +200,11 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const SmemLayout L = smem_layout(NC, BN, CL, prm.kbx, prm.kbt, prm.stages, prm.th_bufs);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar);
-  uint64_t* x_full = bars;
+  uint64_t* x_full = bars;                        // even CTA of a pair: also the odd CTA's relay
   uint64_t* x_empty = x_full + prm.stages;
-  uint64_t* x_peer = x_empty + prm.stages;         // even CTA: the odd CTA's stage landed
-  uint64_t* th_full = x_peer + prm.stages;
+  uint64_t* th_full = x_empty + prm.stages;        // even CTA of a pair: also the odd CTA's relay
   uint64_t* th_empty = th_full + 2;
-  uint64_t* th_peer = th_empty + 2;                // even CTA: the odd CTA's theta landed
-  uint64_t* acc_full = th_peer + 2;
+  uint64_t* acc_full = th_empty + 2;
   uint64_t* acc_empty = acc_full + NBUF;
   uint64_t* drain = acc_empty + NBUF;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
@@ -212,15 +217,16 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   const int n_clusters = gridDim.x / CL;
 
   if (threadIdx.x == 0) {
+    // the even CTA of a pair counts its own producer's arrive and the odd CTA's relay on its full
+    // barriers, so that one wait covers the stage (or theta buffer) in both CTAs
+    const uint32_t fulls = (CL > 1 && rank == 0) ? 2u : 1u;
     for (int i = 0; i < prm.stages; ++i) {
-      ptx::mbar_init(&x_full[i], 1);
+      ptx::mbar_init(&x_full[i], fulls);
       ptx::mbar_init(&x_empty[i], 1);
-      ptx::mbar_init(&x_peer[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
-      ptx::mbar_init(&th_full[i], 1);
+      ptx::mbar_init(&th_full[i], fulls);
       ptx::mbar_init(&th_empty[i], 1);
-      ptx::mbar_init(&th_peer[i], 1);
     }
     for (int i = 0; i < NBUF; ++i) {
       ptx::mbar_init(&acc_full[i], 1);
@@ -315,11 +321,11 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     }
   } else if (warp == 1 && CL > 1 && rank != 0) {
     // ------------------------------------------------------------------ relay (odd CTA of a pair)
-    // each landed theta buffer and X stage of this CTA is announced on the even CTA's th_peer /
-    // x_peer barrier, in the order the MMA thread consumes them
+    // each landed theta buffer and X stage of this CTA is announced by an arrive on the even
+    // CTA's th_full / x_full barrier of the same index, in the order the MMA thread consumes them
     if (lane == 0) {
-      const uint32_t r_th_peer = ptx::cluster_addr(th_peer, 0);
-      const uint32_t r_x_peer = ptx::cluster_addr(x_peer, 0);
+      const uint32_t r_th_peer = ptx::cluster_addr(th_full, 0);
+      const uint32_t r_x_peer = ptx::cluster_addr(x_full, 0);
       int st = 0, tb = 0;
       uint32_t xph = 0, tph = 0;
       bool ok = true;
@@ -365,18 +371,14 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           ksl = bm->ksl;
           k16 = bm->k16;
         }
-        if (!ptx::mbar_wait_bounded(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
-        if constexpr (CL > 1)
-          if (!ptx::mbar_wait_bounded_cluster(&th_peer[tb], tph, abort_flag, limit)) { ok = false; break; }
+        if (!ptx::mbar_wait_bounded_cluster(&th_full[tb], tph, abort_flag, limit)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t thb = ptx::smem_u32(smem + L.off_th + tb * L.th_bytes);
         for (int tile = tile_lo; tile < tile_hi; ++tile) {
           const int buf = acc_count % NBUF;
           const uint32_t aph = (acc_count / NBUF) & 1u;
           if (!ptx::mbar_wait_bounded_cluster(&acc_empty[buf], aph ^ 1u, abort_flag, limit)) { ok = false; break; }
-          if (!ptx::mbar_wait_bounded(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
-          if constexpr (CL > 1)
-            if (!ptx::mbar_wait_bounded_cluster(&x_peer[st], xph, abort_flag, limit)) { ok = false; break; }
+          if (!ptx::mbar_wait_bounded_cluster(&x_full[st], xph, abort_flag, limit)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint64_t dx = ptx::sdesc_sw128(ptx::smem_u32(smem + L.off_x + st * L.x_bytes));
           // the NC classes accumulate into independent TMEM accumulators: issuing each K slice

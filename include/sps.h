@@ -276,7 +276,7 @@ sps_status sps_loglik_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, 
  * on P particles at prefix t (1 <= t <= n) with CUDA events: observation rows per tile (the two
  * widths the outcome count allows, where the pipeline fits shared memory), single CTAs or CTA
  * pairs (256-particle MMAs over two CTAs, each holding half of every X tile), and work items of
- * 512 to 16384 observations. The fastest is kept
+ * 512 to 65536 observations. The fastest is kept
  * in the context and used by every later split-precision call (results change only by the
  * order of FP32/FP64 partial sums). Each candidate runs 1 untimed and 3 timed launches on zero
  * particles; the call synchronises the context's stream.

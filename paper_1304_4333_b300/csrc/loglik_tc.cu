@@ -1568,7 +1568,7 @@ sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out)
         enc.bn = bn;
         if (run_any(ctx, 2, nullptr, 0, smem_bytes, nullptr, false, &mc) != SPS_OK || mc < 1) continue;
       }
-      for (int chunk = 512; chunk <= 16384; chunk *= 2) {
+      for (int chunk = 512; chunk <= 65536; chunk *= 2) {
         if (chunk < bn) continue;
         const double ms = time_shape(bn, cl, mc, chunk);
         ++tried;

@@ -448,9 +448,10 @@ def sps_ladder(w, forms, max_groups: int, seeds: int, seeds_other: int, target: 
 
 
 def run_loglik_only(args):
-    """Profiling entry: `--calls` calls of the fused split-precision log-likelihood on the named
-    workload at t = n with `--particles` particles around the true coefficients (device memory),
-    after one untimed call; prints the per-launch kernel time from the library's CUDA events."""
+    """Profiling entry: `--calls` calls of the fused split-precision log-likelihood (or, with
+    `--grad`, of the log-likelihood and its gradient) on the named workload at t = n with
+    `--particles` particles around the true coefficients (device memory), after one untimed call;
+    prints the per-launch time of the fused kernel from the library's CUDA events."""
     import ctypes as C
     import torch
     import synthetic
@@ -460,17 +461,19 @@ def run_loglik_only(args):
     P = args.particles or w.P
     th = torch.from_numpy(synthetic.particles_around(w.theta_true, P, 0.05, seed=2)).cuda()
     s = Sps(w.X, w.y, w.C, prior_sd=5.0)
-    s.loglik(th, w.n, "split")
+    call = (lambda: s.loglik_grad(th, w.n)) if args.grad else (lambda: s.loglik(th, w.n, "split"))
+    call()
     torch.cuda.synchronize()
     s.lib.sps_set_timing(s.ctx, 1)
     s.lib.sps_counters(s.ctx, 1, None, None, None)
     for _ in range(args.calls):
-        s.loglik(th, w.n, "split")
+        call()
     torch.cuda.synchronize()
     a, b, c = C.c_int64(), C.c_int64(), C.c_double()
     s.lib.sps_counters(s.ctx, 1, C.byref(a), C.byref(b), C.byref(c))
     ms = c.value / max(b.value, 1)
-    print(json.dumps({"workload": w.name, "particles": P, "t": w.n, "launches": b.value, "ms_per_launch": ms,
+    print(json.dumps({"workload": w.name, "kernel": "gradient" if args.grad else "log-likelihood",
+                      "particles": P, "t": w.n, "launches": b.value, "ms_per_launch": ms,
                       "terms_per_s": P * w.n / (ms * 1e-3)}), flush=True)
     s.close()
 
@@ -500,6 +503,7 @@ def main():
                     help="profiling entry: only time the fused log-likelihood on this workload")
     ap.add_argument("--particles", type=int, default=0, help="with --loglik-only: particles (0 = the workload's)")
     ap.add_argument("--calls", type=int, default=2, help="with --loglik-only: timed calls")
+    ap.add_argument("--grad", action="store_true", help="with --loglik-only: the log-likelihood gradient kernel")
     args = ap.parse_args()
     if args.loglik_only:
         run_loglik_only(args)

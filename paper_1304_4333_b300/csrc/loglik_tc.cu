@@ -849,6 +849,12 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
       : "memory");
 }
 
+// 128 TMEM lanes x 256 bits (8 columns) from the rows of a shared-memory operand tile: row i of
+// the 16-element K slice described by `sdesc` (the layout an MMA reads) into lane i.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -869,11 +875,19 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // buffer; the gradient MMAs read A from TMEM) instead of shared memory. C = 2 only.
 constexpr uint32_t kQtHi = 384, kQtLo = 448;
 
-template <int NC, int BN, bool QT>
+// TT: theta also in TMEM (columns 320-383, one copy per theta buffer, copied from its shared-memory
+// tile by tcgen05.cp at the start of each work item): the forward MMAs then read only X from
+// shared memory. An N = 128 MMA with both operands in shared memory reads 8 KB per 64 clocks, the
+// whole shared-memory bandwidth of the SM, and the MMA thread's barrier waits queue behind those
+// reads while the tensor pipe drains; with theta in TMEM the forward MMAs read half as much.
+constexpr uint32_t kTt = 320;
+
+template <int NC, int BN, bool QT, bool TT = false>
 __global__ void __launch_bounds__(grad_threads(NC), 1)
 grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapT,
                const GradParams prm) {
   static_assert(!QT || (NC == 1 && BN == 128), "q in TMEM: 64 columns each for hi and lo");
+  static_assert(!TT || QT, "theta in TMEM only beside q in TMEM");
   static_assert(BN == grad_bn(NC), "tile rows of the shape");
   constexpr int NBUF = grad_nbuf(NC);
   constexpr uint32_t GOFF = grad_goff(NC);
@@ -1003,6 +1017,14 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
         uint64_t dt[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) dt[c] = ptx::sdesc_sw128(thb + static_cast<uint32_t>(c * prm.kbt) * kTileA);
+        // TMEM copy of this item's theta rows (buffer tb): 16 K elements (8 columns) per copy. The
+        // copy and the MMAs that read it are executed in issue order; the buffer is overwritten
+        // only after the producer refilled shared-memory buffer tb, i.e. after every MMA of the
+        // item that last used it completed (th_empty)
+        const uint32_t tt = tmem_base + kTt + static_cast<uint32_t>(tb * prm.kbt * 32);
+        if constexpr (TT) {
+          for (int e = 0; e < prm.kbt * kKB; e += 16) tmem_cp_128x256b(tt + static_cast<uint32_t>(e >> 1), dt[0] + kslice_off(kBM, e));
+        }
         bool first_grad = true;
         int pend_st = -1;
         uint32_t pend_count = 0;
@@ -1051,6 +1073,14 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
           uint32_t d[NC];
 #pragma unroll
           for (int c = 0; c < NC; ++c) d[c] = tmem_base + static_cast<uint32_t>((buf * NC + c) * BN);
+          if constexpr (TT) {
+            for (int i = 0; i < prm.ksh; ++i)   // Th Xh'
+              mma_bf16_ts(d[0], tt + static_cast<uint32_t>(8 * i), dx + kslice_off(BN, 16 * i), idesc_f, i > 0);
+            for (int i = 0; i < prm.ksh; ++i)   // Tl Xh'
+              mma_bf16_ts(d[0], tt + static_cast<uint32_t>((prm.k16 >> 1) + 8 * i), dx + kslice_off(BN, 16 * i), idesc_f, 1);
+            for (int i = 0; i < prm.ksl; ++i)   // Th Xl'
+              mma_bf16_ts(d[0], tt + static_cast<uint32_t>(8 * i), dx + kslice_off(BN, prm.k16 + 16 * i), idesc_f, 1);
+          } else {
           for (int i = 0; i < prm.ksh; ++i) {   // Th_c Xh'
             const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, 16 * i);
 #pragma unroll
@@ -1065,6 +1095,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
             const uint64_t ka = kslice_off(kBM, 16 * i), kb = kslice_off(BN, prm.k16 + 16 * i);
 #pragma unroll
             for (int c = 0; c < NC; ++c) ptx::mma_bf16(d[c], dt[c] + ka, dx + kb, idesc_f, 1);
+          }
           }
           issued_any = true;
           ptx::mma_commit(&acc_full[buf]);
@@ -1711,9 +1742,9 @@ static bool grad_shape(const sps_ctx* ctx, int* BN, int* ng, int* gch, int* stag
   return false;
 }
 
-template <int NC, int BN, bool QT>
+template <int NC, int BN, bool QT, bool TT = false>
 static sps_status run_grad(sps_ctx* ctx, const GradParams& prm, int grid, uint32_t smem_bytes) {
-  auto kern = grad_tc_kernel<NC, BN, QT>;
+  auto kern = grad_tc_kernel<NC, BN, QT, TT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
   if (e == cudaSuccess) {
     kern<<<grid, grad_threads(NC), smem_bytes, ctx->stream>>>(ctx->ll.mapXg, ctx->ll.mapT, prm);
@@ -1794,7 +1825,12 @@ sps_status loglik_grad_tc(sps_ctx* ctx, const double* d_theta, int64_t P, int64_
   const int grid = std::max(1, std::min(ctx->num_sms, prm.n_items));
   hot_begin(ctx);
   sps_status st;
-  if (NC == 1 && qt) st = run_grad<1, 128, true>(ctx, prm, grid, smem_bytes);
+  // theta in TMEM beside q when the gradient accumulators (one chain) end by column 320 and the
+  // theta copies fit columns 320-383
+  const bool tt = qt && ng <= 64 && th_bufs * (enc.kt / 2) <= 64;
+  if (tt) prm.gch = 1;
+  if (NC == 1 && tt) st = run_grad<1, 128, true, true>(ctx, prm, grid, smem_bytes);
+  else if (NC == 1 && qt) st = run_grad<1, 128, true>(ctx, prm, grid, smem_bytes);
   else if (NC == 1) st = run_grad<1, 128, false>(ctx, prm, grid, smem_bytes);
   else if (NC == 2) st = run_grad<2, 64, false>(ctx, prm, grid, smem_bytes);
   else st = run_grad<3, 32, false>(ctx, prm, grid, smem_bytes);

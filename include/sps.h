@@ -102,8 +102,10 @@ typedef struct sps_options {
   int32_t graphs;          /* 1 (default): after its first step, an adaptive M phase of sps_run or
                               sps_mphase runs as one captured CUDA graph (a conditional loop whose
                               body is one M step and a device-side step-size and RNE rule), with one
-                              host synchronisation per phase; results are identical to graphs = 0,
-                              which issues and reads back every step from the host */
+                              host synchronisation per phase; in sps_run_batched, the lockstep M
+                              phase of all models likewise (per-model conditional nodes); results
+                              are identical to graphs = 0, which issues and reads back every step
+                              from the host */
 } sps_options;
 
 typedef struct sps_ctx sps_ctx;
@@ -320,6 +322,13 @@ sps_status sps_state_get(sps_ctx* ctx, const sps_state* st, double* theta, doubl
  * NULL to recompute it at the state's t) and set t (0 <= t <= n). */
 sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const double* ll,
                          int64_t t);
+/* Outputs of the state's particles as sps_run reports them at the end of a run: mean, SD, NSE and
+ * RNE (Eqs. 5-7, 10, over the J groups) of every coordinate of theta and of the log-odds
+ * theta_c' xbar (Eq. 15; D + C - 1 values each), and the per-group log marginal likelihoods
+ * accumulated by the state's C phases with their mean, NSE and pooled value. out: caller
+ * arrays as for sps_run; n_cycles = S phases run, m_steps = M steps run (log_pred ignored).
+ * Waits for the context's stream. */
+sps_status sps_state_result(sps_ctx* ctx, sps_state* st, sps_result* out);
 
 /* C phase (Algorithm 1 step 2(a), Eq. 11, ended by the ESS rule of Algorithm 2 step 1, Eq. 14):
  * from the state's t, multiply the weights by p(y_s | theta) for s = t+1, ... until
@@ -384,9 +393,15 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
  * lockstep: in every M step the proposals of all models still moving are evaluated, each at its
  * model's t, with one batched fused-kernel launch (sps_loglik_batched, in which each model's
  * tiles use the model's own encoding of its covariates); FP32 precision: one launch per model;
- * MALA: each model's own gradient launch, which also gives the log-likelihoods. Marginal
- * likelihoods for comparing the models (Sec. 2.3) are in out[m].log_ml.
- *   out: [M] caller-allocated results as for sps_run (log_pred ignored, graph_steps 0).
+ * MALA: each model's own gradient launch, which also gives the log-likelihoods. A model that
+ * has met its stopping rule leaves the phase: its kernels stop and the batched launch skips its
+ * particle tiles (keeping the launch's work decomposition, so each model's sums round the same
+ * way in every step). With options.graphs, each phase after its first step is one CUDA graph
+ * launch: a conditional loop whose body holds each moving model's kernels under conditional
+ * nodes of its own (the models' kernels run concurrently), the batched launch between them and
+ * device-side step-size and RNE rules per model; the results are identical to graphs = 0.
+ * Marginal likelihoods for comparing the models (Sec. 2.3) are in out[m].log_ml.
+ *   out: [M] caller-allocated results as for sps_run (log_pred ignored).
  * A model's error is returned with its message. */
 sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, double g, int32_t groups,
                            int32_t particles_per_group, sps_result* out);

@@ -79,6 +79,7 @@ SIGNATURES = {
     "sps_state_create": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_P)]),
     "sps_state_destroy": (None, [_P]),
     "sps_state_get": (C.c_int, [_P, _P, _P, _P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "sps_state_result": (C.c_int, [_P, _P, C.POINTER(SpsResult)]),
     "sps_state_set": (C.c_int, [_P, _P, _P, _P, C.c_int64]),
     "sps_cphase": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P]),
     "sps_sphase": (C.c_int, [_P, _P, _P, _P, C.c_int32]),

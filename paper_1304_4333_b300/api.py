@@ -334,7 +334,8 @@ class Sps:
         """Adaptive SPS for nested models (sps_run_batched): model m uses the first ks[m]
         covariates, with the paper's g-prior of its covariates when g is given (else the marginal
         of the context's prior); the M phases of all models run in lockstep with one batched
-        log-likelihood launch per step. Returns one RunResult per model (no schedule)."""
+        log-likelihood launch per step; with graphs (the default) each phase after its first step is
+        one CUDA graph launch. Returns one RunResult per model (no schedule)."""
         ks = [int(v) for v in ks]
         M = len(ks)
         res = (N.SpsResult * M)()
@@ -354,7 +355,7 @@ class Sps:
             arrs, lmg = keep[m]
             r = res[m]
             out.append(RunResult(arrs["mean"], arrs["sd"], arrs["nse"], arrs["rne"], lmg, r.log_ml, r.log_ml_nse,
-                                 r.log_ml_pooled, r.n_cycles, r.m_steps, r.seconds))
+                                 r.log_ml_pooled, r.n_cycles, r.m_steps, r.seconds, graph_steps=r.graph_steps))
         return out
 
     def state(self, J: int, N_: int, seed: int = 0) -> "State":
@@ -477,6 +478,19 @@ class State:
                        _ptr(used) if sigma_used else None, C.byref(info))
         return {"h": info.h, "accept": info.accept_rate, "rne_min": info.rne_min, "h_next": info.h_next,
                 "sigma": used}
+
+    def result(self) -> RunResult:
+        """Outputs of the current particles as a run reports them (sps_state_result)."""
+        m = self.sps.D + self.sps.C - 1
+        arrs = {k: np.zeros(m) for k in ("mean", "sd", "nse", "rne")}
+        lmg = np.zeros(self.J)
+        res = N.SpsResult()
+        for k_, a in arrs.items():
+            setattr(res, k_, a.ctypes.data_as(C.POINTER(C.c_double)))
+        res.log_ml_group = lmg.ctypes.data_as(C.POINTER(C.c_double))
+        self.sps._call("sps_state_result", self.st, C.byref(res))
+        return RunResult(arrs["mean"], arrs["sd"], arrs["nse"], arrs["rne"], lmg, res.log_ml, res.log_ml_nse,
+                         res.log_ml_pooled, res.n_cycles, res.m_steps, 0.0)
 
     def mphase(self, kernel: str = "rw", fixed_steps: int = 0):
         steps = C.c_int32(); a = C.c_double(); r = C.c_double()

@@ -87,6 +87,10 @@ struct BatchModel {
   int ksl;                    // over Xl
 };
 
+// A prepared launch of the batched fused kernel (loglik_split_batched_prepare): its tables are in
+// device memory, so it can be launched, or captured into a graph, without host copies.
+struct SplitBatchedPlan;
+
 // Per-call scratch of the likelihood kernels.
 struct LoglikScratch {
   DevBuf thetaP;              // bf16 [NC * Ppad x kt] operand rows (class-major row blocks)
@@ -102,6 +106,7 @@ struct LoglikScratch {
   DevBuf batch_ptile_t;       // int2 [n_ptiles] prefix length and K-slice mask of each particle tile
   DevBuf batch_lin;           // FP64 [M x NC x k] linear terms of the models
   DevBuf batch_models;        // BatchModel [M]
+  std::shared_ptr<SplitBatchedPlan> bplan;   // the last prepared batched launch
 };
 
 // Device-resident control block of a captured M phase: the step size h and the Philox step word
@@ -244,8 +249,18 @@ sps_status make_map_bf16(sps_ctx* ctx, CUtensorMap* map, const void* base, uint6
 sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
 // Batched nested models (see sps_loglik_batched): one fused-kernel launch for all of them; model
 // m's particles at device d_theta[m] ([P_m x k_m NC]), its results to d_ll[m] ([P_m]).
+// skip (optional, [M]): models whose particle tiles are skipped (their results are not
+// defined); the work decomposition is the same with and without skips.
 sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
-                                const double* const* d_theta, double* const* d_ll);
+                                const double* const* d_theta, double* const* d_ll, const char* skip = nullptr);
+// The same call in two parts: prepare (tables and operand encodings in device memory, the launch
+// shape kept in the context; tiles receives each model's particle-tile range [x, y) of the
+// table of prefix lengths) and launch (kernels only: no allocation, no host copy, so it can be
+// captured). *ptile_table receives that table (int2 {prefix length, slot} per particle tile).
+sps_status loglik_split_batched_prepare(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm,
+                                        const int64_t* tm, const double* const* d_theta, double* const* d_ll,
+                                        const char* skip, std::vector<int2>* tiles, int2** ptile_table);
+sps_status loglik_split_batched_launch(sps_ctx* ctx);
 sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
 sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                            int precision);

@@ -1890,8 +1890,17 @@ static sps_status model_encoding(sps_ctx* ctx, int km, ModelEncoding** out) {
   return SPS_OK;
 }
 
-sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
-                                const double* const* d_theta, double* const* d_ll) {
+struct SplitBatchedPlan {
+  TcParams prm;
+  uint32_t smem_bytes = 0;
+  int M = 0;
+  int64_t PP = 0, Ptot = 0;
+  size_t slices = 0;
+};
+
+sps_status loglik_split_batched_prepare(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm,
+                                        const int64_t* tm, const double* const* d_theta, double* const* d_ll,
+                                        const char* skip, std::vector<int2>* tiles, int2** ptile_table) {
   const int NC = ctx->NC;
   if (NC > 3 || ctx->enc.bn == 0) return fail(ctx, SPS_ERR_UNSUPPORTED, "split precision: unsupported shape");
   XEncoding& enc = ctx->enc;
@@ -1912,11 +1921,12 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
     tmax = std::max<int64_t>(tmax, tm[m]);
   }
   if (PP > (int64_t{1} << 28)) return fail(ctx, SPS_ERR_INVALID_ARG, "batched log-likelihood: too many particles");
-  // the work decomposition of one call over PP operand rows and the longest prefix; each
-  // particle tile then stops at its own model's prefix
-  TcParams prm;
-  uint32_t smem_bytes = 0;
-  if (!plan_call(ctx, PP, tmax, &prm, &smem_bytes))
+  // the work decomposition of one call over PP operand rows and the longest prefix (skipped
+  // models included, so that it does not depend on which models are skipped); each particle
+  // tile then stops at its own model's prefix
+  auto plan = std::make_shared<SplitBatchedPlan>();
+  TcParams& prm = plan->prm;
+  if (!plan_call(ctx, PP, tmax, &prm, &plan->smem_bytes))
     return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
   if (prm.ppad != PP) return fail(ctx, SPS_ERR_INVALID_ARG, "batched log-likelihood: internal padding mismatch");
   // each model's own encoding of its first k_m covariates (built on first use and kept): its tiles
@@ -1934,12 +1944,16 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
     tab[m * kTab + 7] = static_cast<int64_t>(reinterpret_cast<uintptr_t>(me->perm_dev.ptr));
     tab[m * kTab + 8] = me->k16;
   }
-  // per particle tile: its model's prefix length and slot
+  // per particle tile: its model's prefix length (0 for a skipped model: no work item of the
+  // tile has an observation) and slot
   std::vector<int2> ptile_info(static_cast<size_t>(prm.n_ptiles));
+  if (tiles) tiles->assign(static_cast<size_t>(M), make_int2(0, 0));
   for (int m = 0; m < M; ++m) {
     const int64_t r0 = tab[m * kTab + 0] / kBM;
     const int64_t r1 = r0 + (Pm[m] + prow - 1) / prow * prow / kBM;
-    for (int64_t r = r0; r < r1; ++r) ptile_info[r] = make_int2(static_cast<int>(tm[m]), m);
+    const int tl = (skip && skip[m]) ? 0 : static_cast<int>(tm[m]);
+    for (int64_t r = r0; r < r1; ++r) ptile_info[r] = make_int2(tl, m);
+    if (tiles) (*tiles)[m] = make_int2(static_cast<int>(r0), static_cast<int>(r1));
   }
   SPS_CUDA_TRY(S.batch_models.reserve(sizeof(BatchModel) * bms.size()));
   SPS_CUDA_TRY(cudaMemcpyAsync(S.batch_models.ptr, bms.data(), sizeof(BatchModel) * bms.size(),
@@ -1957,11 +1971,33 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
     S.ppad_cap = cap;
   }
   SPS_TRY(make_map_bf16(ctx, &S.mapT, S.thetaP.ptr, static_cast<uint64_t>(NC) * PP, enc.kt, kBM));
+  plan->slices = static_cast<size_t>(prm.n_chunks) * nwg_for(NC);
+  SPS_CUDA_TRY(S.partial.reserve(plan->slices * PP * sizeof(double)));
+  SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
+  prm.partial = S.partial.as<double>();
+  prm.flag = S.flag.as<int>();
+  prm.ptile_info = S.batch_ptile_t.as<int2>();
+  prm.bmodels = S.batch_models.as<BatchModel>();
+  plan->M = M;
+  plan->PP = PP;
+  plan->Ptot = Ptot;
+  S.bplan = plan;
+  if (ptile_table) *ptile_table = S.batch_ptile_t.as<int2>();
+  return SPS_OK;
+}
+
+sps_status loglik_split_batched_launch(sps_ctx* ctx) {
+  LoglikScratch& S = ctx->ll;
+  if (!S.bplan) return fail(ctx, SPS_ERR_STATE, "batched log-likelihood: no prepared launch");
+  SplitBatchedPlan& pl = *S.bplan;
+  XEncoding& enc = ctx->enc;
+  const int NC = ctx->NC, M = pl.M;
+  TcParams prm = pl.prm;
   const int64_t* dtab = S.batch_tab.as<int64_t>();
   {
-    const int64_t rows = static_cast<int64_t>(NC) * PP;
+    const int64_t rows = static_cast<int64_t>(NC) * pl.PP;
     encode_theta_batched_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
-        dtab, M, NC, enc.kt, PP, S.thetaP.as<__nv_bfloat16>());
+        dtab, M, NC, enc.kt, pl.PP, S.thetaP.as<__nv_bfloat16>());
     ++ctx->launches;
     const int64_t warps = static_cast<int64_t>(M) * NC * ctx->k;
     lin_tail_batched_kernel<<<static_cast<unsigned>((warps + 3) / 4), 128, 0, ctx->stream>>>(
@@ -1970,22 +2006,21 @@ sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const in
     ++ctx->launches;
     SPS_CUDA_TRY(cudaGetLastError());
   }
-  const size_t slices = static_cast<size_t>(prm.n_chunks) * nwg_for(NC);
-  SPS_CUDA_TRY(S.partial.reserve(slices * PP * sizeof(double)));
-  SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
-  prm.partial = S.partial.as<double>();
-  prm.flag = S.flag.as<int>();
-  prm.ptile_info = S.batch_ptile_t.as<int2>();
-  prm.bmodels = S.batch_models.as<BatchModel>();
   SPS_CUDA_TRY(cudaMemsetAsync(prm.flag, 0, sizeof(int), ctx->stream));
   if (prm.n_items > 0)
-    SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), smem_bytes, &S.mapT, true, nullptr));
-  finalize_batched_kernel<<<static_cast<unsigned>((Ptot + 255) / 256), 256, 0, ctx->stream>>>(
-      dtab, M, NC, ctx->k, Ptot, S.batch_lin.as<double>(), prm.partial,
-      prm.n_items > 0 ? static_cast<int>(slices) : 0, PP);
+    SPS_TRY(run_any(ctx, enc.cl, &prm, grid_for(ctx, prm), pl.smem_bytes, &S.mapT, true, nullptr));
+  finalize_batched_kernel<<<static_cast<unsigned>((pl.Ptot + 255) / 256), 256, 0, ctx->stream>>>(
+      dtab, M, NC, ctx->k, pl.Ptot, S.batch_lin.as<double>(), prm.partial,
+      prm.n_items > 0 ? static_cast<int>(pl.slices) : 0, pl.PP);
   ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;
+}
+
+sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
+                                const double* const* d_theta, double* const* d_ll, const char* skip) {
+  SPS_TRY(loglik_split_batched_prepare(ctx, M, km, Pm, tm, d_theta, d_ll, skip, nullptr, nullptr));
+  return loglik_split_batched_launch(ctx);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -1277,9 +1278,17 @@ mstep_control_kernel(StepCtl* __restrict__ ctl, const unsigned long long* __rest
                      const double* __restrict__ parts, int J, int F, int S, int N, int64_t P, double K,
                      double target, double h_step, double h_min, double h_max, double* __restrict__ steplog,
                      const double* __restrict__ sigma, int D, double* __restrict__ sigma_log,
-                     cudaGraphConditionalHandle cond) {
+                     cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond2, int model_mode,
+                     int2* __restrict__ ptiles, int pt_lo, int pt_hi) {
   extern __shared__ double sums[];   // [J][F][3]
   __shared__ double rne[kCtlMaxF];
+  if (model_mode && ctl->stop) {   // a stopped model stays stopped (its conditional nodes are off)
+    if (threadIdx.x == 0) {
+      cudaGraphSetConditional(cond, 0u);
+      cudaGraphSetConditional(cond2, 0u);
+    }
+    return;
+  }
   const int r = ctl->r;   // read by every thread before thread 0 advances it
   if (sigma_log)
     for (int e = threadIdx.x; e < D * D; e += blockDim.x)
@@ -1343,6 +1352,27 @@ mstep_control_kernel(StepCtl* __restrict__ ctl, const unsigned long long* __rest
   }
   ctl->stop = stop ? 1 : 0;
   cudaGraphSetConditional(cond, stop ? 0u : 1u);
+  if (model_mode) {
+    // one model of a batched M phase: cond and cond2 switch its own kernels; once it stops, the
+    // batched log-likelihood launch skips its particle tiles (prefix length 0)
+    cudaGraphSetConditional(cond2, stop ? 0u : 1u);
+    if (stop && ptiles)
+      for (int i = pt_lo; i < pt_hi; ++i) ptiles[i].x = 0;
+  }
+}
+
+// Loop condition of a batched M phase: another lockstep step while any model still moves. ctl[M]
+// counts the loop's iterations: past its r_max (the models' step cap, which every model's own
+// rule enforces first) the loop ends with err = 3.
+__global__ void batch_continue_kernel(StepCtl* __restrict__ ctl, int M, cudaGraphConditionalHandle cond) {
+  int any = 0;
+  for (int m = 0; m < M; ++m) any |= (ctl[m].stop == 0) ? 1 : 0;
+  const int it = ++ctl[M].r;
+  if (any && it >= ctl[M].r_max) {
+    ctl[M].err = 3;
+    any = 0;
+  }
+  cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
 }  // namespace
@@ -1867,7 +1897,8 @@ sps_status mphase_graph(sps_ctx* ctx, sps_state* st, int kernel, double K, int r
                                                             st->scratch.as<double>(), st->J, F, kMomParts, st->N,
                                                             st->P, K, target, o.h_step, o.h_min, o.h_max,
                                                             st->steplog.as<double>(), st->cov.as<double>(), ctx->D,
-                                                            want_sigma ? st->sigmalog.as<double>() : nullptr, cond);
+                                                            want_sigma ? st->sigmalog.as<double>() : nullptr, cond,
+                                                            cond, 0, nullptr, 0, 0);
         ++ctx->launches;
         if (cudaGetLastError() != cudaSuccess) is = SPS_ERR_CUDA;
       }
@@ -1932,6 +1963,293 @@ sps_status mphase_graph(sps_ctx* ctx, sps_state* st, int kernel, double K, int r
   }
   st->h = c.h;
   *r_end = c.r;
+  return SPS_OK;
+}
+
+// The rest of a lockstep M phase of a batched run, after its first step, as one graph launch: a
+// conditional WHILE node whose body holds, per model still moving, conditional IF nodes around
+// the model's own kernels (proposal, decisions, monitoring sums and mstep_control_kernel, which
+// switches the model's IF nodes off once its stopping rule is met), between them the one batched
+// fused-kernel evaluation of the proposals (split-precision random walk; the tiles of stopped
+// models are skipped), and batch_continue_kernel, which ends the loop when every model has
+// stopped. The models' IF nodes have no mutual dependencies, so their kernels run concurrently.
+// The graph is captured for each phase (t and the particle buffers change between phases) and
+// launched once; the host synchronises once. The models are the phase's (models[i] with
+// moving[i] after the first step, batched[i] if evaluated by the batched launch); steps[i] is
+// the model's step count, updated. *fallback: the graph could not be built and nothing ran.
+sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, const std::vector<sps_state*>& ss,
+                                const std::vector<char>& moving, const std::vector<char>& batched, int kernel,
+                                std::vector<int>& steps, DevBuf& ctl_buf, bool* fallback) {
+  *fallback = false;
+  const sps_options& o = ctx->opt;
+  auto give_up = [&](const char* what, cudaError_t e) {
+    ctx->last_error = std::string("batched M-phase graph not used: ") + what +
+                      (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : std::string());
+    cudaGetLastError();
+    *fallback = true;
+    return SPS_OK;
+  };
+  const int Mp = static_cast<int>(cs.size());
+  const int F = 1 + ctx->NC;
+  const int J = ss[0]->J;
+  if (F > kCtlMaxF) return give_up("shape", cudaSuccess);
+  const size_t ctl_smem = sizeof(double) * 3 * static_cast<size_t>(J) * F;
+  if (ctl_smem + sizeof(double) * kCtlMaxF > 200 * 1024) return give_up("groups", cudaSuccess);
+  {
+    const cudaError_t ea = cudaFuncSetAttribute(mstep_control_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(ctl_smem));
+    if (ea != cudaSuccess) return give_up("control kernel shared memory", ea);
+  }
+  SPS_CUDA_TRY(ctl_buf.reserve(sizeof(StepCtl) * static_cast<size_t>(Mp + 1)));
+  for (sps_state* st : ss) SPS_CUDA_TRY(st->steplog.reserve(sizeof(double) * 3 * static_cast<size_t>(o.r_max)));
+  if (!ctx->cap_stream) {
+    const cudaError_t ec = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (ec != cudaSuccess) {
+      ctx->cap_stream = nullptr;
+      return give_up("capture stream", ec);
+    }
+  }
+  // the batched evaluation of the proposals, prepared (tables in device memory) before the capture
+  std::vector<int> bpos(Mp, -1);
+  std::vector<int2> tiles;
+  int2* ptab = nullptr;
+  {
+    std::vector<int32_t> bk;
+    std::vector<int64_t> bP, bt;
+    std::vector<const double*> bth;
+    std::vector<double*> bll;
+    std::vector<char> bskip;
+    for (int i = 0; i < Mp; ++i) {
+      if (!batched[i]) continue;
+      bpos[i] = static_cast<int>(bk.size());
+      bk.push_back(cs[i]->k);
+      bP.push_back(ss[i]->P);
+      bt.push_back(ss[i]->t);
+      bth.push_back(ss[i]->theta_prop.as<double>());
+      bll.push_back(ss[i]->ll_prop.as<double>());
+      bskip.push_back(moving[i] ? 0 : 1);
+    }
+    if (!bk.empty())
+      SPS_TRY(loglik_split_batched_prepare(ctx, static_cast<int>(bk.size()), bk.data(), bP.data(), bt.data(),
+                                           bth.data(), bll.data(), bskip.data(), &tiles, &ptab));
+  }
+  StepCtl* d_ctl = ctl_buf.as<StepCtl>();
+  // the models' control blocks, then the loop's iteration count (bounded by the step cap)
+  std::vector<StepCtl> hc(static_cast<size_t>(Mp + 1));
+  for (int i = 0; i < Mp; ++i)
+    hc[i] = StepCtl{ss[i]->h, static_cast<unsigned long long>(ss[i]->step_counter + 1), steps[i], o.r_max,
+                    moving[i] ? 0 : 1, 0};
+  hc[Mp] = StepCtl{0.0, 0ull, 0, o.r_max + 1, 0, 0};
+  const uint64_t gen = buffer_generation();
+  const double target = (kernel == SPS_MKERNEL_MALA) ? o.mala_target_accept : o.target_accept;
+
+  cudaGraph_t g = nullptr;
+  SPS_CUDA_TRY(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+  } guard{g};
+  cudaGraphConditionalHandle wh;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&wh, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams wp{};
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = wh;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+  }
+  if (e != cudaSuccess) return give_up("conditional node", e);
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  // an IF node in the loop body (after deps) whose body graph receives what issue() launches on
+  // the context c, recorded on the capture stream
+  std::string cap_error;
+  auto add_if = [&](cudaGraphConditionalHandle* h, const std::vector<cudaGraphNode_t>& deps, sps_ctx* c,
+                    const std::function<sps_status()>& issue, cudaGraphNode_t* node) -> cudaError_t {
+    cudaError_t ee = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault);
+    if (ee != cudaSuccess) return ee;
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = *h;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    ee = cudaGraphAddNode(node, body, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &ip);
+    if (ee != cudaSuccess) return ee;
+    ee = cudaStreamBeginCaptureToGraph(ctx->cap_stream, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed);
+    if (ee != cudaSuccess) return ee;
+    const cudaStream_t user = c->stream;
+    c->stream = ctx->cap_stream;
+    c->capturing = true;
+    const sps_status is = issue();
+    c->capturing = false;
+    c->stream = user;
+    cudaGraph_t out = nullptr;
+    ee = cudaStreamEndCapture(ctx->cap_stream, &out);
+    if (is != SPS_OK) {
+      cap_error = c->last_error;
+      return cudaErrorUnknown;
+    }
+    return ee;
+  };
+  std::vector<cudaGraphConditionalHandle> hA(Mp), hB(Mp);
+  std::vector<cudaGraphNode_t> nA(Mp), nB(Mp), last;
+  std::vector<int64_t> chain_launches(Mp, 0);
+  for (int i = 0; i < Mp && e == cudaSuccess; ++i) {
+    if (!moving[i]) continue;
+    sps_ctx* c = cs[i];
+    sps_state* st = ss[i];
+    StepCtl* ctl = d_ctl + i;
+    const double K = (st->t >= c->n) ? o.rne_final : o.rne_cycle;
+    const int2 tr = (bpos[i] >= 0) ? tiles[bpos[i]] : make_int2(0, 0);
+    auto control = [&, c, st, ctl, K, tr, i]() -> sps_status {
+      mstep_control_kernel<<<1, 128, ctl_smem, c->stream>>>(ctl, st->counters.as<unsigned long long>(),
+                                                           st->scratch.as<double>(), st->J, F, kMomParts, st->N,
+                                                           st->P, K, target, o.h_step, o.h_min, o.h_max,
+                                                           st->steplog.as<double>(), st->cov.as<double>(), c->D,
+                                                           nullptr, hA[i], batched[i] ? hB[i] : hA[i], 1,
+                                                           batched[i] ? ptab : nullptr, tr.x, tr.y);
+      ++c->launches;
+      SPS_CUDA_TRY(cudaGetLastError());
+      return SPS_OK;
+    };
+    const int64_t l0 = c->launches;
+    if (batched[i]) {
+      // the handle of the second IF node exists before the control kernel that sets it is captured
+      e = cudaGraphConditionalHandleCreate(&hB[i], g, 1, cudaGraphCondAssignDefault);
+      if (e == cudaSuccess)
+        e = add_if(&hA[i], {}, c, [&, c, st, ctl]() { return rw_issue_propose(c, st, nullptr, nullptr, 0.0, 0, ctl); },
+                   &nA[i]);
+    } else {
+      e = add_if(&hA[i], {}, c, [&, c, st, ctl, control]() {
+            SPS_TRY(mstep_issue(c, st, kernel, nullptr, nullptr, 0.0, 0, ctl));
+            return control();
+          }, &nA[i]);
+      last.push_back(nA[i]);
+    }
+    chain_launches[i] = c->launches - l0;
+    c->launches = l0;
+  }
+  int64_t eval_launches = 0;
+  if (e == cudaSuccess && !tiles.empty()) {
+    // the batched evaluation after every batched model's proposal, as a child graph
+    std::vector<cudaGraphNode_t> deps;
+    for (int i = 0; i < Mp; ++i)
+      if (moving[i] && batched[i]) deps.push_back(nA[i]);
+    e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      const cudaStream_t user = ctx->stream;
+      ctx->stream = ctx->cap_stream;
+      ctx->capturing = true;
+      const int64_t l0 = ctx->launches;
+      const sps_status is = loglik_split_batched_launch(ctx);
+      eval_launches = ctx->launches - l0;
+      ctx->launches = l0;
+      ctx->capturing = false;
+      ctx->stream = user;
+      cudaGraph_t ge = nullptr;
+      e = cudaStreamEndCapture(ctx->cap_stream, &ge);
+      if (is != SPS_OK) {
+        cap_error = ctx->last_error;
+        e = cudaErrorUnknown;
+      }
+      cudaGraphNode_t en;
+      if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&en, body, deps.data(), deps.size(), ge);
+      if (ge) cudaGraphDestroy(ge);
+      for (int i = 0; i < Mp && e == cudaSuccess; ++i) {
+        if (!moving[i] || !batched[i]) continue;
+        sps_ctx* c = cs[i];
+        sps_state* st = ss[i];
+        StepCtl* ctl = d_ctl + i;
+        const double K = (st->t >= c->n) ? o.rne_final : o.rne_cycle;
+        const int2 tr = tiles[bpos[i]];
+        const int64_t l0c = c->launches;
+        // hB[i] already exists: create the IF node with it directly
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hB[i];
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        e = cudaGraphAddNode(&nB[i], body, &en, nullptr, 1, &ip);
+        if (e == cudaSuccess)
+          e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) break;
+        const cudaStream_t user_c = c->stream;
+        c->stream = ctx->cap_stream;
+        c->capturing = true;
+        sps_status is2 = rw_issue_accept(c, st, 0, ctl);
+        if (is2 == SPS_OK) {
+          mstep_control_kernel<<<1, 128, ctl_smem, c->stream>>>(ctl, st->counters.as<unsigned long long>(),
+                                                               st->scratch.as<double>(), st->J, F, kMomParts, st->N,
+                                                               st->P, K, target, o.h_step, o.h_min, o.h_max,
+                                                               st->steplog.as<double>(), st->cov.as<double>(), c->D,
+                                                               nullptr, hA[i], hB[i], 1, ptab, tr.x, tr.y);
+          ++c->launches;
+          if (cudaGetLastError() != cudaSuccess) is2 = SPS_ERR_CUDA;
+        }
+        c->capturing = false;
+        c->stream = user_c;
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(ctx->cap_stream, &out);
+        if (is2 != SPS_OK) {
+          cap_error = c->last_error;
+          e = cudaErrorUnknown;
+        }
+        chain_launches[i] += c->launches - l0c;
+        c->launches = l0c;
+        last.push_back(nB[i]);
+      }
+    }
+  }
+  if (e == cudaSuccess) {
+    // another step while any model moves
+    int Mi = Mp;
+    void* args[] = {&d_ctl, &Mi, &wh};
+    cudaKernelNodeParams kp{};
+    kp.func = reinterpret_cast<void*>(batch_continue_kernel);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    cudaGraphNode_t cn;
+    e = cudaGraphAddKernelNode(&cn, body, last.data(), last.size(), &kp);
+  }
+  if (e != cudaSuccess || buffer_generation() != gen) {
+    const std::string why = !cap_error.empty() ? "capture: " + cap_error
+                            : e != cudaSuccess ? std::string("graph construction") : std::string("reallocation");
+    return give_up(why.c_str(), e);
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) return give_up("instantiate", e);
+  struct ExecGuard {
+    cudaGraphExec_t x;
+    ~ExecGuard() { if (x) cudaGraphExecDestroy(x); }
+  } xguard{exec};
+  SPS_CUDA_TRY(cudaMemcpyAsync(d_ctl, hc.data(), sizeof(StepCtl) * hc.size(), cudaMemcpyHostToDevice, ctx->stream));
+  SPS_CUDA_TRY(cudaGraphLaunch(exec, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(hc.data(), d_ctl, sizeof(StepCtl) * hc.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (hc[Mp].err) return fail(ctx, SPS_ERR_STATE, "batched M-phase graph: step cap passed without every model stopping");
+  int iters = 0;
+  for (int i = 0; i < Mp; ++i) {
+    if (!moving[i]) continue;
+    const StepCtl& c = hc[i];
+    sps_state* st = ss[i];
+    const int ran = c.r - steps[i] + (c.err ? 1 : 0);
+    iters = std::max(iters, ran);
+    cs[i]->launches += static_cast<int64_t>(ran) * chain_launches[i];
+    st->graph_steps += ran;
+    st->step_counter = c.step - 1 + (c.err ? 1 : 0);
+    if (kernel == SPS_MKERNEL_RW) st->grad_valid = false;
+    if (c.err == 1) return fail(ctx, SPS_ERR_DEGENERATE, "model context: proposal covariance h V is not positive definite");
+    if (c.err == 2) return fail(ctx, SPS_ERR_NONFINITE, "model context: non-finite log-likelihood of a proposal");
+    st->h = c.h;
+    steps[i] = c.r;
+  }
+  ctx->launches += static_cast<int64_t>(iters) * (eval_launches + 1);
   return SPS_OK;
 }
 
@@ -2240,6 +2558,14 @@ sps_status sps_state_get(sps_ctx* ctx, const sps_state* st, double* theta, doubl
   return SPS_OK;
 }
 
+sps_status sps_state_result(sps_ctx* ctx, sps_state* st, sps_result* out) {
+  if (!ctx) return SPS_ERR_INVALID_ARG;
+  SPS_TRY(check_state(ctx, st));
+  if (!out || !out->mean || !out->sd || !out->nse || !out->rne || !out->log_ml_group)
+    return fail(ctx, SPS_ERR_INVALID_ARG, "sps_state_result: result arrays missing");
+  return finish_run(ctx, st, static_cast<int32_t>(st->cycle_counter), static_cast<int64_t>(st->step_counter), out);
+}
+
 sps_status sps_state_set(sps_ctx* ctx, sps_state* st, const double* theta, const double* ll, int64_t t) {
   SPS_TRY(check_state(ctx, st));
   if (!theta || t < 0 || t > ctx->n) return fail(ctx, SPS_ERR_INVALID_ARG, "state_set: bad arguments");
@@ -2460,19 +2786,26 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
   std::vector<int64_t> bP, bt;
   std::vector<const double*> bth;
   std::vector<double*> bll;
-  auto evaluate = [&](const std::vector<int>& list, bool proposals) -> sps_status {
-    bk.clear(); bP.clear(); bt.clear(); bth.clear(); bll.clear();
+  std::vector<char> bskip;
+  // the log-likelihoods of the listed models' particles (or proposals); with moving, only of the
+  // models moving[m] marks: the batched launch keeps every listed model and skips the tiles of
+  // the others, so that its work decomposition, and with it the rounding of every model's
+  // sums, stays that of the phase's first step (and of the captured phase)
+  auto evaluate = [&](const std::vector<int>& list, bool proposals, const std::vector<char>* moving) -> sps_status {
+    bk.clear(); bP.clear(); bt.clear(); bth.clear(); bll.clear(); bskip.clear();
     for (int m : list) {
       sps_state* st = models.v[m].st;
       const double* th = proposals ? st->theta_prop.as<double>() : st->theta.as<double>();
       double* ll = proposals ? st->ll_prop.as<double>() : st->ll.as<double>();
+      const bool mv = !moving || (*moving)[m];
       if (in_batch[m]) {
         bk.push_back(k_models[m]);
         bP.push_back(st->P);
         bt.push_back(st->t);
         bth.push_back(th);
         bll.push_back(ll);
-      } else {
+        bskip.push_back(mv ? 0 : 1);
+      } else if (mv) {
         sps_ctx* c = models.v[m].c;
         const sps_status e = loglik_dispatch(c, th, st->P, st->t, ll, ctx->opt.precision);
         if (e != SPS_OK) return pass(c, e);
@@ -2480,11 +2813,12 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
     }
     if (bk.empty()) return SPS_OK;
     return loglik_split_batched(ctx, static_cast<int>(bk.size()), bk.data(), bP.data(), bt.data(), bth.data(),
-                                bll.data());
+                                bll.data(), bskip.data());
   };
   const sps_options& o = ctx->opt;
-  DevBuf jobs_dev;
+  DevBuf jobs_dev, ctl_buf;
   SPS_CUDA_TRY(jobs_dev.reserve(sizeof(CholJob) * static_cast<size_t>(M)));
+  bool use_graph = o.graphs != 0;
   while (true) {
     std::vector<int> active;
     for (int m = 0; m < M; ++m)
@@ -2511,13 +2845,15 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
       }
     } else {
       for (int m : active) in_batch[m] = split;
-      SPS_TRY(evaluate(active, false));   // cached log-likelihoods with the proposals' function
+      SPS_TRY(evaluate(active, false, nullptr));   // cached log-likelihoods with the proposals' function
       for (int m : active) {
         models.v[m].st->ll_stale = false;
         models.v[m].st->ll_kind = split ? 0 : 1;
       }
     }
     std::vector<int> run = active, r(M, 0);
+    std::vector<char> moving(M, 0);
+    for (int m : active) moving[m] = 1;
     std::vector<double> hs(M);
     std::vector<uint64_t> steps(M);
     std::vector<CholJob> jobs;
@@ -2564,7 +2900,7 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
                                               md.st->lp_prop.as<double>());
           if (e != SPS_OK) return pass(md.c, e);
         }
-        SPS_TRY(evaluate(run, true));
+        SPS_TRY(evaluate(active, true, &moving));
         // every model's decisions and read-back enqueued, then one synchronisation
         for (int m : run) {
           Model& md = models.v[m];
@@ -2584,8 +2920,31 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
         ++r[m];
         const double K = (md.st->t >= n) ? o.rne_final : o.rne_cycle;
         if (!(info.rne_min >= K || r[m] >= o.r_max)) next.push_back(m);
+        else moving[m] = 0;
       }
       run.swap(next);
+      if (use_graph && !run.empty()) {
+        // the rest of the phase as one graph launch
+        std::vector<sps_ctx*> pc;
+        std::vector<sps_state*> ps;
+        std::vector<char> pm, pb;
+        std::vector<int> pr;
+        for (int m : active) {
+          pc.push_back(models.v[m].c);
+          ps.push_back(models.v[m].st);
+          pm.push_back(moving[m]);
+          pb.push_back(in_batch[m] && !mala);
+          pr.push_back(r[m]);
+        }
+        bool fallback = false;
+        SPS_TRY(batched_mphase_graph(ctx, pc, ps, pm, pb, ctx->opt.mkernel, pr, ctl_buf, &fallback));
+        if (!fallback) {
+          for (size_t i = 0; i < active.size(); ++i) r[active[i]] = pr[i];
+          run.clear();
+        } else {
+          use_graph = false;
+        }
+      }
     }
     for (int m : active) models.v[m].steps += r[m];
   }

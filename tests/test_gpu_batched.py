@@ -131,3 +131,32 @@ def test_batched_small_nested_case_against_oracle(cuda):
                        np.random.Generator(np.random.PCG64(23 + km)))
         comb = math.hypot(r.log_ml_nse, o.log_ml_nse)
         assert abs(r.log_ml - o.log_ml) < 4 * max(comb, 1e-3), (km, r.log_ml, o.log_ml, comb)
+
+
+def _batched(X, y, C, ks, J, N, graphs, **kw):
+    from paper_1304_4333_b300 import Sps
+    s = Sps(X, y, C, prior_sd=5.0, seed=31, graphs=graphs, **kw)
+    try:
+        return s.run_batched(ks, J, N)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("C,prec,mkernel", [(2, "split", "rw"), (3, "split", "rw"), (2, "fp32", "rw"),
+                                            (3, "split", "mala")])
+def test_batched_graph_phases_identical_to_host_steps(cuda, C, prec, mkernel):
+    # the captured lockstep M phases (per-model conditional nodes, one batched evaluation per step,
+    # device-side step-size and stopping rules) take the same decisions with the same rounding as
+    # the host-driven lockstep loop: every output of every model is bit for bit the same
+    X, y = _nested_case(n=300, k=5, C=C, seed=40 + C)
+    ks = [1, 3, 5]
+    g = _batched(X, y, C, ks, 8, 256, 1, precision=prec, mkernel=mkernel)
+    h = _batched(X, y, C, ks, 8, 256, 0, precision=prec, mkernel=mkernel)
+    for a, b in zip(g, h):
+        assert a.n_cycles == b.n_cycles and a.m_steps == b.m_steps
+        np.testing.assert_array_equal(a.log_ml_group, b.log_ml_group)
+        for f in ("mean", "sd", "nse", "rne"):
+            np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+        assert b.graph_steps == 0
+    # most steps ran inside the graphs (every phase's first step runs on the host)
+    assert sum(a.graph_steps for a in g) > 0.5 * sum(a.m_steps for a in g)

@@ -340,3 +340,58 @@ def test_cycle_without_host_outputs_is_bitwise_the_same(cuda, kernel):
         ga, gb = a.get(), b.get()
         for key in ("theta", "ll"):
             np.testing.assert_array_equal(ga[key], gb[key])
+
+
+def _mnl_case(n=600, k=4, C=3, seed=61):
+    g = np.random.Generator(np.random.PCG64(seed))
+    X = g.standard_normal((n, k))
+    X[:, 0] = 1.0
+    beta = 0.5 * g.standard_normal((k, C - 1))
+    eta = np.concatenate([np.zeros((n, 1)), X @ beta], axis=1)
+    y = np.argmax(eta + g.gumbel(size=eta.shape), axis=1).astype(np.int32)
+    return X, y
+
+
+@pytest.mark.parametrize("C", [2, 3])
+def test_step_rules_and_outputs_on_identical_inputs(cuda, C):
+    # the library's acceptance rate, step-size rule and RNE of one M step (Algorithm 2 step
+    # 2(c)ii-iii), and the run outputs of a state (Eqs. 5-7, 10, 15 and the log ML of the groups),
+    # against the oracle's functions applied to the same particles and log-likelihoods
+    if C == 2:
+        w = synthetic.make_c1()
+        X, y = w.X, w.y
+    else:
+        X, y = _mnl_case()
+    J, N = 8, 256
+    s = _ctx(X, y, C)
+    st = s.state(J, N, seed=19)
+    theta0 = st.get()["theta"]
+    t_new, _, inc = st.cphase()
+    st.sphase()
+    before = st.get()
+    info = st.mstep("rw")
+    after = st.get()
+    moved = np.any(after["theta"] != before["theta"], axis=1)
+    assert info["accept"] == moved.mean()
+    assert 0.0 < info["accept"] < 1.0
+    assert info["h_next"] == OS.next_h(info["h"], info["accept"], OS.SpsOptions())
+    xbar = X.mean(axis=0)
+    mon = OS.group_moments(OS.monitoring_values(after["theta"], after["ll"], xbar, C), J, N)
+    assert info["rne_min"] == pytest.approx(mon.rne.min(), rel=1e-9)
+    r = st.result()
+    g = np.concatenate([after["theta"], OS.monitoring_values(after["theta"], after["ll"], xbar, C)[:, 1:]], axis=1)
+    mom = OS.group_moments(g, J, N)
+    np.testing.assert_allclose(r.mean, mom.mean, rtol=1e-12, atol=1e-14)
+    for f in ("sd", "nse", "rne"):
+        np.testing.assert_allclose(getattr(r, f), getattr(mom, f), rtol=1e-9)
+    # the groups' log ML after one cycle: the C phase's increments, which follow the oracle's
+    # C phase on the same initial particles (FP32 terms: 1e-5)
+    np.testing.assert_array_equal(r.log_ml_group, inc)
+    _, logw_o, _ = OS.cphase(X, y, C, theta0, 0, J, N)
+    want = np.array([OS.log_mean_exp(logw_o[j * N:(j + 1) * N]) for j in range(J)])
+    np.testing.assert_allclose(r.log_ml_group, want, rtol=1e-5, atol=1e-5)
+    assert r.log_ml == pytest.approx(inc.mean(), rel=1e-14)
+    assert r.log_ml_nse == pytest.approx(inc.std(ddof=1) / np.sqrt(J), rel=1e-12)
+    assert r.log_ml_pooled == pytest.approx(inc.max() + np.log(np.mean(np.exp(inc - inc.max()))), rel=1e-12)
+    assert r.n_cycles == 1 and r.m_steps == 1
+    s.close()

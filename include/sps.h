@@ -396,10 +396,13 @@ sps_status sps_run(sps_ctx* ctx, int32_t groups, int32_t particles_per_group,
  * MALA: each model's own gradient launch, which also gives the log-likelihoods. A model that
  * has met its stopping rule leaves the phase: its kernels stop and the batched launch skips its
  * particle tiles (keeping the launch's work decomposition, so each model's sums round the same
- * way in every step). With options.graphs, each phase after its first step is one CUDA graph
- * launch: a conditional loop whose body holds each moving model's kernels under conditional
- * nodes of its own (the models' kernels run concurrently), the batched launch between them and
- * device-side step-size and RNE rules per model; the results are identical to graphs = 0.
+ * way in every step). With options.graphs, a cycle is two CUDA graph launches: the C and S
+ * phases of all models (a conditional loop over C-phase blocks with the ESS stopping rule and
+ * the next block decided on the device, each model under conditional nodes of its own, then
+ * the S phases), and, after the M phase's first step, the rest of the lockstep M phase (a
+ * conditional loop whose body holds each moving model's kernels under its own conditional
+ * nodes, the batched launch between them and device-side step-size and RNE rules per model).
+ * The models' kernels run concurrently; the results are identical to graphs = 0.
  * Marginal likelihoods for comparing the models (Sec. 2.3) are in out[m].log_ml.
  *   out: [M] caller-allocated results as for sps_run (log_pred ignored).
  * A model's error is returned with its message. */

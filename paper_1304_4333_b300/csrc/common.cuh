@@ -121,6 +121,22 @@ struct StepCtl {
   int err;
 };
 
+// Device-resident control of a captured C phase (one per state): the block of observations in
+// progress, decided on the device from the ESS of the previous block's rows.
+struct CphaseCtl {
+  int64_t range[2];   // observations [s, s + b) of the block in progress
+  int64_t block;      // rows of that block before the cap at the data's end (doubles up to max_rows)
+  int64_t max_rows;
+  int64_t n;
+  int64_t P;
+  int64_t t_new;      // the phase's end, once done
+  int64_t row;        // the block row that the advance step reads
+  int64_t blocks;     // blocks run
+  double frac;        // ESS fraction of the stopping rule
+  int done;
+  int err;
+};
+
 // Incremented by every device-buffer (re)allocation: a captured graph whose generation differs
 // may point at freed memory and is captured again.
 uint64_t buffer_generation();
@@ -279,9 +295,10 @@ sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out)
 void hot_begin(sps_ctx* ctx);
 void hot_end(sps_ctx* ctx);
 // C-phase running log weights for observations [s_lo, s_hi): d_lw[j*P + p] = d_lw_in[p] plus the
-// terms of observations s_lo..s_lo+j, as Kahan pairs (s, c) of value s - c.
+// terms of observations s_lo..s_lo+j, as Kahan pairs (s, c) of value s - c. With d_range the
+// block is [d_range[0], d_range[1]) read on the device (s_lo, s_hi ignored).
 sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
-                             int64_t s_hi, const float2* d_lw_in, float2* d_lw);
+                             int64_t s_hi, const float2* d_lw_in, float2* d_lw, const int64_t* d_range = nullptr);
 // Log-likelihood and gradient (FP32 products, FP64 sums across 32-observation tiles).
 // Log-likelihood and gradient with the tensor cores (split precision; C - 1 <= 2 and covariate
 // widths whose gradient accumulators fit TMEM); SPS_ERR_UNSUPPORTED otherwise, nothing launched.

@@ -59,8 +59,14 @@ __global__ void __launch_bounds__(kP)
 fp32_terms_kernel(const double* __restrict__ theta, int64_t P, int k, int NC,
                   const float* __restrict__ X, const int* __restrict__ y, int64_t s_begin,
                   int64_t s_end, int64_t chunk, int mode, double* __restrict__ out,
-                  float2* __restrict__ lw_out, const float2* __restrict__ lw_in) {
+                  float2* __restrict__ lw_out, const float2* __restrict__ lw_in,
+                  const int64_t* __restrict__ range) {
   extern __shared__ float smf[];
+  if (range) {   // a C-phase block whose observations [range[0], range[1]) are decided on the device
+    s_begin = range[0];
+    s_end = range[1];
+    chunk = s_end - s_begin;
+  }
   const int D = k * NC;
   float* th = smf;                          // [D][128]
   float* xs = th + D * kP;                  // [kTS][k]
@@ -113,9 +119,15 @@ template <int KMAX, int NC>
 __global__ void __launch_bounds__(kP)
 fp32_terms_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const float* __restrict__ X,
                       const int* __restrict__ y, int64_t s_begin, int64_t s_end, int64_t chunk, int mode,
-                      double* __restrict__ out, float2* __restrict__ lw_out, const float2* __restrict__ lw_in) {
+                      double* __restrict__ out, float2* __restrict__ lw_out, const float2* __restrict__ lw_in,
+                      const int64_t* __restrict__ range) {
   __shared__ __align__(16) float xs[kTS][KMAX];
   __shared__ int ys[kTS];
+  if (range) {
+    s_begin = range[0];
+    s_end = range[1];
+    chunk = s_end - s_begin;
+  }
   const int D = k * NC;
   const int64_t p = static_cast<int64_t>(blockIdx.x) * kP + threadIdx.x;
   const int64_t s_lo = s_begin + static_cast<int64_t>(blockIdx.y) * chunk;
@@ -172,14 +184,15 @@ fp32_terms_reg_kernel(const double* __restrict__ theta, int64_t P, int k, const 
 
 // Launch the register variant when the model fits one of its instantiations.
 bool launch_reg(sps_ctx* ctx, dim3 grid, const double* theta, int64_t P, int64_t s_begin, int64_t s_end,
-                int64_t chunk, int mode, double* out, float2* lw_out, const float2* lw_in) {
+                int64_t chunk, int mode, double* out, float2* lw_out, const float2* lw_in,
+                const int64_t* range = nullptr) {
   const int k = ctx->k, NC = ctx->NC;
   const float* X = ctx->Xf.as<float>();
   const int* y = ctx->y.as<int>();
 #define SPS_REG_CASE(KM, NCM)                                                                          \
   if (NC == NCM && k <= KM) {                                                                          \
     fp32_terms_reg_kernel<KM, NCM><<<grid, kP, 0, ctx->stream>>>(theta, P, k, X, y, s_begin, s_end, chunk, \
-                                                                 mode, out, lw_out, lw_in);            \
+                                                                 mode, out, lw_out, lw_in, range);     \
     ++ctx->launches;                                                                                   \
     return true;                                                                                       \
   }
@@ -231,7 +244,7 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
                                       static_cast<int>(smem)));
     fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
                                                        ctx->y.as<int>(), 0, t, chunk, 0, partial, nullptr,
-                                                       nullptr); ++ctx->launches;
+                                                       nullptr, nullptr); ++ctx->launches;
   }
   SPS_CUDA_TRY(cudaGetLastError());
   sum_slices_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(
@@ -241,18 +254,18 @@ sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t
 }
 
 sps_status cphase_increments(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t s_lo,
-                             int64_t s_hi, const float2* d_lw_in, float2* d_lw) {
+                             int64_t s_hi, const float2* d_lw_in, float2* d_lw, const int64_t* d_range) {
   const size_t smem = fp32_smem(ctx->k, ctx->NC);
   if (ctx->NC > kMaxNC || smem > 200 * 1024)
     return fail(ctx, SPS_ERR_UNSUPPORTED, "C phase: k*(C-1) too large");
   const int64_t ptiles = (P + kP - 1) / kP;
   dim3 grid(static_cast<unsigned>(ptiles), 1);
-  if (!launch_reg(ctx, grid, d_theta, P, s_lo, s_hi, s_hi - s_lo, 1, nullptr, d_lw, d_lw_in)) {
+  if (!launch_reg(ctx, grid, d_theta, P, s_lo, s_hi, s_hi - s_lo, 1, nullptr, d_lw, d_lw_in, d_range)) {
     SPS_CUDA_TRY(cudaFuncSetAttribute(fp32_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem)));
     fp32_terms_kernel<<<grid, kP, smem, ctx->stream>>>(d_theta, P, ctx->k, ctx->NC, ctx->Xf.as<float>(),
                                                        ctx->y.as<int>(), s_lo, s_hi, s_hi - s_lo, 1, nullptr,
-                                                       d_lw, d_lw_in); ++ctx->launches;
+                                                       d_lw, d_lw_in, d_range); ++ctx->launches;
   }
   SPS_CUDA_TRY(cudaGetLastError());
   return SPS_OK;

@@ -523,9 +523,9 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           const float lsum = (la.x + la.y) + (lb.x + lb.y);
           tile_val = fmaf(0.5f, lsum, ptx::lg2_approx(pa.x * pa.y) + ptx::lg2_approx(pb.x * pb.y));
         } else {
-          // four chains: sums of the shifts m and products of the shifted sums (< NC + 1 <= 4
-          // each), binary exponents moved to an integer every eight 16-column reads (at most 32
-          // factors per chain in between)
+          // four chains: sums of the shifts m and products of the sums 1 + sum_c 2^u_c (or, for
+          // a chunk where that overflows, of the shifted sums, < NC + 1 <= 4 each), binary
+          // exponents moved to an integer after every 16-column read
           float la[4] = {0.f, 0.f, 0.f, 0.f};
           float pr[4] = {1.f, 1.f, 1.f, 1.f};
           int pexp = 0;
@@ -546,19 +546,23 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             ptx::tmem_wait_ld();
             if (ch == NCH16 - 1) release();
             const int j0 = ch * 16;
-            if (whole) {
+            const int lim = whole ? 16 : valid - j0;   // columns of this chunk inside [0, t)
+            // direct form: sx = 1 + sum_c 2^u_c, no shift, while no factor or product overflows
+            // (|u| below about 30 for every particle near the posterior); the product chains
+            // start each chunk in [1, 2), so an overflow shows as an infinite chain
+            float pf[4] = {pr[0], pr[1], pr[2], pr[3]};
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                float m = 0.f;
+            for (int j = 0; j < 16; ++j) {
+              float sx = 1.f;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) m = fmaxf(m, v[c][j]);
-                float sx = ptx::ex2_approx(-m);
+              for (int c = 0; c < NC; ++c) sx += ptx::ex2_approx(v[c][j]);
+              pf[j & 3] *= (j < lim) ? sx : 1.f;
+            }
+            if ((pf[0] + pf[1]) + (pf[2] + pf[3]) < INFINITY) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) sx += ptx::ex2_approx(v[c][j] - m);
-                la[j & 3] += m;
-                pr[j & 3] *= sx;
-              }
+              for (int q = 0; q < 4; ++q) pr[q] = pf[q];
             } else {
+              // shifted form, log2 sum_c 2^u_c = m + log2 sum_c 2^(u_c - m), m = max(0, u_c)
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
                 float m = 0.f;
@@ -567,14 +571,13 @@ loglik_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 float sx = ptx::ex2_approx(-m);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) sx += ptx::ex2_approx(v[c][j] - m);
-                const bool in = (j0 + j) < valid;
+                const bool in = j < lim;
                 la[j & 3] += in ? m : 0.f;
                 pr[j & 3] *= in ? sx : 1.f;
               }
             }
-            if ((ch & 7) == 7) renorm();
+            renorm();
           }
-          renorm();
           const float pm = (pr[0] * pr[1]) * (pr[2] * pr[3]);   // product of four mantissas < 16
           const float lsum = (la[0] + la[1]) + (la[2] + la[3]);
           tile_val = (lsum + static_cast<float>(pexp)) + ptx::lg2_approx(pm);

@@ -222,10 +222,13 @@ __device__ float block_max_f(float v, float* sh) {
 // The merge rescales the parts to the row maximum and returns (sum e)^2 / sum e^2.
 constexpr int kEssParts = 8;
 
+// range (optional): a C-phase block decided on the device; rows past its length are skipped.
 template <class InT>
-__global__ void ess_part_kernel(const InT* __restrict__ lw, int64_t P, double* __restrict__ parts) {
+__global__ void ess_part_kernel(const InT* __restrict__ lw, int64_t P, double* __restrict__ parts,
+                                const int64_t* __restrict__ range) {
   __shared__ float shf[33];
   __shared__ double sh[33];
+  if (range && static_cast<int64_t>(blockIdx.x) >= range[1] - range[0]) return;
   const InT* row = lw + static_cast<int64_t>(blockIdx.x) * P;
   const int64_t per = (P + gridDim.y - 1) / gridDim.y;
   const int64_t lo = blockIdx.y * per, hi = min(P, lo + per);
@@ -254,8 +257,10 @@ __global__ void ess_part_kernel(const InT* __restrict__ lw, int64_t P, double* _
   }
 }
 
-__global__ void ess_merge_kernel(const double* __restrict__ parts, int rows, int nparts, double* __restrict__ ess) {
+__global__ void ess_merge_kernel(const double* __restrict__ parts, int rows, int nparts, double* __restrict__ ess,
+                                 const int64_t* __restrict__ range) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (range) rows = static_cast<int>(range[1] - range[0]);
   if (r >= rows) return;
   const double* q = parts + static_cast<int64_t>(r) * nparts * 3;
   float M = -INFINITY;
@@ -269,6 +274,62 @@ __global__ void ess_merge_kernel(const double* __restrict__ parts, int rows, int
     s2 += f * f * q[3 * i + 2];
   }
   ess[r] = (s2 > 0.0) ? s1 * s1 / s2 : 0.0;
+}
+
+// The stopping rule of a captured C phase (Algorithm 2 step 1, as cphase_impl applies it on the
+// host): the first row j of the block with ESS / P below the fraction, or the data's last
+// observation, ends the phase at t = s + j + 1 (row j is read into the log weights); otherwise
+// the last row becomes the running state and the next block, of twice the rows up to max_rows,
+// starts at s + b. Sets the model's conditional node (another block while not done). One thread.
+__global__ void cphase_scan_kernel(CphaseCtl* __restrict__ cc, const double* __restrict__ ess,
+                                   cudaGraphConditionalHandle more) {
+  const int64_t s = cc->range[0], b = cc->range[1] - cc->range[0];
+  int done = 0;
+  for (int64_t j = 0; j < b; ++j) {
+    const int64_t sj = s + j + 1;
+    if (ess[j] / static_cast<double>(cc->P) < cc->frac || sj == cc->n) {
+      cc->row = j;
+      cc->t_new = sj;
+      done = 1;
+      break;
+    }
+  }
+  cc->blocks += 1;
+  if (!done) {
+    cc->row = b - 1;
+    const int64_t s2 = s + b;
+    const int64_t blk = (cc->block * 2 < cc->max_rows) ? cc->block * 2 : cc->max_rows;
+    cc->block = blk;
+    cc->range[0] = s2;
+    cc->range[1] = s2 + ((blk < cc->n - s2) ? blk : cc->n - s2);
+  }
+  cc->done = done;
+  cudaGraphSetConditional(more, done ? 0u : 1u);
+}
+
+// After the scan: the stop row to FP64 log weights (as lw_to_f64_kernel), else the block's last
+// row to the running state (as the host's device-to-device copy).
+__global__ void cphase_advance_kernel(const CphaseCtl* __restrict__ cc, const float2* __restrict__ rows, int64_t P,
+                                      float2* __restrict__ lwstate, double* __restrict__ logw) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= P) return;
+  const float2 v = rows[cc->row * P + p];
+  if (cc->done) logw[p] = f32_to_f64(v.x) - f32_to_f64(v.y);
+  else lwstate[p] = v;
+}
+
+// Loop condition of the captured C phases of several models: another block while any model's
+// phase goes on. cc[M] counts the loop's iterations: at its max_rows (a bound no data reaches)
+// the loop ends with err = 1.
+__global__ void cphase_continue_kernel(CphaseCtl* __restrict__ cc, int M, cudaGraphConditionalHandle cond) {
+  int any = 0;
+  for (int m = 0; m < M; ++m) any |= cc[m].done ? 0 : 1;
+  const int64_t it = ++cc[M].row;
+  if (any && it >= cc[M].max_rows) {
+    cc[M].err = 1;
+    any = 0;
+  }
+  cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
 // logw[p] = value of the Kahan pair row[p] in FP64.
@@ -2258,21 +2319,49 @@ sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, c
 // the first s with ESS / P below the threshold (or at t_target / n); then the per-group log
 // marginal-likelihood increments and the cached log-likelihood at the new t. One synchronisation
 // per block, plus one to return the increments when lme_out is given.
+// C-phase block rows: at most 1024 and 2^25 running weights.
+static int64_t cphase_max_rows(int64_t P) { return std::max<int64_t>(1, std::min<int64_t>(1024, (int64_t{1} << 25) / P)); }
+static int64_t cphase_first_block(const sps_ctx* ctx, int64_t max_rows) {
+  return std::max<int64_t>(1, std::min<int64_t>(ctx->opt.cphase_block > 0 ? ctx->opt.cphase_block : 64, max_rows));
+}
+
+// The C phase's buffers: block rows of running weights, the running state, the rows' ESS (plus
+// one slot that keeps the ESS at the stop row of a known-target C phase), group maxima.
+static sps_status cphase_reserve(sps_ctx* ctx, sps_state* st, bool lpl) {
+  const int64_t P = st->P, max_rows = cphase_max_rows(P);
+  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(float2) * max_rows * P));
+  SPS_CUDA_TRY(st->lwstate.reserve(sizeof(float2) * P));
+  const int64_t ess_slot = std::max<int64_t>(max_rows, st->J);
+  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * (ess_slot + 1)));
+  SPS_CUDA_TRY(st->gmax.reserve(sizeof(double) * st->J));
+  if (lpl) SPS_CUDA_TRY(st->lpl_dev.reserve(sizeof(double) * max_rows * st->J));
+  return SPS_OK;
+}
+
+// After the stop row: the log marginal likelihood increment per group (added to the state's
+// log ML), the group maxima, and the cached log-likelihood advanced by the log weights.
+static sps_status cphase_tail(sps_ctx* ctx, sps_state* st) {
+  group_lme_part_kernel<<<dim3(st->J, kLmeParts), 256, 0, ctx->stream>>>(st->logw.as<double>(), st->N,
+                                                                         st->scratch.as<double>()); ++ctx->launches;
+  group_lme_merge_kernel<<<(st->J + 63) / 64, 64, 0, ctx->stream>>>(st->scratch.as<double>(), st->J, kLmeParts, st->N,
+                                                                    st->ess_buf.as<double>(), st->logml.as<double>(),
+                                                                    st->gmax.as<double>()); ++ctx->launches;
+  add_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(st->ll.as<double>(),
+                                                                                   st->logw.as<double>(), st->P);
+  ++ctx->launches;
+  SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
 sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t_new, double* ess_out,
                        double* lme_out, double* lpl_out) {
   const int64_t n = ctx->n, P = st->P;
   if (st->t >= n) return fail(ctx, SPS_ERR_STATE, "C phase: no observations left");
   if (t_target > 0 && (t_target <= st->t || t_target > n)) return fail(ctx, SPS_ERR_INVALID_ARG, "C phase: bad t_target");
-  const int64_t max_rows = std::max<int64_t>(1, std::min<int64_t>(1024, (int64_t{1} << 25) / P));
-  int64_t block = std::max<int64_t>(1, std::min<int64_t>(ctx->opt.cphase_block > 0 ? ctx->opt.cphase_block : 64, max_rows));
-  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(float2) * max_rows * P));
-  SPS_CUDA_TRY(st->lwstate.reserve(sizeof(float2) * P));
-  // ESS of the rows of a block (the group log-mean-exp increments after the loop), plus one slot
-  // that keeps the ESS at the stop row of a known-target C phase
+  const int64_t max_rows = cphase_max_rows(P);
+  int64_t block = cphase_first_block(ctx, max_rows);
+  SPS_TRY(cphase_reserve(ctx, st, lpl_out != nullptr));
   const int64_t ess_slot = std::max<int64_t>(max_rows, st->J);
-  SPS_CUDA_TRY(st->ess_buf.reserve(sizeof(double) * (ess_slot + 1)));
-  SPS_CUDA_TRY(st->gmax.reserve(sizeof(double) * st->J));
-  if (lpl_out) SPS_CUDA_TRY(st->lpl_dev.reserve(sizeof(double) * max_rows * st->J));
   SPS_CUDA_TRY(cudaMemsetAsync(st->lwstate.ptr, 0, sizeof(float2) * P, ctx->stream));
   float2* rows = st->lwbuf.as<float2>();
   int64_t s = st->t;
@@ -2287,9 +2376,9 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
     const int64_t b = known ? std::min<int64_t>(block, t_target - s) : std::min<int64_t>(block, n - s);
     SPS_TRY(cphase_increments(ctx, st->theta.as<double>(), P, s, s + b, st->lwstate.as<float2>(), rows));
     ess_part_kernel<float2><<<dim3(static_cast<unsigned>(b), kEssParts), 512, 0, ctx->stream>>>(
-        rows, P, st->scratch.as<double>()); ++ctx->launches;
+        rows, P, st->scratch.as<double>(), nullptr); ++ctx->launches;
     ess_merge_kernel<<<static_cast<unsigned>((b + 63) / 64), 64, 0, ctx->stream>>>(
-        st->scratch.as<double>(), static_cast<int>(b), kEssParts, st->ess_buf.as<double>()); ++ctx->launches;
+        st->scratch.as<double>(), static_cast<int>(b), kEssParts, st->ess_buf.as<double>(), nullptr); ++ctx->launches;
     if (lpl_out) {
       row_group_lme_kernel<<<dim3(static_cast<unsigned>(b), st->J), 256, 0, ctx->stream>>>(
           rows, P, st->N, st->lpl_dev.as<double>()); ++ctx->launches;
@@ -2349,14 +2438,7 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
     block = std::min<int64_t>(block * 2, max_rows);
   }
   // log marginal likelihood increment per group, group maxima, cached log-likelihood at the new t
-  group_lme_part_kernel<<<dim3(st->J, kLmeParts), 256, 0, ctx->stream>>>(st->logw.as<double>(), st->N,
-                                                                         st->scratch.as<double>()); ++ctx->launches;
-  group_lme_merge_kernel<<<(st->J + 63) / 64, 64, 0, ctx->stream>>>(st->scratch.as<double>(), st->J, kLmeParts, st->N,
-                                                                    st->ess_buf.as<double>(), st->logml.as<double>(),
-                                                                    st->gmax.as<double>()); ++ctx->launches;
-  add_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, ctx->stream>>>(st->ll.as<double>(),
-                                                                               st->logw.as<double>(), P); ++ctx->launches;
-  SPS_CUDA_TRY(cudaGetLastError());
+  SPS_TRY(cphase_tail(ctx, st));
   if (known && ess_out) {
     SPS_CUDA_TRY(cudaMemcpyAsync(&ess_found, st->ess_buf.as<double>() + ess_slot, sizeof(double),
                                  cudaMemcpyDeviceToHost, ctx->stream));
@@ -2376,11 +2458,10 @@ sps_status cphase_impl(sps_ctx* ctx, sps_state* st, int64_t t_target, int64_t* t
 
 // S phase (Algorithm 1 step 2(b)): quantised weights, per-group integer-CDF draws, gather.
 // The C-phase row buffer holds the quantised weights (uint64 [P]) here.
-sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_idx_out, int* h_idx_out = nullptr) {
-  if (!st->have_weights) return fail(ctx, SPS_ERR_STATE, "S phase before a C phase");
+// The S phase's kernels (Philox step word `step` unless uniforms d_u are given): counters cleared,
+// quantised weights, per-group draws, the gathered particles into the proposal buffers.
+static sps_status sphase_issue(sps_ctx* ctx, sps_state* st, const double* d_u, uint64_t step) {
   SPS_CUDA_TRY(cudaMemsetAsync(st->counters.ptr, 0, sizeof(Counters), ctx->stream));
-  const uint64_t step = ++st->cycle_counter;
-  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(unsigned long long) * st->P));
   unsigned long long* q = st->lwbuf.as<unsigned long long>();
   resample_q_kernel<<<static_cast<unsigned>((st->P + 255) / 256), 256, 0, ctx->stream>>>(
       st->logw.as<double>(), 0, st->N, st->P, st->gmax.as<double>(), q); ++ctx->launches;
@@ -2390,6 +2471,23 @@ sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_id
       st->theta.as<double>(), st->ll.as<double>(), st->lp.as<double>(), st->idx.as<int>(), st->P, st->N, ctx->D,
       st->theta_prop.as<double>(), st->ll_prop.as<double>(), st->lp_prop.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
+  return SPS_OK;
+}
+
+// After the S phase's kernels ran: the gathered particles become the state's.
+static void sphase_commit(sps_state* st) {
+  swapbuf(st->theta, st->theta_prop);
+  swapbuf(st->ll, st->ll_prop);
+  swapbuf(st->lp, st->lp_prop);
+  st->have_weights = false;
+  st->grad_valid = false;   // gradients are not gathered
+}
+
+sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_idx_out, int* h_idx_out = nullptr) {
+  if (!st->have_weights) return fail(ctx, SPS_ERR_STATE, "S phase before a C phase");
+  SPS_CUDA_TRY(st->lwbuf.reserve(sizeof(unsigned long long) * st->P));
+  const uint64_t step = ++st->cycle_counter;
+  SPS_TRY(sphase_issue(ctx, st, d_u, step));
   if (d_idx_out)
     SPS_CUDA_TRY(cudaMemcpyAsync(d_idx_out, st->idx.ptr, sizeof(int) * st->P, cudaMemcpyDeviceToDevice, ctx->stream));
   if (h_idx_out)   // completes with the counters' synchronisation below
@@ -2397,11 +2495,220 @@ sps_status sphase_impl(sps_ctx* ctx, sps_state* st, const double* d_u, int* d_id
   Counters c;
   SPS_TRY(read_counters(ctx, st, &c));
   if (c.res_bad) return fail(ctx, SPS_ERR_DEGENERATE, "all resampling weights of a group vanished");
-  swapbuf(st->theta, st->theta_prop);
-  swapbuf(st->ll, st->ll_prop);
-  swapbuf(st->lp, st->lp_prop);
-  st->have_weights = false;
-  st->grad_valid = false;   // gradients are not gathered
+  sphase_commit(st);
+  return SPS_OK;
+}
+
+// The C and S phases of several models (a cycle of a batched run, Algorithm 1 steps 2(a)-(b)) as
+// one graph launch: per model the running weights cleared, then a conditional WHILE node whose
+// body holds, per model, a conditional IF node around one C-phase block (running weights of the
+// block's observations, their ESS, cphase_scan_kernel, which applies the stopping rule and
+// picks the next block, and cphase_advance_kernel), then per model the C phase's tail (log ML
+// increments, cached log-likelihood) and the S phase's kernels. The same kernels and decisions
+// as cphase_impl and sphase_impl, without their host round trips; the models' branches run
+// concurrently. Captured for each cycle (the Philox step words and buffers change); the host
+// synchronises once. *fallback: the graph could not be built and nothing ran.
+sps_status batched_cs_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, const std::vector<sps_state*>& ss,
+                            DevBuf& cc_buf, bool* fallback) {
+  *fallback = false;
+  auto give_up = [&](const char* what, cudaError_t e) {
+    ctx->last_error = std::string("batched C/S-phase graph not used: ") + what +
+                      (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : std::string());
+    cudaGetLastError();
+    *fallback = true;
+    return SPS_OK;
+  };
+  const int Mp = static_cast<int>(cs.size());
+  for (int i = 0; i < Mp; ++i) {
+    if (ss[i]->t >= cs[i]->n) return fail(ctx, SPS_ERR_STATE, "C phase: no observations left");
+    SPS_TRY(cphase_reserve(cs[i], ss[i], false));
+    SPS_CUDA_TRY(ss[i]->lwbuf.reserve(sizeof(unsigned long long) * ss[i]->P));
+  }
+  SPS_CUDA_TRY(cc_buf.reserve(sizeof(CphaseCtl) * static_cast<size_t>(Mp + 1)));
+  if (!ctx->cap_stream) {
+    const cudaError_t ec = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (ec != cudaSuccess) {
+      ctx->cap_stream = nullptr;
+      return give_up("capture stream", ec);
+    }
+  }
+  CphaseCtl* d_cc = cc_buf.as<CphaseCtl>();
+  std::vector<CphaseCtl> hc(static_cast<size_t>(Mp + 1));
+  int64_t iter_cap = 64;
+  for (int i = 0; i < Mp; ++i) {
+    const int64_t n = cs[i]->n, P = ss[i]->P, t = ss[i]->t;
+    const int64_t mr = cphase_max_rows(P), b0 = cphase_first_block(cs[i], mr);
+    CphaseCtl& c = hc[i];
+    c = CphaseCtl{};
+    c.range[0] = t;
+    c.range[1] = t + std::min<int64_t>(b0, n - t);
+    c.block = b0;
+    c.max_rows = mr;
+    c.n = n;
+    c.P = P;
+    c.frac = cs[i]->opt.ess_fraction;
+    iter_cap = std::max<int64_t>(iter_cap, (n - t) / b0 + 64);   // every block takes at least b0 rows
+  }
+  hc[Mp] = CphaseCtl{};
+  hc[Mp].max_rows = iter_cap;
+  const uint64_t gen = buffer_generation();
+
+  cudaGraph_t g = nullptr;
+  SPS_CUDA_TRY(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+  } guard{g};
+  std::string cap_error;
+  // what issue() launches on the context c, recorded on the capture stream into `into`
+  auto record = [&](cudaGraph_t into, sps_ctx* c, const std::function<sps_status()>& issue) -> cudaError_t {
+    cudaError_t ee = cudaStreamBeginCaptureToGraph(ctx->cap_stream, into, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed);
+    if (ee != cudaSuccess) return ee;
+    const cudaStream_t user = c->stream;
+    c->stream = ctx->cap_stream;
+    c->capturing = true;
+    const sps_status is = issue();
+    c->capturing = false;
+    c->stream = user;
+    cudaGraph_t out = nullptr;
+    ee = cudaStreamEndCapture(ctx->cap_stream, &out);
+    if (is != SPS_OK) {
+      cap_error = c->last_error;
+      return cudaErrorUnknown;
+    }
+    return ee;
+  };
+  // the same as a child graph node of g after deps
+  auto child = [&](const std::vector<cudaGraphNode_t>& deps, sps_ctx* c, const std::function<sps_status()>& issue,
+                   cudaGraphNode_t* node) -> cudaError_t {
+    cudaGraph_t sub = nullptr;
+    cudaError_t ee = cudaGraphCreate(&sub, 0);
+    if (ee != cudaSuccess) return ee;
+    ee = record(sub, c, issue);
+    if (ee == cudaSuccess)
+      ee = cudaGraphAddChildGraphNode(node, g, deps.empty() ? nullptr : deps.data(), deps.size(), sub);
+    cudaGraphDestroy(sub);
+    return ee;
+  };
+  cudaError_t e = cudaSuccess;
+  std::vector<cudaGraphNode_t> init(Mp);
+  for (int i = 0; i < Mp && e == cudaSuccess; ++i) {
+    sps_ctx* c = cs[i];
+    sps_state* st = ss[i];
+    e = child({}, c, [c, st]() {
+          sps_ctx* ctx = c;   // the model's context takes any error
+          SPS_CUDA_TRY(cudaMemsetAsync(st->lwstate.ptr, 0, sizeof(float2) * st->P, ctx->stream));
+          return SPS_OK;
+        }, &init[i]);
+  }
+  cudaGraphConditionalHandle wh;
+  cudaGraphNodeParams wp{};
+  cudaGraphNode_t wnode;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&wh, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = wh;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, init.data(), nullptr, init.size(), &wp);
+  }
+  std::vector<cudaGraphNode_t> ifs(Mp);
+  std::vector<int64_t> block_launches(Mp, 0), tail_launches(Mp, 0);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    for (int i = 0; i < Mp && e == cudaSuccess; ++i) {
+      sps_ctx* c = cs[i];
+      sps_state* st = ss[i];
+      CphaseCtl* cc = d_cc + i;
+      const int64_t mr = hc[i].max_rows;
+      cudaGraphConditionalHandle hi;
+      e = cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault);
+      if (e != cudaSuccess) break;
+      cudaGraphNodeParams ip{};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = hi;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      e = cudaGraphAddNode(&ifs[i], body, nullptr, nullptr, 0, &ip);
+      if (e != cudaSuccess) break;
+      const int64_t l0 = c->launches;
+      e = record(ip.conditional.phGraph_out[0], c, [c, st, cc, mr, hi]() {
+        sps_ctx* ctx = c;   // the model's context takes any error
+        const int64_t P = st->P;
+        float2* rows = st->lwbuf.as<float2>();
+        SPS_TRY(cphase_increments(c, st->theta.as<double>(), P, 0, 0, st->lwstate.as<float2>(), rows, cc->range));
+        ess_part_kernel<float2><<<dim3(static_cast<unsigned>(mr), kEssParts), 512, 0, c->stream>>>(
+            rows, P, st->scratch.as<double>(), cc->range); ++c->launches;
+        ess_merge_kernel<<<static_cast<unsigned>((mr + 63) / 64), 64, 0, c->stream>>>(
+            st->scratch.as<double>(), static_cast<int>(mr), kEssParts, st->ess_buf.as<double>(), cc->range);
+        ++c->launches;
+        cphase_scan_kernel<<<1, 1, 0, c->stream>>>(cc, st->ess_buf.as<double>(), hi); ++c->launches;
+        cphase_advance_kernel<<<static_cast<unsigned>((P + 255) / 256), 256, 0, c->stream>>>(
+            cc, rows, P, st->lwstate.as<float2>(), st->logw.as<double>()); ++c->launches;
+        SPS_CUDA_TRY(cudaGetLastError());
+        return SPS_OK;
+      });
+      block_launches[i] = c->launches - l0;
+      c->launches = l0;
+    }
+    if (e == cudaSuccess) {
+      int Mi = Mp;
+      void* args[] = {&d_cc, &Mi, &wh};
+      cudaKernelNodeParams kp{};
+      kp.func = reinterpret_cast<void*>(cphase_continue_kernel);
+      kp.gridDim = dim3(1);
+      kp.blockDim = dim3(1);
+      kp.sharedMemBytes = 0;
+      kp.kernelParams = args;
+      cudaGraphNode_t cn;
+      e = cudaGraphAddKernelNode(&cn, body, ifs.data(), ifs.size(), &kp);
+    }
+  }
+  for (int i = 0; i < Mp && e == cudaSuccess; ++i) {
+    sps_ctx* c = cs[i];
+    sps_state* st = ss[i];
+    const uint64_t step = st->cycle_counter + 1;
+    cudaGraphNode_t tn;
+    const int64_t l0 = c->launches;
+    e = child({wnode}, c, [c, st, step]() {
+          SPS_TRY(cphase_tail(c, st));
+          return sphase_issue(c, st, nullptr, step);
+        }, &tn);
+    tail_launches[i] = c->launches - l0;
+    c->launches = l0;
+  }
+  if (e != cudaSuccess || buffer_generation() != gen) {
+    const std::string why = !cap_error.empty() ? "capture: " + cap_error
+                            : e != cudaSuccess ? std::string("graph construction") : std::string("reallocation");
+    return give_up(why.c_str(), e);
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) return give_up("instantiate", e);
+  struct ExecGuard {
+    cudaGraphExec_t x;
+    ~ExecGuard() { if (x) cudaGraphExecDestroy(x); }
+  } xguard{exec};
+  SPS_CUDA_TRY(cudaMemcpyAsync(d_cc, hc.data(), sizeof(CphaseCtl) * hc.size(), cudaMemcpyHostToDevice, ctx->stream));
+  SPS_CUDA_TRY(cudaGraphLaunch(exec, ctx->stream));
+  SPS_CUDA_TRY(cudaMemcpyAsync(hc.data(), d_cc, sizeof(CphaseCtl) * hc.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<Counters> cnt(static_cast<size_t>(Mp));
+  for (int i = 0; i < Mp; ++i)
+    SPS_CUDA_TRY(cudaMemcpyAsync(&cnt[i], ss[i]->counters.ptr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+  SPS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (hc[Mp].err) return fail(ctx, SPS_ERR_STATE, "batched C-phase graph: block loop passed its bound");
+  for (int i = 0; i < Mp; ++i) {
+    sps_ctx* c = cs[i];
+    sps_state* st = ss[i];
+    c->launches += hc[i].blocks * block_launches[i] + tail_launches[i];
+    st->t = hc[i].t_new;
+    st->ll_stale = true;
+    st->cycle_counter += 1;
+    if (cnt[i].res_bad) return fail(ctx, SPS_ERR_DEGENERATE, "model context: all resampling weights of a group vanished");
+    sphase_commit(st);
+  }
+  ctx->launches += hc[Mp].row;   // the loop's condition kernel
   return SPS_OK;
 }
 
@@ -2816,21 +3123,37 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
                                 bll.data(), bskip.data());
   };
   const sps_options& o = ctx->opt;
-  DevBuf jobs_dev, ctl_buf;
+  DevBuf jobs_dev, ctl_buf, cc_buf;
   SPS_CUDA_TRY(jobs_dev.reserve(sizeof(CholJob) * static_cast<size_t>(M)));
-  bool use_graph = o.graphs != 0;
+  bool use_graph = o.graphs != 0, use_cs_graph = o.graphs != 0;
   while (true) {
     std::vector<int> active;
     for (int m = 0; m < M; ++m)
       if (models.v[m].st->t < n) active.push_back(m);
     if (active.empty()) break;
-    // C and S phases per model (Algorithm 1 steps 2(a), 2(b))
+    // C and S phases per model (Algorithm 1 steps 2(a), 2(b)): with graphs, all models' phases in
+    // one graph launch; else one model after the other from the host
+    bool cs_done = false;
+    if (use_cs_graph) {
+      std::vector<sps_ctx*> pc;
+      std::vector<sps_state*> ps;
+      for (int m : active) {
+        pc.push_back(models.v[m].c);
+        ps.push_back(models.v[m].st);
+      }
+      bool fallback = false;
+      SPS_TRY(batched_cs_graph(ctx, pc, ps, cc_buf, &fallback));
+      cs_done = !fallback;
+      if (fallback) use_cs_graph = false;
+    }
     for (int m : active) {
       Model& md = models.v[m];
-      int64_t tn = 0;
-      sps_status e = cphase_impl(md.c, md.st, 0, &tn, nullptr, nullptr, nullptr);
-      if (e == SPS_OK) e = sphase_impl(md.c, md.st, nullptr, nullptr);
-      if (e != SPS_OK) return pass(md.c, e);
+      if (!cs_done) {
+        int64_t tn = 0;
+        sps_status e = cphase_impl(md.c, md.st, 0, &tn, nullptr, nullptr, nullptr);
+        if (e == SPS_OK) e = sphase_impl(md.c, md.st, nullptr, nullptr);
+        if (e != SPS_OK) return pass(md.c, e);
+      }
       ++md.L;
     }
     // M phases in lockstep (Algorithm 2 step 2(c)): every step of the models still moving is
@@ -3033,8 +3356,9 @@ sps_status sps_ess(sps_ctx* ctx, const double* logw, int64_t P, int32_t J, doubl
   double* pm = (mem == SPS_MEM_DEVICE && lme) ? lme : dm.as<double>();
   DevBuf dparts;
   SPS_CUDA_TRY(dparts.reserve(sizeof(double) * std::max<size_t>(3 * kEssParts, 2 * static_cast<size_t>(J) * kLmeParts)));
-  ess_part_kernel<double><<<dim3(1, kEssParts), 512, 0, ctx->stream>>>(pl, P, dparts.as<double>()); ++ctx->launches;
-  ess_merge_kernel<<<1, 64, 0, ctx->stream>>>(dparts.as<double>(), 1, kEssParts, pe); ++ctx->launches;
+  ess_part_kernel<double><<<dim3(1, kEssParts), 512, 0, ctx->stream>>>(pl, P, dparts.as<double>(), nullptr);
+  ++ctx->launches;
+  ess_merge_kernel<<<1, 64, 0, ctx->stream>>>(dparts.as<double>(), 1, kEssParts, pe, nullptr); ++ctx->launches;
   group_lme_part_kernel<<<dim3(J, kLmeParts), 256, 0, ctx->stream>>>(pl, static_cast<int>(P / J),
                                                                      dparts.as<double>()); ++ctx->launches;
   group_lme_merge_kernel<<<(J + 63) / 64, 64, 0, ctx->stream>>>(dparts.as<double>(), J, kLmeParts,

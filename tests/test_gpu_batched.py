@@ -137,7 +137,10 @@ def _batched(X, y, C, ks, J, N, graphs, **kw):
     from paper_1304_4333_b300 import Sps
     s = Sps(X, y, C, prior_sd=5.0, seed=31, graphs=graphs, **kw)
     try:
-        return s.run_batched(ks, J, N)
+        r = s.run_batched(ks, J, N)
+        # a graph that could not be built leaves its reason here (and the run continues from the host)
+        assert "not used" not in s.lib.sps_last_error(s.ctx).decode()
+        return r
     finally:
         s.close()
 
@@ -145,9 +148,10 @@ def _batched(X, y, C, ks, J, N, graphs, **kw):
 @pytest.mark.parametrize("C,prec,mkernel", [(2, "split", "rw"), (3, "split", "rw"), (2, "fp32", "rw"),
                                             (3, "split", "mala")])
 def test_batched_graph_phases_identical_to_host_steps(cuda, C, prec, mkernel):
-    # the captured lockstep M phases (per-model conditional nodes, one batched evaluation per step,
-    # device-side step-size and stopping rules) take the same decisions with the same rounding as
-    # the host-driven lockstep loop: every output of every model is bit for bit the same
+    # the captured C and S phases (device-side ESS stopping rule and block choice) and lockstep M
+    # phases (per-model conditional nodes, one batched evaluation per step, device-side step-size
+    # and stopping rules) take the same decisions with the same rounding as the host-driven
+    # loops: every output of every model is bit for bit the same
     X, y = _nested_case(n=300, k=5, C=C, seed=40 + C)
     ks = [1, 3, 5]
     g = _batched(X, y, C, ks, 8, 256, 1, precision=prec, mkernel=mkernel)

@@ -375,15 +375,22 @@ def test_step_rules_and_outputs_on_identical_inputs(cuda, C):
     assert info["accept"] == moved.mean()
     assert 0.0 < info["accept"] < 1.0
     assert info["h_next"] == OS.next_h(info["h"], info["accept"], OS.SpsOptions())
+    # the library evaluates the log-odds theta_c' xbar as an FP32 dot product (a monitoring
+    # function needs no more): 1e-7 relative per value, about 1e-6 on the moments built from them
     xbar = X.mean(axis=0)
     mon = OS.group_moments(OS.monitoring_values(after["theta"], after["ll"], xbar, C), J, N)
-    assert info["rne_min"] == pytest.approx(mon.rne.min(), rel=1e-9)
+    assert info["rne_min"] == pytest.approx(mon.rne.min(), rel=1e-5)
     r = st.result()
     g = np.concatenate([after["theta"], OS.monitoring_values(after["theta"], after["ll"], xbar, C)[:, 1:]], axis=1)
     mom = OS.group_moments(g, J, N)
-    np.testing.assert_allclose(r.mean, mom.mean, rtol=1e-12, atol=1e-14)
+    D = after["theta"].shape[1]
+    # theta's own coordinates: FP64 sums of FP64 values
+    np.testing.assert_allclose(r.mean[:D], mom.mean[:D], rtol=1e-12, atol=1e-14)
     for f in ("sd", "nse", "rne"):
-        np.testing.assert_allclose(getattr(r, f), getattr(mom, f), rtol=1e-9)
+        np.testing.assert_allclose(getattr(r, f)[:D], getattr(mom, f)[:D], rtol=1e-9)
+    np.testing.assert_allclose(r.mean[D:], mom.mean[D:], rtol=1e-6, atol=1e-7)
+    for f in ("sd", "nse", "rne"):
+        np.testing.assert_allclose(getattr(r, f)[D:], getattr(mom, f)[D:], rtol=1e-5)
     # the groups' log ML after one cycle: the C phase's increments, which follow the oracle's
     # C phase on the same initial particles (FP32 terms: 1e-5)
     np.testing.assert_array_equal(r.log_ml_group, inc)

@@ -478,6 +478,41 @@ def run_loglik_only(args):
     s.close()
 
 
+def run_phase_kernels(args):
+    """Profiling entry for the simulator's other kernels: `--calls` cycles on the named workload's
+    J x N particles (around the true coefficients, near the end of its data): C phase over 64
+    observations, S phase, one random-walk and one MALA M step, then one standalone Philox
+    generation of P x D / 4 words; after one untimed cycle. Prints the wall time per phase
+    (host clock around a synchronised call) for the timed cycles."""
+    import torch
+    import synthetic
+    from paper_1304_4333_b300 import Sps
+    torch.cuda.set_device(0)
+    w = synthetic.make_workload(args.phase_kernels)
+    s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=1)
+    st = s.state(w.J, w.N, seed=100)
+    t0 = w.n - C_BLOCK * (args.calls + 1)
+    st.set(synthetic.particles_around(w.theta_true, w.P, 0.05, seed=2), None, t0)
+    words = max(1, w.P * w.D // 4)
+    phases = {"cphase": lambda: st.cphase(st.get_t() + C_BLOCK, outputs=False),
+              "sphase": lambda: st.sphase(indices=False),
+              "mstep_rw": lambda: st.mstep("rw", sigma_used=False),
+              "mstep_mala": lambda: st.mstep("mala", sigma_used=False),
+              "philox": lambda: s.philox((7, 11), (0, 0, 0, 0), words)}
+    ms = {k: [] for k in phases}
+    for i in range(args.calls + 1):
+        for k, f in phases.items():
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            f()
+            torch.cuda.synchronize()
+            if i > 0:
+                ms[k].append((time.perf_counter() - a) * 1e3)
+    print(json.dumps({"workload": w.name, "particles": w.P, "D": w.D, "cycles": args.calls,
+                      "ms_per_call": {k: (sum(v) / len(v) if v else None) for k, v in ms.items()}}), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,11 +537,16 @@ def main():
     ap.add_argument("--loglik-only", default="", choices=["", "c1", "c2", "c3", "c4", "c5"],
                     help="profiling entry: only time the fused log-likelihood on this workload")
     ap.add_argument("--particles", type=int, default=0, help="with --loglik-only: particles (0 = the workload's)")
-    ap.add_argument("--calls", type=int, default=2, help="with --loglik-only: timed calls")
+    ap.add_argument("--calls", type=int, default=2, help="with --loglik-only / --phase-kernels: timed calls")
     ap.add_argument("--grad", action="store_true", help="with --loglik-only: the log-likelihood gradient kernel")
+    ap.add_argument("--phase-kernels", default="", choices=["", "c1", "c2", "c3", "c4"],
+                    help="profiling entry: simulator cycles (C, S, random-walk and MALA M steps, Philox) on this workload")
     args = ap.parse_args()
     if args.loglik_only:
         run_loglik_only(args)
+        return
+    if args.phase_kernels:
+        run_phase_kernels(args)
         return
     if args.gpus != 1:
         print(json.dumps({"metric": METRIC, "impl": args.impl, "n_gpus": args.gpus,

@@ -1056,19 +1056,30 @@ accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restri
 
 constexpr int kMalaThreads = 64;
 
-// Gradient of the prior log density, -Prec (theta - mu), component i (FP64).
-__device__ __forceinline__ double prior_grad(const double* th, const double* mu, const double* prec, int D,
-                                             bool full, int i) {
-  if (!full) return -prec[i] * (th[i] - mu[i]);
-  double a = 0.0;
-  for (int j = 0; j < D; ++j) a = fma(prec[i * D + j], th[j] - mu[j], a);
+// Gradient of the prior log density, -Prec (theta - mu), component i, in FP32 (the MALA drift
+// needs no more: any deterministic drift gives an exact Metropolis-Hastings kernel, and FP64
+// arithmetic is scarce on this GPU): from the particle's centred
+// coordinates dc[j * kMalaThreads] = f32(theta_j) - f32(mu_j) and the FP32 copy of a full
+// precision matrix (stored after the FP64 one).
+__device__ __forceinline__ float prior_grad_f32(const float* dc, const double* prec, int D, bool full, int i) {
+  if (!full) return -(f64_to_f32(prec[i]) * dc[i * kMalaThreads]);
+  const float* pi = reinterpret_cast<const float*>(prec + static_cast<size_t>(D) * D) + static_cast<size_t>(i) * D;
+  float a = 0.f;
+  for (int j = 0; j < D; ++j) a = fmaf(pi[j], dc[j * kMalaThreads], a);
   return -a;
 }
 
 // Four threads per particle (64 particles per block): each takes every fourth row of the
-// triangular products; the sums over a particle's coordinates (|z|^2, |w|^2), the prior log
-// kernel and the accept decision stay with its first thread, in the original order.
+// triangular products and every fourth coordinate of the squared norms |z|^2 and |w|^2 (FP32,
+// combined by shuffles); the prior log kernel and the accept decision stay with its first thread.
 constexpr int kMalaSub = 4;
+
+// Sum of v over the four lanes of a particle (FP32, the same order in every lane).
+__device__ __forceinline__ float quad_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
 
 __global__ void __launch_bounds__(kMalaThreads * kMalaSub)
 mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gll, int64_t P, int D,
@@ -1092,10 +1103,14 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
   const int64_t p = p0 + pp;
   const bool live = pp < np;
   if (live) {
+    // the centred coordinates in vs until v is formed, then the gradient of the log posterior
     const double* t = th + p * D;
-    for (int i = sub; i < D; i += kMalaSub)
-      gs[i * kMalaThreads + pp] = static_cast<float>(gll[p * D + i] + prior_grad(t, mu, prec, D, full, i));
+    for (int i = sub; i < D; i += kMalaSub) vs[i * kMalaThreads + pp] = f64_to_f32(t[i]) - f64_to_f32(mu[i]);
   }
+  __syncwarp();
+  if (live)
+    for (int i = sub; i < D; i += kMalaSub)
+      gs[i * kMalaThreads + pp] = f64_to_f32(gll[p * D + i]) + prior_grad_f32(vs + pp, prec, D, full, i);
   if (z_given) {
     // given normals (step-level parity), rounded to FP32 like the drawn ones
     for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
@@ -1133,14 +1148,13 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
       zq_o[p * D + i] = vs[i * kMalaThreads + pp];
     }
   }
+  float zp = 0.f;
+  if (live)
+    for (int d = sub; d < D; d += kMalaSub) zp = fmaf(zs[d * kMalaThreads + pp], zs[d * kMalaThreads + pp], zp);
+  const float z2 = quad_sum(zp);
   __syncwarp();   // the particle's new row is complete (global writes of its four lanes)
   if (live && sub == 0) {
-    double z2 = 0.0;
-    for (int d = 0; d < D; ++d) {
-      const float zd = zs[d * kMalaThreads + pp];
-      z2 += static_cast<double>(zd) * zd;
-    }
-    z2_o[p] = z2;
+    z2_o[p] = f32_to_f64(z2);
     lp_o[p] = prior_log_kernel(o, mu, prec, D, full);
   }
 }
@@ -1160,8 +1174,8 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
   extern __shared__ float ms[];
   const int T = D * (D + 1) / 2;
   float* Ls = ms;
-  float* gs = ms + ((T + 3) & ~3);                                   // [D][64]
-  double* ws = reinterpret_cast<double*>(gs + ((D * kMalaThreads + 1) & ~1));   // [D][64]
+  float* gs = ms + ((T + 3) & ~3);                 // [D][64]
+  float* ws = gs + D * kMalaThreads;               // [D][64]: centred coordinates of theta', then w
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
   const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kMalaThreads;
   const int np = static_cast<int>(P - p0 < kMalaThreads ? P - p0 : kMalaThreads);
@@ -1170,24 +1184,24 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
   const bool live = pp < np;
   if (live) {
     const double* tp = th_p + p * D;
-    for (int i = sub; i < D; i += kMalaSub)
-      gs[i * kMalaThreads + pp] = static_cast<float>(g_p[p * D + i] + prior_grad(tp, mu, prec, D, full, i));
+    for (int i = sub; i < D; i += kMalaSub) ws[i * kMalaThreads + pp] = f64_to_f32(tp[i]) - f64_to_f32(mu[i]);
   }
+  __syncwarp();
+  if (live)
+    for (int i = sub; i < D; i += kMalaSub)
+      gs[i * kMalaThreads + pp] = f64_to_f32(g_p[p * D + i]) + prior_grad_f32(ws + pp, prec, D, full, i);
   __syncthreads();
+  float wp = 0.f;
   if (live)
     for (int j = sub; j < D; j += kMalaSub) {   // w_j = z_j + (1/2) (L' g')_j
       float b = 0.f;
       for (int i = j; i < D; ++i) b = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaThreads + pp], b);
-      ws[j * kMalaThreads + pp] = static_cast<double>(zq[p * D + j]) + 0.5 * static_cast<double>(b);
+      const float w = fmaf(0.5f, b, zq[p * D + j]);
+      wp = fmaf(w, w, wp);
     }
-  __syncwarp();
+  const double w2 = f32_to_f64(quad_sum(wp));
   bool acc = false;
   if (live && sub == 0) {
-    double w2 = 0.0;
-    for (int j = 0; j < D; ++j) {
-      const double w = ws[j * kMalaThreads + pp];
-      w2 = fma(w, w, w2);
-    }
     const double lpp = ll_p[p];
     if (!isfinite(lpp)) atomicOr(nonfinite, 1);
     const double la = (lpp - ll[p]) + (lp_p[p] - lp[p]) - 0.5 * w2 + 0.5 * z2[p];
@@ -1766,8 +1780,7 @@ static sps_status mala_issue(sps_ctx* ctx, sps_state* st, uint64_t step, const u
   const int D = ctx->D;
   const int T = D * (D + 1) / 2;
   const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 3 * static_cast<size_t>(D) * kMalaThreads);
-  const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + ((static_cast<size_t>(D) * kMalaThreads + 1) & ~1)) +
-                        sizeof(double) * static_cast<size_t>(D) * kMalaThreads;
+  const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kMalaThreads);
   SPS_CUDA_TRY(cudaFuncSetAttribute(mala_propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem_p)));
   SPS_CUDA_TRY(cudaFuncSetAttribute(mala_accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

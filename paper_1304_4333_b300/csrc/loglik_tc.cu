@@ -1632,7 +1632,7 @@ sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out)
   if (out) {
     out->tile_rows = bb;
     out->cluster = bc;
-    out->chunk_obs = bk > 0 ? bk : 4096;
+    out->chunk_obs = bk > 0 ? bk : 16384;   // 0: the default of plan_call
     out->n_candidates = tried;
     out->ms = best;
     out->ms_default = ms_default;
@@ -1732,9 +1732,11 @@ static bool grad_shape(const sps_ctx* ctx, int* BN, int* ng, int* gch, int* stag
   if (*qt) {
     *gch = (off + 2 * *ng <= static_cast<int>(kQtHi)) ? 2 : 1;
   } else {
-    // 32-column TMEM reads of the last accumulator may run 16 columns past it
-    *gch = (off + NC * 2 * *ng + 16 <= 512) ? 2 : 1;
-    if (off + NC * *gch * *ng + 16 > 512) return false;
+    // the 32-column TMEM reads of the last accumulator run 16 columns past it when ng is an odd
+    // multiple of 16 (C = 3, k = 74 with alternating columns: ng = 128 fills the 512 columns)
+    const int over = (*ng % 32) ? 32 - *ng % 32 : 0;
+    *gch = (off + NC * 2 * *ng + over <= 512) ? 2 : 1;
+    if (off + NC * *gch * *ng + over > 512) return false;
   }
   const int kbx = enc.kx / kKB, kbt = enc.kt / kKB;
   for (int q = 2; q >= 1; --q)

@@ -68,6 +68,31 @@ def test_tensor_core_gradient_against_oracle(cuda, C, n, k, t):
     s32.close()
 
 
+def test_tensor_core_gradient_fills_tensor_memory(cuda):
+    # C = 3 with 74 alternating continuous / 0-1 columns (the largest nested model of c5): the
+    # gradient accumulators take the 256 tensor-memory columns beside the forward ones exactly
+    from paper_1304_4333_b300 import Sps
+    g = np.random.Generator(np.random.PCG64(74))
+    n, k, C = 900, 74, 3
+    X = g.standard_normal((n, k))
+    X[:, 1::2] = (g.random((n, k // 2)) < 0.25).astype(float)
+    y = g.integers(0, C, n).astype(np.int32)
+    D = k * (C - 1)
+    th = (0.8 / np.sqrt(k)) * g.standard_normal((300, D))
+    s = Sps(X, y, C, prior_sd=5.0, precision="split")
+    ll, G = s.loglik_grad(th, n)
+    ll_o, G_o = OL.loglik_grad(X, y, th, C, n)
+    bound = 1e-5 * np.abs(G_o) + 2.0 ** -13 * _eta_bound(X, th, C, n)
+    assert np.all(np.abs(G - G_o) <= bound), np.max(np.abs(G - G_o) - bound)
+    s32 = Sps(X, y, C, prior_sd=5.0, precision="fp32")
+    _, G32 = s32.loglik_grad(th, n)
+    assert not np.array_equal(G, G32)      # the tensor-core kernel ran, not the FP32 form
+    rel = np.linalg.norm(G - G_o, axis=1) / np.linalg.norm(G_o, axis=1)
+    assert rel.max() < 1e-4
+    s.close()
+    s32.close()
+
+
 def test_tensor_core_gradient_device_and_zero_theta(cuda):
     # theta = 0: p = 1/C for every term, so G_c = sum_s (1[y_s = c] - 1/C) x_s exactly up to the
     # BF16 split of X (exact for these columns) and FP32 accumulation

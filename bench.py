@@ -513,6 +513,28 @@ def run_phase_kernels(args):
     s.close()
 
 
+def run_batched_sps(args):
+    """Model comparison on c5: the batched simulator over the first `--models` nested models
+    (k = 5, 8, ...; the paper's g-prior with g = 1 for each model's covariates, 16 x 1024
+    particles each), random walk or MALA (`--mkernel`). Prints one JSON line per model (log
+    marginal likelihood, its NSE, cycles, M steps) and one with the wall time of the run."""
+    import torch
+    import synthetic
+    from paper_1304_4333_b300 import Sps
+    torch.cuda.set_device(0)
+    w = synthetic.make_workload("c5")
+    ks = [int(k) for k in w.model_k[:args.models]]
+    s = Sps(w.X, w.y, w.C, prior_sd=5.0, seed=1, mkernel=args.mkernel)
+    t0 = time.perf_counter()
+    rs = s.run_batched(ks, w.J, w.N, g=1.0)
+    wall = time.perf_counter() - t0
+    for k, r in zip(ks, rs):
+        print(json.dumps({"k": k, "log_ml": r.log_ml, "log_ml_nse": r.log_ml_nse, "cycles": r.n_cycles,
+                          "m_steps": r.m_steps, "graph_steps": r.graph_steps}), flush=True)
+    print(json.dumps({"workload": "c5", "models": len(ks), "mkernel": args.mkernel, "wall_s": wall}), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -539,6 +561,9 @@ def main():
     ap.add_argument("--particles", type=int, default=0, help="with --loglik-only: particles (0 = the workload's)")
     ap.add_argument("--calls", type=int, default=2, help="with --loglik-only / --phase-kernels: timed calls")
     ap.add_argument("--grad", action="store_true", help="with --loglik-only: the log-likelihood gradient kernel")
+    ap.add_argument("--batched-sps", action="store_true",
+                    help="model comparison on c5: the batched simulator over --models nested models")
+    ap.add_argument("--models", type=int, default=24, help="with --batched-sps: the first m of c5's models")
     ap.add_argument("--phase-kernels", default="", choices=["", "c1", "c2", "c3", "c4"],
                     help="profiling entry: simulator cycles (C, S, random-walk and MALA M steps, Philox) on this workload")
     args = ap.parse_args()
@@ -547,6 +572,9 @@ def main():
         return
     if args.phase_kernels:
         run_phase_kernels(args)
+        return
+    if args.batched_sps:
+        run_batched_sps(args)
         return
     if args.gpus != 1:
         print(json.dumps({"metric": METRIC, "impl": args.impl, "n_gpus": args.gpus,

@@ -1468,6 +1468,7 @@ sps_status run_any(sps_ctx* ctx, int CL, const TcParams* prm, int grid, uint32_t
   if (NC == 1 && BN == 128) return run_cl<1, 128>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
   if (NC == 2 && BN == 128) return run_cl<2, 128>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
   if (NC == 2 && BN == 64) return run_cl<2, 64>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
+  if (NC == 3 && BN == 128) return run_cl<3, 128>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
   if (NC == 3 && BN == 64) return run_cl<3, 64>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
   if (NC == 3 && BN == 32) return run_cl<3, 32>(ctx, CL, prm, grid, smem_bytes, mapT, timed, max_clusters);
   return fail(ctx, SPS_ERR_UNSUPPORTED, "no tensor-core tile for this shape");
@@ -1538,16 +1539,20 @@ double tc_waves(const sps_ctx* ctx, int64_t P, int64_t t) {
 // holding half of every X tile): the widest tile for the outcome count that keeps at least
 // three X stages in shared memory (0 when none fits).
 int tc_tile_rows(int NC, int kx, int kt, int CL) {
-  const int cands[3][2] = {{256, 128}, {128, 64}, {64, 32}};
+  // C = 4: one 384-column accumulator of 128-observation tiles (its epilogue groups share each
+  // tile by columns) before two of 64 (c3: 6.12 -> 4.40 ms per launch; N = 128 MMAs run at
+  // about 102 clocks against 119 for N = 64); 32-observation tiles for wide rows
+  const int cands[3][3] = {{256, 128, 0}, {128, 64, 0}, {128, 64, 32}};
   if (NC < 1 || NC > 3) return 0;
-  for (int q = 0; q < 2; ++q) {
+  int last = 0;
+  for (int q = 0; q < 3 && cands[NC - 1][q] > 0; ++q) {
     const int BN = cands[NC - 1][q];
     int st = 0, tb = 0;
     if (pick_stages(NC, BN, CL, kx / kKB, kt / kKB, &st, &tb) && st >= 3) return BN;
+    last = BN;
   }
-  const int BN = cands[NC - 1][1];
   int st = 0, tb = 0;
-  return pick_stages(NC, BN, CL, kx / kKB, kt / kKB, &st, &tb) ? BN : 0;
+  return pick_stages(NC, last, CL, kx / kKB, kt / kKB, &st, &tb) ? last : 0;
 }
 
 // One launch shape of the fused kernel: tile rows, cluster size (with its co-resident
@@ -1594,7 +1599,7 @@ sps_status tc_autotune(sps_ctx* ctx, int64_t P, int64_t t, sps_tune_result* out)
   const double ms_default = time_shape(bn0, cl0, mc0, ch0);
   double best = ms_default;
   int bb = bn0, bc = cl0, bm = mc0, bk = ch0, tried = 1;
-  const int cands[3][2] = {{256, 128}, {128, 64}, {64, 32}};
+  const int cands[3][2] = {{256, 128}, {128, 64}, {128, 64}};
   const char* env = getenv("SPS_TC_CLUSTER");
   const bool allow_cl2 = !(env && env[0] == '1' && env[1] == 0);
   for (int q = 0; q < 2; ++q) {

@@ -279,7 +279,8 @@ sps_status ensure_lin(sps_ctx* ctx, int64_t t) {
                                                             ctx->y.as<int>(), ctx->k, ctx->NC, t,
                                                             ctx->lin.as<double>()); ++ctx->launches;
   SPS_CUDA_TRY(cudaGetLastError());
-  ctx->lin_t = t;
+  // inside a stream capture the kernel only runs if the graph does: leave the cache as it was
+  if (!ctx->capturing) ctx->lin_t = t;
   return SPS_OK;
 }
 

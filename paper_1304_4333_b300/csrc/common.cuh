@@ -99,14 +99,12 @@ struct LoglikScratch {
   DevBuf partial;             // FP64 partial sums [slices x Ppad]
   DevBuf flag;                // int error/timeout flag
   DevBuf theta_in, ll_out, grad_out, aux;   // staging for host-memory calls
-  DevBuf batch_tab;           // int64 [M x 7] model table of a batched call
   DevBuf gpartial;            // FP32 [n_chunks x Ppad x NC ng] gradient partial sums (tensor cores)
   CUtensorMap mapXg;          // X tiles of the gradient kernel (box rows mapXg_rows)
   int mapXg_rows = 0;
-  DevBuf batch_ptile_t;       // int2 [n_ptiles] prefix length and K-slice mask of each particle tile
   DevBuf batch_lin;           // FP64 [M x NC x k] linear terms of the models
   DevBuf batch_models;        // BatchModel [M]
-  std::shared_ptr<SplitBatchedPlan> bplan;   // the last prepared batched launch
+  std::shared_ptr<SplitBatchedPlan> bplan[2];   // prepared batched launches (two slots)
 };
 
 // Device-resident control block of a captured M phase: the step size h and the Philox step word
@@ -270,13 +268,15 @@ sps_status loglik_split(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t 
 sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
                                 const double* const* d_theta, double* const* d_ll, const char* skip = nullptr);
 // The same call in two parts: prepare (tables and operand encodings in device memory, the launch
-// shape kept in the context; tiles receives each model's particle-tile range [x, y) of the
-// table of prefix lengths) and launch (kernels only: no allocation, no host copy, so it can be
-// captured). *ptile_table receives that table (int2 {prefix length, slot} per particle tile).
-sps_status loglik_split_batched_prepare(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm,
+// shape kept in the context's plan slot 0 or 1; tiles receives each model's particle-tile range
+// [x, y) of the table of prefix lengths) and launch (kernels only: no allocation, no host copy,
+// so it can be captured). *ptile_table receives that table (int2 {prefix length, slot} per
+// particle tile). The two slots' launches share the operand and partial-sum buffers: they must
+// run one after the other.
+sps_status loglik_split_batched_prepare(sps_ctx* ctx, int plan_slot, int M, const int32_t* km, const int64_t* Pm,
                                         const int64_t* tm, const double* const* d_theta, double* const* d_ll,
                                         const char* skip, std::vector<int2>* tiles, int2** ptile_table);
-sps_status loglik_split_batched_launch(sps_ctx* ctx);
+sps_status loglik_split_batched_launch(sps_ctx* ctx, int plan_slot);
 sps_status loglik_fp32(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll);
 sps_status loglik_dispatch(sps_ctx* ctx, const double* d_theta, int64_t P, int64_t t, double* d_ll,
                            int precision);

@@ -1913,9 +1913,11 @@ struct SplitBatchedPlan {
   int M = 0;
   int64_t PP = 0, Ptot = 0;
   size_t slices = 0;
+  DevBuf tab;     // int64 [M x kTab] model table of this launch
+  DevBuf ptile;   // int2 [n_ptiles] prefix length and model slot of each particle tile
 };
 
-sps_status loglik_split_batched_prepare(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm,
+sps_status loglik_split_batched_prepare(sps_ctx* ctx, int plan_slot, int M, const int32_t* km, const int64_t* Pm,
                                         const int64_t* tm, const double* const* d_theta, double* const* d_ll,
                                         const char* skip, std::vector<int2>* tiles, int2** ptile_table) {
   const int NC = ctx->NC;
@@ -1941,7 +1943,9 @@ sps_status loglik_split_batched_prepare(sps_ctx* ctx, int M, const int32_t* km, 
   // the work decomposition of one call over PP operand rows and the longest prefix (skipped
   // models included, so that it does not depend on which models are skipped); each particle
   // tile then stops at its own model's prefix
-  auto plan = std::make_shared<SplitBatchedPlan>();
+  if (plan_slot < 0 || plan_slot > 1) return fail(ctx, SPS_ERR_INVALID_ARG, "batched log-likelihood: plan slot");
+  if (!S.bplan[plan_slot]) S.bplan[plan_slot] = std::make_shared<SplitBatchedPlan>();
+  SplitBatchedPlan* plan = S.bplan[plan_slot].get();
   TcParams& prm = plan->prm;
   if (!plan_call(ctx, PP, tmax, &prm, &plan->smem_bytes))
     return fail(ctx, SPS_ERR_UNSUPPORTED, "covariate count too large for the tensor-core tile");
@@ -1975,12 +1979,12 @@ sps_status loglik_split_batched_prepare(sps_ctx* ctx, int M, const int32_t* km, 
   SPS_CUDA_TRY(S.batch_models.reserve(sizeof(BatchModel) * bms.size()));
   SPS_CUDA_TRY(cudaMemcpyAsync(S.batch_models.ptr, bms.data(), sizeof(BatchModel) * bms.size(),
                                cudaMemcpyHostToDevice, ctx->stream));
-  SPS_CUDA_TRY(S.batch_tab.reserve(sizeof(int64_t) * tab.size()));
-  SPS_CUDA_TRY(S.batch_ptile_t.reserve(sizeof(int2) * ptile_info.size()));
+  SPS_CUDA_TRY(plan->tab.reserve(sizeof(int64_t) * tab.size()));
+  SPS_CUDA_TRY(plan->ptile.reserve(sizeof(int2) * ptile_info.size()));
   SPS_CUDA_TRY(S.batch_lin.reserve(sizeof(double) * M * NC * ctx->k));
-  SPS_CUDA_TRY(cudaMemcpyAsync(S.batch_tab.ptr, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice,
+  SPS_CUDA_TRY(cudaMemcpyAsync(plan->tab.ptr, tab.data(), sizeof(int64_t) * tab.size(), cudaMemcpyHostToDevice,
                                ctx->stream));
-  SPS_CUDA_TRY(cudaMemcpyAsync(S.batch_ptile_t.ptr, ptile_info.data(), sizeof(int2) * ptile_info.size(),
+  SPS_CUDA_TRY(cudaMemcpyAsync(plan->ptile.ptr, ptile_info.data(), sizeof(int2) * ptile_info.size(),
                                cudaMemcpyHostToDevice, ctx->stream));
   if (S.ppad_cap < PP) {
     const int64_t cap = std::max<int64_t>(PP, S.ppad_cap * 3 / 2 / kBM * kBM);
@@ -1993,24 +1997,24 @@ sps_status loglik_split_batched_prepare(sps_ctx* ctx, int M, const int32_t* km, 
   SPS_CUDA_TRY(S.flag.reserve(sizeof(int)));
   prm.partial = S.partial.as<double>();
   prm.flag = S.flag.as<int>();
-  prm.ptile_info = S.batch_ptile_t.as<int2>();
+  prm.ptile_info = plan->ptile.as<int2>();
   prm.bmodels = S.batch_models.as<BatchModel>();
   plan->M = M;
   plan->PP = PP;
   plan->Ptot = Ptot;
-  S.bplan = plan;
-  if (ptile_table) *ptile_table = S.batch_ptile_t.as<int2>();
+  if (ptile_table) *ptile_table = plan->ptile.as<int2>();
   return SPS_OK;
 }
 
-sps_status loglik_split_batched_launch(sps_ctx* ctx) {
+sps_status loglik_split_batched_launch(sps_ctx* ctx, int plan_slot) {
   LoglikScratch& S = ctx->ll;
-  if (!S.bplan) return fail(ctx, SPS_ERR_STATE, "batched log-likelihood: no prepared launch");
-  SplitBatchedPlan& pl = *S.bplan;
+  if (plan_slot < 0 || plan_slot > 1 || !S.bplan[plan_slot])
+    return fail(ctx, SPS_ERR_STATE, "batched log-likelihood: no prepared launch");
+  SplitBatchedPlan& pl = *S.bplan[plan_slot];
   XEncoding& enc = ctx->enc;
   const int NC = ctx->NC, M = pl.M;
   TcParams prm = pl.prm;
-  const int64_t* dtab = S.batch_tab.as<int64_t>();
+  const int64_t* dtab = pl.tab.as<int64_t>();
   {
     const int64_t rows = static_cast<int64_t>(NC) * pl.PP;
     encode_theta_batched_kernel<<<static_cast<unsigned>((rows + 7) / 8), 256, 0, ctx->stream>>>(
@@ -2036,8 +2040,8 @@ sps_status loglik_split_batched_launch(sps_ctx* ctx) {
 
 sps_status loglik_split_batched(sps_ctx* ctx, int M, const int32_t* km, const int64_t* Pm, const int64_t* tm,
                                 const double* const* d_theta, double* const* d_ll, const char* skip) {
-  SPS_TRY(loglik_split_batched_prepare(ctx, M, km, Pm, tm, d_theta, d_ll, skip, nullptr, nullptr));
-  return loglik_split_batched_launch(ctx);
+  SPS_TRY(loglik_split_batched_prepare(ctx, 0, M, km, Pm, tm, d_theta, d_ll, skip, nullptr, nullptr));
+  return loglik_split_batched_launch(ctx, 0);
 }
 
 // ------------------------------------------------------------------------------------------

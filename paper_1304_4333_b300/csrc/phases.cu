@@ -2040,8 +2040,9 @@ sps_status mphase_graph(sps_ctx* ctx, sps_state* st, int kernel, double K, int r
   return SPS_OK;
 }
 
-// The rest of a lockstep M phase of a batched run, after its first step, as one graph launch: a
-// conditional WHILE node whose body holds, per model still moving, conditional IF nodes around
+// The rest of a lockstep M phase of a batched run, after its first step (or, with prepare, the
+// whole phase: first the cached log-likelihoods, and for MALA the gradients, at the phase's t),
+// as one graph launch: a conditional WHILE node whose body holds, per model still moving, conditional IF nodes around
 // the model's own kernels (proposal, decisions, monitoring sums and mstep_control_kernel, which
 // switches the model's IF nodes off once its stopping rule is met), between them the one batched
 // fused-kernel evaluation of the proposals (split-precision random walk; the tiles of stopped
@@ -2053,7 +2054,7 @@ sps_status mphase_graph(sps_ctx* ctx, sps_state* st, int kernel, double K, int r
 // the model's step count, updated. *fallback: the graph could not be built and nothing ran.
 sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, const std::vector<sps_state*>& ss,
                                 const std::vector<char>& moving, const std::vector<char>& batched, int kernel,
-                                std::vector<int>& steps, DevBuf& ctl_buf, bool* fallback) {
+                                bool prepare, std::vector<int>& steps, DevBuf& ctl_buf, bool* fallback) {
   *fallback = false;
   const sps_options& o = ctx->opt;
   auto give_up = [&](const char* what, cudaError_t e) {
@@ -2103,10 +2104,36 @@ sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, c
       bll.push_back(ss[i]->ll_prop.as<double>());
       bskip.push_back(moving[i] ? 0 : 1);
     }
-    if (!bk.empty())
-      SPS_TRY(loglik_split_batched_prepare(ctx, static_cast<int>(bk.size()), bk.data(), bP.data(), bt.data(),
+    if (!bk.empty()) {
+      SPS_TRY(loglik_split_batched_prepare(ctx, 0, static_cast<int>(bk.size()), bk.data(), bP.data(), bt.data(),
                                            bth.data(), bll.data(), bskip.data(), &tiles, &ptab));
+      if (prepare) {
+        // the cached log-likelihoods at the phase's t, by the same batched launch (plan slot 1)
+        for (size_t q = 0; q < bk.size(); ++q) bskip[q] = 0;
+        std::vector<const double*> cth;
+        std::vector<double*> cll;
+        for (int i = 0; i < Mp; ++i)
+          if (batched[i]) {
+            cth.push_back(ss[i]->theta.as<double>());
+            cll.push_back(ss[i]->ll.as<double>());
+          }
+        SPS_TRY(loglik_split_batched_prepare(ctx, 1, static_cast<int>(bk.size()), bk.data(), bP.data(), bt.data(),
+                                             cth.data(), cll.data(), bskip.data(), nullptr, nullptr));
+      }
+    }
   }
+  // with prepare, the models outside the batched launch (MALA, FP32) refresh their cached
+  // log-likelihoods (and gradients) at the phase's t eagerly, on the stream ahead of the graph:
+  // their launchers size buffers and caches by t, which must happen outside the capture
+  if (prepare)
+    for (int i = 0; i < Mp; ++i)
+      if (!batched[i]) {
+        const sps_status e = mstep_prepare(cs[i], ss[i], kernel);
+        if (e != SPS_OK) {
+          ctx->last_error = std::string("model context: ") + cs[i]->last_error;
+          return e;
+        }
+      }
   StepCtl* d_ctl = ctl_buf.as<StepCtl>();
   // the models' control blocks, then the loop's iteration count (bounded by the step cap)
   std::vector<StepCtl> hc(static_cast<size_t>(Mp + 1));
@@ -2123,8 +2150,44 @@ sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, c
     cudaGraph_t g;
     ~GraphGuard() { if (g) cudaGraphDestroy(g); }
   } guard{g};
+  std::string cap_error;
+  // with prepare: the phase's first evaluations as child graphs of g, before the loop
+  std::vector<cudaGraphNode_t> pre;
+  int64_t prep_launches = 0;
+  cudaError_t e = cudaSuccess;
+  if (prepare) {
+    auto child = [&](sps_ctx* c, const std::function<sps_status()>& issue) -> cudaError_t {
+      cudaError_t ee = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+      if (ee != cudaSuccess) return ee;
+      const cudaStream_t user = c->stream;
+      c->stream = ctx->cap_stream;
+      c->capturing = true;
+      const int64_t l0 = c->launches;
+      const sps_status is = issue();
+      prep_launches += c->launches - l0;
+      c->launches = l0;
+      c->capturing = false;
+      c->stream = user;
+      cudaGraph_t sub = nullptr;
+      ee = cudaStreamEndCapture(ctx->cap_stream, &sub);
+      if (is != SPS_OK) {
+        cap_error = c->last_error;
+        ee = cudaErrorUnknown;
+      }
+      cudaGraphNode_t nd;
+      if (ee == cudaSuccess) ee = cudaGraphAddChildGraphNode(&nd, g, nullptr, 0, sub);
+      if (sub) cudaGraphDestroy(sub);
+      if (ee == cudaSuccess) pre.push_back(nd);
+      return ee;
+    };
+    if (!tiles.empty()) e = child(ctx, [&]() { return loglik_split_batched_launch(ctx, 1); });
+    if (e != cudaSuccess) {
+      const std::string why = !cap_error.empty() ? "capture: " + cap_error : std::string("prepare nodes");
+      return give_up(why.c_str(), e);
+    }
+  }
   cudaGraphConditionalHandle wh;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&wh, g, 1, cudaGraphCondAssignDefault);
+  e = cudaGraphConditionalHandleCreate(&wh, g, 1, cudaGraphCondAssignDefault);
   cudaGraphNodeParams wp{};
   cudaGraphNode_t wnode;
   if (e == cudaSuccess) {
@@ -2132,13 +2195,12 @@ sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, c
     wp.conditional.handle = wh;
     wp.conditional.type = cudaGraphCondTypeWhile;
     wp.conditional.size = 1;
-    e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+    e = cudaGraphAddNode(&wnode, g, pre.empty() ? nullptr : pre.data(), nullptr, pre.size(), &wp);
   }
   if (e != cudaSuccess) return give_up("conditional node", e);
   cudaGraph_t body = wp.conditional.phGraph_out[0];
   // an IF node in the loop body (after deps) whose body graph receives what issue() launches on
   // the context c, recorded on the capture stream
-  std::string cap_error;
   auto add_if = [&](cudaGraphConditionalHandle* h, const std::vector<cudaGraphNode_t>& deps, sps_ctx* c,
                     const std::function<sps_status()>& issue, cudaGraphNode_t* node) -> cudaError_t {
     cudaError_t ee = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault);
@@ -2217,7 +2279,7 @@ sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, c
       ctx->stream = ctx->cap_stream;
       ctx->capturing = true;
       const int64_t l0 = ctx->launches;
-      const sps_status is = loglik_split_batched_launch(ctx);
+      const sps_status is = loglik_split_batched_launch(ctx, 0);
       eval_launches = ctx->launches - l0;
       ctx->launches = l0;
       ctx->capturing = false;
@@ -2323,7 +2385,13 @@ sps_status batched_mphase_graph(sps_ctx* ctx, const std::vector<sps_ctx*>& cs, c
     st->h = c.h;
     steps[i] = c.r;
   }
-  ctx->launches += static_cast<int64_t>(iters) * (eval_launches + 1);
+  ctx->launches += static_cast<int64_t>(iters) * (eval_launches + 1) + prep_launches;
+  if (prepare)
+    for (int i = 0; i < Mp; ++i)
+      if (batched[i]) {
+        ss[i]->ll_stale = false;
+        ss[i]->ll_kind = 0;
+      }
   return SPS_OK;
 }
 
@@ -3138,7 +3206,7 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
   const sps_options& o = ctx->opt;
   DevBuf jobs_dev, ctl_buf, cc_buf;
   SPS_CUDA_TRY(jobs_dev.reserve(sizeof(CholJob) * static_cast<size_t>(M)));
-  bool use_graph = o.graphs != 0, use_cs_graph = o.graphs != 0;
+  bool use_graph = o.graphs != 0, use_cs_graph = o.graphs != 0, warm = false;
   while (true) {
     std::vector<int> active;
     for (int m = 0; m < M; ++m)
@@ -3171,8 +3239,35 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
     }
     // M phases in lockstep (Algorithm 2 step 2(c)): every step of the models still moving is
     // one batched evaluation of their proposals; a model leaves when its RNE criterion or the
-    // step cap is met
-    if (mala) {
+    // step cap is met. With graphs, after the first cycle (which sizes every buffer) the whole
+    // phase is one graph launch; else its first step runs from the host and the rest as a graph.
+    std::vector<int> run = active, r(M, 0);
+    for (int m : active) in_batch[m] = split && !mala;
+    if (use_graph && warm) {
+      std::vector<sps_ctx*> pc;
+      std::vector<sps_state*> ps;
+      std::vector<char> pm, pb;
+      std::vector<int> pr;
+      for (int m : active) {
+        pc.push_back(models.v[m].c);
+        ps.push_back(models.v[m].st);
+        pm.push_back(1);
+        pb.push_back(in_batch[m]);
+        pr.push_back(0);
+      }
+      bool fallback = false;
+      SPS_TRY(batched_mphase_graph(ctx, pc, ps, pm, pb, ctx->opt.mkernel, true, pr, ctl_buf, &fallback));
+      if (!fallback) {
+        for (size_t i = 0; i < active.size(); ++i) r[active[i]] = pr[i];
+        run.clear();
+      } else {
+        use_graph = false;
+      }
+    }
+    warm = true;
+    if (run.empty()) {
+      // the phase ran in the graph
+    } else if (mala) {
       // MALA: each model's log-likelihood and gradient come from its own gradient launch (the
       // cached values at the start of the phase included)
       for (int m : active) {
@@ -3180,16 +3275,14 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
         if (e != SPS_OK) return pass(models.v[m].c, e);
       }
     } else {
-      for (int m : active) in_batch[m] = split;
       SPS_TRY(evaluate(active, false, nullptr));   // cached log-likelihoods with the proposals' function
       for (int m : active) {
         models.v[m].st->ll_stale = false;
         models.v[m].st->ll_kind = split ? 0 : 1;
       }
     }
-    std::vector<int> run = active, r(M, 0);
     std::vector<char> moving(M, 0);
-    for (int m : active) moving[m] = 1;
+    for (int m : run) moving[m] = 1;
     std::vector<double> hs(M);
     std::vector<uint64_t> steps(M);
     std::vector<CholJob> jobs;
@@ -3273,7 +3366,7 @@ sps_status sps_run_batched(sps_ctx* ctx, int32_t M, const int32_t* k_models, dou
           pr.push_back(r[m]);
         }
         bool fallback = false;
-        SPS_TRY(batched_mphase_graph(ctx, pc, ps, pm, pb, ctx->opt.mkernel, pr, ctl_buf, &fallback));
+        SPS_TRY(batched_mphase_graph(ctx, pc, ps, pm, pb, ctx->opt.mkernel, false, pr, ctl_buf, &fallback));
         if (!fallback) {
           for (size_t i = 0; i < active.size(); ++i) r[active[i]] = pr[i];
           run.clear();

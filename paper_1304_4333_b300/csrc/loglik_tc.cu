@@ -1512,6 +1512,13 @@ bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t
   while (chunk_tiles > 2 &&
          static_cast<int64_t>(prm->n_pgroups) * ((prm->n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
     chunk_tiles /= 2;
+  // chunks of (nearly) equal length: the persistent CTAs take work items round robin, and a short
+  // last chunk left some CTAs a whole chunk's tiles more than others (c2: 20 000 observations in
+  // chunks of 64 and 15 tiles; now 40 and 39)
+  if (prm->n_tiles > 0) {
+    const int nch = (prm->n_tiles + chunk_tiles - 1) / chunk_tiles;
+    chunk_tiles = (prm->n_tiles + nch - 1) / nch;
+  }
   prm->chunk_tiles = chunk_tiles;
   prm->n_chunks = std::max(1, (prm->n_tiles + chunk_tiles - 1) / chunk_tiles);
   prm->n_items = prm->n_tiles > 0 ? prm->n_pgroups * prm->n_chunks : 0;

@@ -1482,6 +1482,32 @@ int grid_for(const sps_ctx* ctx, const TcParams& prm) {
   return CL * std::max(1, std::min(cap, prm.n_items));
 }
 
+// Tiles of the busiest of g_max clusters (g_max or fewer when there are fewer items) that take
+// the work items (chunk-major: item = chunk * gp + particle group, chunks of ct tiles, the last
+// one shorter) round robin, counting each item's start (its theta tile, its partial sums) as two
+// tiles.
+static int64_t busiest_cluster_tiles(int n_tiles, int ct, int64_t gp, int64_t g_max) {
+  constexpr int kItemCost = 2;
+  const int nch = (n_tiles + ct - 1) / ct;
+  const int64_t items = gp * nch;
+  const int64_t g = std::max<int64_t>(1, std::min<int64_t>(g_max, items));
+  int64_t worst = 0;
+  for (int64_t c = 0; c < g; ++c) {
+    int64_t load = 0;
+    for (int q = 0; q < nch; ++q) {
+      const int64_t a = q * gp, b = (q + 1) * gp;   // the items of chunk q: [a, b)
+      if (b - 1 < c) continue;
+      const int64_t j0 = (a > c) ? (a - c + g - 1) / g : 0;   // c + j g in [a, b)
+      const int64_t j1 = (b - 1 - c) / g;
+      if (j1 < j0) continue;
+      const int tiles = std::min(ct, n_tiles - q * ct);
+      load += (j1 - j0 + 1) * (tiles + kItemCost);
+    }
+    worst = std::max(worst, load);
+  }
+  return worst;
+}
+
 // Work decomposition and pipeline depth of one call; false when the tile does not fit.
 bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t* smem_bytes) {
   const XEncoding& enc = ctx->enc;
@@ -1512,12 +1538,24 @@ bool plan_call(const sps_ctx* ctx, int64_t P, int64_t t, TcParams* prm, uint32_t
   while (chunk_tiles > 2 &&
          static_cast<int64_t>(prm->n_pgroups) * ((prm->n_tiles + chunk_tiles - 1) / chunk_tiles) < want_items)
     chunk_tiles /= 2;
-  // chunks of (nearly) equal length: the persistent CTAs take work items round robin, and a short
-  // last chunk left some CTAs a whole chunk's tiles more than others (c2: 20 000 observations in
-  // chunks of 64 and 15 tiles; now 40 and 39)
+  // the persistent clusters take work items round robin: where equal chunks (as many, or up to
+  // three more) leave the busiest cluster at least 2 % less work than this length, take them (a
+  // short last chunk, or one item more for some clusters, decides the launch's tail; c3: 4.47 ->
+  // 4.29 ms per launch; c2 and c4 keep their lengths)
   if (prm->n_tiles > 0) {
-    const int nch = (prm->n_tiles + chunk_tiles - 1) / chunk_tiles;
-    chunk_tiles = (prm->n_tiles + nch - 1) / nch;
+    const int nch0 = (prm->n_tiles + chunk_tiles - 1) / chunk_tiles;
+    const int64_t base = busiest_cluster_tiles(prm->n_tiles, chunk_tiles, prm->n_pgroups, grid_max);
+    int64_t best = base;
+    int best_ct = chunk_tiles;
+    for (int nch = nch0; nch <= nch0 + 3 && nch <= prm->n_tiles; ++nch) {
+      const int ct = (prm->n_tiles + nch - 1) / nch;
+      const int64_t w = busiest_cluster_tiles(prm->n_tiles, ct, prm->n_pgroups, grid_max);
+      if (w < best && 50 * w <= 49 * base) {
+        best = w;
+        best_ct = ct;
+      }
+    }
+    chunk_tiles = best_ct;
   }
   prm->chunk_tiles = chunk_tiles;
   prm->n_chunks = std::max(1, (prm->n_tiles + chunk_tiles - 1) / chunk_tiles);

@@ -1055,17 +1055,20 @@ accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __restri
 //   log alpha = ll' - ll + lp' - lp - |w|^2 / 2 + |z|^2 / 2.
 
 constexpr int kMalaThreads = 64;
+// Row stride of the [D][particles] shared-memory arrays: 72, so that the 8 particles x 4 lanes of
+// a warp (coordinate j = lane + 4 m) fall on 32 different banks ((8 j + particle) mod 32)
+constexpr int kMalaStride = kMalaThreads + 8;
 
 // Gradient of the prior log density, -Prec (theta - mu), component i, in FP32 (the MALA drift
 // needs no more: any deterministic drift gives an exact Metropolis-Hastings kernel, and FP64
 // arithmetic is scarce on this GPU): from the particle's centred
-// coordinates dc[j * kMalaThreads] = f32(theta_j) - f32(mu_j) and the FP32 copy of a full
+// coordinates dc[j * kMalaStride] = f32(theta_j) - f32(mu_j) and the FP32 copy of a full
 // precision matrix (stored after the FP64 one).
 __device__ __forceinline__ float prior_grad_f32(const float* dc, const double* prec, int D, bool full, int i) {
-  if (!full) return -(f64_to_f32(prec[i]) * dc[i * kMalaThreads]);
+  if (!full) return -(f64_to_f32(prec[i]) * dc[i * kMalaStride]);
   const float* pi = reinterpret_cast<const float*>(prec + static_cast<size_t>(D) * D) + static_cast<size_t>(i) * D;
   float a = 0.f;
-  for (int j = 0; j < D; ++j) a = fmaf(pi[j], dc[j * kMalaThreads], a);
+  for (int j = 0; j < D; ++j) a = fmaf(pi[j], dc[j * kMalaStride], a);
   return -a;
 }
 
@@ -1093,9 +1096,9 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
   extern __shared__ float ms[];
   const int T = D * (D + 1) / 2;
   float* Ls = ms;                                  // [T] packed lower triangle
-  float* gs = ms + ((T + 3) & ~3);                 // [D][64] gradient of the log posterior
-  float* zs = gs + D * kMalaThreads;               // [D][64] normals
-  float* vs = zs + D * kMalaThreads;               // [D][64] v = (1/2) L' g + z
+  float* gs = ms + ((T + 3) & ~3);                 // [D][72] gradient of the log posterior
+  float* zs = gs + D * kMalaStride;                // [D][72] normals
+  float* vs = zs + D * kMalaStride;                // [D][72] v = (1/2) L' g + z
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
   const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kMalaThreads;
   const int np = static_cast<int>(P - p0 < kMalaThreads ? P - p0 : kMalaThreads);
@@ -1105,36 +1108,36 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
   if (live) {
     // the centred coordinates in vs until v is formed, then the gradient of the log posterior
     const double* t = th + p * D;
-    for (int i = sub; i < D; i += kMalaSub) vs[i * kMalaThreads + pp] = f64_to_f32(t[i]) - f64_to_f32(mu[i]);
+    for (int i = sub; i < D; i += kMalaSub) vs[i * kMalaStride + pp] = f64_to_f32(t[i]) - f64_to_f32(mu[i]);
   }
   __syncwarp();
   if (live)
     for (int i = sub; i < D; i += kMalaSub)
-      gs[i * kMalaThreads + pp] = f64_to_f32(gll[p * D + i]) + prior_grad_f32(vs + pp, prec, D, full, i);
+      gs[i * kMalaStride + pp] = f64_to_f32(gll[p * D + i]) + prior_grad_f32(vs + pp, prec, D, full, i);
   if (z_given) {
     // given normals (step-level parity), rounded to FP32 like the drawn ones
     for (int q = threadIdx.x; q < np * D; q += blockDim.x) {
       const int qp = q / D, d = q - qp * D;
-      zs[d * kMalaThreads + qp] = static_cast<float>(z_given[(p0 + qp) * D + d]);
+      zs[d * kMalaStride + qp] = static_cast<float>(z_given[(p0 + qp) * D + d]);
     }
   } else {
     // draw (particle p, word q) as before: counter p * ceil(D / 4) + q
     const int per = (D + 3) / 4;
     for (int q = threadIdx.x; q < np * per; q += blockDim.x) {
-      const int qp = q / per, qq = q - qp * per;
+      const int qq = q / np, qp = q - qq * np;   // consecutive threads: consecutive particles
       const uint4 r = draw(seed, static_cast<uint32_t>((p0 + qp) * per + qq), kStreamPropose, step);
       const float2 a = normals2(r.x, r.y), b = normals2(r.z, r.w);
       const float v[4] = {a.x, a.y, b.x, b.y};
       for (int u = 0; u < 4; ++u)
-        if (4 * qq + u < D) zs[(4 * qq + u) * kMalaThreads + qp] = v[u];
+        if (4 * qq + u < D) zs[(4 * qq + u) * kMalaStride + qp] = v[u];
     }
   }
   __syncthreads();
   if (live)
     for (int j = sub; j < D; j += kMalaSub) {   // v_j = (1/2) (L' g)_j + z_j
       float a = 0.f;
-      for (int i = j; i < D; ++i) a = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaThreads + pp], a);
-      vs[j * kMalaThreads + pp] = fmaf(0.5f, a, zs[j * kMalaThreads + pp]);
+      for (int i = j; i < D; ++i) a = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaStride + pp], a);
+      vs[j * kMalaStride + pp] = fmaf(0.5f, a, zs[j * kMalaStride + pp]);
     }
   __syncwarp();
   double* o = th_o + p * D;
@@ -1143,14 +1146,14 @@ mala_propose_kernel(const double* __restrict__ th, const double* __restrict__ gl
     for (int i = sub; i < D; i += kMalaSub) {
       const float* Li = Ls + i * (i + 1) / 2;
       float dlt = 0.f;
-      for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], vs[j * kMalaThreads + pp], dlt);
+      for (int j = 0; j <= i; ++j) dlt = fmaf(Li[j], vs[j * kMalaStride + pp], dlt);
       o[i] = t[i] + static_cast<double>(dlt);
-      zq_o[p * D + i] = vs[i * kMalaThreads + pp];
+      zq_o[p * D + i] = vs[i * kMalaStride + pp];
     }
   }
   float zp = 0.f;
   if (live)
-    for (int d = sub; d < D; d += kMalaSub) zp = fmaf(zs[d * kMalaThreads + pp], zs[d * kMalaThreads + pp], zp);
+    for (int d = sub; d < D; d += kMalaSub) zp = fmaf(zs[d * kMalaStride + pp], zs[d * kMalaStride + pp], zp);
   const float z2 = quad_sum(zp);
   __syncwarp();   // the particle's new row is complete (global writes of its four lanes)
   if (live && sub == 0) {
@@ -1174,8 +1177,8 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
   extern __shared__ float ms[];
   const int T = D * (D + 1) / 2;
   float* Ls = ms;
-  float* gs = ms + ((T + 3) & ~3);                 // [D][64]
-  float* ws = gs + D * kMalaThreads;               // [D][64]: centred coordinates of theta', then w
+  float* gs = ms + ((T + 3) & ~3);                 // [D][72]
+  float* ws = gs + D * kMalaStride;                // [D][72]: centred coordinates of theta', then w
   for (int e = threadIdx.x; e < T; e += blockDim.x) Ls[e] = L32[e];
   const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kMalaThreads;
   const int np = static_cast<int>(P - p0 < kMalaThreads ? P - p0 : kMalaThreads);
@@ -1184,18 +1187,18 @@ mala_accept_kernel(double* __restrict__ th, double* __restrict__ ll, double* __r
   const bool live = pp < np;
   if (live) {
     const double* tp = th_p + p * D;
-    for (int i = sub; i < D; i += kMalaSub) ws[i * kMalaThreads + pp] = f64_to_f32(tp[i]) - f64_to_f32(mu[i]);
+    for (int i = sub; i < D; i += kMalaSub) ws[i * kMalaStride + pp] = f64_to_f32(tp[i]) - f64_to_f32(mu[i]);
   }
   __syncwarp();
   if (live)
     for (int i = sub; i < D; i += kMalaSub)
-      gs[i * kMalaThreads + pp] = f64_to_f32(g_p[p * D + i]) + prior_grad_f32(ws + pp, prec, D, full, i);
+      gs[i * kMalaStride + pp] = f64_to_f32(g_p[p * D + i]) + prior_grad_f32(ws + pp, prec, D, full, i);
   __syncthreads();
   float wp = 0.f;
   if (live)
     for (int j = sub; j < D; j += kMalaSub) {   // w_j = z_j + (1/2) (L' g')_j
       float b = 0.f;
-      for (int i = j; i < D; ++i) b = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaThreads + pp], b);
+      for (int i = j; i < D; ++i) b = fmaf(Ls[i * (i + 1) / 2 + j], gs[i * kMalaStride + pp], b);
       const float w = fmaf(0.5f, b, zq[p * D + j]);
       wp = fmaf(w, w, wp);
     }
@@ -1779,8 +1782,8 @@ static sps_status mala_issue(sps_ctx* ctx, sps_state* st, uint64_t step, const u
                              const double* z_given, const double* u_given, double* la_out, int* acc_out) {
   const int D = ctx->D;
   const int T = D * (D + 1) / 2;
-  const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 3 * static_cast<size_t>(D) * kMalaThreads);
-  const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kMalaThreads);
+  const size_t smem_p = sizeof(float) * (((T + 3) & ~3) + 3 * static_cast<size_t>(D) * kMalaStride);
+  const size_t smem_a = sizeof(float) * (((T + 3) & ~3) + 2 * static_cast<size_t>(D) * kMalaStride);
   SPS_CUDA_TRY(cudaFuncSetAttribute(mala_propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem_p)));
   SPS_CUDA_TRY(cudaFuncSetAttribute(mala_accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

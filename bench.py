@@ -160,6 +160,51 @@ def oracle_single_thread(name: str, seconds: float, particles: int):
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
+def oracle_sps():
+    """The whole simulator against the oracle's. c1: one adaptive SPS run (random walk, 4 x 256
+    particles, n = 500) in the oracle (plain FP64 numpy) and one on the GPU (split precision,
+    after an untimed run). c2: the oracle's SPS time extrapolated -- labelled as such -- from the
+    oracle's measured log-likelihood rate on c2 and the log-likelihood terms of a recorded GPU run
+    (M steps: sum over cycles of R_l t_l P; C phases: n P); the oracle's other work is not
+    counted, so the figure is a lower bound."""
+    import numpy as np
+    import synthetic
+    from oracle import smc as OS
+    from paper_1304_4333_b300 import Sps
+    out = {}
+    w1 = synthetic.make_c1()
+    prior = OS.GaussianPrior.isotropic(w1.D, w1.prior_sd)
+    t0 = time.perf_counter()
+    ro = OS.sps_run(w1.X, w1.y, w1.C, prior, w1.J, w1.N, np.random.Generator(np.random.PCG64(1)))
+    t_or = time.perf_counter() - t0
+    s = Sps(w1.X, w1.y, w1.C, prior_sd=w1.prior_sd, seed=1)
+    s.run(w1.J, w1.N, record=False)
+    t0 = time.perf_counter()
+    rg = s.run(w1.J, w1.N, record=False)
+    t_gpu = time.perf_counter() - t0
+    s.close()
+    out["c1"] = {"groups_x_particles": f"{w1.J} x {w1.N}", "oracle_wall_s": t_or, "gpu_wall_s": t_gpu,
+                 "oracle_log_ml": ro.log_ml, "oracle_log_ml_nse": ro.log_ml_nse,
+                 "gpu_log_ml": rg.log_ml, "gpu_log_ml_nse": rg.log_ml_nse,
+                 "oracle_m_steps": int(sum(c.R for c in ro.cycles)), "gpu_m_steps": int(rg.m_steps)}
+    w2 = synthetic.make_c2()
+    s = Sps(w2.X, w2.y, w2.C, prior_sd=5.0, seed=1)
+    t0 = time.perf_counter()
+    rg = s.run(w2.J, w2.N, record=True)
+    t_gpu = time.perf_counter() - t0
+    s.close()
+    sch = rg.schedule
+    terms = float(np.sum(np.asarray(sch.R, dtype=np.float64) * np.asarray(sch.t, dtype=np.float64))) * w2.P \
+        + float(w2.n) * w2.P
+    rate = oracle_throughput(w2, seconds=5.0, particles=64)
+    out["c2"] = {"groups_x_particles": f"{w2.J} x {w2.N}", "gpu_wall_s": t_gpu, "gpu_m_steps": int(rg.m_steps),
+                 "gpu_cycles": int(rg.n_cycles), "loglik_terms": terms, "oracle_terms_per_s": rate["value"],
+                 "oracle_wall_s_extrapolated": terms / rate["value"],
+                 "label": "extrapolated: the oracle's log-likelihood rate on c2 (" + rate["sample"] + ") times the "
+                          "terms of the GPU run's M steps and C phases; a lower bound"}
+    return out
+
+
 def run_reference(args):
     """The oracle arm: the plain FP64 CPU log-likelihood on c4, each step a bounded sample (16
     particles over all 10^6 observations)."""
@@ -398,6 +443,7 @@ def run_ours(args):
         try:
             line["cpu_baseline"] = oracle_throughput(w4, seconds=10.0, particles=16)
             line["cpu_baseline"]["single_thread"] = oracle_single_thread("c4", 6.0, 16)
+            line["cpu_baseline"]["sps"] = oracle_sps()
         except Exception as exc:      # the GPU figures are reported whatever happens here
             line["cpu_baseline"] = {"error": repr(exc)}
     print(json.dumps(line), flush=True)

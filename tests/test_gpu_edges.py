@@ -14,10 +14,11 @@ prefixes of a whole tile or more, over the particles whose log-likelihood is not
 fit (|ll| >= 0.1 t). Where every term is close to zero (a single observation with |eta| large,
 one outcome that a particle predicts almost surely) the error is set by the rounding of eta, not
 by the size of ll, and only the bound applies. With one outcome throughout, the split path's
-rounding of theta (hi + lo BF16 keep 16 bits of its mantissa) moves every term's eta the same
-way: the errors add up instead of cancelling as they do when the residuals y_s - p_s change
-sign, and the relative error reaches a few 1e-5 (within the bound, which assumes no
-cancellation); that case asserts the bound and reports the relative error.
+errors in eta (hi + lo BF16 keep 16 bits of each operand's mantissa) add up instead of cancelling
+as they do when the residuals y_s - p_s change sign, and for C = 2 the kernel's sum of |eta| / 2
+cancels against the linear part theta . X'(y - 1/2) on well-predicted observations: the relative
+error reaches a few 1e-5 (within the bound, which assumes no cancellation); that case asserts the
+bound and reports the relative error.
 """
 import ctypes as C
 

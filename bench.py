@@ -25,9 +25,11 @@ pinned host buffers (theta in, log-likelihoods out, copies inside the timed regi
 oracle (plain FP64 numpy) is timed on a bounded sample as the CPU baseline, on all host cores
 and on one, and is the `--impl reference` arm.
 
-`sps.ladder`: the wall time of whole simulator runs (sps_run) on c2 to log-ML NSE <= 0.05,
-groups doubled from 16 until seed 1 reaches the target (the plain FP32 form starts at the
-rung the split random walk reached), then further seeds at that rung (`--ladder-seeds`).
+`sps.ladder`: the wall time of whole simulator runs (sps_run) on c2 to log-ML NSE <= 0.05:
+seed 1 from 16 groups, the groups doubled while its NSE is above 1.5x the target, then set to
+where NSE ~ 1/sqrt(groups) predicts the target (with a margin) until seed 1 reaches it (the plain
+FP32 form starts at the rung the split random walk reached); then further seeds at that rung
+(`--ladder-seeds`).
 
 SM clocks and throttle reasons are sampled by one-shot nvidia-smi queries between timed steps
 (after the first, middle and last step), never during one.
@@ -37,6 +39,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -449,14 +452,30 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def next_rung(J: int, nse: float, target: float, max_groups: int, step: int = 16) -> int:
+    """Groups of the ladder's next rung after a run at J groups that ended at log-ML NSE `nse`
+    above the target: twice J while nse > 1.5 target (an NSE estimated from few groups is too
+    noisy to extrapolate from); closer in, the groups at which NSE ~ 1 / sqrt(groups) reaches the
+    target, times 1.15 (about two standard errors of an NSE estimated from some hundred groups),
+    rounded up to a multiple of `step`, at least J + step and at most 2 J; never above
+    max_groups."""
+    if nse > 1.5 * target:
+        nxt = 2 * J
+    else:
+        want = J * (nse / target) ** 2 * 1.15
+        nxt = min(max(int(math.ceil(want / step)) * step, J + step), 2 * J)
+    return min(nxt, max_groups)
+
+
 def sps_ladder(w, forms, max_groups: int, seeds: int, seeds_other: int, target: float = 0.05):
     """The wall-time half of the metric as a measured protocol: for each form (precision, M
-    kernel), run seed 1 at the workload's groups x particles and double the number of groups
-    (particles per group stay at the workload's value, the resampling bound) until its log-ML
-    NSE is at most the target; then run seeds 2..`seeds` (split MALA) or 2..`seeds_other` (the
-    other forms) at that rung and report the median wall time with each seed's NSE. The plain FP32 random walk starts at the rung the split random walk
-    reached (the same Metropolis kernel on the same data: the two differ only in rounding). A form
-    whose seed 1 misses the target at max_groups reports its last rung with "reached": false."""
+    kernel), run seed 1 at the workload's groups x particles and raise the number of groups
+    (`next_rung`; particles per group stay at the workload's value, the resampling bound) until
+    its log-ML NSE is at most the target; then run seeds 2..`seeds` (split MALA) or
+    2..`seeds_other` (the other forms) at that rung and report the median wall time with each
+    seed's NSE. The plain FP32 random walk starts at the rung the split random walk reached (the
+    same Metropolis kernel on the same data: the two differ only in rounding). A form whose seed
+    1 misses the target at max_groups reports its last rung with "reached": false."""
     from paper_1304_4333_b300 import Sps
     out = {}
     for prec, mk in forms:
@@ -474,9 +493,9 @@ def sps_ladder(w, forms, max_groups: int, seeds: int, seeds_other: int, target: 
         rungs = []
         while True:
             rungs.append(one(J, 1))
-            if rungs[-1]["log_ml_nse"] <= target or 2 * J > max_groups:
+            if rungs[-1]["log_ml_nse"] <= target or J >= max_groups:
                 break
-            J *= 2
+            J = next_rung(J, rungs[-1]["log_ml_nse"], target, max_groups)
         reached = rungs[-1]["log_ml_nse"] <= target
         ns = seeds if (prec, mk) == ("split", "mala") else seeds_other
         runs = [rungs[-1]] + ([one(J, sd) for sd in range(2, ns + 1)] if reached else [])

@@ -31,7 +31,20 @@ def test_clock_probe_parses_nvidia_smi(monkeypatch):
     assert bench.ClockProbe(0).summary()["reasons"] == ["unsampled"]
 
 
-def test_sps_ladder_doubles_groups_then_runs_three_seeds(monkeypatch):
+def test_next_rung_doubles_far_from_the_target_then_predicts():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.next_rung(16, 0.40, 0.05, 1024) == 32          # far: double
+    assert bench.next_rung(256, 0.0758, 0.05, 1024) == 512      # above 1.5x the target: double
+    # 512 (0.0506 / 0.05)^2 1.15 = 603.0 -> 608 (a multiple of 16)
+    assert bench.next_rung(512, 0.0506, 0.05, 1024) == 608
+    assert bench.next_rung(512, 0.0501, 0.05, 1024) == 592      # at least 15 % more groups
+    assert bench.next_rung(512, 0.0500001, 0.05, 4096) >= 528   # at least one step more
+    assert bench.next_rung(128, 0.074, 0.05, 4096) == 256       # at most twice
+    assert bench.next_rung(512, 0.06, 0.05, 600) == 600         # never above the cap
+
+
+def test_sps_ladder_raises_groups_then_runs_three_seeds(monkeypatch):
     # the wall-time protocol of the bench, on a stand-in simulator whose NSE falls as 1/sqrt(J)
     sys.path.insert(0, ROOT)
     import types
@@ -62,9 +75,12 @@ def test_sps_ladder_doubles_groups_then_runs_three_seeds(monkeypatch):
     assert len(m["seeds"]) == 1
     out = bench.sps_ladder(w, [("split", "rw")], max_groups=4096, seeds=3, seeds_other=3)
     r = out["split_rw"]
-    assert r["reached"] and r["rung"] == "1024 groups x 4096"
+    # doubling to 512 (NSE 0.0571 < 0.075), then 512 (0.0571 / 0.05)^2 1.15 = 768.3 -> 784 groups
+    # (NSE 0.0462)
+    assert [x["groups"] for x in r["ladder_seed1"]] == [16, 32, 64, 128, 256, 512, 784]
+    assert r["reached"] and r["rung"] == "784 groups x 4096"
     assert [x["seed"] for x in r["seeds"]] == [1, 2, 3]
-    assert r["median_wall_s"] == 10.24
+    assert r["median_wall_s"] == 7.84
     assert out["target_log_ml_nse"] == 0.05
 
 
@@ -95,7 +111,8 @@ def test_sps_ladder_fp32_starts_at_the_split_rung(monkeypatch):
     assert [r["seed"] for r in out["split_mala"]["seeds"]] == [1, 2, 3]
     assert [r["seed"] for r in out["split_rw"]["seeds"]] == [1]
     fp = [r for r in runs if r[0] == ("fp32", "rw")]
-    assert fp == [(("fp32", "rw"), 1024, 1)]
+    # the split random walk reached the target at 768 groups (512 -> 754.4 -> 768)
+    assert fp == [(("fp32", "rw"), 768, 1)]
     assert out["speedup_split_mala_vs_fp32_rw"] == 1.0
 
 

@@ -7,6 +7,8 @@
 * One outcome observed throughout, and an intercept-only model (no continuous column, so no
   low-part MMAs).
 * Arguments the library must refuse with SPS_ERR_INVALID_ARG; the context stays usable.
+* The tensor-core gradient with linear predictors in the hundreds (p saturated at 0 or 1), held
+  to the bound of test_gpu_grad_tc.
 
 Tolerances as in test_gpu_loglik: every particle within the relative bar (1e-5 split, 1e-6 FP32)
 plus the propagated rounding bound of its linear predictors, and the relative bar on its own for
@@ -175,3 +177,32 @@ def test_invalid_arguments_are_refused_and_the_context_stays_usable(torch_cuda):
         # the context still computes
         for prec in ("split", "fp32"):
             _check(s.loglik(th, n, prec), ref, X, th, C_, n, prec)
+
+
+def _grad_bound(X, th, C_, t):
+    """The tensor-core gradient's bound (as in test_gpu_grad_tc): 2^-13 sum_s (1 + |eta_s|) |x_si|
+    per entry, on top of 1e-5 of the oracle gradient."""
+    k = X.shape[1]
+    Xt = X[:t]
+    out = np.zeros_like(th)
+    for c in range(C_ - 1):
+        eta = th[:, c * k:(c + 1) * k] @ Xt.T
+        out[:, c * k:(c + 1) * k] = (1.0 + np.abs(eta)) @ np.abs(Xt)
+    return 2.0 ** -13 * out
+
+
+@pytest.mark.parametrize("C_", [2, 3, 4])
+def test_gradient_with_linear_predictors_in_the_hundreds(torch_cuda, C_):
+    # p_s saturates at 0 or 1: the sigmoid / softmax of the gradient's epilogue must not overflow
+    from oracle.logit import loglik_grad as oracle_grad
+    n, k = 300, 6
+    X, y = _mk(n, k, C_, 61, exact_cols=2)
+    theta = np.random.Generator(np.random.PCG64(62)).standard_normal((200, k * (C_ - 1))) * 80.0
+    s = _sps(X, y, C_)
+    for t in (1, 130, n):
+        ll, G = s.loglik_grad(theta, t)
+        ll_o, G_o = oracle_grad(X, y, theta, C_, t)
+        assert np.all(np.isfinite(G)) and np.all(np.isfinite(ll))
+        bound = 1e-5 * np.abs(G_o) + _grad_bound(X, theta, C_, t)
+        assert np.all(np.abs(G - G_o) <= bound), np.max(np.abs(G - G_o) - bound)
+        _check(ll, ll_o, X, theta, C_, t, "split")

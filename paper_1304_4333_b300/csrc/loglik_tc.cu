@@ -895,7 +895,11 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
   // single group takes whole tiles and the others idle
   constexpr int GPW = (NBUF == 2) ? 2 : 1;        // working groups per accumulator
   constexpr int COLS = BN / GPW;
-  constexpr int NCH = COLS / 32;
+  // TMEM loads of W columns per class: 32 for C = 2, 16 for C > 2 (two or three classes of 32
+  // values each left the epilogue short of registers: C = 3, k = 74, 16 384 particles at 10^5
+  // observations 5.30 -> 4.83 ms per launch; C = 4 (c3) 22.28 -> 20.21 ms)
+  constexpr int W = (NC == 1) ? 32 : 16;
+  constexpr int NCH = COLS / W;
   static_assert(COLS % 32 == 0, "32-column TMEM loads");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -1168,9 +1172,12 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
         int pexp = 0;
 #pragma unroll 1
         for (int ch = 0; ch < NCH; ++ch) {
-          float v[NC][32];
+          float v[NC][W];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * 32, v[c]);
+          for (int c = 0; c < NC; ++c) {
+            if constexpr (W == 32) ptx::tmem_ld_32x32b_x32(tbase + c * BN + ch * W, v[c]);
+            else ptx::tmem_ld_32x32b_x16(tbase + c * BN + ch * W, v[c]);
+          }
           ptx::tmem_wait_ld();
           if (ch == NCH - 1) {
             ptx::tc_fence_before();
@@ -1178,10 +1185,10 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
             if (lane == 0) ptx::mbar_arrive(&acc_empty[buf]);
           }
           // per column: the log-likelihood factor and q (overwrites v with q)
-          if (NC == 1 && (ch * 32 + 32) <= valid) {
+          if (NC == 1 && (ch * W + W) <= valid) {
             // whole chunk: no masks
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < W; ++j) {
               const float u = v[0][j];
               const float a = fabsf(u);
               const float e = ptx::ex2_approx(-a);
@@ -1193,8 +1200,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
             }
           } else
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const bool in = (ch * 32 + j) < valid;
+          for (int j = 0; j < W; ++j) {
+            const bool in = (ch * W + j) < valid;
             if constexpr (NC == 1) {
               const float u = v[0][j];
               const float a = fabsf(u);
@@ -1221,7 +1228,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
               for (int c = 0; c < NC; ++c) v[c][j] = in ? ec[c] * r : 0.f;
             }
           }
-          if ((ch & 3) == 3) {
+          if (((ch + 1) * W) % 128 == 0) {   // every 128 terms, as with 32-column chunks
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
               const int bits = __float_as_int(pr[qq]);
@@ -1245,7 +1252,7 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
               if (!ok) break;
               ptx::tc_fence_after();
             }
-            const uint32_t wcol = static_cast<uint32_t>((col0 + ch * 32) >> 1);
+            const uint32_t wcol = static_cast<uint32_t>((col0 + ch * W) >> 1);
             tmem_st_32x32b_x16(tmem_base + lane_base + kQtHi + wcol, hw);
             tmem_st_32x32b_x16(tmem_base + lane_base + kQtLo + wcol, lw);
           } else {
@@ -1253,8 +1260,8 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
 #pragma unroll
           for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int g8 = 0; g8 < 4; ++g8) {
-              const int col = col0 + ch * 32 + g8 * 8;   // observation within the tile
+            for (int g8 = 0; g8 < W / 8; ++g8) {
+              const int col = col0 + ch * W + g8 * 8;    // observation within the tile
               const uint32_t kb = static_cast<uint32_t>(col >> 6);
               const uint32_t chunk16 = static_cast<uint32_t>((col & 63) >> 3) ^ static_cast<uint32_t>(row & 7);
               uint32_t hw[4], lw[4];

@@ -895,11 +895,11 @@ grad_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__
   // single group takes whole tiles and the others idle
   constexpr int GPW = (NBUF == 2) ? 2 : 1;        // working groups per accumulator
   constexpr int COLS = BN / GPW;
-  // TMEM loads of W columns per class: 32 for C = 2, 8 for C = 3, 16 for C = 4 (two or three
-  // classes of 32 values each left the epilogue short of registers: C = 3, k = 74, 16 384
-  // particles at 10^5 observations 5.30 -> 4.83 ms per launch with 16 columns, 4.70 ms with 8,
-  // which leaves no spill at 96 registers a thread; C = 4 (c3) 22.28 -> 20.21 ms)
-  constexpr int W = (NC == 1) ? 32 : (NC == 2 ? 8 : 16);
+  // TMEM loads of W columns per class: 32 for C = 2, 8 for C > 2 (two or three classes of 32
+  // values each left the epilogue short of registers: C = 3, k = 74, 16 384 particles at 10^5
+  // observations 5.30 -> 4.83 ms per launch with 16 columns, 4.70 ms with 8, which leaves no
+  // spill at 96 registers a thread; C = 4 (c3) 22.28 -> 20.21 ms with 16 columns, 19.93 with 8)
+  constexpr int W = (NC == 1) ? 32 : 8;
   constexpr int NCH = COLS / W;
   static_assert(COLS % 32 == 0, "32-column TMEM loads");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
